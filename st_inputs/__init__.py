@@ -1,0 +1,54 @@
+"""Seeded synthetic inputs shared by the CUDA library's tests/benchmark and the oracle.
+
+This module only draws random numbers and applies index rules; it contains none
+of the solver's arithmetic.  The workloads follow the paper's problem statement
+(Section 3, eq. EddyCurrent: materials sigma, nu = mu^{-1} per element and a source
+J on the unit cube); the concrete recipe is ours:
+
+  * materials(n, kind, seed): per Kuhn tet (tet index 6*cube + permutation, cube
+    index ci + n*(cj + n*ck)):
+      kind "unit"      : nu = sigma = 1
+      kind "two_material": nu = 1e-3 for tets of cubes whose centre lies in
+                         [0.25, 0.75]^3, else 1; sigma = 10**U(-1, 1) per tet.
+  * excitation(seed): the source J(x, t) = g(t) curl psi(x) with
+      psi(x) = sum_{m<4} a_m sin(pi k_m . x + phi_m),  a_m ~ N(0, I_3),
+      k_m uniform in {1,2,3}^3, phi_m ~ U(0, 2 pi),  g(t) = sin(pi t / T) + 1,
+    returned as its parameters (a, k, phase); each side evaluates J itself.
+
+Random streams: numpy Generator(PCG64(seed)).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_MODES = 4
+
+
+def materials(n: int, kind: str = "two_material", seed: int = 0):
+    nt = 6 * n ** 3
+    if kind == "unit":
+        return np.ones(nt), np.ones(nt)
+    if kind != "two_material":
+        raise ValueError(kind)
+    c = np.arange(n ** 3)
+    ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+    centre = (np.stack([ci, cj, ck], axis=1) + 0.5) / n
+    inside = np.all((centre >= 0.25) & (centre <= 0.75), axis=1)
+    nu = np.repeat(np.where(inside, 1e-3, 1.0), 6)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sigma = 10.0 ** rng.uniform(-1.0, 1.0, size=nt)
+    return nu, sigma
+
+
+def excitation(seed: int = 0):
+    rng = np.random.Generator(np.random.PCG64(10_000 + seed))
+    a = rng.normal(size=(N_MODES, 3))
+    k = rng.integers(1, 4, size=(N_MODES, 3)).astype(np.float64)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=N_MODES)
+    return {"a": a, "k": k, "phase": phase}
+
+
+def random_iterate(shape, seed: int = 0):
+    """Uniform [0, 1) values, e.g. the random start of the power iteration (Section 5.1)."""
+    rng = np.random.Generator(np.random.PCG64(20_000 + seed))
+    return rng.uniform(0.0, 1.0, size=shape)

@@ -1,0 +1,363 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle component against something other than itself:
+closed forms, exact integer identities, invariants, brute force on tiny inputs,
+or values the paper reports.  A plausible slip (a dropped term, a wrong sign, a
+transposed block) breaks at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import st_inputs
+from oracle.mesh import kuhn_mesh, LOCAL_EDGES, fine_tet_parents, tet_barycentres
+from oracle.fem import (assemble_edge_matrices, discrete_gradient, nodal_stiffness,
+                        tet_geometry)
+from oracle.transfer import edge_prolongation, node_prolongation, round_dyadic
+from oracle.timeblocks import time_blocks, time_prolongation_block, time_load_weights
+from oracle.spacetime import (build_space_hierarchy, SlabOperator, apply_L, spacetime_matrix,
+                              sequential_solve, smoother_S, correction_A, restrict_time,
+                              prolong_time)
+from oracle.multigrid import build_time_hierarchy, SpaceTimeMG, coarsening_lambda
+from oracle.load import space_load, spacetime_load
+
+
+# ---------------------------------------------------------------- mesh
+@pytest.mark.parametrize("n,ne,nei", [(4, 604, 316), (8, 4184, 3032)])
+def test_kuhn_counts(n, ne, nei):
+    m = kuhn_mesh(n)
+    assert len(m.edges) == ne
+    assert m.edge_interior.sum() == nei
+    assert len(m.edges) - m.edge_interior.sum() == 18 * n * n
+    assert m.vert_interior.sum() == (n - 1) ** 3
+    # closed form: axis edges 3n(n+1)^2, face diagonals 3n^2(n+1), body diagonals n^3
+    assert len(m.edges) == 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3
+
+
+def test_kuhn_euler_characteristic_and_volumes():
+    m = kuhn_mesh(3)
+    faces = set()
+    for t in m.tets:
+        for f in itertools.combinations(sorted(t), 3):
+            faces.add(f)
+    V, E, F, T = len(m.xyz), len(m.edges), len(faces), len(m.tets)
+    assert V - E + F - T == 1          # a ball
+    vol, _ = tet_geometry(m)
+    assert np.allclose(vol, 1.0 / (6 * 27), rtol=0, atol=1e-15)
+    assert abs(vol.sum() - 1.0) < 1e-13
+
+
+def test_refinement_parents_nested():
+    parents = fine_tet_parents(2)
+    fine, coarse = kuhn_mesh(4), kuhn_mesh(2)
+    assert np.bincount(parents, minlength=len(coarse.tets)).tolist() == [8] * len(coarse.tets)
+    # every fine vertex of a fine tet lies in its parent (barycentric >= 0)
+    from oracle.fem import barycentric
+    for t in range(0, len(fine.tets), 7):
+        for v in fine.tets[t]:
+            lam = barycentric(coarse, parents[t], fine.xyz[v])
+            assert lam.min() > -1e-12
+
+
+# ---------------------------------------------------------------- spatial matrices
+def _face_edge_incidence(m):
+    index = {tuple(e): i for i, e in enumerate(m.edges.tolist())}
+    faces = sorted({f for t in m.tets for f in itertools.combinations(sorted(t.tolist()), 3)})
+    rows, cols, vals = [], [], []
+    for fi, (a, b, c) in enumerate(faces):
+        # boundary of the oriented triangle a->b->c: (a,b) + (b,c) - (a,c)
+        for (u, v), s in (((a, b), 1), ((b, c), 1), ((a, c), -1)):
+            rows.append(fi); cols.append(index[(u, v)]); vals.append(s)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(len(faces), len(m.edges))).tocsr()
+
+
+def test_curl_grad_zero_integer():
+    m = kuhn_mesh(3)
+    C = _face_edge_incidence(m).astype(np.int64)
+    G = discrete_gradient(m, interior=False).astype(np.int64)
+    assert abs(C @ G).max() == 0   # curl o grad = 0, exactly in integers (Section 3.2)
+
+
+def test_KG_zero_and_Kn_identity():
+    n = 4
+    m = kuhn_mesh(n)
+    nu, sigma = st_inputs.materials(n, "two_material", 3)
+    M, K = assemble_edge_matrices(m, nu, sigma)
+    G = discrete_gradient(m)
+    Kn = nodal_stiffness(m, sigma)
+    assert abs(K @ G).max() <= 1e-13 * abs(K).max()
+    assert abs(G.T @ M @ G - Kn).max() <= 1e-13 * abs(Kn).max()
+
+
+def test_rank_curlcurl_and_spectrum():
+    n = 4
+    m = kuhn_mesh(n)
+    nu, sigma = st_inputs.materials(n, "two_material", 2)
+    M, K = assemble_edge_matrices(m, nu, sigma)
+    Kd, Md = K.toarray(), M.toarray()
+    assert np.linalg.matrix_rank(Kd, tol=1e-10 * abs(Kd).max()) == 316 - 27
+    # M SPD; M^-1 K has real non-negative eigenvalues (premise of Section 2.1)
+    assert np.linalg.eigvalsh(Md).min() > 0
+    import scipy.linalg as sla
+    ev = sla.eigh(Kd, Md, eigvals_only=True)
+    assert ev.min() > -1e-10 * ev.max()
+    assert np.sum(ev < 1e-9 * ev.max()) == 27   # kernel of curl = range of G
+
+
+def _interpolant(m, field):
+    """Edge DoFs u_e = line integral of `field` along e (exact for the affine
+    fields a + b x x used below by the midpoint rule)."""
+    a, b = m.edges[:, 0], m.edges[:, 1]
+    xa, xb = m.xyz[a], m.xyz[b]
+    return np.einsum("ed,ed->e", field(0.5 * (xa + xb)), xb - xa)
+
+
+def test_patch_affine_fields():
+    """Whitney elements reproduce a + b x x, so the energies are exact integrals."""
+    n = 3
+    m = kuhn_mesh(n)
+    rng = np.random.default_rng(7)
+    nu = rng.uniform(0.5, 2.0, 6 * n ** 3)
+    sigma = rng.uniform(0.5, 2.0, 6 * n ** 3)
+    M, K = assemble_edge_matrices(m, nu, sigma, interior=False)
+    a, b = rng.normal(size=3), rng.normal(size=3)
+    field = lambda x: a[None, :] + np.cross(b[None, :], x)
+    u = _interpolant(m, field)
+    vol, _ = tet_geometry(m)
+    # curl (a + b x x) = 2 b
+    assert abs(u @ K @ u - np.sum(nu * vol) * 4 * b @ b) < 1e-11
+    # int_T sigma |a + b x x|^2 by the 4-point degree-2 rule (exact for quadratics)
+    sq5 = np.sqrt(5.0)
+    al, be = (5 + 3 * sq5) / 20, (5 - sq5) / 20
+    P = m.xyz[m.tets]
+    exact = 0.0
+    for q in range(4):
+        lam = np.full(4, be); lam[q] = al
+        x = np.einsum("v,tvd->td", lam, P)
+        exact += np.sum(sigma * vol / 4 * np.sum(field(x) ** 2, axis=1))
+    assert abs(u @ M @ u - exact) < 1e-12 * exact
+    # constant fields are curl-free
+    assert abs(K @ _interpolant(m, lambda x: np.tile(a, (len(x), 1)))).max() < 1e-12
+
+
+# ---------------------------------------------------------------- transfers
+def test_prolongations_commute_and_reproduce():
+    coarse, fine = kuhn_mesh(2), kuhn_mesh(4)
+    Px = round_dyadic(edge_prolongation(coarse, fine))
+    Pn = round_dyadic(node_prolongation(coarse, fine))
+    Gc, Gf = discrete_gradient(coarse), discrete_gradient(fine)
+    assert abs(Px @ Gc - Gf @ Pn).max() == 0.0
+    # dyadic entries
+    assert np.all(Px.data * 4 == np.round(Px.data * 4))
+    # affine fields with zero tangential trace are not available on 2^3, so check on
+    # all edges: interpolation then prolongation == fine interpolation
+    from oracle.transfer import edge_prolongation as ep
+    rng = np.random.default_rng(1)
+    a, b = rng.normal(size=3), rng.normal(size=3)
+    field = lambda x: a[None, :] + np.cross(b[None, :], x)
+    # rebuild an all-edge prolongation by temporarily treating every edge as interior
+    cf, ff = kuhn_mesh(2), kuhn_mesh(4)
+    cf.edge_interior[:] = True; ff.edge_interior[:] = True
+    P_all = ep(cf, ff)
+    assert abs(P_all @ _interpolant(cf, field) - _interpolant(ff, field)).max() < 1e-13
+
+
+def test_node_prolongation_reproduces_linear():
+    coarse, fine = kuhn_mesh(2), kuhn_mesh(4)
+    coarse.vert_interior[:] = True; fine.vert_interior[:] = True
+    Pn = node_prolongation(coarse, fine)
+    c = np.array([0.3, -1.2, 2.0])
+    assert abs(Pn @ (coarse.xyz @ c + 0.7) - (fine.xyz @ c + 0.7)).max() < 1e-13
+
+
+# ---------------------------------------------------------------- time blocks
+def test_dg0_is_implicit_euler():
+    Kt, Mt, Nt = time_blocks(0, 0.125)
+    assert Kt.tolist() == [[1.0]] and Nt.tolist() == [[-1.0]]
+    assert abs(Mt[0, 0] - 0.125) < 1e-16   # A_tau = M + tau K, sub-diagonal -M (eq. timeStepping)
+
+
+def test_dg1_matches_radau_iia_stability():
+    """DG(1) on y' = -lam y reproduces the 3rd-order Radau IIA amplification
+    R(z) = (1 + z/3) / (1 - 2z/3 + z^2/6) at slab ends (textbook, independent)."""
+    tau = 0.3
+    Kt, Mt, Nt = time_blocks(1, tau)
+    for lam in (0.0, 0.7, 5.0, 80.0):
+        A = Kt + lam * Mt                      # scalar "M = 1, K = lam"
+        u = np.linalg.solve(A, -Nt @ np.array([1.0, 0.0]))   # previous slab = constant 1
+        end = u[0] + u[1]                      # phi_0(1) + phi_1(1)
+        z = -lam * tau
+        R = (1 + z / 3) / (1 - 2 * z / 3 + z * z / 6)
+        assert abs(end - R) < 1e-14
+    ev = np.linalg.eigvals(np.linalg.solve(Mt, Kt)) * tau
+    assert np.allclose(sorted(ev, key=lambda c: c.imag), [2 - 1j * np.sqrt(2), 2 + 1j * np.sqrt(2)])
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_time_galerkin_identity(p):
+    """P_t^T L_tau P_t == L_{2 tau}: the coarse time operator is the re-discretisation."""
+    Ntf, tau = 8, 0.1
+    def Lt(tau_, N):
+        Kt, Mt, Nt = time_blocks(p, tau_)
+        # scalar space (M = 1, K = 2.5) exercises both blocks
+        D = Kt + 2.5 * Mt
+        return np.kron(np.eye(N), D) + np.kron(np.eye(N, k=-1), Nt)
+    P0, P1 = time_prolongation_block(p)
+    q = p + 1
+    P = np.zeros((Ntf * q, Ntf // 2 * q))
+    for k in range(Ntf // 2):
+        P[2 * k * q:(2 * k + 1) * q, k * q:(k + 1) * q] = P0
+        P[(2 * k + 1) * q:(2 * k + 2) * q, k * q:(k + 1) * q] = P1
+    assert abs(P.T @ Lt(tau, Ntf) @ P - Lt(2 * tau, Ntf // 2)).max() < 1e-14
+
+
+def test_time_prolongation_blocks_closed_form():
+    P0, P1 = time_prolongation_block(1)
+    assert np.allclose(P0, [[1, -0.5], [0, 0.5]], atol=1e-15)
+    assert np.allclose(P1, [[1, 0.5], [0, 0.5]], atol=1e-15)
+
+
+def test_time_load_weights_polynomial():
+    c = time_load_weights(1, 4, 2.0, lambda t: 3.0 + 0 * t)
+    assert np.allclose(c[:, 0], 1.5) and np.allclose(c[:, 1], 0.0, atol=1e-15)
+    c = time_load_weights(1, 1, 1.0, lambda t: t)     # int t (2t-1) dt = 1/6
+    assert abs(c[0, 1] - 1.0 / 6.0) < 1e-15
+
+
+# ---------------------------------------------------------------- space-time system
+@pytest.mark.parametrize("p", [0, 1])
+def test_direct_solve_equals_time_stepping(p):
+    n, N_t = 2, 5
+    nu, sigma = st_inputs.materials(4, "two_material", 1)
+    sl = build_space_hierarchy(4, 1, nu, sigma)
+    tau = 1.0 / N_t
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(N_t, p + 1, sl[0].ne))
+    L = spacetime_matrix(sl[0], p, tau, N_t)
+    xd = spla.spsolve(L.tocsc(), f.ravel()).reshape(f.shape)
+    xs = sequential_solve(SlabOperator(sl[0], p, tau), f)
+    assert np.linalg.norm(xd - xs) <= 1e-12 * np.linalg.norm(xs)
+    # apply_L agrees with the assembled matrix
+    assert np.linalg.norm(apply_L(sl[0], *time_blocks(p, tau), xs).ravel() - L @ xs.ravel()) \
+        <= 1e-13 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_block_jacobi_nilpotent_and_halving(p):
+    """omega = 1: the Jacobi error matrix is strictly block lower -> exact after N_t
+    sweeps; omega = 0.5 on one slab halves the error exactly (eq. StandardSmoother)."""
+    nu, sigma = st_inputs.materials(4, "unit")
+    sl = build_space_hierarchy(4, 1, nu, sigma)
+    N_t, tau = 4, 0.25
+    slab = SlabOperator(sl[0], p, tau)
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=(N_t, p + 1, sl[0].ne))
+    xs = sequential_solve(slab, f)
+    x = np.zeros_like(f)
+    for k in range(N_t):
+        assert np.linalg.norm(x - xs) > 1e-6 * np.linalg.norm(xs)
+        x = smoother_S(slab, f, x, 1.0)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+    x0 = rng.normal(size=(1, p + 1, sl[0].ne))
+    x1 = smoother_S(slab, f[:1], x0, 0.5)
+    e0, e1 = x0 - xs[:1], x1 - xs[:1]
+    assert np.linalg.norm(e1 - 0.5 * e0) <= 1e-12 * np.linalg.norm(e0)
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_nodal_correction_removes_gradient_error(p):
+    """A with an exact K_n^{-1} annihilates any error in range(G) (eq. AuxNodalSm)."""
+    nu, sigma = st_inputs.materials(4, "two_material", 5)
+    sl = build_space_hierarchy(4, 1, nu, sigma)
+    N_t, tau = 6, 1.0 / 6
+    slab = SlabOperator(sl[0], p, tau)
+    rng = np.random.default_rng(2)
+    f = rng.normal(size=(N_t, p + 1, sl[0].ne))
+    xs = sequential_solve(slab, f)
+    phi = rng.normal(size=(N_t, p + 1, sl[0].nn))
+    x = xs + (sl[0].G @ phi.reshape(-1, sl[0].nn).T).T.reshape(xs.shape)
+    xa = correction_A(slab, f, x)
+    assert np.linalg.norm(xa - xs) <= 1e-11 * np.linalg.norm(xs)
+    # for DG(0) the time part is the running sum Sigma_t of the paper
+    if p == 0:
+        from oracle.spacetime import time_integrate
+        Kt, Mt, Nt = time_blocks(0, tau)
+        z = rng.normal(size=(N_t, 1, 3))
+        assert np.allclose(time_integrate(Kt, Nt, z), np.cumsum(z, axis=0), atol=1e-14)
+
+
+def test_space_load_constant_field():
+    """For constant j = c and u the interpolant of a constant c', u . b = |Omega| c . c'
+    over all edges (Whitney functions reproduce constants)."""
+    m = kuhn_mesh(3)
+    m.edge_interior[:] = True
+    exc = {"a": np.zeros((1, 3)), "k": np.zeros((1, 3)), "phase": np.zeros(1)}
+    # j(x) = pi cos(0) (k x a) = 0 for k = 0; use a direct constant instead:
+    import oracle.load as ld
+    c = np.array([0.4, -1.1, 0.25])
+    orig = ld.source_space
+    ld.source_space = lambda x, e: np.tile(c, (len(x), 1))
+    try:
+        b = space_load(m, exc)
+    finally:
+        ld.source_space = orig
+    c2 = np.array([1.3, 0.2, -0.7])
+    u = _interpolant(m, lambda x: np.tile(c2, (len(x), 1)))
+    assert abs(u @ b - c @ c2) < 1e-13
+
+
+# ---------------------------------------------------------------- multigrid
+def test_two_grid_config_small_converges_to_time_stepping():
+    n, N_t = 4, 16
+    nu, sigma = st_inputs.materials(n, "unit")
+    sl = build_space_hierarchy(n, 1, nu, sigma)
+    f = spacetime_load(sl[0].mesh, st_inputs.excitation(0), 0, N_t, 1.0)
+    tl = build_time_hierarchy(N_t, 1.0, n, 1, nu, sigma, max_levels=2)
+    assert [(l.s, l.N_t) for l in tl] == [(0, 16), (0, 8)]
+    mg = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1)
+    x, hist = mg.solve(f, rtol=1e-10)
+    xs = sequential_solve(mg.slabs[0], f)
+    assert hist[-1] <= 1e-10 and len(hist) - 1 <= 10
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_coarsening_rule_values():
+    """lambda = min(nu/sigma) tau / h_T^2 with h_T = sqrt(3)/n (longest Kuhn edge)."""
+    nu, sigma = st_inputs.materials(16, "two_material", 0)
+    lam = coarsening_lambda(16, 1.0 / 256, nu, sigma)
+    assert abs(lam - 1e-3 / sigma[nu < 1].max() / 256 / (3.0 / 256)) < 1e-15 or lam < 1e-4
+    tl = build_time_hierarchy(256, 1.0, 16, 3, nu, sigma)
+    assert all(l.s == 0 for l in tl) and [l.N_t for l in tl][-1] == 1   # never coarsens space
+    nu1, s1 = st_inputs.materials(16, "unit")
+    tl = build_time_hierarchy(16, 1.0, 16, 3, nu1, s1)
+    # lambda at level 0: (1/16) / (3/256) = 5.33 >= 0.1 -> coarsen space at once
+    assert [(l.s, l.N_t) for l in tl][:3] == [(0, 16), (1, 8), (2, 4)]
+
+
+@pytest.mark.slow
+def test_paper_section31_spatial_coarsening_needs_A():
+    """Section 3.1: with spatial coarsening the plain S smoother is 'completely
+    ineffective'; the hybrid SAS restores convergence (Section 4.1)."""
+    nf, N_t = 8, 64
+    nu, sigma = st_inputs.materials(nf, "unit")
+    sl = build_space_hierarchy(nf, 2, nu, sigma)
+    T = N_t / 512.0
+    tl = build_time_hierarchy(N_t, T, nf, 2, nu, sigma, mode="full_top", max_levels=2)
+    x0 = st_inputs.random_iterate((N_t, 1, sl[0].ne), 0)
+    r_S, _ = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1, use_A=False).convergence_rate(x0, max_iter=8)
+    r_SAS, _ = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1).convergence_rate(x0, max_iter=8)
+    assert r_S > 0.9 and r_SAS < 0.5
+
+
+def test_paper_high_lambda_rate():
+    """Section 5.1: for large lambda the two-grid SAS rate is 2^-4."""
+    nf, N_t = 4, 8
+    nu, sigma = st_inputs.materials(nf, "unit")
+    sl = build_space_hierarchy(nf, 1, nu, sigma)
+    tl = build_time_hierarchy(N_t, 64.0, nf, 1, nu, sigma, mode="semi_time", max_levels=2)
+    x0 = st_inputs.random_iterate((N_t, 1, sl[0].ne), 0)
+    r, _ = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1).convergence_rate(x0, max_iter=12)
+    assert abs(r - 2.0 ** -4) < 0.01
