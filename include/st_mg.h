@@ -1,0 +1,197 @@
+/*
+ * st_mg.h -- C ABI of the GB300 space-time multigrid library for the transient
+ * eddy-current equation  sigma dA/dt + curl(nu curl A) = J  (Neumueller and
+ * Schwalsberger, "A parallel space-time multigrid method for the eddy-current
+ * equation", arXiv 1911.09548).
+ *
+ * The library builds, on one GPU, the all-at-once space-time system of Section 2.1
+ * (lowest-order Nedelec elements in space, Section 3; DG(0) = implicit Euler or
+ * DG(1) in time) and applies the space-time V-cycle of Section 2.1 with the hybrid
+ * smoother of Section 4 (block-Jacobi S, eq. StandardSmoother, around the nodal
+ * auxiliary-space correction A, eq. AuxNodalSm) to all time slabs at once, with
+ * spatial coarsening where the rule of eq. CoarseningRule allows it.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  Mesh.  The finest mesh is the Kuhn mesh of [0,1]^3 with n_cube cubes per side:
+ *    vertex (i,j,k) has id i + (n+1)(j + (n+1)k); cube (ci,cj,ck) has id
+ *    ci + n(cj + n ck) and holds tets 6*cube + p, p = 0..5 indexing the axis
+ *    permutations (x,y,z) in lexicographic order; the tet of permutation (a,b,c)
+ *    is the vertex chain corner, +e_a, +e_b, +e_c.  Edges are sorted vertex pairs
+ *    (lo, hi), numbered lexicographically and oriented lo -> hi.  Coarser space
+ *    levels are the Kuhn meshes n/2, n/4, ... (uniform refinement, Section 5.1).
+ *  Boundary.  Homogeneous Dirichlet u x n = 0: unknowns are the interior edges
+ *    (edges not contained in a face of the cube), in increasing edge id order.
+ *  Space-time vectors (f, x, r) of a time level with N_t slabs and degree p are
+ *    double arrays  v[e * (N_t*(p+1)) + n*(p+1) + i]  -- edge-major, time
+ *    contiguous -- for interior edge e, slab n, time basis function i
+ *    (p = 1: Legendre phi_0 = 1, phi_1 = 2s - 1 on the slab, s in [0,1]).
+ *  Nodal vectors use the same layout over interior vertices.
+ *  Pointers named *_dev are device pointers (cudaMalloc / torch CUDA memory) on
+ *  the device that was current at st_mg_setup; they are read/written on the
+ *  handle's stream and the call returns after the work is queued unless it says
+ *  otherwise.  The caller owns every buffer it passes; the handle owns all device
+ *  memory it allocates (matrices, factors, workspace) until st_mg_destroy.
+ *  Errors.  Every function returns an int status (ST_MG_OK = 0); no exception or
+ *  abort crosses the ABI.  st_mg_last_error() gives a message for the calling
+ *  thread's last failure.  A handle is not thread safe.
+ */
+#ifndef ST_MG_H
+#define ST_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ST_MG_OK                0
+#define ST_MG_ERR_INVALID_ARG   1
+#define ST_MG_ERR_OOM           2
+#define ST_MG_ERR_CUDA          3
+#define ST_MG_ERR_DIVERGED      4
+#define ST_MG_ERR_NOT_CONVERGED 5
+#define ST_MG_ERR_NUMERIC       6   /* zero pivot in a factorisation */
+
+typedef struct st_mg_s* st_mg_t;
+
+/* Problem statement (Section 3, eq. EddyCurrent; Section 2.1 time stepping). */
+typedef struct {
+    int32_t n_cube;          /* cubes per side of the finest Kuhn mesh (>= 2, even if n_space_levels > 1) */
+    int32_t n_space_levels;  /* nested meshes n_cube, n_cube/2, ... available for coarsening (>= 1) */
+    const double* nu;        /* host [6 n_cube^3] reluctivity 1/mu per finest tet, > 0 */
+    const double* sigma;     /* host [6 n_cube^3] conductivity per finest tet, > 0 */
+    double T;                /* end time (> 0); the time interval is (0, T) */
+    int32_t N_t;             /* number of time slabs on the finest level (>= 1) */
+    int32_t degree;          /* DG degree in time: 0 (implicit Euler) or 1 */
+} st_mg_problem;
+
+/* Method parameters (Sections 2.1, 2.2, 4, 5). */
+typedef struct {
+    double omega;            /* damping of the block-Jacobi smoother S (paper: 0.5) */
+    int32_t nu_pre;          /* pre-smoother S^nu_pre A S^nu_pre */
+    int32_t nu_post;         /* post-smoother S^nu_post A S^nu_post */
+    double lambda_crit;      /* coarsening rule threshold (paper: 0.1) */
+    int32_t coarsen;         /* 0: eq. CoarseningRule, 1: time only ("Semi-time"),
+                                2: space on the first transition only ("Full", Table FullMethod) */
+    int32_t max_levels;      /* cap on the number of time levels (2 = two-grid); 0 = no cap */
+    int32_t min_coarse_slabs;/* stop coarsening at <= this many slabs (>= 1) */
+    int32_t nodal_solve;     /* 0: exact K_n^{-1} (factor), 1: damped Jacobi sweeps (weight 2/3) */
+    int32_t nodal_jacobi_sweeps;
+    int32_t use_A;           /* 1: hybrid smoother with A; 0: plain S only */
+    int32_t setup_threads;   /* host threads for the factorisations; 0 = all cores */
+} st_mg_options;
+
+/* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,
+ * coarsening by the rule, no level cap, exact nodal solve, A on. */
+int st_mg_default_options(st_mg_options* opt);
+
+/* Build the hierarchy: meshes, matrices M_sigma, K_nu, G, K_n (Section 3,
+ * eq. AuxNodalSm), spatial prolongations, the time levels with the coarsening
+ * decision of eq. CoarseningRule, and one slab factor per time level (every slab
+ * of a level shares A_slab, Section 2.1) plus one K_n factor per space level,
+ * all uploaded to the current device.  `stream` is a cudaStream_t (NULL = legacy
+ * default stream) used by every later call.  Host work (assembly and the sparse
+ * factorisations) runs on setup_threads threads.  On success *out owns all of it. */
+int st_mg_setup(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out);
+
+/* Host-only variant of st_mg_setup for inspecting the setup without a GPU: builds
+ * the meshes, matrices, hierarchy and factors on the host and allocates no device
+ * memory.  Such a handle accepts only st_mg_sizes, st_mg_level_info,
+ * st_mg_debug_get, st_mg_debug_host_slab_solve and st_mg_destroy; every other
+ * call returns ST_MG_ERR_INVALID_ARG. */
+int st_mg_setup_host(const st_mg_problem* prob, const st_mg_options* opt, st_mg_t* out);
+
+void st_mg_destroy(st_mg_t h);
+
+/* Sizes of the finest level: interior edges, interior nodes, space-time unknowns
+ * (n_edge * N_t * (degree+1)), and the number of time levels. */
+int st_mg_sizes(st_mg_t h, int64_t* n_edge, int64_t* n_node, int64_t* n_dof, int32_t* n_levels);
+
+/* Time level `level` (0 = finest): its space level, slab count and step tau. */
+int st_mg_level_info(st_mg_t h, int32_t level, int32_t* space_level, int32_t* N_t, double* tau,
+                     int64_t* n_edge, int64_t* n_node);
+
+/* Right-hand side f on the finest level for J(x,t) = g(t) curl psi(x),
+ * psi = sum_m a_m sin(pi k_m . x + phase_m), g(t) = sin(pi t / T) + 1:
+ *   f[e, n, i] = int_{I_n} g phi_i dt * int_Omega curl psi . w_e dx
+ * (3-point Gauss per slab, 4-point degree-2 rule per tet).  a, k: host [n_modes*3];
+ * phase: host [n_modes].  f_dev: device, finest layout. */
+int st_mg_assemble_load(st_mg_t h, int32_t n_modes, const double* a, const double* k,
+                        const double* phase, double* f_dev);
+
+/* ---- individual steps of the hot path (each on time level `level`) ---- */
+
+/* r = f - L x (Section 2.1: block lower-bidiagonal L with K_t(x)M + M_t(x)K on the
+ * diagonal and N_t(x)M below).  If norm_out != NULL, also ||r||_2 (blocking). */
+int st_mg_residual(st_mg_t h, int32_t level, const double* f_dev, const double* x_dev,
+                   double* r_dev, double* norm_out);
+
+/* y = (I (x) A_slab^{-1}) r: the slab solve of eq. StandardSmoother on every slab. */
+int st_mg_slab_solve(st_mg_t h, int32_t level, const double* r_dev, double* y_dev);
+
+/* One block-Jacobi sweep x <- x + omega (I (x) A_slab^{-1})(f - L x)  (eq. StandardSmoother). */
+int st_mg_smooth_S(st_mg_t h, int32_t level, const double* f_dev, double* x_dev);
+
+/* One nodal auxiliary-space correction x <- x + G L_t^{-1} K_n^{-1} G^T (f - L x)
+ * (eq. AuxNodalSm; L_t^{-1} is the running sum Sigma_t for DG(0)). */
+int st_mg_correct_A(st_mg_t h, int32_t level, const double* f_dev, double* x_dev);
+
+/* Parts of A: y = G^T r (edge -> node, per time unknown);  z = K_n^{-1} y (or the
+ * Jacobi sweeps of the options);  w = L_t^{-1} z (time integration);  x += G w. */
+int st_mg_grad_T(st_mg_t h, int32_t level, const double* r_dev, double* y_dev);
+int st_mg_nodal_solve(st_mg_t h, int32_t level, const double* y_dev, double* z_dev);
+int st_mg_time_integrate(st_mg_t h, int32_t level, const double* z_dev, double* w_dev);
+int st_mg_grad_add(st_mg_t h, int32_t level, const double* w_dev, double* x_dev);
+
+/* Coarse-grid transfers between level and level+1: time (pairs of slabs, DG
+ * prolongation blocks) and, where the hierarchy coarsens space, P_x.
+ * restrict: rc = (P_t (x) P_x)^T r.  prolong_add: x += (P_t (x) P_x) ec. */
+int st_mg_restrict(st_mg_t h, int32_t level, const double* r_dev, double* rc_dev);
+int st_mg_prolong_add(st_mg_t h, int32_t level, const double* ec_dev, double* x_dev);
+
+/* Exact solve L x = f on the coarsest level (one slab: slab factor; several slabs:
+ * forward substitution in time).  x_dev is overwritten. */
+int st_mg_coarse_solve(st_mg_t h, const double* f_dev, double* x_dev);
+
+/* ---- the whole method ---- */
+
+/* One V-cycle on the finest level (x updated in place).  If rel_res_out != NULL,
+ * also ||f - L x|| / ||f|| after the cycle (blocking). */
+int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_out);
+
+/* V-cycles from the given x until ||f - L x|| / ||f|| <= rtol or maxit cycles.
+ * iters, rel_res: host outputs; history (nullable): host [maxit + 1] relative
+ * residuals (entry 0 = start).  Returns ST_MG_ERR_NOT_CONVERGED if maxit is
+ * reached, ST_MG_ERR_DIVERGED on a non-finite residual or growth above 1e3 x. */
+int st_mg_solve(st_mg_t h, const double* f_dev, double* x_dev, double rtol, int32_t maxit,
+                int32_t* iters, double* rel_res, double* history);
+
+/* The same solve from HOST buffers: f_host is copied to the device, x_host is the
+ * start value and receives the result; copies are part of the call (blocking). */
+int st_mg_solve_host(st_mg_t h, const double* f_host, double* x_host, double rtol, int32_t maxit,
+                     int32_t* iters, double* rel_res, double* history);
+
+/* Debug getters for bit-exact checks of the setup (host buffers).
+ *  what: 1 edges [ne_all*2] int32 (lo, hi) of space level `level`;
+ *        2 interior edge ids [n_edge] int32;  3 interior vertex ids [n_node] int32;
+ *        4 CSR row pointer of the edge matrices [n_edge+1] int64; 5 CSR columns int32;
+ *        6 M_sigma values double; 7 K_nu values double;
+ *        8 G as (tail, head) interior node per interior edge [n_edge*2] int32 (-1 = boundary);
+ *        9 K_n row pointer int64; 10 K_n columns int32; 11 K_n values double;
+ *       12 P_x (level -> level+1 coarse) row pointer int64; 13 columns int32; 14 values double.
+ * With host_buf == NULL, *bytes receives the size needed. */
+int st_mg_debug_get(st_mg_t h, int32_t what, int32_t level, void* host_buf, int64_t* bytes);
+
+/* Setup check for host-only handles: y = (I (x) A_slab^{-1}) r on time level
+ * `level`, evaluated on the host with the same factor and complex transformation
+ * the device path uses.  r_host, y_host: host arrays in the level's layout. */
+int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, double* y_host);
+
+const char* st_mg_strerror(int status);
+const char* st_mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ST_MG_H */

@@ -1,0 +1,252 @@
+"""ctypes binding of libstmg (include/st_mg.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and raises
+StMgError on a non-zero status.  Device buffers are passed as torch CUDA tensors
+(float64, contiguous) or raw integer addresses; the library does all the work.
+The binding loads the in-tree library and fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB_PATH
+
+_i32, _i64, _dbl, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_P = ctypes.POINTER
+
+
+class StMgError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn}: status {status} ({msg})")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n_cube", _i32), ("n_space_levels", _i32), ("nu", _P(_dbl)), ("sigma", _P(_dbl)),
+                ("T", _dbl), ("N_t", _i32), ("degree", _i32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("omega", _dbl), ("nu_pre", _i32), ("nu_post", _i32), ("lambda_crit", _dbl),
+                ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
+                ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
+                ("setup_threads", _i32)]
+
+
+_SIGS = {
+    "st_mg_default_options": [_P(Options)],
+    "st_mg_setup": [_P(Problem), _P(Options), _vp, _P(_vp)],
+    "st_mg_setup_host": [_P(Problem), _P(Options), _P(_vp)],
+    "st_mg_destroy": [_vp],
+    "st_mg_sizes": [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i32)],
+    "st_mg_level_info": [_vp, _i32, _P(_i32), _P(_i32), _P(_dbl), _P(_i64), _P(_i64)],
+    "st_mg_assemble_load": [_vp, _i32, _P(_dbl), _P(_dbl), _P(_dbl), _vp],
+    "st_mg_residual": [_vp, _i32, _vp, _vp, _vp, _P(_dbl)],
+    "st_mg_slab_solve": [_vp, _i32, _vp, _vp],
+    "st_mg_smooth_S": [_vp, _i32, _vp, _vp],
+    "st_mg_correct_A": [_vp, _i32, _vp, _vp],
+    "st_mg_grad_T": [_vp, _i32, _vp, _vp],
+    "st_mg_nodal_solve": [_vp, _i32, _vp, _vp],
+    "st_mg_time_integrate": [_vp, _i32, _vp, _vp],
+    "st_mg_grad_add": [_vp, _i32, _vp, _vp],
+    "st_mg_restrict": [_vp, _i32, _vp, _vp],
+    "st_mg_prolong_add": [_vp, _i32, _vp, _vp],
+    "st_mg_coarse_solve": [_vp, _vp, _vp],
+    "st_mg_vcycle": [_vp, _vp, _vp, _P(_dbl)],
+    "st_mg_solve": [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _P(_dbl)],
+    "st_mg_solve_host": [_vp, _P(_dbl), _P(_dbl), _dbl, _i32, _P(_i32), _P(_dbl), _P(_dbl)],
+    "st_mg_debug_get": [_vp, _i32, _i32, _vp, _P(_i64)],
+    "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
+    "st_mg_strerror": [ctypes.c_int],
+    "st_mg_last_error": [],
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libstmg.so (built by __graft_entry__.build() or `python -m paper_1911_09548_gb300._build`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libstmg is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name in ("st_mg_strerror", "st_mg_last_error") else (
+                None if name == "st_mg_destroy" else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, fn: str):
+    if status != 0:
+        raise StMgError(status, fn, lib().st_mg_last_error().decode())
+    return status
+
+
+def _addr(t) -> int:
+    """Device (or host) address of a torch tensor / numpy array / int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        if hasattr(t, "dtype") and str(t.dtype) != "torch.float64":
+            raise TypeError("buffers must be float64")
+        if not t.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_P(_dbl))
+
+
+# ----------------------------------------------------------------- thin wrappers
+def st_mg_default_options() -> Options:
+    o = Options()
+    _check(lib().st_mg_default_options(ctypes.byref(o)), "st_mg_default_options")
+    return o
+
+
+def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree):
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree)
+    p._keep = (nu, sigma)
+    return p
+
+
+def st_mg_setup(prob: Problem, opt: Options, stream: int = 0) -> int:
+    h = _vp()
+    _check(lib().st_mg_setup(ctypes.byref(prob), ctypes.byref(opt), _vp(stream), ctypes.byref(h)), "st_mg_setup")
+    return h.value
+
+
+def st_mg_setup_host(prob: Problem, opt: Options) -> int:
+    h = _vp()
+    _check(lib().st_mg_setup_host(ctypes.byref(prob), ctypes.byref(opt), ctypes.byref(h)), "st_mg_setup_host")
+    return h.value
+
+
+def st_mg_destroy(h: int):
+    lib().st_mg_destroy(_vp(h))
+
+
+def st_mg_sizes(h):
+    ne, nn, nd, nl = _i64(), _i64(), _i64(), _i32()
+    _check(lib().st_mg_sizes(_vp(h), ctypes.byref(ne), ctypes.byref(nn), ctypes.byref(nd), ctypes.byref(nl)),
+           "st_mg_sizes")
+    return ne.value, nn.value, nd.value, nl.value
+
+
+def st_mg_level_info(h, level):
+    s, nt, tau, ne, nn = _i32(), _i32(), _dbl(), _i64(), _i64()
+    _check(lib().st_mg_level_info(_vp(h), level, ctypes.byref(s), ctypes.byref(nt), ctypes.byref(tau),
+                                  ctypes.byref(ne), ctypes.byref(nn)), "st_mg_level_info")
+    return {"space_level": s.value, "N_t": nt.value, "tau": tau.value, "n_edge": ne.value, "n_node": nn.value}
+
+
+def st_mg_assemble_load(h, a, k, phase, f_dev):
+    a = np.ascontiguousarray(a, np.float64).ravel()
+    k = np.ascontiguousarray(k, np.float64).ravel()
+    phase = np.ascontiguousarray(phase, np.float64).ravel()
+    _check(lib().st_mg_assemble_load(_vp(h), len(phase), _dptr(a), _dptr(k), _dptr(phase), _vp(_addr(f_dev))),
+           "st_mg_assemble_load")
+
+
+def st_mg_residual(h, level, f, x, r, want_norm=False):
+    nrm = _dbl()
+    _check(lib().st_mg_residual(_vp(h), level, _vp(_addr(f)), _vp(_addr(x)), _vp(_addr(r)),
+                                ctypes.byref(nrm) if want_norm else None), "st_mg_residual")
+    return nrm.value if want_norm else None
+
+
+def _two(name):
+    def fn(h, level, a, b):
+        _check(getattr(lib(), name)(_vp(h), level, _vp(_addr(a)), _vp(_addr(b))), name)
+    fn.__name__ = name
+    return fn
+
+
+st_mg_slab_solve = _two("st_mg_slab_solve")
+st_mg_smooth_S = _two("st_mg_smooth_S")
+st_mg_correct_A = _two("st_mg_correct_A")
+st_mg_grad_T = _two("st_mg_grad_T")
+st_mg_nodal_solve = _two("st_mg_nodal_solve")
+st_mg_time_integrate = _two("st_mg_time_integrate")
+st_mg_grad_add = _two("st_mg_grad_add")
+st_mg_restrict = _two("st_mg_restrict")
+st_mg_prolong_add = _two("st_mg_prolong_add")
+
+
+def st_mg_coarse_solve(h, f, x):
+    _check(lib().st_mg_coarse_solve(_vp(h), _vp(_addr(f)), _vp(_addr(x))), "st_mg_coarse_solve")
+
+
+def st_mg_vcycle(h, f, x, want_res=False):
+    rr = _dbl()
+    _check(lib().st_mg_vcycle(_vp(h), _vp(_addr(f)), _vp(_addr(x)), ctypes.byref(rr) if want_res else None),
+           "st_mg_vcycle")
+    return rr.value if want_res else None
+
+
+def _solve_outputs(maxit):
+    return _i32(), _dbl(), np.zeros(maxit + 1)
+
+
+def st_mg_solve(h, f, x, rtol, maxit):
+    it, rr, hist = _solve_outputs(maxit)
+    st = lib().st_mg_solve(_vp(h), _vp(_addr(f)), _vp(_addr(x)), rtol, maxit, ctypes.byref(it), ctypes.byref(rr),
+                           _dptr(hist))
+    if st not in (0, 5):
+        _check(st, "st_mg_solve")
+    return {"status": st, "iters": it.value, "rel_res": rr.value, "history": hist[:it.value + 1]}
+
+
+def st_mg_solve_host(h, f_host: np.ndarray, x_host: np.ndarray, rtol, maxit):
+    assert f_host.dtype == np.float64 and x_host.dtype == np.float64
+    assert f_host.flags.c_contiguous and x_host.flags.c_contiguous
+    it, rr, hist = _solve_outputs(maxit)
+    st = lib().st_mg_solve_host(_vp(h), _dptr(f_host), _dptr(x_host), rtol, maxit, ctypes.byref(it),
+                                ctypes.byref(rr), _dptr(hist))
+    if st not in (0, 5):
+        _check(st, "st_mg_solve_host")
+    return {"status": st, "iters": it.value, "rel_res": rr.value, "history": hist[:it.value + 1]}
+
+
+_DEBUG_TYPES = {1: np.int32, 2: np.int32, 3: np.int32, 4: np.int64, 5: np.int32, 6: np.float64, 7: np.float64,
+                8: np.int32, 9: np.int64, 10: np.int32, 11: np.float64, 12: np.int64, 13: np.int32,
+                14: np.float64}
+
+
+def st_mg_debug_get(h, what, level):
+    nb = _i64(0)
+    _check(lib().st_mg_debug_get(_vp(h), what, level, None, ctypes.byref(nb)), "st_mg_debug_get")
+    dt = _DEBUG_TYPES[what]
+    out = np.zeros(nb.value // np.dtype(dt).itemsize, dtype=dt)
+    _check(lib().st_mg_debug_get(_vp(h), what, level, _vp(out.ctypes.data), ctypes.byref(nb)), "st_mg_debug_get")
+    return out
+
+
+def st_mg_debug_host_slab_solve(h, level, r_host: np.ndarray) -> np.ndarray:
+    r_host = np.ascontiguousarray(r_host, np.float64)
+    y = np.zeros_like(r_host)
+    _check(lib().st_mg_debug_host_slab_solve(_vp(h), level, _dptr(r_host), _dptr(y)), "st_mg_debug_host_slab_solve")
+    return y
+
+
+def st_mg_strerror(status: int) -> str:
+    return lib().st_mg_strerror(status).decode()

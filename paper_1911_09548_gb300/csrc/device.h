@@ -1,0 +1,112 @@
+// Launch interface between the host runtime and the CUDA kernels.  Plain
+// pointers and sizes only; every launcher queues work on `st` and returns the
+// launch status (cudaGetLastError) without synchronising.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace stmg {
+
+// One supernode of a nested-dissection factor as the GPU sees it.
+struct DevNode {
+  int32_t col0, nc, nr, pad;
+  int64_t w_off, row_off, u_off, g_off;
+};
+
+// Factor of one matrix (slab matrix of a time level, or K_n of a space level).
+// T = double (real symmetric) or double2 (complex symmetric, x = re, y = im).
+template <typename T>
+struct DevFactor {
+  int32_t n = 0, nnodes = 0, max_depth = 0;
+  DevNode* nodes = nullptr;
+  T* W = nullptr;                 // per-node blocks W_s = [L11^-1; -L21 L11^-1], row-major
+  T* Dinv = nullptr;              // [n], permuted order
+  int32_t* rows = nullptr;        // struct(s) lists, permuted indices
+  int32_t* gsrc = nullptr;        // forward gather table, 2 per front position
+  int32_t* iperm = nullptr;       // original index -> permuted position
+  // per depth d: tiles [tile_off[d], tile_off[d+1]) as (node, row tile)
+  int2* fwd_tiles = nullptr;
+  int2* bwd_tiles = nullptr;
+  int64_t* h_fwd_off = nullptr;   // host arrays, size max_depth + 2
+  int64_t* h_bwd_off = nullptr;
+  int64_t u_rows = 0;
+  double macs_per_rhs = 0;        // complex/real multiply-adds of one solve per right-hand side
+};
+
+// Row tile height of the supernodal products (tiles are built on the host with it).
+constexpr int kSnBM = 64;
+
+// ---- supernodal solve: X = A^{-1} Q on `nrhs` columns, leading dimension ld.
+// Q (in) is overwritten by X (out); Z and U are workspaces ([n*ld], [u_rows*ld]).
+cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, int nrhs, int ld,
+                          cudaStream_t st);
+cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, int nrhs, int ld,
+                          cudaStream_t st);
+
+// ---- space-time kernels.  Edge-major layout v[e*ncols + n*q + i], ncols = N_t*q.
+struct CsrView {
+  int32_t nrows;
+  const int64_t* rowptr;
+  const int32_t* col;
+};
+
+// r = f - L x.  DG(0): a = M + tau K, m = M.  DG(1): m = M, k0 = tau K, k1 = tau K / 3.
+// partial (nullable): one double per block with the block's sum of r^2 (deterministic
+// second stage by reduce_partials).  Returns the number of blocks via *nblocks.
+cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x,
+                         double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
+cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
+                         const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
+int residual_blocks(int nrows);
+// out[0] = sum of partial[0..n) in a fixed order.
+cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st);
+// out[0] = sum v^2 over n values (deterministic two-stage); partial has >= 1024 entries.
+cudaError_t norm2_sq(const double* v, int64_t n, double* partial, double* out, cudaStream_t st);
+
+// Slab right-hand sides -> permuted solve columns (slabs slab0 .. slab0+cnt-1 of a
+// source with row length src_ld).  DG(1) maps the pair (r0, r1) to c0 r0 + c1 r1.
+cudaError_t slab_pre_dg0(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                         double* Q, int ld, cudaStream_t st);
+cudaError_t slab_pre_dg1(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                         double2 c0, double2 c1, double2* Q, int ld, cudaStream_t st);
+// Solution columns -> slabs.  mode 0: x = v;  mode 1: x += omega * v.
+// DG(1): u_i = 2 Re(s_i v) with s = (1, s1).
+cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
+                          int slab0, int cnt, double omega, int mode, cudaStream_t st);
+cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
+                          int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st);
+// Nodal solve columns: Q[iperm[v]][j] = y[v][j];  z[v][j] = X[iperm[v]][j].
+cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
+                        cudaStream_t st);
+cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
+                         cudaStream_t st);
+
+// y[v][j] = sum over incident interior edges of G[e][v] r[e][j]  (G^T, node-major CSR,
+// gt_sign = +1 head / -1 tail).
+cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st);
+// x[e][j] += w[head][j] - w[tail][j]  (G w), -1 = boundary vertex.
+cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const double* w, double* x,
+                     int ncols, cudaStream_t st);
+// w = L_t^{-1} z per node row (DG(0): running sum; DG(1): upwind recurrence).
+cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st);
+// One damped Jacobi sweep on K_n: zo = zi + wgt * D^{-1} (y - K_n zi).
+cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
+                         double* zo, int ncols, double wgt, cudaStream_t st);
+
+// Time transfers between N_t (fine) and N_t/2 (coarse) slabs, same space level.
+cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st);
+cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st);
+// Space transfers per time column: out = P in (P given as CSR rows), beta 0 overwrite / 1 add.
+cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,
+                     cudaStream_t st);
+// Coarse forward substitution: g[e][i] = f[e][n q + i] - sum_j N_t[i][j] (M x_{n-1})_j.
+cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t,
+                        int n, int degree, cudaStream_t st);
+// Elementwise helpers.
+cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st);
+cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st);
+// Outer-product load f[e][n q + i] = c[n q + i] * b[e].
+cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, cudaStream_t st);
+
+}  // namespace stmg

@@ -1,0 +1,1033 @@
+// Host runtime and C ABI of the space-time multigrid library (see include/st_mg.h).
+//
+// Setup builds, per space level s (finest first), the Kuhn mesh, M_sigma and K_nu
+// (assembled on the finest mesh, Galerkin products P_x^T A P_x below it), G, K_n
+// and P_x; per time level l the coarsening decision of eq. CoarseningRule, the
+// residual coefficient arrays and the factor of the shared slab matrix; then it
+// uploads everything and sizes one workspace.  The V-cycle (Section 2.1) with the
+// hybrid smoother S^nu A S^nu (Section 4) is a fixed sequence of kernel launches
+// on the handle's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/st_mg.h"
+#include "device.h"
+#include "host.h"
+
+using namespace stmg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct CudaError {
+  cudaError_t e;
+  const char* where;
+};
+
+
+#define CK(call)                                                    \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) throw CudaError{e_, #call};              \
+  } while (0)
+
+}  // namespace
+
+struct st_mg_s {
+  st_mg_problem prob{};
+  st_mg_options opt{};
+  std::vector<double> nu, sigma;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool host_only = false;              // built by st_mg_setup_host: no device state
+  double* stage_f = nullptr;           // host-buffer solve staging (allocated on first use)
+  double* stage_x = nullptr;
+  int q = 1;
+  std::vector<void*> allocs;
+
+  template <typename T>
+  T* dalloc(int64_t count) {
+    void* p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
+    allocs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* d = dalloc<T>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  }
+
+  struct Space {
+    KuhnMesh mesh;
+    Csr M, K, Kn, Px, PxT, GT;            // Px: prolongation from space level s+1 to s
+    std::vector<int32_t> gtail, ghead;
+    std::vector<int8_t> gt_sign;
+    int32_t ne = 0, nn = 0;
+    // device
+    int64_t* rowptr = nullptr; int32_t* col = nullptr; double* Mv = nullptr;
+    int32_t* gtail_d = nullptr; int32_t* ghead_d = nullptr;
+    int64_t* gt_rowptr = nullptr; int32_t* gt_col = nullptr; int8_t* gt_sign_d = nullptr;
+    int64_t* kn_rowptr = nullptr; int32_t* kn_col = nullptr; double* kn_val = nullptr; double* kn_dinv = nullptr;
+    int64_t* px_rowptr = nullptr; int32_t* px_col = nullptr; double* px_val = nullptr;
+    int64_t* pxt_rowptr = nullptr; int32_t* pxt_col = nullptr; double* pxt_val = nullptr;
+    SupernodalFactor<double> knF;
+    DevFactor<double> kn;
+    std::vector<int64_t> kn_fwd_off, kn_bwd_off;
+    NDCoords ecoord, ncoord;
+  };
+  std::vector<Space> space;
+
+  struct Level {
+    int s = 0, N_t = 1;
+    double tau = 1.0;
+    double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;   // residual coefficients per nnz
+    SupernodalFactor<double> fr;
+    SupernodalFactor<cplx> fc;
+    DevFactor<double> dr;
+    DevFactor<double2> dc;
+    std::vector<int64_t> fwd_off, bwd_off;
+    double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
+    int64_t len = 0;
+  };
+  std::vector<Level> lv;
+
+  // workspaces
+  void *sQ = nullptr, *sZ = nullptr, *sU = nullptr;
+  int ld_slab = 1;
+  double *nQ = nullptr, *nZ = nullptr, *nU = nullptr;
+  int ld_nod = 1;
+  double *ny = nullptr, *nz = nullptr, *nw = nullptr;
+  double* tmp_fine = nullptr;
+  double* g1 = nullptr;                 // one-slab right-hand side of the forward substitution
+  double* r0 = nullptr;                 // finest residual
+  double* partial = nullptr;
+  double* scalar = nullptr;
+  double2 c0{}, c1{}, s1{};             // DG(1) complex slab transformation
+
+  ~st_mg_s() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+using Handle = st_mg_s;
+
+CsrView view(const Handle::Space& S) { return CsrView{S.ne, S.rowptr, S.col}; }
+
+template <typename T, typename DT>
+void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, std::vector<int64_t>& fo,
+                     std::vector<int64_t>& bo) {
+  static_assert(sizeof(T) == sizeof(DT), "layout");
+  D.n = F.n;
+  D.nnodes = (int32_t)F.nodes.size();
+  D.max_depth = F.max_depth;
+  std::vector<DevNode> nodes(F.nodes.size());
+  for (size_t s = 0; s < F.nodes.size(); ++s) {
+    const auto& a = F.nodes[s];
+    nodes[s] = DevNode{a.col0, a.nc, a.nr, 0, a.w_off, a.row_off, a.u_off, F.gather_off[s]};
+  }
+  std::vector<int2> ft, bt;
+  fo.assign(F.max_depth + 2, 0);
+  bo.assign(F.max_depth + 2, 0);
+  for (int d = 0; d <= F.max_depth; ++d) {
+    fo[d] = (int64_t)ft.size();
+    bo[d] = (int64_t)bt.size();
+    for (size_t s = 0; s < F.nodes.size(); ++s) {
+      const auto& a = F.nodes[s];
+      if (a.depth != d) continue;
+      const int mf = (a.nc + a.nr + kSnBM - 1) / kSnBM, mb = (a.nc + kSnBM - 1) / kSnBM;
+      for (int t = 0; t < mf; ++t) ft.push_back(make_int2((int)s, t));
+      for (int t = 0; t < mb; ++t) bt.push_back(make_int2((int)s, t));
+    }
+  }
+  fo[F.max_depth + 1] = (int64_t)ft.size();
+  bo[F.max_depth + 1] = (int64_t)bt.size();
+  D.nodes = h.upload(nodes);
+  D.W = reinterpret_cast<DT*>(h.upload(F.W));
+  D.Dinv = reinterpret_cast<DT*>(h.upload(F.Dinv));
+  D.rows = h.upload(F.rows);
+  D.gsrc = h.upload(F.gsrc);
+  D.iperm = h.upload(F.iperm);
+  D.fwd_tiles = h.upload(ft);
+  D.bwd_tiles = h.upload(bt);
+  D.h_fwd_off = fo.data();
+  D.h_bwd_off = bo.data();
+  D.u_rows = F.u_rows;
+  D.macs_per_rhs = F.flops_apply_per_rhs;
+}
+
+int hw_threads(int req) {
+  if (req > 0) return req;
+  unsigned n = std::thread::hardware_concurrency();
+  return n ? (int)n : 1;
+}
+
+// ---------------------------------------------------------------- operations
+void op_residual(Handle& h, int l, const double* f, const double* x, double* r, double* norm_sq_host) {
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  int nb = 0;
+  double* part = norm_sq_host ? h.partial : nullptr;
+  if (h.prob.degree == 0)
+    CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t, part, &nb, h.stream));
+  else
+    CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t, part, &nb, h.stream));
+  if (norm_sq_host) {
+    CK(reduce_partials(h.partial, nb, h.scalar, h.stream));
+    CK(cudaMemcpyAsync(norm_sq_host, h.scalar, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    CK(cudaStreamSynchronize(h.stream));
+  }
+}
+
+// Slab solve on slabs [slab0, slab0+cnt) of src (row length src_ld doubles) into dst
+// (row length dst_ld) at slab dst0: mode 0 assign, mode 1 dst += omega * A^{-1} src.
+void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, int cnt, double* dst, int dst_ld,
+                  int dst0, double omega, int mode) {
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  if (h.prob.degree == 0) {
+    double* Q = static_cast<double*>(h.sQ);
+    CK(slab_pre_dg0(src, src_ld, slab0, cnt, L.dr.iperm, S.ne, Q, h.ld_slab, h.stream));
+    CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), cnt, h.ld_slab, h.stream));
+    CK(slab_post_dg0(Q, h.ld_slab, L.dr.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+  } else {
+    const double inv_tau = 1.0 / L.tau;
+    const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
+    const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
+    double2* Q = static_cast<double2*>(h.sQ);
+    CK(slab_pre_dg1(src, src_ld, slab0, cnt, L.dc.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+    CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU), cnt, h.ld_slab, h.stream));
+    CK(slab_post_dg1(Q, h.ld_slab, L.dc.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+  }
+}
+
+double* level_r(Handle& h, int l) { return l == 0 ? h.r0 : h.lv[l].r; }
+
+void op_smooth_S(Handle& h, int l, const double* f, double* x) {
+  auto& L = h.lv[l];
+  double* r = level_r(h, l);
+  op_residual(h, l, f, x, r, nullptr);
+  const int ld = L.N_t * h.q;
+  op_slab_cols(h, l, r, ld, 0, L.N_t, x, ld, 0, h.opt.omega, 1);
+}
+
+void op_grad_T(Handle& h, int l, const double* r, double* y) {
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  CK(grad_T(CsrView{S.nn, S.gt_rowptr, S.gt_col}, S.gt_sign_d, r, y, L.N_t * h.q, h.stream));
+}
+
+void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  const int ncols = L.N_t * h.q;
+  if (h.opt.nodal_solve == 0) {
+    CK(gather_perm(y, ncols, S.kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
+    CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, ncols, h.ld_nod, h.stream));
+    CK(scatter_perm(h.nQ, h.ld_nod, S.kn.iperm, S.nn, z, ncols, h.stream));
+  } else {
+    // damped Jacobi from z = 0, ping-pong through the nodal workspace
+    const int64_t n = (int64_t)S.nn * ncols;
+    CK(vec_fill(z, n, 0.0, h.stream));
+    CsrView kv{S.nn, S.kn_rowptr, S.kn_col};
+    for (int it = 0; it < h.opt.nodal_jacobi_sweeps; ++it) {
+      CK(nodal_jacobi(kv, S.kn_val, S.kn_dinv, y, z, h.nQ, ncols, 2.0 / 3.0, h.stream));
+      CK(vec_copy(h.nQ, z, n, h.stream));
+    }
+  }
+}
+
+void op_time_integrate(Handle& h, int l, const double* z, double* w) {
+  auto& L = h.lv[l];
+  CK(time_integrate(z, w, h.space[L.s].nn, L.N_t, h.prob.degree, h.stream));
+}
+
+void op_grad_add(Handle& h, int l, const double* w, double* x) {
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  CK(grad_add(S.gtail_d, S.ghead_d, S.ne, w, x, L.N_t * h.q, h.stream));
+}
+
+void op_correct_A(Handle& h, int l, const double* f, double* x) {
+  double* r = level_r(h, l);
+  op_residual(h, l, f, x, r, nullptr);
+  op_grad_T(h, l, r, h.ny);
+  op_nodal_solve(h, l, h.ny, h.nz);
+  op_time_integrate(h, l, h.nz, h.nw);
+  op_grad_add(h, l, h.nw, x);
+}
+
+bool space_coarsened(Handle& h, int l) { return h.lv[l + 1].s != h.lv[l].s; }
+
+void op_restrict(Handle& h, int l, const double* r, double* rc) {
+  auto& L = h.lv[l];
+  auto& Sf = h.space[L.s];
+  const int Nc = h.lv[l + 1].N_t;
+  if (space_coarsened(h, l)) {
+    CK(time_restrict(r, h.tmp_fine, Sf.ne, Nc, h.prob.degree, h.stream));
+    CK(csr_spmm(CsrView{Sf.PxT.nrows, Sf.pxt_rowptr, Sf.pxt_col}, Sf.pxt_val, h.tmp_fine, rc, Nc * h.q, 0,
+                h.stream));
+  } else {
+    CK(time_restrict(r, rc, Sf.ne, Nc, h.prob.degree, h.stream));
+  }
+}
+
+void op_prolong_add(Handle& h, int l, const double* ec, double* x) {
+  auto& L = h.lv[l];
+  auto& Sf = h.space[L.s];
+  const int Nc = h.lv[l + 1].N_t;
+  if (space_coarsened(h, l)) {
+    CK(csr_spmm(CsrView{Sf.Px.nrows, Sf.px_rowptr, Sf.px_col}, Sf.px_val, ec, h.tmp_fine, Nc * h.q, 0, h.stream));
+    CK(time_prolong_add(h.tmp_fine, x, Sf.ne, Nc, h.prob.degree, h.stream));
+  } else {
+    CK(time_prolong_add(ec, x, Sf.ne, Nc, h.prob.degree, h.stream));
+  }
+}
+
+void op_coarse_solve(Handle& h, const double* f, double* x) {
+  const int l = (int)h.lv.size() - 1;
+  auto& L = h.lv[l];
+  auto& S = h.space[L.s];
+  const int ld = L.N_t * h.q;
+  if (L.N_t == 1) {
+    op_slab_cols(h, l, f, ld, 0, 1, x, ld, 0, 1.0, 0);
+    return;
+  }
+  for (int n = 0; n < L.N_t; ++n) {
+    CK(history_rhs(view(S), S.Mv, f, x, h.g1, L.N_t, n, h.prob.degree, h.stream));
+    op_slab_cols(h, l, h.g1, h.q, 0, 1, x, ld, n, 1.0, 0);
+  }
+}
+
+void op_smooth(Handle& h, int l, const double* f, double* x, int nu) {
+  for (int k = 0; k < nu; ++k) op_smooth_S(h, l, f, x);
+  if (h.opt.use_A) op_correct_A(h, l, f, x);
+  for (int k = 0; k < nu; ++k) op_smooth_S(h, l, f, x);
+}
+
+void op_vcycle(Handle& h, int l, const double* f, double* x) {
+  if (l == (int)h.lv.size() - 1) {
+    op_coarse_solve(h, f, x);
+    return;
+  }
+  op_smooth(h, l, f, x, h.opt.nu_pre);
+  double* r = level_r(h, l);
+  op_residual(h, l, f, x, r, nullptr);
+  auto& C = h.lv[l + 1];
+  op_restrict(h, l, r, C.f);
+  CK(vec_fill(C.x, C.len, 0.0, h.stream));
+  op_vcycle(h, l + 1, C.f, C.x);
+  op_prolong_add(h, l, C.x, x);
+  op_smooth(h, l, f, x, h.opt.nu_post);
+}
+
+double f_norm(Handle& h, const double* f) {
+  double v = 0.0;
+  CK(norm2_sq(f, h.lv[0].len, h.partial, h.scalar, h.stream));
+  CK(cudaMemcpyAsync(&v, h.scalar, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return std::sqrt(v);
+}
+
+// ---------------------------------------------------------------- setup
+int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_mg_t* out, bool host_only) {
+  if (!pr || !op || !out) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const int n = pr->n_cube, nsl = pr->n_space_levels;
+  if (n < 2 || nsl < 1 || pr->N_t < 1 || !(pr->T > 0) || (pr->degree != 0 && pr->degree != 1) || !pr->nu ||
+      !pr->sigma)
+    return fail(ST_MG_ERR_INVALID_ARG, "invalid problem (n_cube >= 2, n_space_levels >= 1, N_t >= 1, T > 0, degree 0|1)");
+  if ((n >> (nsl - 1)) < 2 || (n % (1 << (nsl - 1))) != 0)
+    return fail(ST_MG_ERR_INVALID_ARG, "n_cube must be divisible by 2^(n_space_levels-1) with coarsest >= 2");
+  if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
+      op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
+      op->nodal_jacobi_sweeps < 0)
+    return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
+  const int64_t nt = (int64_t)6 * n * n * n;
+  for (int64_t t = 0; t < nt; ++t)
+    if (!(pr->nu[t] > 0) || !(pr->sigma[t] > 0) || !std::isfinite(pr->nu[t]) || !std::isfinite(pr->sigma[t]))
+      return fail(ST_MG_ERR_INVALID_ARG, "nu and sigma must be positive and finite");
+
+  std::unique_ptr<Handle> h(new Handle());
+  Handle& H = *h;
+  H.prob = *pr;
+  H.opt = *op;
+  H.nu.assign(pr->nu, pr->nu + nt);
+  H.sigma.assign(pr->sigma, pr->sigma + nt);
+  H.prob.nu = H.nu.data();
+  H.prob.sigma = H.sigma.data();
+  H.stream = static_cast<cudaStream_t>(stream);
+  H.q = pr->degree + 1;
+  H.host_only = host_only;
+  if (!host_only) CK(cudaGetDevice(&H.device));
+
+  // ---- space hierarchy
+  H.space.resize(nsl);
+  for (int s = 0; s < nsl; ++s) {
+    auto& S = H.space[s];
+    build_kuhn(n >> s, S.mesh);
+    S.ne = (int32_t)S.mesh.int_edges.size();
+    S.nn = (int32_t)S.mesh.int_verts.size();
+    gradient_pairs(S.mesh, S.gtail, S.ghead);
+    for (int32_t e : S.mesh.int_edges) {
+      int i, j, k;
+      S.mesh.vijk(S.mesh.edge_lo[e], i, j, k);
+      S.ecoord.x.push_back(i); S.ecoord.y.push_back(j); S.ecoord.z.push_back(k);
+    }
+    for (int32_t v : S.mesh.int_verts) {
+      int i, j, k;
+      S.mesh.vijk(v, i, j, k);
+      S.ncoord.x.push_back(i); S.ncoord.y.push_back(j); S.ncoord.z.push_back(k);
+    }
+  }
+  assemble_edge(H.space[0].mesh, H.nu.data(), H.sigma.data(), H.space[0].M, H.space[0].K);
+  assemble_nodal(H.space[0].mesh, H.sigma.data(), H.space[0].Kn);
+  for (int s = 0; s + 1 < nsl; ++s) {
+    auto& F = H.space[s];
+    auto& C = H.space[s + 1];
+    edge_prolongation(C.mesh, F.mesh, F.Px);
+    F.PxT = csr_transpose(F.Px);
+    C.M = csr_galerkin(F.Px, F.M);
+    C.K = csr_galerkin(F.Px, F.K);
+    C.Kn = nodal_from_gradient(C.M, C.gtail, C.ghead, C.nn);
+    if (C.M.col != C.K.col) return fail(ST_MG_ERR_NUMERIC, "coarse M and K patterns differ");
+  }
+  for (auto& S : H.space) {
+    S.GT = csr_transpose(gradient_csr(S.gtail, S.ghead, S.nn));
+    S.gt_sign.resize(S.GT.val.size());
+    for (size_t q = 0; q < S.GT.val.size(); ++q) S.gt_sign[q] = S.GT.val[q] > 0 ? 1 : -1;
+  }
+
+  // ---- time hierarchy (eq. CoarseningRule with h_T = sqrt(3)/n for every Kuhn tet)
+  double min_ratio = INFINITY;
+  for (int64_t t = 0; t < nt; ++t) min_ratio = std::min(min_ratio, H.nu[t] / H.sigma[t]);
+  {
+    Handle::Level L0;
+    L0.s = 0;
+    L0.N_t = pr->N_t;
+    L0.tau = pr->T / pr->N_t;
+    H.lv.push_back(L0);
+  }
+  const int cap = op->max_levels > 0 ? op->max_levels : 1 << 20;
+  while ((int)H.lv.size() < cap) {
+    const auto& cur = H.lv.back();
+    if (cur.N_t <= op->min_coarse_slabs || (cur.N_t % 2) != 0) break;
+    const bool can_space = cur.s + 1 < nsl;
+    bool coarsen = false;
+    if (op->coarsen == 0) {
+      const double hT = std::sqrt(3.0) / (double)(n >> cur.s);
+      coarsen = can_space && (min_ratio * cur.tau / (hT * hT) >= op->lambda_crit);
+    } else if (op->coarsen == 2) {
+      coarsen = can_space && H.lv.size() == 1;
+    }
+    Handle::Level C;
+    C.s = cur.s + (coarsen ? 1 : 0);
+    C.N_t = cur.N_t / 2;
+    C.tau = cur.tau * 2.0;
+    H.lv.push_back(C);
+  }
+
+  // ---- DG(1) complex transformation: M_t^{-1} K_t = S diag(mu, conj mu) S^{-1},
+  // mu tau = 2 + i sqrt2, s_0 = (1, 1 + i sqrt2); row 0 of S^{-1} M_t^{-1} is
+  // (1/2 + i/(2 sqrt2), -3i/(2 sqrt2)) / tau.
+  const double r2 = std::sqrt(2.0);
+  H.c0 = make_double2(0.5, 0.5 / r2);
+  H.c1 = make_double2(0.0, -1.5 / r2);
+  H.s1 = make_double2(1.0, r2);
+
+  // ---- factorisations (all levels concurrently)
+  const int nthr = hw_threads(op->setup_threads);
+  std::vector<std::string> errs(H.lv.size() + H.space.size());
+  std::vector<int> rcs(errs.size(), 0);
+  {
+    const int njobs = (int)errs.size();
+    const int inner = std::max(1, nthr / std::max(1, njobs));
+    std::vector<std::thread> jobs;
+    std::mutex mu;
+    int next = 0;
+    auto worker = [&]() {
+      for (;;) {
+        int j;
+        {
+          std::lock_guard<std::mutex> g(mu);
+          j = next++;
+        }
+        if (j >= njobs) return;
+        if (j < (int)H.lv.size()) {
+          auto& L = H.lv[j];
+          auto& S = H.space[L.s];
+          if (pr->degree == 0) {
+            std::vector<double> v(S.M.val.size());
+            for (size_t q = 0; q < v.size(); ++q) v[q] = S.M.val[q] + L.tau * S.K.val[q];
+            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, 64, L.fr, errs[j], inner);
+          } else {
+            const double mr = 2.0 / L.tau, mi = r2 / L.tau;   // mu = (2 + i sqrt2) / tau
+            std::vector<cplx> v(S.M.val.size());
+            for (size_t q = 0; q < v.size(); ++q) v[q] = cplx(S.K.val[q] + mr * S.M.val[q], mi * S.M.val[q]);
+            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, 64, L.fc, errs[j], inner);
+          }
+        } else {
+          auto& S = H.space[j - H.lv.size()];
+          rcs[j] = factor_nd_threads(S.Kn, S.Kn.val, S.ncoord, 48, S.knF, errs[j], inner);
+        }
+      }
+    };
+    const int nw = std::min(nthr, njobs);
+    for (int t = 0; t < nw; ++t) jobs.emplace_back(worker);
+    for (auto& t : jobs) t.join();
+  }
+  for (size_t j = 0; j < rcs.size(); ++j)
+    if (rcs[j]) return fail(rcs[j] == 6 ? ST_MG_ERR_NUMERIC : ST_MG_ERR_INVALID_ARG, "factorisation: " + errs[j]);
+  for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q;
+  if (host_only) {
+    *out = h.release();
+    return ST_MG_OK;
+  }
+
+  // ---- upload
+  for (auto& S : H.space) {
+    S.rowptr = H.upload(S.M.rowptr);
+    S.col = H.upload(S.M.col);
+    S.Mv = H.upload(S.M.val);
+    S.gtail_d = H.upload(S.gtail);
+    S.ghead_d = H.upload(S.ghead);
+    S.gt_rowptr = H.upload(S.GT.rowptr);
+    S.gt_col = H.upload(S.GT.col);
+    S.gt_sign_d = H.upload(S.gt_sign);
+    S.kn_rowptr = H.upload(S.Kn.rowptr);
+    S.kn_col = H.upload(S.Kn.col);
+    S.kn_val = H.upload(S.Kn.val);
+    std::vector<double> dinv(S.nn);
+    for (int32_t v = 0; v < S.nn; ++v)
+      for (int64_t q = S.Kn.rowptr[v]; q < S.Kn.rowptr[v + 1]; ++q)
+        if (S.Kn.col[q] == v) dinv[v] = 1.0 / S.Kn.val[q];
+    S.kn_dinv = H.upload(dinv);
+    if (!S.Px.rowptr.empty()) {
+      S.px_rowptr = H.upload(S.Px.rowptr);
+      S.px_col = H.upload(S.Px.col);
+      S.px_val = H.upload(S.Px.val);
+      S.pxt_rowptr = H.upload(S.PxT.rowptr);
+      S.pxt_col = H.upload(S.PxT.col);
+      S.pxt_val = H.upload(S.PxT.val);
+    }
+    make_dev_factor(H, S.knF, S.kn, S.kn_fwd_off, S.kn_bwd_off);
+    S.knF = SupernodalFactor<double>();   // host copy no longer needed
+  }
+  int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0;
+  int max_nt = 1;
+  for (size_t l = 0; l < H.lv.size(); ++l) {
+    auto& L = H.lv[l];
+    auto& S = H.space[L.s];
+    const size_t nnz = S.M.val.size();
+    std::vector<double> a(nnz), b(nnz), c(nnz);
+    if (pr->degree == 0) {
+      for (size_t q = 0; q < nnz; ++q) { a[q] = S.M.val[q] + L.tau * S.K.val[q]; b[q] = S.M.val[q]; }
+      L.v0 = H.upload(a);
+      L.v1 = H.upload(b);
+      make_dev_factor(H, L.fr, L.dr, L.fwd_off, L.bwd_off);
+      max_u = std::max<int64_t>(max_u, L.fr.u_rows);
+      L.fr = SupernodalFactor<double>();
+    } else {
+      for (size_t q = 0; q < nnz; ++q) {
+        a[q] = S.M.val[q];
+        b[q] = L.tau * S.K.val[q];
+        c[q] = L.tau * S.K.val[q] / 3.0;
+      }
+      L.v0 = H.upload(a);
+      L.v1 = H.upload(b);
+      L.v2 = H.upload(c);
+      make_dev_factor(H, L.fc, L.dc, L.fwd_off, L.bwd_off);
+      max_u = std::max<int64_t>(max_u, L.fc.u_rows);
+      L.fc = SupernodalFactor<cplx>();
+    }
+    L.len = (int64_t)S.ne * L.N_t * H.q;
+    if (l > 0) {
+      L.f = H.dalloc<double>(L.len);
+      L.x = H.dalloc<double>(L.len);
+      L.r = H.dalloc<double>(L.len);
+    }
+    if (l + 1 < H.lv.size() && H.lv[l + 1].s != L.s)
+      max_len_fine_tmp = std::max<int64_t>(max_len_fine_tmp, (int64_t)S.ne * H.lv[l + 1].N_t * H.q);
+    max_ne = std::max<int64_t>(max_ne, S.ne);
+    max_nn = std::max<int64_t>(max_nn, S.nn);
+    max_nt = std::max(max_nt, L.N_t);
+    max_un = std::max<int64_t>(max_un, S.kn.u_rows);
+  }
+  const size_t esz = pr->degree == 0 ? sizeof(double) : sizeof(double2);
+  H.ld_slab = max_nt;
+  H.sQ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
+  H.sZ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
+  H.sU = H.dalloc<char>((int64_t)(std::max<int64_t>(max_u, 1) * H.ld_slab * esz));
+  H.ld_nod = max_nt * H.q;
+  H.nQ = H.dalloc<double>(max_nn * H.ld_nod);
+  H.nZ = H.dalloc<double>(max_nn * H.ld_nod);
+  H.nU = H.dalloc<double>(std::max<int64_t>(max_un, 1) * H.ld_nod);
+  H.ny = H.dalloc<double>(max_nn * H.ld_nod);
+  H.nz = H.dalloc<double>(max_nn * H.ld_nod);
+  H.nw = H.dalloc<double>(max_nn * H.ld_nod);
+  H.tmp_fine = H.dalloc<double>(std::max<int64_t>(max_len_fine_tmp, 1));
+  H.g1 = H.dalloc<double>(max_ne * H.q);
+  H.r0 = H.dalloc<double>(H.lv[0].len);
+  H.partial = H.dalloc<double>(std::max(1024, residual_blocks((int)max_ne)));
+  H.scalar = H.dalloc<double>(1);
+  CK(cudaDeviceSynchronize());
+  *out = h.release();
+  return ST_MG_OK;
+}
+
+template <typename Fn>
+int guarded(Fn fn) {
+  try {
+    return fn();
+  } catch (const CudaError& e) {
+    return fail(e.e == cudaErrorMemoryAllocation ? ST_MG_ERR_OOM : ST_MG_ERR_CUDA,
+                std::string(e.where) + ": " + cudaGetErrorString(e.e));
+  } catch (const std::bad_alloc&) {
+    return fail(ST_MG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(ST_MG_ERR_INVALID_ARG, e.what());
+  }
+}
+
+int check_dev(st_mg_t h) {
+  if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
+  if (h->host_only) return fail(ST_MG_ERR_INVALID_ARG, "handle was built by st_mg_setup_host (no device state)");
+  return ST_MG_OK;
+}
+
+int check_level(st_mg_t h, int32_t level) {
+  if (int rc = check_dev(h)) return rc;
+  if (level < 0 || level >= (int32_t)h->lv.size()) return fail(ST_MG_ERR_INVALID_ARG, "level out of range");
+  return ST_MG_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_ptrs(std::initializer_list<const void*> ps) {
+  for (const void* p : ps) {
+    if (!p) return fail(ST_MG_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(p)) return fail(ST_MG_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  }
+  return ST_MG_OK;
+}
+
+int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit, int32_t* iters, double* rel_res,
+               double* history) {
+  const double fn = f_norm(H, f);
+  const double denom = fn > 0 ? fn : 1.0;
+  double nsq = 0.0;
+  op_residual(H, 0, f, x, H.r0, &nsq);
+  double rel = std::sqrt(nsq) / denom;
+  const double rel0 = rel;
+  if (history) history[0] = rel;
+  int it = 0;
+  int status = ST_MG_OK;
+  while (rel > rtol && it < maxit) {
+    op_vcycle(H, 0, f, x);
+    op_residual(H, 0, f, x, H.r0, &nsq);
+    rel = std::sqrt(nsq) / denom;
+    ++it;
+    if (history) history[it] = rel;
+    if (!std::isfinite(rel) || rel > 1e3 * std::max(rel0, 1e-300)) {
+      status = fail(ST_MG_ERR_DIVERGED, "residual diverged");
+      break;
+    }
+  }
+  if (status == ST_MG_OK && rel > rtol) status = fail(ST_MG_ERR_NOT_CONVERGED, "maxit reached");
+  if (iters) *iters = it;
+  if (rel_res) *rel_res = rel;
+  return status;
+}
+
+}  // namespace
+
+// Host evaluation of one factor on one right-hand side, in the same forward /
+// backward order as the device kernels (setup check on host-only handles).
+template <typename T>
+void host_factor_apply(const SupernodalFactor<T>& F, std::vector<T>& b) {
+  const int n = F.n;
+  std::vector<T> q(n), z(n), x(n), U(F.u_rows);
+  for (int i = 0; i < n; ++i) q[F.iperm[i]] = b[i];
+  for (size_t s = 0; s < F.nodes.size(); ++s) {
+    const auto& nd = F.nodes[s];
+    const int m = nd.nc + nd.nr;
+    std::vector<T> f(m);
+    for (int p = 0; p < m; ++p) {
+      T v = p < nd.nc ? q[nd.col0 + p] : T(0.0);
+      for (int c = 0; c < 2; ++c) {
+        const int32_t src = F.gsrc[(F.gather_off[s] + p) * 2 + c];
+        if (src >= 0) v = v + U[src];
+      }
+      f[p] = v;
+    }
+    const T* W = F.W.data() + nd.w_off;
+    for (int r = 0; r < m; ++r) {
+      T acc(0.0);
+      for (int k = 0; k < nd.nc; ++k) acc = acc + W[(int64_t)r * nd.nc + k] * f[k];
+      if (r < nd.nc) z[nd.col0 + r] = F.Dinv[nd.col0 + r] * acc;
+      else U[nd.u_off + r - nd.nc] = f[r] + acc;
+    }
+  }
+  for (int s = (int)F.nodes.size() - 1; s >= 0; --s) {
+    const auto& nd = F.nodes[s];
+    const int m = nd.nc + nd.nr;
+    const T* W = F.W.data() + nd.w_off;
+    for (int i = 0; i < nd.nc; ++i) {
+      T acc(0.0);
+      for (int k = 0; k < m; ++k) {
+        const T g = k < nd.nc ? z[nd.col0 + k] : x[F.rows[nd.row_off + k - nd.nc]];
+        acc = acc + W[(int64_t)k * nd.nc + i] * g;
+      }
+      x[nd.col0 + i] = acc;
+    }
+  }
+  for (int i = 0; i < n; ++i) b[i] = x[F.iperm[i]];
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+int st_mg_default_options(st_mg_options* o) {
+  if (!o) return fail(ST_MG_ERR_INVALID_ARG, "null options");
+  o->omega = 0.5;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->lambda_crit = 0.1;
+  o->coarsen = 0;
+  o->max_levels = 0;
+  o->min_coarse_slabs = 1;
+  o->nodal_solve = 0;
+  o->nodal_jacobi_sweeps = 3;
+  o->use_A = 1;
+  o->setup_threads = 0;
+  return ST_MG_OK;
+}
+
+int st_mg_setup(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out) {
+  return guarded([&]() { return do_setup(prob, opt, stream, out, false); });
+}
+
+int st_mg_setup_host(const st_mg_problem* prob, const st_mg_options* opt, st_mg_t* out) {
+  return guarded([&]() { return do_setup(prob, opt, nullptr, out, true); });
+}
+
+void st_mg_destroy(st_mg_t h) {
+  if (!h) return;
+  if (!h->host_only) cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+int st_mg_sizes(st_mg_t h, int64_t* n_edge, int64_t* n_node, int64_t* n_dof, int32_t* n_levels) {
+  if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
+  if (n_edge) *n_edge = h->space[0].ne;
+  if (n_node) *n_node = h->space[0].nn;
+  if (n_dof) *n_dof = h->lv[0].len;
+  if (n_levels) *n_levels = (int32_t)h->lv.size();
+  return ST_MG_OK;
+}
+
+int st_mg_level_info(st_mg_t h, int32_t level, int32_t* space_level, int32_t* N_t, double* tau, int64_t* n_edge,
+                     int64_t* n_node) {
+  if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
+  if (level < 0 || level >= (int32_t)h->lv.size()) return fail(ST_MG_ERR_INVALID_ARG, "level out of range");
+  const auto& L = h->lv[level];
+  if (space_level) *space_level = L.s;
+  if (N_t) *N_t = L.N_t;
+  if (tau) *tau = L.tau;
+  if (n_edge) *n_edge = h->space[L.s].ne;
+  if (n_node) *n_node = h->space[L.s].nn;
+  return ST_MG_OK;
+}
+
+int st_mg_assemble_load(st_mg_t h, int32_t n_modes, const double* a, const double* k, const double* phase,
+                        double* f_dev) {
+  if (int rc = check_dev(h)) return rc;
+  if (n_modes < 0 || (n_modes > 0 && (!a || !k || !phase))) return fail(ST_MG_ERR_INVALID_ARG, "bad load");
+  if (int rc = check_ptrs({f_dev})) return rc;
+  return guarded([&]() {
+    Handle& H = *h;
+    std::vector<double> b;
+    space_load(H.space[0].mesh, n_modes, a, k, phase, b);
+    // time weights c[n q + i] = int_{I_n} g(t) phi_i dt, 3-point Gauss-Legendre per slab
+    const auto& L = H.lv[0];
+    const double x3 = std::sqrt(0.6);
+    const double gx[3] = {0.5 * (1.0 - x3), 0.5, 0.5 * (1.0 + x3)};
+    const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    std::vector<double> c((size_t)L.N_t * H.q, 0.0);
+    for (int n = 0; n < L.N_t; ++n)
+      for (int p = 0; p < 3; ++p) {
+        const double t = (n + gx[p]) * L.tau;
+        const double g = std::sin(M_PI * t / H.prob.T) + 1.0;
+        c[(size_t)n * H.q] += L.tau * gw[p] * g;
+        if (H.q == 2) c[(size_t)n * 2 + 1] += L.tau * gw[p] * g * (2.0 * gx[p] - 1.0);
+      }
+    double* db = H.dalloc<double>((int64_t)b.size());
+    double* dc = H.dalloc<double>((int64_t)c.size());
+    CK(cudaMemcpyAsync(db, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
+    CK(cudaMemcpyAsync(dc, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
+    CK(outer_load(db, dc, f_dev, H.space[0].ne, L.N_t * H.q, H.stream));
+    CK(cudaStreamSynchronize(H.stream));
+    // release the temporaries
+    for (void* p : {static_cast<void*>(db), static_cast<void*>(dc)}) {
+      auto it = std::find(H.allocs.begin(), H.allocs.end(), p);
+      if (it != H.allocs.end()) H.allocs.erase(it);
+      cudaFree(p);
+    }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_residual(st_mg_t h, int32_t level, const double* f_dev, const double* x_dev, double* r_dev,
+                   double* norm_out) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
+  return guarded([&]() {
+    double nsq = 0.0;
+    op_residual(*h, level, f_dev, x_dev, r_dev, norm_out ? &nsq : nullptr);
+    if (norm_out) *norm_out = std::sqrt(nsq);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_slab_solve(st_mg_t h, int32_t level, const double* r_dev, double* y_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({r_dev, y_dev})) return rc;
+  return guarded([&]() {
+    const int ld = h->lv[level].N_t * h->q;
+    op_slab_cols(*h, level, r_dev, ld, 0, h->lv[level].N_t, y_dev, ld, 0, 1.0, 0);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_smooth_S(st_mg_t h, int32_t level, const double* f_dev, double* x_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_smooth_S(*h, level, f_dev, x_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_correct_A(st_mg_t h, int32_t level, const double* f_dev, double* x_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_correct_A(*h, level, f_dev, x_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_grad_T(st_mg_t h, int32_t level, const double* r_dev, double* y_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({r_dev, y_dev})) return rc;
+  return guarded([&]() {
+    op_grad_T(*h, level, r_dev, y_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_nodal_solve(st_mg_t h, int32_t level, const double* y_dev, double* z_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({y_dev, z_dev})) return rc;
+  return guarded([&]() {
+    op_nodal_solve(*h, level, y_dev, z_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_time_integrate(st_mg_t h, int32_t level, const double* z_dev, double* w_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({z_dev, w_dev})) return rc;
+  return guarded([&]() {
+    op_time_integrate(*h, level, z_dev, w_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_grad_add(st_mg_t h, int32_t level, const double* w_dev, double* x_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({w_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_grad_add(*h, level, w_dev, x_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_restrict(st_mg_t h, int32_t level, const double* r_dev, double* rc_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (level + 1 >= (int32_t)h->lv.size()) return fail(ST_MG_ERR_INVALID_ARG, "no coarser level");
+  if (int rc = check_ptrs({r_dev, rc_dev})) return rc;
+  return guarded([&]() {
+    op_restrict(*h, level, r_dev, rc_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_prolong_add(st_mg_t h, int32_t level, const double* ec_dev, double* x_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (level + 1 >= (int32_t)h->lv.size()) return fail(ST_MG_ERR_INVALID_ARG, "no coarser level");
+  if (int rc = check_ptrs({ec_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_prolong_add(*h, level, ec_dev, x_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_coarse_solve(st_mg_t h, const double* f_dev, double* x_dev) {
+  if (int rc = check_dev(h)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_coarse_solve(*h, f_dev, x_dev);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_out) {
+  if (int rc = check_dev(h)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev})) return rc;
+  return guarded([&]() {
+    op_vcycle(*h, 0, f_dev, x_dev);
+    if (rel_res_out) {
+      const double fn = f_norm(*h, f_dev);
+      double nsq = 0.0;
+      op_residual(*h, 0, f_dev, x_dev, h->r0, &nsq);
+      *rel_res_out = std::sqrt(nsq) / (fn > 0 ? fn : 1.0);
+    }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_solve(st_mg_t h, const double* f_dev, double* x_dev, double rtol, int32_t maxit, int32_t* iters,
+                double* rel_res, double* history) {
+  if (int rc = check_dev(h)) return rc;
+  if (maxit < 0) return fail(ST_MG_ERR_INVALID_ARG, "bad solve arguments");
+  if (int rc = check_ptrs({f_dev, x_dev})) return rc;
+  return guarded([&]() { return solve_loop(*h, f_dev, x_dev, rtol, maxit, iters, rel_res, history); });
+}
+
+int st_mg_solve_host(st_mg_t h, const double* f_host, double* x_host, double rtol, int32_t maxit, int32_t* iters,
+                     double* rel_res, double* history) {
+  if (int rc = check_dev(h)) return rc;
+  if (!f_host || !x_host || maxit < 0) return fail(ST_MG_ERR_INVALID_ARG, "bad solve arguments");
+  return guarded([&]() {
+    Handle& H = *h;
+    const int64_t n = H.lv[0].len;
+    // device staging buffers are allocated on the first call and kept by the handle
+    if (!H.stage_f) {
+      H.stage_f = H.dalloc<double>(n);
+      H.stage_x = H.dalloc<double>(n);
+    }
+    CK(cudaMemcpyAsync(H.stage_f, f_host, n * sizeof(double), cudaMemcpyHostToDevice, H.stream));
+    CK(cudaMemcpyAsync(H.stage_x, x_host, n * sizeof(double), cudaMemcpyHostToDevice, H.stream));
+    const int st = solve_loop(H, H.stage_f, H.stage_x, rtol, maxit, iters, rel_res, history);
+    CK(cudaMemcpyAsync(x_host, H.stage_x, n * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+    CK(cudaStreamSynchronize(H.stream));
+    return st;
+  });
+}
+
+int st_mg_debug_get(st_mg_t h, int32_t what, int32_t level, void* host_buf, int64_t* bytes) {
+  if (!h || !bytes) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  if (level < 0 || level >= (int32_t)h->space.size()) return fail(ST_MG_ERR_INVALID_ARG, "space level out of range");
+  const auto& S = h->space[level];
+  const void* src = nullptr;
+  int64_t nb = 0;
+  std::vector<int32_t> tmp;
+  switch (what) {
+    case 1:
+      tmp.resize(2 * S.mesh.ne);
+      for (int64_t e = 0; e < S.mesh.ne; ++e) { tmp[2 * e] = S.mesh.edge_lo[e]; tmp[2 * e + 1] = S.mesh.edge_hi[e]; }
+      src = tmp.data(); nb = (int64_t)tmp.size() * 4; break;
+    case 2: src = S.mesh.int_edges.data(); nb = (int64_t)S.mesh.int_edges.size() * 4; break;
+    case 3: src = S.mesh.int_verts.data(); nb = (int64_t)S.mesh.int_verts.size() * 4; break;
+    case 4: src = S.M.rowptr.data(); nb = (int64_t)S.M.rowptr.size() * 8; break;
+    case 5: src = S.M.col.data(); nb = (int64_t)S.M.col.size() * 4; break;
+    case 6: src = S.M.val.data(); nb = (int64_t)S.M.val.size() * 8; break;
+    case 7: src = S.K.val.data(); nb = (int64_t)S.K.val.size() * 8; break;
+    case 8:
+      tmp.resize(2 * S.gtail.size());
+      for (size_t e = 0; e < S.gtail.size(); ++e) { tmp[2 * e] = S.gtail[e]; tmp[2 * e + 1] = S.ghead[e]; }
+      src = tmp.data(); nb = (int64_t)tmp.size() * 4; break;
+    case 9: src = S.Kn.rowptr.data(); nb = (int64_t)S.Kn.rowptr.size() * 8; break;
+    case 10: src = S.Kn.col.data(); nb = (int64_t)S.Kn.col.size() * 4; break;
+    case 11: src = S.Kn.val.data(); nb = (int64_t)S.Kn.val.size() * 8; break;
+    case 12: src = S.Px.rowptr.data(); nb = (int64_t)S.Px.rowptr.size() * 8; break;
+    case 13: src = S.Px.col.data(); nb = (int64_t)S.Px.col.size() * 4; break;
+    case 14: src = S.Px.val.data(); nb = (int64_t)S.Px.val.size() * 8; break;
+    default: return fail(ST_MG_ERR_INVALID_ARG, "unknown debug item");
+  }
+  if (!host_buf) {
+    *bytes = nb;
+    return ST_MG_OK;
+  }
+  if (*bytes < nb) return fail(ST_MG_ERR_INVALID_ARG, "debug buffer too small");
+  if (nb) std::memcpy(host_buf, src, (size_t)nb);
+  *bytes = nb;
+  return ST_MG_OK;
+}
+
+int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, double* y_host) {
+  if (!h || !r_host || !y_host) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  if (!h->host_only) return fail(ST_MG_ERR_INVALID_ARG, "only for handles built by st_mg_setup_host");
+  if (level < 0 || level >= (int32_t)h->lv.size()) return fail(ST_MG_ERR_INVALID_ARG, "level out of range");
+  return guarded([&]() {
+    Handle& H = *h;
+    const auto& L = H.lv[level];
+    const int ne = H.space[L.s].ne, q = H.q, ld = L.N_t * q;
+    for (int n = 0; n < L.N_t; ++n) {
+      if (q == 1) {
+        std::vector<double> b(ne);
+        for (int e = 0; e < ne; ++e) b[e] = r_host[(int64_t)e * ld + n];
+        host_factor_apply(L.fr, b);
+        for (int e = 0; e < ne; ++e) y_host[(int64_t)e * ld + n] = b[e];
+      } else {
+        const cplx c0(H.c0.x / L.tau, H.c0.y / L.tau), c1(H.c1.x / L.tau, H.c1.y / L.tau), s1(H.s1.x, H.s1.y);
+        std::vector<cplx> b(ne);
+        for (int e = 0; e < ne; ++e)
+          b[e] = r_host[(int64_t)e * ld + 2 * n] * c0 + r_host[(int64_t)e * ld + 2 * n + 1] * c1;
+        host_factor_apply(L.fc, b);
+        for (int e = 0; e < ne; ++e) {
+          y_host[(int64_t)e * ld + 2 * n] = 2.0 * b[e].re;
+          y_host[(int64_t)e * ld + 2 * n + 1] = 2.0 * (s1 * b[e]).re;
+        }
+      }
+    }
+    return ST_MG_OK;
+  });
+}
+
+const char* st_mg_strerror(int s) {
+  switch (s) {
+    case ST_MG_OK: return "ok";
+    case ST_MG_ERR_INVALID_ARG: return "invalid argument";
+    case ST_MG_ERR_OOM: return "out of memory";
+    case ST_MG_ERR_CUDA: return "CUDA error";
+    case ST_MG_ERR_DIVERGED: return "diverged";
+    case ST_MG_ERR_NOT_CONVERGED: return "not converged";
+    case ST_MG_ERR_NUMERIC: return "numerical breakdown (zero pivot)";
+    default: return "unknown status";
+  }
+}
+
+const char* st_mg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,543 @@
+// Space-time kernels of the V-cycle (Sections 2.1, 2.2, 3.3 of the paper), all on
+// the edge-major layout v[e * ncols + n*q + i] (q = DG degree + 1): the row of one
+// spatial unknown holds all slabs, so a CSR gather of a neighbour reads one
+// contiguous vector and a warp's loads coalesce.
+#include "device.h"
+
+namespace stmg {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int RES_WARPS = 8;   // rows (warps) per block of the residual kernels
+constexpr int SPL = 8;         // slabs per lane per pass (32 * SPL slabs per pass)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Block sum of per-thread values in a fixed order -> out (thread 0 writes).
+template <int NTH>
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+  __shared__ double red[NTH / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NTH / 32; ++w) s += red[w];
+    *out = s;
+  }
+}
+
+// r_n = f_n - (K_t (x) M + M_t (x) K) x_n - (N_t (x) M) x_{n-1} for DG(1), with
+// K_t = [[1,1],[-1,1]], M_t = tau diag(1, 1/3), N_t = [[-1,-1],[1,1]]:
+//   r0 = f0 - (A0 + A1 + B0) + c,  r1 = f1 - (A1 - A0 + B1) - c
+// where A_i = M x_i, B0 = tau K x0, B1 = (tau/3) K x1 on slab n and
+// c = (M (x0 + x1)) of slab n-1 = A0 + A1 of the previous slab.
+__global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, const int64_t* __restrict__ rowptr,
+                                                                 const int32_t* __restrict__ col,
+                                                                 const double* __restrict__ m,
+                                                                 const double* __restrict__ k0,
+                                                                 const double* __restrict__ k1,
+                                                                 const double* __restrict__ f,
+                                                                 const double* __restrict__ x,
+                                                                 double* __restrict__ r, int N_t,
+                                                                 double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * RES_WARPS + warp;
+  double sq = 0.0;
+  if (row < nrows) {
+    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+    const int64_t ld = 2 * (int64_t)N_t;
+    const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
+    double2* r2 = reinterpret_cast<double2*>(r + row * ld);
+    double carry = 0.0;   // A0 + A1 of the slab before this pass
+    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+      double A0[SPL], A1[SPL], B0[SPL], B1[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = 0.0;
+      for (int64_t q = beg; q < end; ++q) {
+        const int64_t c = col[q];
+        const double mv = m[q], kv0 = k0[q], kv1 = k1[q];
+        const double2* xr = reinterpret_cast<const double2*>(x + c * ld);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const int n = n0 + 32 * j + lane;
+          if (n < N_t) {
+            const double2 v = xr[n];
+            A0[j] = fma(mv, v.x, A0[j]);
+            A1[j] = fma(mv, v.y, A1[j]);
+            B0[j] = fma(kv0, v.x, B0[j]);
+            B1[j] = fma(kv1, v.y, B1[j]);
+          }
+        }
+      }
+      double prevA = carry;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        const double As = A0[j] + A1[j];
+        const double up = __shfl_up_sync(FULL, As, 1);
+        const double from31 = __shfl_sync(FULL, prevA, 31);
+        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        prevA = As;
+        const int n = n0 + 32 * j + lane;
+        if (n < N_t) {
+          const double2 fv = f2[n];
+          double2 rv;
+          rv.x = fv.x - (As + B0[j]) + c;
+          rv.y = fv.y - ((A1[j] - A0[j]) + B1[j]) - c;
+          r2[n] = rv;
+          sq = fma(rv.x, rv.x, sq);
+          sq = fma(rv.y, rv.y, sq);
+        }
+      }
+      carry = __shfl_sync(FULL, prevA, 31);
+    }
+  }
+  if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
+}
+
+// DG(0) (implicit Euler, eq. timeStepping): r_n = f_n - (M + tau K) x_n + M x_{n-1}.
+__global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, const int64_t* __restrict__ rowptr,
+                                                                 const int32_t* __restrict__ col,
+                                                                 const double* __restrict__ a,
+                                                                 const double* __restrict__ m,
+                                                                 const double* __restrict__ f,
+                                                                 const double* __restrict__ x,
+                                                                 double* __restrict__ r, int N_t,
+                                                                 double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * RES_WARPS + warp;
+  double sq = 0.0;
+  if (row < nrows) {
+    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+    const int64_t ld = N_t;
+    double carry = 0.0;
+    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+      double Ax[SPL], Mx[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = 0.0;
+      for (int64_t q = beg; q < end; ++q) {
+        const int64_t c = col[q];
+        const double av = a[q], mv = m[q];
+        const double* xr = x + c * ld;
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const int n = n0 + 32 * j + lane;
+          if (n < N_t) {
+            const double v = xr[n];
+            Ax[j] = fma(av, v, Ax[j]);
+            Mx[j] = fma(mv, v, Mx[j]);
+          }
+        }
+      }
+      double prev = carry;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        const double up = __shfl_up_sync(FULL, Mx[j], 1);
+        const double from31 = __shfl_sync(FULL, prev, 31);
+        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        prev = Mx[j];
+        const int n = n0 + 32 * j + lane;
+        if (n < N_t) {
+          const double rv = f[row * ld + n] - Ax[j] + c;
+          r[row * ld + n] = rv;
+          sq = fma(rv, rv, sq);
+        }
+      }
+      carry = __shfl_sync(FULL, prev, 31);
+    }
+  }
+  if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  block_sum_store<256>(s, out);
+}
+
+constexpr int NORM_BLOCKS = 1024;
+__global__ void k_norm_partial(const double* __restrict__ v, int64_t n, double* __restrict__ partial) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(v[i], v[i], s);
+  block_sum_store<256>(s, partial + blockIdx.x);
+}
+
+__global__ void k_slab_pre_dg0(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+                               const int32_t* __restrict__ iperm, double* __restrict__ Q, int ld) {
+  const int e = blockIdx.x;
+  const double* src = r + (int64_t)e * src_ld;
+  double* dst = Q + (int64_t)iperm[e] * ld;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = src[slab0 + k];
+}
+
+__global__ void k_slab_pre_dg1(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+                               const int32_t* __restrict__ iperm, double2 c0, double2 c1,
+                               double2* __restrict__ Q, int ld) {
+  const int e = blockIdx.x;
+  const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
+  double2* dst = Q + (int64_t)iperm[e] * ld;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const double2 v = src[slab0 + k];
+    dst[k] = make_double2(c0.x * v.x + c1.x * v.y, c0.y * v.x + c1.y * v.y);
+  }
+}
+
+__global__ void k_slab_post_dg0(const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+                                double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
+  const int e = blockIdx.x;
+  const double* src = X + (int64_t)iperm[e] * ld;
+  double* dst = x + (int64_t)e * dst_ld + slab0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const double v = src[k];
+    if (mode == 0) dst[k] = v;
+    else dst[k] = fma(omega, v, dst[k]);
+  }
+}
+
+__global__ void k_slab_post_dg1(const double2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+                                double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
+                                double omega, int mode) {
+  const int e = blockIdx.x;
+  const double2* src = X + (int64_t)iperm[e] * ld;
+  double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * dst_ld) + slab0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const double2 v = src[k];
+    const double u0 = 2.0 * v.x;
+    const double u1 = 2.0 * (s1.x * v.x - s1.y * v.y);
+    if (mode == 0) {
+      dst[k] = make_double2(u0, u1);
+    } else {
+      double2 o = dst[k];
+      o.x = fma(omega, u0, o.x);
+      o.y = fma(omega, u1, o.y);
+      dst[k] = o;
+    }
+  }
+}
+
+__global__ void k_gather_perm(const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
+                              double* __restrict__ Q, int ld) {
+  const int v = blockIdx.x;
+  const double* src = y + (int64_t)v * ncols;
+  double* dst = Q + (int64_t)iperm[v] * ld;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = src[j];
+}
+
+__global__ void k_scatter_perm(const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+                               double* __restrict__ z, int ncols) {
+  const int v = blockIdx.x;
+  const double* src = X + (int64_t)iperm[v] * ld;
+  double* dst = z + (int64_t)v * ncols;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = src[j];
+}
+
+// y = G^T r: warp per node, lanes over the time columns.
+__global__ void k_grad_T(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         const int8_t* __restrict__ sgn, const double* __restrict__ r, double* __restrict__ y,
+                         int ncols) {
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (v >= nrows) return;
+  const int64_t beg = rowptr[v], end = rowptr[v + 1];
+  for (int j = lane; j < ncols; j += 32) {
+    double s = 0.0;
+    for (int64_t q = beg; q < end; ++q) {
+      const double rv = r[(int64_t)col[q] * ncols + j];
+      s = sgn[q] > 0 ? s + rv : s - rv;
+    }
+    y[(int64_t)v * ncols + j] = s;
+  }
+}
+
+// x += G w: G has -1 at the tail and +1 at the head of each edge.
+__global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __restrict__ head,
+                           const double* __restrict__ w, double* __restrict__ x, int ncols) {
+  const int e = blockIdx.x;
+  const int t = tail[e], h = head[e];
+  double* xr = x + (int64_t)e * ncols;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+    double d = 0.0;
+    if (h >= 0) d += w[(int64_t)h * ncols + j];
+    if (t >= 0) d -= w[(int64_t)t * ncols + j];
+    xr[j] += d;
+  }
+}
+
+// w = L_t^{-1} z along the slabs of each node row (eq. AuxNodalSm).
+// DG(0): L_t = bidiag(1, -1), so w_n = sum_{j<=n} z_j (the running sum Sigma_t).
+// DG(1): K_t w_n = z_n - N_t w_{n-1} with K_t = [[1,1],[-1,1]], N_t = [[-1,-1],[1,1]]
+//   gives w_n = ((z0 - z1)/2 + e_{n-1}, (z0 + z1)/2) with the end values
+//   e_n = w_n0 + w_n1 = e_{n-1} + z0_n: a running sum of z0.
+// Warp per node: each lane sums a contiguous chunk, a warp scan gives its carry.
+__global__ void k_time_integrate(const double* __restrict__ z, double* __restrict__ w, int nrows, int N_t,
+                                 int degree) {
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (v >= nrows) return;
+  const int q = degree + 1;
+  const int C = (N_t + 31) / 32;
+  const int n0 = lane * C, n1 = min(N_t, n0 + C);
+  const double* zr = z + (int64_t)v * N_t * q;
+  double* wr = w + (int64_t)v * N_t * q;
+  double s = 0.0;
+  for (int n = n0; n < n1; ++n) s += zr[n * q];
+  double incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  double e = incl - s;   // exclusive carry
+  for (int n = n0; n < n1; ++n) {
+    if (degree == 0) {
+      e += zr[n];
+      wr[n] = e;
+    } else {
+      const double z0 = zr[2 * n], z1 = zr[2 * n + 1];
+      wr[2 * n] = 0.5 * (z0 - z1) + e;
+      wr[2 * n + 1] = 0.5 * (z0 + z1);
+      e += z0;
+    }
+  }
+}
+
+__global__ void k_nodal_jacobi(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ kv, const double* __restrict__ dinv,
+                               const double* __restrict__ y, const double* __restrict__ zi, double* __restrict__ zo,
+                               int ncols, double wgt) {
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (v >= nrows) return;
+  const int64_t beg = rowptr[v], end = rowptr[v + 1];
+  const double dv = dinv[v] * wgt;
+  for (int j = lane; j < ncols; j += 32) {
+    double s = 0.0;
+    for (int64_t q = beg; q < end; ++q) s = fma(kv[q], zi[(int64_t)col[q] * ncols + j], s);
+    const int64_t o = (int64_t)v * ncols + j;
+    zo[o] = zi[o] + dv * (y[o] - s);
+  }
+}
+
+// Time restriction r_c = P_t^T r and prolongation x += P_t e_c between 2 Nc fine and
+// Nc coarse slabs.  DG(0): a coarse slab is the two fine slabs (P_t = [1; 1]).  DG(1),
+// Legendre basis: coarse (1, 2s-1) restricted to the first fine half is
+// (1, -1/2 + phi_1/2), to the second (1, 1/2 + phi_1/2), i.e. the blocks
+// P0 = [[1, -1/2], [0, 1/2]] and P1 = [[1, 1/2], [0, 1/2]].
+__global__ void k_time_restrict(const double* __restrict__ r, double* __restrict__ rc, int Nc, int degree) {
+  const int e = blockIdx.x;
+  if (degree == 0) {
+    const double* src = r + (int64_t)e * 2 * Nc;
+    double* dst = rc + (int64_t)e * Nc;
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) dst[k] = src[2 * k] + src[2 * k + 1];
+  } else {
+    const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * 4 * Nc);
+    double2* dst = reinterpret_cast<double2*>(rc + (int64_t)e * 2 * Nc);
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+      const double2 a = src[2 * k], b = src[2 * k + 1];   // fine slab 2k and 2k+1, (i=0, i=1)
+      dst[k] = make_double2(a.x + b.x, 0.5 * (a.y - a.x + b.x + b.y));
+    }
+  }
+}
+
+__global__ void k_time_prolong_add(const double* __restrict__ ec, double* __restrict__ x, int Nc, int degree) {
+  const int e = blockIdx.x;
+  if (degree == 0) {
+    const double* src = ec + (int64_t)e * Nc;
+    double* dst = x + (int64_t)e * 2 * Nc;
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+      const double v = src[k];
+      dst[2 * k] += v;
+      dst[2 * k + 1] += v;
+    }
+  } else {
+    const double2* src = reinterpret_cast<const double2*>(ec + (int64_t)e * 2 * Nc);
+    double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * 4 * Nc);
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+      const double2 v = src[k];
+      double2 a = dst[2 * k], b = dst[2 * k + 1];
+      a.x += v.x - 0.5 * v.y;
+      a.y += 0.5 * v.y;
+      b.x += v.x + 0.5 * v.y;
+      b.y += 0.5 * v.y;
+      dst[2 * k] = a;
+      dst[2 * k + 1] = b;
+    }
+  }
+}
+
+__global__ void k_csr_spmm(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ pv, const double* __restrict__ in, double* __restrict__ out,
+                           int ncols, int beta) {
+  const int lane = threadIdx.x & 31;
+  const int rrow = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (rrow >= nrows) return;
+  const int64_t beg = rowptr[rrow], end = rowptr[rrow + 1];
+  for (int j = lane; j < ncols; j += 32) {
+    double s = 0.0;
+    for (int64_t q = beg; q < end; ++q) s = fma(pv[q], in[(int64_t)col[q] * ncols + j], s);
+    const int64_t o = (int64_t)rrow * ncols + j;
+    out[o] = beta ? out[o] + s : s;
+  }
+}
+
+__global__ void k_history_rhs(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ m, const double* __restrict__ f,
+                              const double* __restrict__ x, double* __restrict__ g, int N_t, int n, int degree) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrows) return;
+  const int q = degree + 1;
+  const int64_t ld = (int64_t)N_t * q;
+  double mx0 = 0.0, mx1 = 0.0;
+  if (n > 0) {
+    for (int64_t p = rowptr[e]; p < rowptr[e + 1]; ++p) {
+      const double* xr = x + (int64_t)col[p] * ld + (int64_t)(n - 1) * q;
+      mx0 = fma(m[p], xr[0], mx0);
+      if (degree == 1) mx1 = fma(m[p], xr[1], mx1);
+    }
+  }
+  if (degree == 0) {
+    g[e] = f[e * ld + n] + mx0;                      // -N_t M x_{n-1} with N_t = -1
+  } else {
+    const double s = mx0 + mx1;                      // N_t = [[-1,-1],[1,1]]
+    g[2 * e] = f[e * ld + 2 * n] + s;
+    g[2 * e + 1] = f[e * ld + 2 * n + 1] - s;
+  }
+}
+
+__global__ void k_fill(double* v, int64_t n, double value) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = value;
+}
+__global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+__global__ void k_outer_load(const double* __restrict__ b, const double* __restrict__ c, double* __restrict__ f,
+                             int ncols) {
+  const int e = blockIdx.x;
+  const double be = b[e];
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * ncols + j] = c[j] * be;
+}
+
+unsigned grid1(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+int residual_blocks(int nrows) { return (nrows + RES_WARPS - 1) / RES_WARPS; }
+
+cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x, double* r,
+                         int N_t, double* partial, int* nblocks, cudaStream_t st) {
+  const int nb = residual_blocks(A.nrows);
+  if (nblocks) *nblocks = nb;
+  if (nb > 0)
+    k_residual_dg0<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
+                         const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
+  const int nb = residual_blocks(A.nrows);
+  if (nblocks) *nblocks = nb;
+  if (nb > 0)
+    k_residual_dg1<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st) {
+  k_reduce_partials<<<1, 256, 0, st>>>(partial, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t norm2_sq(const double* v, int64_t n, double* partial, double* out, cudaStream_t st) {
+  k_norm_partial<<<NORM_BLOCKS, 256, 0, st>>>(v, n, partial);
+  k_reduce_partials<<<1, 256, 0, st>>>(partial, NORM_BLOCKS, out);
+  return cudaGetLastError();
+}
+
+cudaError_t slab_pre_dg0(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                         double* Q, int ld, cudaStream_t st) {
+  if (nrows > 0) k_slab_pre_dg0<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld);
+  return cudaGetLastError();
+}
+cudaError_t slab_pre_dg1(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                         double2 c0, double2 c1, double2* Q, int ld, cudaStream_t st) {
+  if (nrows > 0) k_slab_pre_dg1<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld);
+  return cudaGetLastError();
+}
+cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
+                          int slab0, int cnt, double omega, int mode, cudaStream_t st) {
+  if (nrows > 0) k_slab_post_dg0<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode);
+  return cudaGetLastError();
+}
+cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
+                          int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
+  if (nrows > 0) k_slab_post_dg1<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode);
+  return cudaGetLastError();
+}
+cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
+                        cudaStream_t st) {
+  if (nrows > 0) k_gather_perm<<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld);
+  return cudaGetLastError();
+}
+cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
+                         cudaStream_t st) {
+  if (nrows > 0) k_scatter_perm<<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols);
+  return cudaGetLastError();
+}
+cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {
+  if (GT.nrows > 0) k_grad_T<<<grid1(GT.nrows, 8), 256, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols);
+  return cudaGetLastError();
+}
+cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const double* w, double* x, int ncols,
+                     cudaStream_t st) {
+  if (nedges > 0) k_grad_add<<<nedges, 128, 0, st>>>(tail, head, w, x, ncols);
+  return cudaGetLastError();
+}
+cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st) {
+  if (nrows > 0) k_time_integrate<<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree);
+  return cudaGetLastError();
+}
+cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
+                         double* zo, int ncols, double wgt, cudaStream_t st) {
+  if (Kn.nrows > 0)
+    k_nodal_jacobi<<<grid1(Kn.nrows, 8), 256, 0, st>>>(Kn.nrows, Kn.rowptr, Kn.col, kval, dinv, y, zi, zo, ncols,
+                                                       wgt);
+  return cudaGetLastError();
+}
+cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st) {
+  if (nrows > 0) k_time_restrict<<<nrows, 128, 0, st>>>(r, rc, Nc, degree);
+  return cudaGetLastError();
+}
+cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st) {
+  if (nrows > 0) k_time_prolong_add<<<nrows, 128, 0, st>>>(ec, x, Nc, degree);
+  return cudaGetLastError();
+}
+cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,
+                     cudaStream_t st) {
+  if (P.nrows > 0) k_csr_spmm<<<grid1(P.nrows, 8), 256, 0, st>>>(P.nrows, P.rowptr, P.col, pval, in, out, ncols, beta);
+  return cudaGetLastError();
+}
+cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t, int n,
+                        int degree, cudaStream_t st) {
+  if (A.nrows > 0) k_history_rhs<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, f, x, g, N_t, n, degree);
+  return cudaGetLastError();
+}
+cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st) {
+  if (n > 0) k_fill<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(v, n, value);
+  return cudaGetLastError();
+}
+cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st) {
+  if (n > 0) k_copy<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, cudaStream_t st) {
+  if (nrows > 0) k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols);
+  return cudaGetLastError();
+}
+
+}  // namespace stmg

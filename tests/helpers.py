@@ -1,0 +1,38 @@
+"""Shared test helpers: layout conversion and oracle set-ups (test infrastructure)."""
+import numpy as np
+
+import st_inputs
+from oracle.multigrid import SpaceTimeMG, build_time_hierarchy
+from oracle.spacetime import build_space_hierarchy
+
+MODES = {0: "rule", 1: "semi_time", 2: "full_top"}
+
+
+def to_lib(v):
+    """Oracle (N_t, q, N_e) -> library layout (N_e, N_t*q)."""
+    nt, q, ne = v.shape
+    return np.ascontiguousarray(v.transpose(2, 0, 1).reshape(ne, nt * q))
+
+
+def from_lib(v, q):
+    """Library layout (N_e, N_t*q) -> oracle (N_t, q, N_e)."""
+    ne, c = v.shape
+    return np.ascontiguousarray(v.reshape(ne, c // q, q).transpose(1, 2, 0))
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def oracle_mg(n, nsl, nu, sigma, T, N_t, p, coarsen=0, max_levels=0, nu_pre=1, nu_post=1, lambda_crit=0.1,
+              nodal="exact", jacobi_sweeps=0, use_A=True, omega=0.5):
+    sl = build_space_hierarchy(n, nsl, nu, sigma)
+    tl = build_time_hierarchy(N_t, T, n, nsl, nu, sigma, mode=MODES[coarsen], lambda_crit=lambda_crit,
+                              max_levels=max_levels if max_levels > 0 else 64)
+    mg = SpaceTimeMG(sl, tl, p, omega, nu_pre, nu_post, nodal=nodal, jacobi_sweeps=jacobi_sweeps, use_A=use_A)
+    return sl, tl, mg
+
+
+def materials(n, kind, seed=0):
+    return st_inputs.materials(n, kind, seed)
