@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the space-time multigrid V-cycle (arXiv 1911.09548) on one GB300.
+
+Workload (one "step" = one V-cycle, i.e. every step of the hot path: residuals,
+block-Jacobi slab solves, nodal auxiliary-space corrections, time transfers,
+coarsest solve, residual norm): Kuhn mesh of 16^3 cubes (26416 interior edges),
+nu = 1e-3 in [0.25, 0.75]^3 and 1 outside, sigma log-uniform in [0.1, 10] per tet
+(seed 0), T = 1, N_t = 256 slabs, DG(1) in time, V(2,2) with the hybrid smoother
+SSASS, omega = 0.5, time coarsening on every level (the coarsening rule never
+admits space coarsening here), 9 time levels.  Inputs are synthetic (st_inputs).
+
+Metric: space-time DoFs smoothed per second = fine-level DoFs x fine-level S
+applications per V-cycle (2 nu_pre + 2 nu_post = 8) x V-cycles / time; also the
+time to a 1e-8 relative residual from x = 0 (p50/p99 over seeds).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun as N independent replicas (one excitation each).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="kuhn16_dg1_Nt256_V22", n=16, N_t=256, degree=1, T=1.0, nu_pre=2, nu_post=2,
+                materials="two_material", seed=0)
+METRIC = "space-time DoFs smoothed/s"
+UNIT = "DoF/s"
+# FP64 FMA throughput of this machine's GB300 measured with a dependent-free FMA loop
+# over 152 x 8 blocks (1.20 TFLOP/s; NVIDIA's nominal FP64 figure is 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.20
+CPU_SAMPLE_SLABS = 16
+
+
+def smoothed_per_cycle(dofs, nu_pre, nu_post):
+    return dofs * (2 * nu_pre + 2 * nu_post)
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(nslabs: int, reps: int, seed: int = 0):
+    """Time `reps` block-Jacobi sweeps S of the oracle on `nslabs` slabs of the
+    workload's finest level (16^3, DG(1), tau = 1/256); factorisation excluded."""
+    import numpy as np
+
+    import st_inputs
+    from oracle.load import spacetime_load
+    from oracle.spacetime import SlabOperator, build_space_hierarchy, smoother_S
+
+    W = WORKLOAD
+    nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
+    sl = build_space_hierarchy(W["n"], 1, nu, sigma)
+    t0 = time.time()
+    slab = SlabOperator(sl[0], W["degree"], W["T"] / W["N_t"])
+    t_setup = time.time() - t0
+    f = spacetime_load(sl[0].mesh, st_inputs.excitation(seed), W["degree"], W["N_t"], W["T"])[:nslabs]
+    x = np.zeros_like(f)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        x = smoother_S(slab, f, x, 0.5)
+        times.append(time.perf_counter() - t0)
+    dofs = f.size
+    return {"times": times, "dofs_per_step": dofs, "setup_s": t_setup}
+
+
+def _oracle_worker(q, nslabs, reps):
+    try:
+        q.put(oracle_sample(nslabs, reps))
+    except Exception as e:  # reported, never silently dropped
+        q.put({"error": repr(e)})
+
+
+def cpu_baseline_desc(res, nslabs):
+    total = sum(res["times"])
+    return {"value": res["dofs_per_step"] * len(res["times"]) / total, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": (f"{len(res['times'])} oracle block-Jacobi sweeps S on {nslabs} of the 256 slabs of the "
+                       f"16^3 DG(1) finest level ({res['dofs_per_step']} DoFs each; SciPy SuperLU slab solve and "
+                       f"sparse products, single-threaded; factorisation {res['setup_s']:.0f} s excluded)")}
+
+
+def run_reference(args):
+    """Reference arm: the oracle, as it stands, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    res = oracle_sample(CPU_SAMPLE_SLABS, args.warmup + args.steps)
+    timed = res["times"][args.warmup:]
+    res_t = dict(res, times=timed)
+    value = res["dofs_per_step"] * len(timed) / sum(timed)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "sample": f"{CPU_SAMPLE_SLABS} slabs per step"},
+            "impl": "reference", "cpu_baseline": cpu_baseline_desc(res_t, CPU_SAMPLE_SLABS),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--solves", type=int, default=3, help="time-to-1e-8 solves (seeds) for p50/p99")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    # CPU baseline in a spawned process (rank 0, N = 1), overlapping the GPU work
+    cpu_q = cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ctx = mp.get_context("spawn")
+        cpu_q = ctx.Queue()
+        cpu_proc = ctx.Process(target=_oracle_worker, args=(cpu_q, CPU_SAMPLE_SLABS, 8), daemon=True)
+        cpu_proc.start()
+
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    import st_inputs
+
+    W = WORKLOAD
+    nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                             nu_post=W["nu_post"], stream=stream.cuda_stream)
+    setup_s = time.time() - t0
+    f = S.load(st_inputs.excitation(W["seed"] + rank))
+    x = S.zeros()
+    per_cycle = smoothed_per_cycle(S.n_dof, W["nu_pre"], W["nu_post"])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        S.vcycle(f, x)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    launches0 = stmg.st_mg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        S.vcycle(f, x)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = stmg.st_mg_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * per_cycle * args.steps / (ms_max / 1e3)
+
+    # dominant kernel: the supernodal slab solve of the finest level (forward and
+    # backward product kernels of every nested-dissection depth), timed alone
+    st = stmg.st_mg_factor_stats(S.h, 0)
+    r = S.residual(f, x)
+    y = S.zeros()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stmg.st_mg_slab_solve(S.h, 0, r, y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        stmg.st_mg_slab_solve(S.h, 0, r, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    slab_ms = e0.elapsed_time(e1) / reps
+    flops_per_mac = 8.0 if W["degree"] == 1 else 2.0
+    slab_flops = st["macs_per_rhs"] * flops_per_mac * W["N_t"]
+    achieved = slab_flops / (slab_ms / 1e3) / 1e12
+
+    # time to 1e-8 from x = 0, several excitations
+    solve_ms, solve_iters = [], []
+    for s in range(args.solves):
+        fs = S.load(st_inputs.excitation(100 + s + 1000 * rank))
+        xs = S.zeros()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = S.solve(fs, xs, rtol=1e-8, maxit=60)
+        torch.cuda.synchronize()
+        solve_ms.append(1e3 * (time.perf_counter() - a))
+        solve_iters.append(out["iters"])
+        del fs, xs
+
+    # end to end through the public host-buffer API: H2D of f and x, one V-cycle,
+    # residual norms, D2H of x, every step
+    fh = torch.empty(S.level_shape(), dtype=torch.float64).pin_memory()
+    xh = torch.zeros(S.level_shape(), dtype=torch.float64).pin_memory()
+    fh.copy_(f.cpu())
+    fnp, xnp = fh.numpy(), xh.numpy()
+    S.solve_host(fnp, xnp, rtol=0.0, maxit=1)   # first call allocates the staging buffers
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        a = time.perf_counter()
+        S.solve_host(fnp, xnp, rtol=0.0, maxit=1)
+        e2e_times.append(time.perf_counter() - a)
+    e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times)
+
+    cpu_base = None
+    if cpu_proc is not None:
+        res = cpu_q.get(timeout=1800)
+        cpu_proc.join(timeout=60)
+        cpu_base = cpu_baseline_desc(res, CPU_SAMPLE_SLABS) if "error" not in res else {"error": res["error"]}
+
+    if rank == 0:
+        solve_sorted = sorted(solve_ms)
+        p99 = solve_sorted[min(len(solve_sorted) - 1, int(round(0.99 * (len(solve_sorted) - 1))))]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
+                       "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": S.n_levels,
+                       "dofs": S.n_dof, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
+            "time_to_1e-8_s": {"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
+                                "v_cycles": solve_iters},
+            "setup_s": setup_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "supernodal slab solve, finest level (k_sn_forward + k_sn_backward)",
+                         "peak_source": "measured FP64 FMA throughput of this pool's GB300",
+                         "ms_per_launch_group": slab_ms},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * S.n_dof * 8,
+                    "d2h_bytes_per_step": S.n_dof * 8 + 16},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if cpu_base is not None:
+            line["cpu_baseline"] = cpu_base
+        print(json.dumps(line))
+    S.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -188,6 +188,15 @@ int st_mg_debug_get(st_mg_t h, int32_t what, int32_t level, void* host_buf, int6
  * the device path uses.  r_host, y_host: host arrays in the level's layout. */
 int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, double* y_host);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all handles). */
+int st_mg_launch_count(int64_t* count);
+
+/* Slab factor of time level `level`: multiply-adds of one forward+backward solve per
+ * right-hand side (complex multiply-adds for DG(1), real for DG(0); the triangular
+ * blocks L11^{-1} counted once), device bytes of its dense blocks, and the depth of
+ * its nested-dissection tree (the solve launches 2 (depth+1) product kernels). */
+int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* factor_bytes, int32_t* depth);
+
 const char* st_mg_strerror(int status);
 const char* st_mg_last_error(void);
 

@@ -60,6 +60,8 @@ _SIGS = {
     "st_mg_solve_host": [_vp, _P(_dbl), _P(_dbl), _dbl, _i32, _P(_i32), _P(_dbl), _P(_dbl)],
     "st_mg_debug_get": [_vp, _i32, _i32, _vp, _P(_i64)],
     "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
+    "st_mg_launch_count": [_P(_i64)],
+    "st_mg_factor_stats": [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)],
     "st_mg_strerror": [ctypes.c_int],
     "st_mg_last_error": [],
 }
@@ -246,6 +248,19 @@ def st_mg_debug_host_slab_solve(h, level, r_host: np.ndarray) -> np.ndarray:
     y = np.zeros_like(r_host)
     _check(lib().st_mg_debug_host_slab_solve(_vp(h), level, _dptr(r_host), _dptr(y)), "st_mg_debug_host_slab_solve")
     return y
+
+
+def st_mg_launch_count() -> int:
+    c = _i64()
+    _check(lib().st_mg_launch_count(ctypes.byref(c)), "st_mg_launch_count")
+    return c.value
+
+
+def st_mg_factor_stats(h, level):
+    m, b, d = _dbl(), _i64(), _i32()
+    _check(lib().st_mg_factor_stats(_vp(h), level, ctypes.byref(m), ctypes.byref(b), ctypes.byref(d)),
+           "st_mg_factor_stats")
+    return {"macs_per_rhs": m.value, "factor_bytes": b.value, "depth": d.value}
 
 
 def st_mg_strerror(status: int) -> str:

@@ -34,6 +34,10 @@ struct DevFactor {
   double macs_per_rhs = 0;        // complex/real multiply-adds of one solve per right-hand side
 };
 
+// Number of kernels launched by this library since load (all launchers add to it).
+int64_t launch_count();
+void count_launches(int64_t n);
+
 // Row tile height of the supernodal products (tiles are built on the host with it).
 constexpr int kSnBM = 64;
 

@@ -247,7 +247,8 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
     roff += nd.nr;
     uoff += nd.nr;
     goff += nd.nc + nd.nr;
-    F.flops_apply_per_rhs += 2.0 * (double)(nd.nc + nd.nr) * nd.nc;
+    // forward + backward multiply-adds of one right-hand side (triangular L11^{-1} counted once)
+    F.flops_apply_per_rhs += 2.0 * ((double)nd.nc * (nd.nc + 1) / 2.0 + (double)nd.nr * nd.nc);
   }
   F.u_rows = uoff;
   F.W.assign(woff, T(0.0));

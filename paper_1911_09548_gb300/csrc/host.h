@@ -111,7 +111,7 @@ struct SupernodalFactor {
   std::vector<int32_t> gsrc;            // [sum (nc+nr)] * 2
   int32_t max_depth = 0;
   int64_t u_rows = 0;                   // total update-buffer rows
-  double flops_apply_per_rhs = 0;       // multiply-adds of one forward+backward per rhs
+  double flops_apply_per_rhs = 0;       // multiply-adds (real or complex) of one forward+backward per rhs
 };
 
 struct NDCoords {                        // integer "min corner" of each unknown

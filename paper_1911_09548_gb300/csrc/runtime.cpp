@@ -106,6 +106,7 @@ struct st_mg_s {
     std::vector<int64_t> fwd_off, bwd_off;
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
+    int64_t w_bytes = 0;                                   // device bytes of the slab factor blocks
   };
   std::vector<Level> lv;
 
@@ -544,6 +545,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
       make_dev_factor(H, L.fr, L.dr, L.fwd_off, L.bwd_off);
+      L.w_bytes = (int64_t)L.fr.W.size() * 8;
       max_u = std::max<int64_t>(max_u, L.fr.u_rows);
       L.fr = SupernodalFactor<double>();
     } else {
@@ -556,6 +558,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       L.v1 = H.upload(b);
       L.v2 = H.upload(c);
       make_dev_factor(H, L.fc, L.dc, L.fwd_off, L.bwd_off);
+      L.w_bytes = (int64_t)L.fc.W.size() * 16;
       max_u = std::max<int64_t>(max_u, L.fc.u_rows);
       L.fc = SupernodalFactor<cplx>();
     }
@@ -1013,6 +1016,22 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
     }
     return ST_MG_OK;
   });
+}
+
+int st_mg_launch_count(int64_t* count) {
+  if (!count) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  *count = launch_count();
+  return ST_MG_OK;
+}
+
+int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* factor_bytes, int32_t* depth) {
+  if (int rc = check_level(h, level)) return rc;
+  const auto& L = h->lv[level];
+  const bool c = h->prob.degree == 1;
+  if (macs_per_rhs) *macs_per_rhs = c ? L.dc.macs_per_rhs : L.dr.macs_per_rhs;
+  if (factor_bytes) *factor_bytes = L.w_bytes;
+  if (depth) *depth = c ? L.dc.max_depth : L.dr.max_depth;
+  return ST_MG_OK;
 }
 
 const char* st_mg_strerror(int s) {

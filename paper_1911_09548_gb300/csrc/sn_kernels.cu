@@ -194,14 +194,14 @@ cudaError_t sn_solve_impl(const DevFactor<T>& F, T* Q, T* Z, T* U, int nrhs, int
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
     if (b > a)
-      k_sn_forward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc,
-                                                                       F.fwd_tiles + a, Q, Z, U, nrhs, ld);
+      { k_sn_forward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc,
+                                                                       F.fwd_tiles + a, Q, Z, U, nrhs, ld); count_launches(1); }
   }
   for (int d = 0; d <= F.max_depth; ++d) {
     const int64_t a = F.h_bwd_off[d], b = F.h_bwd_off[d + 1];
     if (b > a)
-      k_sn_backward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z,
-                                                                        Q, nrhs, ld);
+      { k_sn_backward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z,
+                                                                        Q, nrhs, ld); count_launches(1); }
   }
   return cudaGetLastError();
 }

@@ -2,6 +2,8 @@
 // the edge-major layout v[e * ncols + n*q + i] (q = DG degree + 1): the row of one
 // spatial unknown holds all slabs, so a CSR gather of a neighbour reads one
 // contiguous vector and a warp's loads coalesce.
+#include <atomic>
+
 #include "device.h"
 
 namespace stmg {
@@ -426,7 +428,12 @@ __global__ void k_outer_load(const double* __restrict__ b, const double* __restr
 
 unsigned grid1(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+std::atomic<int64_t> g_launches{0};
+
 }  // namespace
+
+int64_t launch_count() { return g_launches.load(); }
+void count_launches(int64_t n) { g_launches += n; }
 
 int residual_blocks(int nrows) { return (nrows + RES_WARPS - 1) / RES_WARPS; }
 
@@ -435,7 +442,7 @@ cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const doub
   const int nb = residual_blocks(A.nrows);
   if (nblocks) *nblocks = nb;
   if (nb > 0)
-    k_residual_dg0<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial);
+    { k_residual_dg0<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial); count_launches(1); }
   return cudaGetLastError();
 }
 
@@ -444,99 +451,99 @@ cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const dou
   const int nb = residual_blocks(A.nrows);
   if (nblocks) *nblocks = nb;
   if (nb > 0)
-    k_residual_dg1<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial);
+    { k_residual_dg1<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st) {
-  k_reduce_partials<<<1, 256, 0, st>>>(partial, n, out);
+  { k_reduce_partials<<<1, 256, 0, st>>>(partial, n, out); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t norm2_sq(const double* v, int64_t n, double* partial, double* out, cudaStream_t st) {
-  k_norm_partial<<<NORM_BLOCKS, 256, 0, st>>>(v, n, partial);
-  k_reduce_partials<<<1, 256, 0, st>>>(partial, NORM_BLOCKS, out);
+  { k_norm_partial<<<NORM_BLOCKS, 256, 0, st>>>(v, n, partial); count_launches(1); }
+  { k_reduce_partials<<<1, 256, 0, st>>>(partial, NORM_BLOCKS, out); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t slab_pre_dg0(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) k_slab_pre_dg0<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld);
+  if (nrows > 0) { k_slab_pre_dg0<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg1(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double2 c0, double2 c1, double2* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) k_slab_pre_dg1<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld);
+  if (nrows > 0) { k_slab_pre_dg1<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
                           int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) k_slab_post_dg0<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode);
+  if (nrows > 0) { k_slab_post_dg0<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) k_slab_post_dg1<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode);
+  if (nrows > 0) { k_slab_post_dg1<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
                         cudaStream_t st) {
-  if (nrows > 0) k_gather_perm<<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld);
+  if (nrows > 0) { k_gather_perm<<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                          cudaStream_t st) {
-  if (nrows > 0) k_scatter_perm<<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols);
+  if (nrows > 0) { k_scatter_perm<<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {
-  if (GT.nrows > 0) k_grad_T<<<grid1(GT.nrows, 8), 256, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols);
+  if (GT.nrows > 0) { k_grad_T<<<grid1(GT.nrows, 8), 256, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const double* w, double* x, int ncols,
                      cudaStream_t st) {
-  if (nedges > 0) k_grad_add<<<nedges, 128, 0, st>>>(tail, head, w, x, ncols);
+  if (nedges > 0) { k_grad_add<<<nedges, 128, 0, st>>>(tail, head, w, x, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st) {
-  if (nrows > 0) k_time_integrate<<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree);
+  if (nrows > 0) { k_time_integrate<<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
                          double* zo, int ncols, double wgt, cudaStream_t st) {
   if (Kn.nrows > 0)
-    k_nodal_jacobi<<<grid1(Kn.nrows, 8), 256, 0, st>>>(Kn.nrows, Kn.rowptr, Kn.col, kval, dinv, y, zi, zo, ncols,
-                                                       wgt);
+    { k_nodal_jacobi<<<grid1(Kn.nrows, 8), 256, 0, st>>>(Kn.nrows, Kn.rowptr, Kn.col, kval, dinv, y, zi, zo, ncols,
+                                                       wgt); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) k_time_restrict<<<nrows, 128, 0, st>>>(r, rc, Nc, degree);
+  if (nrows > 0) { k_time_restrict<<<nrows, 128, 0, st>>>(r, rc, Nc, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) k_time_prolong_add<<<nrows, 128, 0, st>>>(ec, x, Nc, degree);
+  if (nrows > 0) { k_time_prolong_add<<<nrows, 128, 0, st>>>(ec, x, Nc, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,
                      cudaStream_t st) {
-  if (P.nrows > 0) k_csr_spmm<<<grid1(P.nrows, 8), 256, 0, st>>>(P.nrows, P.rowptr, P.col, pval, in, out, ncols, beta);
+  if (P.nrows > 0) { k_csr_spmm<<<grid1(P.nrows, 8), 256, 0, st>>>(P.nrows, P.rowptr, P.col, pval, in, out, ncols, beta); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t, int n,
                         int degree, cudaStream_t st) {
-  if (A.nrows > 0) k_history_rhs<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, f, x, g, N_t, n, degree);
+  if (A.nrows > 0) { k_history_rhs<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, f, x, g, N_t, n, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st) {
-  if (n > 0) k_fill<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(v, n, value);
+  if (n > 0) { k_fill<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(v, n, value); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st) {
-  if (n > 0) k_copy<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(a, b, n);
+  if (n > 0) { k_copy<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(a, b, n); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, cudaStream_t st) {
-  if (nrows > 0) k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols);
+  if (nrows > 0) { k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 
