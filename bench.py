@@ -156,6 +156,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--solves", type=int, default=3, help="time-to-1e-8 solves (seeds) for p50/p99")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "slab"],
+                    help="slab: set up the workload, run two finest-level slab solves and exit (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -176,7 +179,7 @@ def main():
 
     # CPU baseline in a spawned process (rank 0, N = 1), overlapping the GPU work
     cpu_q = cpu_proc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.mode == "bench":
         ctx = mp.get_context("spawn")
         cpu_q = ctx.Queue()
         cpu_proc = ctx.Process(target=_oracle_worker, args=(cpu_q, CPU_SAMPLE_SLABS, 8), daemon=True)
@@ -197,6 +200,14 @@ def main():
     f = S.load(st_inputs.excitation(W["seed"] + rank))
     x = S.zeros()
     per_cycle = smoothed_per_cycle(S.n_dof, W["nu_pre"], W["nu_post"])
+    if args.mode == "slab":
+        r = S.residual(f, x)
+        y = S.zeros()
+        for _ in range(2):
+            stmg.st_mg_slab_solve(S.h, 0, r, y)
+        torch.cuda.synchronize()
+        S.close()
+        return 0
 
     def barrier():
         if dist is not None:
@@ -266,13 +277,14 @@ def main():
     xh = torch.zeros(S.level_shape(), dtype=torch.float64).pin_memory()
     fh.copy_(f.cpu())
     fnp, xnp = fh.numpy(), xh.numpy()
-    S.solve_host(fnp, xnp, rtol=0.0, maxit=1)   # first call allocates the staging buffers
+    if not args.no_e2e:
+        S.solve_host(fnp, xnp, rtol=0.0, maxit=1)   # first call allocates the staging buffers
     e2e_times = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(0 if args.no_e2e else max(1, args.steps)):
         a = time.perf_counter()
         S.solve_host(fnp, xnp, rtol=0.0, maxit=1)
         e2e_times.append(time.perf_counter() - a)
-    e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times)
+    e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
     cpu_base = None
     if cpu_proc is not None:
@@ -282,7 +294,7 @@ def main():
 
     if rank == 0:
         solve_sorted = sorted(solve_ms)
-        p99 = solve_sorted[min(len(solve_sorted) - 1, int(round(0.99 * (len(solve_sorted) - 1))))]
+        p99 = solve_sorted[min(len(solve_sorted) - 1, int(round(0.99 * (len(solve_sorted) - 1))))] if solve_ms else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -291,8 +303,8 @@ def main():
                        "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": S.n_levels,
                        "dofs": S.n_dof, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
-            "time_to_1e-8_s": {"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
-                                "v_cycles": solve_iters},
+            "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
+                                 "v_cycles": solve_iters} if solve_ms else None),
             "setup_s": setup_s,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
