@@ -197,6 +197,27 @@ int st_mg_launch_count(int64_t* count);
  * its nested-dissection tree (the solve launches 2 (depth+1) product kernels). */
 int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* factor_bytes, int32_t* depth);
 
+/* Allocation-free l2 norm: norm_dev[0] = ||v||_2 for the n doubles at v_dev, queued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).  The paper has no
+ * counterpart; this is a library service.  It is the library's deterministic
+ * two-stage norm (the solver's stopping test) for callers that cannot allocate
+ * device memory at the point where they need the norm -- a control loop that must
+ * not stall on cudaMalloc/cudaFree (both may synchronise the whole device), or a
+ * host framework that owns the device allocator and forbids allocations by
+ * libraries.  It needs no handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ * Scratch: one partial sum per 4096 elements lives in a file-scope device array of
+ * 32768 doubles (256 KiB) that every GPU which loads the library holds until the
+ * process exits; hence n <= 134217728 (larger n returns ST_MG_ERR_INVALID_ARG).
+ * The first call on a device, with that device current, looks the array up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  Every call
+ * shares the array and it keeps the last call's partial sums (each call overwrites
+ * the entries it reads), so calls that overlap on the GPU (other streams, other
+ * threads, before an earlier call finished) race and must be serialised by the
+ * caller.  v_dev and norm_dev: device pointers, 8-byte aligned; the result is
+ * written on the stream (read it after synchronising). */
+int st_mg_norm2_noalloc(const double* v_dev, int64_t n, void* stream, double* norm_dev);
+
 const char* st_mg_strerror(int status);
 const char* st_mg_last_error(void);
 

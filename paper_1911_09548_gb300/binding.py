@@ -62,6 +62,7 @@ _SIGS = {
     "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
     "st_mg_launch_count": [_P(_i64)],
     "st_mg_factor_stats": [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)],
+    "st_mg_norm2_noalloc": [_vp, _i64, _vp, _vp],
     "st_mg_strerror": [ctypes.c_int],
     "st_mg_last_error": [],
 }
@@ -261,6 +262,11 @@ def st_mg_factor_stats(h, level):
     _check(lib().st_mg_factor_stats(_vp(h), level, ctypes.byref(m), ctypes.byref(b), ctypes.byref(d)),
            "st_mg_factor_stats")
     return {"macs_per_rhs": m.value, "factor_bytes": b.value, "depth": d.value}
+
+
+def st_mg_norm2_noalloc(v_dev, n, stream, norm_dev):
+    _check(lib().st_mg_norm2_noalloc(_vp(_addr(v_dev)), n, _vp(stream), _vp(_addr(norm_dev))),
+           "st_mg_norm2_noalloc")
 
 
 def st_mg_strerror(status: int) -> str:

@@ -47,6 +47,10 @@ struct CudaError {
 
 }  // namespace
 
+namespace stmg {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace stmg
+
 struct st_mg_s {
   st_mg_problem prob{};
   st_mg_options opt{};
