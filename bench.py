@@ -34,14 +34,25 @@ WORKLOAD = dict(name="kuhn16_dg1_Nt256_V22", n=16, N_t=256, degree=1, T=1.0, nu_
                 materials="two_material", seed=0)
 METRIC = "space-time DoFs smoothed/s"
 UNIT = "DoF/s"
-# FP64 FMA throughput of this machine's GB300 measured with a dependent-free FMA loop
-# over 152 x 8 blocks (1.20 TFLOP/s; NVIDIA's nominal FP64 figure is 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 1.20
 CPU_SAMPLE_SLABS = 16
 
 
 def smoothed_per_cycle(dofs, nu_pre, nu_post):
     return dofs * (2 * nu_pre + 2 * nu_post)
+
+
+def reduce_max(value: float, dist=None, device="cpu") -> float:
+    """Max over ranks (the slowest replica sets the job's time)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, per_cycle: float, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: every replica smooths per_cycle DoFs per step."""
+    return world * per_cycle * steps / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -233,11 +244,8 @@ def main():
     clk = clocks.stop()
     launches = stmg.st_mg_launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * per_cycle * args.steps / (ms_max / 1e3)
+    ms_max = reduce_max(ms, dist, "cuda")
+    value = replica_value(world, per_cycle, args.steps, ms_max)
 
     # dominant kernel: the supernodal slab solve of the finest level (forward and
     # backward product kernels of every nested-dissection depth), timed alone
@@ -257,6 +265,7 @@ def main():
     flops_per_mac = 8.0 if W["degree"] == 1 else 2.0
     slab_flops = st["macs_per_rhs"] * flops_per_mac * W["N_t"]
     achieved = slab_flops / (slab_ms / 1e3) / 1e12
+    fp64_peak = stmg.st_mg_probe_fp64(S.h)       # roof of the FP64 kernels, measured in this run
 
     # time to 1e-8 from x = 0, several excitations
     solve_ms, solve_iters = [], []
@@ -306,10 +315,10 @@ def main():
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),
             "setup_s": setup_s,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "supernodal slab solve, finest level (k_sn_forward + k_sn_backward)",
-                         "peak_source": "measured FP64 FMA throughput of this pool's GB300",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": None,
+                         "kernel": "supernodal slab solve, finest level (k_sn_forward/backward, split-K near the root)",
+                         "peak_source": "FP64 FMA throughput measured in this run (st_mg_probe_fp64)",
                          "ms_per_launch_group": slab_ms},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * S.n_dof * 8,
                     "d2h_bytes_per_step": S.n_dof * 8 + 16},

@@ -188,6 +188,11 @@ int st_mg_debug_get(st_mg_t h, int32_t what, int32_t level, void* host_buf, int6
  * the device path uses.  r_host, y_host: host arrays in the level's layout. */
 int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, double* y_host);
 
+/* Measured FP64 FMA throughput of the handle's device in TFLOP/s (about 70 ms of
+ * independent FMA chains on 8 blocks per SM; blocking).  The FP64 kernels of this
+ * library are bound by this pipe, so it is the roof their efficiency is quoted against. */
+int st_mg_probe_fp64(st_mg_t h, double* tflops);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);
 

@@ -60,6 +60,7 @@ _SIGS = {
     "st_mg_solve_host": [_vp, _P(_dbl), _P(_dbl), _dbl, _i32, _P(_i32), _P(_dbl), _P(_dbl)],
     "st_mg_debug_get": [_vp, _i32, _i32, _vp, _P(_i64)],
     "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
+    "st_mg_probe_fp64": [_vp, _P(_dbl)],
     "st_mg_launch_count": [_P(_i64)],
     "st_mg_factor_stats": [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)],
     "st_mg_norm2_noalloc": [_vp, _i64, _vp, _vp],
@@ -249,6 +250,12 @@ def st_mg_debug_host_slab_solve(h, level, r_host: np.ndarray) -> np.ndarray:
     y = np.zeros_like(r_host)
     _check(lib().st_mg_debug_host_slab_solve(_vp(h), level, _dptr(r_host), _dptr(y)), "st_mg_debug_host_slab_solve")
     return y
+
+
+def st_mg_probe_fp64(h) -> float:
+    t = _dbl()
+    _check(lib().st_mg_probe_fp64(_vp(h), ctypes.byref(t)), "st_mg_probe_fp64")
+    return t.value
 
 
 def st_mg_launch_count() -> int:

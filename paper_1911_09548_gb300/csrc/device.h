@@ -32,7 +32,26 @@ struct DevFactor {
   int64_t* h_bwd_off = nullptr;
   int64_t u_rows = 0;
   double macs_per_rhs = 0;        // complex/real multiply-adds of one solve per right-hand side
+  // split-K path for few right-hand sides: per depth, work items (node, row0, k0, k1)
+  // of kSkRows rows and units (node, row0, item_begin, item_end) that reduce them
+  int4* fs_items = nullptr;
+  int4* fs_units = nullptr;
+  int4* bs_items = nullptr;
+  int4* bs_units = nullptr;
+  int64_t* h_fs_item_off = nullptr;   // host, size max_depth + 2
+  int64_t* h_fs_unit_off = nullptr;
+  int64_t* h_bs_item_off = nullptr;
+  int64_t* h_bs_unit_off = nullptr;
+  int64_t max_items = 0;              // largest item count of one depth (partial buffer rows / kSkRows)
+  int32_t n_sm = 152;                 // multiprocessors of the device (wave size of the tiled path)
 };
+
+// Split-K path: rows per item, columns per item, and the largest right-hand-side
+// count it serves (complex: kSkMaxRhsC, real: kSkMaxRhsR).
+constexpr int kSkRows = 32;
+constexpr int kSkK = 128;
+constexpr int kSkMaxRhsC = 16;
+constexpr int kSkMaxRhsR = 32;
 
 // Number of kernels launched by this library since load (all launchers add to it).
 int64_t launch_count();
@@ -43,10 +62,12 @@ constexpr int kSnBM = 64;
 
 // ---- supernodal solve: X = A^{-1} Q on `nrhs` columns, leading dimension ld.
 // Q (in) is overwritten by X (out); Z and U are workspaces ([n*ld], [u_rows*ld]).
-cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, int nrhs, int ld,
+// P is the split-K partial buffer: max_items * kSkRows * (max right-hand sides per
+// solve, rounded up to the column block) elements.  Null disables the split-K path.
+cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,
                           cudaStream_t st);
-cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, int nrhs, int ld,
-                          cudaStream_t st);
+cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
+                          int ld, cudaStream_t st);
 
 // ---- space-time kernels.  Edge-major layout v[e*ncols + n*q + i], ncols = N_t*q.
 struct CsrView {
@@ -107,6 +128,8 @@ cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* ou
 // Coarse forward substitution: g[e][i] = f[e][n q + i] - sum_j N_t[i][j] (M x_{n-1})_j.
 cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t,
                         int n, int degree, cudaStream_t st);
+// FP64 FMA throughput probe: blocks x 256 threads x iters x 8 FMAs (out: >= blocks doubles).
+cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st);
 // Elementwise helpers.
 cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st);
 cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st);

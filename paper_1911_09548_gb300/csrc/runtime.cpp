@@ -39,6 +39,11 @@ struct CudaError {
 };
 
 
+// Host-side tile and item lists of one factor (kept alive: the device view points at them).
+struct FactorLists {
+  std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu;
+};
+
 #define CK(call)                                                    \
   do {                                                              \
     cudaError_t e_ = (call);                                        \
@@ -58,6 +63,7 @@ struct st_mg_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   bool host_only = false;              // built by st_mg_setup_host: no device state
+  int n_sm = 152;
   double* stage_f = nullptr;           // host-buffer solve staging (allocated on first use)
   double* stage_x = nullptr;
   int q = 1;
@@ -94,7 +100,7 @@ struct st_mg_s {
     int64_t* pxt_rowptr = nullptr; int32_t* pxt_col = nullptr; double* pxt_val = nullptr;
     SupernodalFactor<double> knF;
     DevFactor<double> kn;
-    std::vector<int64_t> kn_fwd_off, kn_bwd_off;
+    FactorLists kn_lists;
     NDCoords ecoord, ncoord;
   };
   std::vector<Space> space;
@@ -107,7 +113,7 @@ struct st_mg_s {
     SupernodalFactor<cplx> fc;
     DevFactor<double> dr;
     DevFactor<double2> dc;
-    std::vector<int64_t> fwd_off, bwd_off;
+    FactorLists lists;
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
     int64_t w_bytes = 0;                                   // device bytes of the slab factor blocks
@@ -115,9 +121,9 @@ struct st_mg_s {
   std::vector<Level> lv;
 
   // workspaces
-  void *sQ = nullptr, *sZ = nullptr, *sU = nullptr;
+  void *sQ = nullptr, *sZ = nullptr, *sU = nullptr, *sP = nullptr;   // sP: split-K partials
   int ld_slab = 1;
-  double *nQ = nullptr, *nZ = nullptr, *nU = nullptr;
+  double *nQ = nullptr, *nZ = nullptr, *nU = nullptr, *nP = nullptr;
   int ld_nod = 1;
   double *ny = nullptr, *nz = nullptr, *nw = nullptr;
   double* tmp_fine = nullptr;
@@ -139,8 +145,9 @@ using Handle = st_mg_s;
 CsrView view(const Handle::Space& S) { return CsrView{S.ne, S.rowptr, S.col}; }
 
 template <typename T, typename DT>
-void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, std::vector<int64_t>& fo,
-                     std::vector<int64_t>& bo) {
+void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, FactorLists& Lh) {
+  std::vector<int64_t>& fo = Lh.fo;
+  std::vector<int64_t>& bo = Lh.bo;
   static_assert(sizeof(T) == sizeof(DT), "layout");
   D.n = F.n;
   D.nnodes = (int32_t)F.nodes.size();
@@ -166,6 +173,52 @@ void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, 
   }
   fo[F.max_depth + 1] = (int64_t)ft.size();
   bo[F.max_depth + 1] = (int64_t)bt.size();
+  // split-K items: forward rows [0, nc+nr) against K [0, nc) (rows inside L11^{-1}
+  // stop at their last row); backward rows [0, nc) against K [row0, nc+nr)
+  std::vector<int4> fsi, fsu, bsi, bsu;
+  Lh.fsi.assign(F.max_depth + 2, 0);
+  Lh.fsu.assign(F.max_depth + 2, 0);
+  Lh.bsi.assign(F.max_depth + 2, 0);
+  Lh.bsu.assign(F.max_depth + 2, 0);
+  int64_t max_items = 0;
+  for (int d = 0; d <= F.max_depth; ++d) {
+    Lh.fsi[d] = (int64_t)fsi.size();
+    Lh.fsu[d] = (int64_t)fsu.size();
+    Lh.bsi[d] = (int64_t)bsi.size();
+    Lh.bsu[d] = (int64_t)bsu.size();
+    for (size_t s = 0; s < F.nodes.size(); ++s) {
+      const auto& a = F.nodes[s];
+      if (a.depth != d) continue;
+      const int m = a.nc + a.nr;
+      for (int r0 = 0; r0 < m; r0 += kSkRows) {
+        const int kend = (r0 + kSkRows <= a.nc) ? r0 + kSkRows : a.nc;
+        const int first = (int)fsi.size();
+        for (int k0 = 0; k0 < kend; k0 += kSkK) fsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + kSkK, kend)));
+        fsu.push_back(make_int4((int)s, r0, first, (int)fsi.size()));
+      }
+      for (int r0 = 0; r0 < a.nc; r0 += kSkRows) {
+        const int first = (int)bsi.size();
+        for (int k0 = r0; k0 < m; k0 += kSkK) bsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + kSkK, m)));
+        bsu.push_back(make_int4((int)s, r0, first, (int)bsi.size()));
+      }
+    }
+    max_items = std::max<int64_t>(max_items, (int64_t)fsi.size() - Lh.fsi[d]);
+    max_items = std::max<int64_t>(max_items, (int64_t)bsi.size() - Lh.bsi[d]);
+  }
+  Lh.fsi[F.max_depth + 1] = (int64_t)fsi.size();
+  Lh.fsu[F.max_depth + 1] = (int64_t)fsu.size();
+  Lh.bsi[F.max_depth + 1] = (int64_t)bsi.size();
+  Lh.bsu[F.max_depth + 1] = (int64_t)bsu.size();
+  D.fs_items = h.upload(fsi);
+  D.fs_units = h.upload(fsu);
+  D.bs_items = h.upload(bsi);
+  D.bs_units = h.upload(bsu);
+  D.h_fs_item_off = Lh.fsi.data();
+  D.h_fs_unit_off = Lh.fsu.data();
+  D.h_bs_item_off = Lh.bsi.data();
+  D.h_bs_unit_off = Lh.bsu.data();
+  D.max_items = max_items;
+  D.n_sm = h.n_sm;
   D.nodes = h.upload(nodes);
   D.W = reinterpret_cast<DT*>(h.upload(F.W));
   D.Dinv = reinterpret_cast<DT*>(h.upload(F.Dinv));
@@ -212,7 +265,8 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
   if (h.prob.degree == 0) {
     double* Q = static_cast<double*>(h.sQ);
     CK(slab_pre_dg0(src, src_ld, slab0, cnt, L.dr.iperm, S.ne, Q, h.ld_slab, h.stream));
-    CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), cnt, h.ld_slab, h.stream));
+    CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
+                     cnt, h.ld_slab, h.stream));
     CK(slab_post_dg0(Q, h.ld_slab, L.dr.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   } else {
     const double inv_tau = 1.0 / L.tau;
@@ -220,7 +274,8 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
     double2* Q = static_cast<double2*>(h.sQ);
     CK(slab_pre_dg1(src, src_ld, slab0, cnt, L.dc.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-    CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU), cnt, h.ld_slab, h.stream));
+    CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
+                     static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
     CK(slab_post_dg1(Q, h.ld_slab, L.dc.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   }
 }
@@ -247,7 +302,7 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
   const int ncols = L.N_t * h.q;
   if (h.opt.nodal_solve == 0) {
     CK(gather_perm(y, ncols, S.kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
-    CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, ncols, h.ld_nod, h.stream));
+    CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
     CK(scatter_perm(h.nQ, h.ld_nod, S.kn.iperm, S.nn, z, ncols, h.stream));
   } else {
     // damped Jacobi from z = 0, ping-pong through the nodal workspace
@@ -383,7 +438,10 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.stream = static_cast<cudaStream_t>(stream);
   H.q = pr->degree + 1;
   H.host_only = host_only;
-  if (!host_only) CK(cudaGetDevice(&H.device));
+  if (!host_only) {
+    CK(cudaGetDevice(&H.device));
+    CK(cudaDeviceGetAttribute(&H.n_sm, cudaDevAttrMultiProcessorCount, H.device));
+  }
 
   // ---- space hierarchy
   H.space.resize(nsl);
@@ -534,10 +592,11 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       S.pxt_col = H.upload(S.PxT.col);
       S.pxt_val = H.upload(S.PxT.val);
     }
-    make_dev_factor(H, S.knF, S.kn, S.kn_fwd_off, S.kn_bwd_off);
+    make_dev_factor(H, S.knF, S.kn, S.kn_lists);
     S.knF = SupernodalFactor<double>();   // host copy no longer needed
   }
-  int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0;
+  int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0, max_items = 0, max_kn_items = 0;
+  for (auto& S : H.space) max_kn_items = std::max<int64_t>(max_kn_items, S.kn.max_items);
   int max_nt = 1;
   for (size_t l = 0; l < H.lv.size(); ++l) {
     auto& L = H.lv[l];
@@ -548,7 +607,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       for (size_t q = 0; q < nnz; ++q) { a[q] = S.M.val[q] + L.tau * S.K.val[q]; b[q] = S.M.val[q]; }
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
-      make_dev_factor(H, L.fr, L.dr, L.fwd_off, L.bwd_off);
+      make_dev_factor(H, L.fr, L.dr, L.lists);
+      max_items = std::max<int64_t>(max_items, L.dr.max_items);
       L.w_bytes = (int64_t)L.fr.W.size() * 8;
       max_u = std::max<int64_t>(max_u, L.fr.u_rows);
       L.fr = SupernodalFactor<double>();
@@ -561,7 +621,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
       L.v2 = H.upload(c);
-      make_dev_factor(H, L.fc, L.dc, L.fwd_off, L.bwd_off);
+      make_dev_factor(H, L.fc, L.dc, L.lists);
+      max_items = std::max<int64_t>(max_items, L.dc.max_items);
       L.w_bytes = (int64_t)L.fc.W.size() * 16;
       max_u = std::max<int64_t>(max_u, L.fc.u_rows);
       L.fc = SupernodalFactor<cplx>();
@@ -584,17 +645,24 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.sQ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
   H.sZ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
   H.sU = H.dalloc<char>((int64_t)(std::max<int64_t>(max_u, 1) * H.ld_slab * esz));
+  {
+    const int nbk = pr->degree == 0 ? kSkMaxRhsR : kSkMaxRhsC;
+    const int64_t cols = (int64_t)((H.ld_slab + nbk - 1) / nbk) * nbk;
+    H.sP = H.dalloc<char>((int64_t)(std::max<int64_t>(max_items, 1) * kSkRows * cols * esz));
+  }
   H.ld_nod = max_nt * H.q;
   H.nQ = H.dalloc<double>(max_nn * H.ld_nod);
   H.nZ = H.dalloc<double>(max_nn * H.ld_nod);
   H.nU = H.dalloc<double>(std::max<int64_t>(max_un, 1) * H.ld_nod);
+  H.nP = H.dalloc<double>(std::max<int64_t>(max_kn_items, 1) * kSkRows *
+                          ((int64_t)((H.ld_nod + kSkMaxRhsR - 1) / kSkMaxRhsR) * kSkMaxRhsR));
   H.ny = H.dalloc<double>(max_nn * H.ld_nod);
   H.nz = H.dalloc<double>(max_nn * H.ld_nod);
   H.nw = H.dalloc<double>(max_nn * H.ld_nod);
   H.tmp_fine = H.dalloc<double>(std::max<int64_t>(max_len_fine_tmp, 1));
   H.g1 = H.dalloc<double>(max_ne * H.q);
   H.r0 = H.dalloc<double>(H.lv[0].len);
-  H.partial = H.dalloc<double>(std::max(1024, residual_blocks((int)max_ne)));
+  H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
   H.scalar = H.dalloc<double>(1);
   CK(cudaDeviceSynchronize());
   *out = h.release();
@@ -1018,6 +1086,29 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
         }
       }
     }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_probe_fp64(st_mg_t h, double* tflops) {
+  if (int rc = check_dev(h)) return rc;
+  if (!tflops) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    Handle& H = *h;
+    const int blocks = 8 * H.n_sm, iters = 1 << 14;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(fp64_probe(H.partial, blocks, 256, H.stream));   // warm-up
+    CK(cudaEventRecord(e0, H.stream));
+    CK(fp64_probe(H.partial, blocks, iters, H.stream));
+    CK(cudaEventRecord(e1, H.stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
     return ST_MG_OK;
   });
 }

@@ -426,6 +426,17 @@ __global__ void k_outer_load(const double* __restrict__ b, const double* __restr
   for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * ncols + j] = c[j] * be;
 }
 
+// FP64 pipe throughput probe: eight independent FMA chains per thread.
+__global__ void k_fp64_probe(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  const double s = warp_sum(x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7);
+  if ((threadIdx.x & 31) == 0 && s == 12345.678) out[blockIdx.x] = s;   // keeps the chains live
+}
+
 unsigned grid1(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 std::atomic<int64_t> g_launches{0};
@@ -436,6 +447,11 @@ int64_t launch_count() { return g_launches.load(); }
 void count_launches(int64_t n) { g_launches += n; }
 
 int residual_blocks(int nrows) { return (nrows + RES_WARPS - 1) / RES_WARPS; }
+
+cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st) {
+  { k_fp64_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-7); count_launches(1); }
+  return cudaGetLastError();
+}
 
 cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x, double* r,
                          int N_t, double* partial, int* nblocks, cudaStream_t st) {
