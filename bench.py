@@ -168,6 +168,9 @@ def main():
     ap.add_argument("--solves", type=int, default=3, help="time-to-1e-8 solves (seeds) for p50/p99")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
+    ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 2],
+                    help="slab-solve arithmetic of the main line: 0 FP64, 2 double-float (FP64-accurate)")
     ap.add_argument("--mode", default="bench", choices=["bench", "slab"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers)")
     args = ap.parse_args()
@@ -206,8 +209,9 @@ def main():
     stream = torch.cuda.current_stream()
     t0 = time.time()
     S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                             nu_post=W["nu_post"], stream=stream.cuda_stream)
+                             nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec)
     setup_s = time.time() - t0
+    n_levels, n_dof = S.n_levels, S.n_dof
     f = S.load(st_inputs.excitation(W["seed"] + rank))
     x = S.zeros()
     per_cycle = smoothed_per_cycle(S.n_dof, W["nu_pre"], W["nu_post"])
@@ -268,7 +272,7 @@ def main():
     fp64_peak = stmg.st_mg_probe_fp64(S.h)       # roof of the FP64 kernels, measured in this run
 
     # time to 1e-8 from x = 0, several excitations
-    solve_ms, solve_iters = [], []
+    solve_ms, solve_iters, fp64_solutions = [], [], []
     for s in range(args.solves):
         fs = S.load(st_inputs.excitation(100 + s + 1000 * rank))
         xs = S.zeros()
@@ -278,7 +282,8 @@ def main():
         torch.cuda.synchronize()
         solve_ms.append(1e3 * (time.perf_counter() - a))
         solve_iters.append(out["iters"])
-        del fs, xs
+        fp64_solutions.append(xs)
+        del fs
 
     # end to end through the public host-buffer API: H2D of f and x, one V-cycle,
     # residual norms, D2H of x, every step
@@ -295,6 +300,59 @@ def main():
         e2e_times.append(time.perf_counter() - a)
     e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
+    # mixed precision (FP32 slab apply, FP64 residual/nodal/coarsest): same workload
+    mixed = None
+    if args.mixed:
+        S.close()
+        del S
+        torch.cuda.synchronize()
+        Sm = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=1)
+        fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
+        xm = Sm.zeros()
+        for _ in range(args.warmup):
+            Sm.vcycle(fm, xm)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            Sm.vcycle(fm, xm)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_m = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+        st_m = stmg.st_mg_factor_stats(Sm.h, 0)
+        rm = Sm.residual(fm, xm)
+        ym = Sm.zeros()
+        stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        slab_ms_m = e0.elapsed_time(e1) / reps
+        msolve, miters, merr = [], [], []
+        for s_ in range(args.solves):
+            fs = Sm.load(st_inputs.excitation(100 + s_ + 1000 * rank))
+            xs = Sm.zeros()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            out = Sm.solve(fs, xs, rtol=1e-8, maxit=60)
+            torch.cuda.synchronize()
+            msolve.append(1e3 * (time.perf_counter() - a))
+            miters.append(out["iters"])
+            if s_ < len(fp64_solutions):
+                ref = fp64_solutions[s_]
+                merr.append(float(torch.linalg.vector_norm(xs - ref) / torch.linalg.vector_norm(ref)))
+        mixed = {"value": replica_value(world, per_cycle, args.steps, ms_m), "unit": UNIT,
+                 "ms_per_step": ms_m / args.steps, "slab_prec": "fp32 factor apply, fp64 residual/nodal/coarsest",
+                 "slab_solve_ms": slab_ms_m,
+                 "slab_solve_fp32_tflops": st_m["macs_per_rhs"] * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12,
+                 "time_to_1e-8_s": ({"p50": statistics.median(msolve) / 1e3, "n": len(msolve), "v_cycles": miters}
+                                    if msolve else None),
+                 "rel_err_vs_fp64_solution": merr}
+        Sm.close()
+        S = None
+
     cpu_base = None
     if cpu_proc is not None:
         res = cpu_q.get(timeout=1800)
@@ -309,8 +367,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
-                       "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": S.n_levels,
-                       "dofs": S.n_dof, "parallelism": f"replicas x{world}",
+                       "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": n_levels,
+                       "dofs": n_dof, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),
@@ -320,15 +378,18 @@ def main():
                          "kernel": "supernodal slab solve, finest level (k_sn_forward/backward, split-K near the root)",
                          "peak_source": "FP64 FMA throughput measured in this run (st_mg_probe_fp64)",
                          "ms_per_launch_group": slab_ms},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * S.n_dof * 8,
-                    "d2h_bytes_per_step": S.n_dof * 8 + 16},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n_dof * 8,
+                    "d2h_bytes_per_step": n_dof * 8 + 16},
             "gpu_launches": launches,
             "clocks": clk,
         }
         if cpu_base is not None:
             line["cpu_baseline"] = cpu_base
+        if mixed is not None:
+            line["mixed"] = mixed
         print(json.dumps(line))
-    S.close()
+    if S is not None:
+        S.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

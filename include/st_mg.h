@@ -80,6 +80,13 @@ typedef struct {
     int32_t nodal_jacobi_sweeps;
     int32_t use_A;           /* 1: hybrid smoother with A; 0: plain S only */
     int32_t setup_threads;   /* host threads for the factorisations; 0 = all cores */
+    int32_t slab_prec;       /* slab-solve arithmetic: 0 FP64; 1 mixed: the FP64 factor rounded to
+                                FP32 and applied in FP32 on every level but the coarsest (residual,
+                                factorisation, nodal and coarsest solves stay FP64; the V-cycle acts
+                                as iterative refinement, Section 2.1's "sufficiently well approximated");
+                                2 double-float: the factor as FP32 (hi, lo) pairs applied with
+                                error-free FP32 products and sums (about 48 significant bits), on the
+                                FP32 pipes, which on GB300 run 58x the FP64 rate */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

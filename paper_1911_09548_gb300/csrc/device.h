@@ -15,12 +15,15 @@ struct DevNode {
 };
 
 // Factor of one matrix (slab matrix of a time level, or K_n of a space level).
-// T = double (real symmetric) or double2 (complex symmetric, x = re, y = im).
-template <typename T>
+// T = memory type of right-hand sides and pivots: double (real symmetric), double2
+// (complex symmetric, x = re, y = im), or float / float2 (mixed precision);
+// WT = memory type of the blocks W: T, or FP32 (hi, lo) pairs for the double-float
+// path (float2 real, float4 complex).
+template <typename T, typename WT = T>
 struct DevFactor {
   int32_t n = 0, nnodes = 0, max_depth = 0;
   DevNode* nodes = nullptr;
-  T* W = nullptr;                 // per-node blocks W_s = [L11^-1; -L21 L11^-1], row-major
+  WT* W = nullptr;                // per-node blocks W_s = [L11^-1; -L21 L11^-1], row-major
   T* Dinv = nullptr;              // [n], permuted order
   int32_t* rows = nullptr;        // struct(s) lists, permuted indices
   int32_t* gsrc = nullptr;        // forward gather table, 2 per front position
@@ -69,6 +72,19 @@ cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, doub
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
                           int ld, cudaStream_t st);
 
+// Mixed precision: the same solve with the factor and the right-hand sides in FP32
+// (factor computed in FP64 and rounded once at setup).
+cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
+                           cudaStream_t st);
+cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, float2* U, float2* P, int nrhs, int ld,
+                           cudaStream_t st);
+
+// FP64-accurate double-float path (W as FP32 pairs, FP64 right-hand sides).
+cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
+                             int ld, cudaStream_t st);
+cudaError_t sn_solve_cplx_df(const DevFactor<double2, float4>& F, double2* Q, double2* Z, double2* U, double2* P,
+                             int nrhs, int ld, cudaStream_t st);
+
 // ---- space-time kernels.  Edge-major layout v[e*ncols + n*q + i], ncols = N_t*q.
 struct CsrView {
   int32_t nrows;
@@ -101,6 +117,15 @@ cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nro
                           int slab0, int cnt, double omega, int mode, cudaStream_t st);
 cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st);
+// FP32 variants for the mixed-precision slab solve (FP64 in, FP32 solve, FP64 out).
+cudaError_t slab_pre_dg0f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                          float* Q, int ld, cudaStream_t st);
+cudaError_t slab_pre_dg1f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                          double2 c0, double2 c1, float2* Q, int ld, cudaStream_t st);
+cudaError_t slab_post_dg0f(const float* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
+                           int slab0, int cnt, double omega, int mode, cudaStream_t st);
+cudaError_t slab_post_dg1f(const float2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
+                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st);
 // Nodal solve columns: Q[iperm[v]][j] = y[v][j];  z[v][j] = X[iperm[v]][j].
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
                         cudaStream_t st);

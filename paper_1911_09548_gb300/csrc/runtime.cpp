@@ -16,6 +16,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/st_mg.h"
@@ -113,6 +114,11 @@ struct st_mg_s {
     SupernodalFactor<cplx> fc;
     DevFactor<double> dr;
     DevFactor<double2> dc;
+    DevFactor<float> drf;                                   // mixed precision (FP32 apply)
+    DevFactor<float2> dcf;
+    DevFactor<double, float2> drd;                          // double-float (FP64-accurate) apply
+    DevFactor<double2, float4> dcd;
+    int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float
     FactorLists lists;
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
@@ -144,11 +150,51 @@ using Handle = st_mg_s;
 
 CsrView view(const Handle::Space& S) { return CsrView{S.ne, S.rowptr, S.col}; }
 
-template <typename T, typename DT>
-void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, FactorLists& Lh) {
+// Element conversion of factor blocks to the device type (FP64 as is, or rounded to FP32).
+inline void to_dev(double a, double& b) { b = a; }
+inline void to_dev(const cplx& a, double2& b) { b = make_double2(a.re, a.im); }
+inline void to_dev(double a, float& b) { b = (float)a; }
+inline void to_dev(const cplx& a, float2& b) { b = make_float2((float)a.re, (float)a.im); }
+// double-float pairs: hi = FP32 rounding, lo = FP32 rounding of the remainder
+inline void to_dev(double a, float2& b, int) {
+  const float h = (float)a;
+  b = make_float2(h, (float)(a - (double)h));
+}
+inline void to_dev(const cplx& a, float4& b) {
+  const float rh = (float)a.re, ih = (float)a.im;
+  b = make_float4(rh, (float)(a.re - (double)rh), ih, (float)(a.im - (double)ih));
+}
+template <typename DT, typename T>
+std::vector<DT> convert(const std::vector<T>& v) {
+  std::vector<DT> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) to_dev(v[i], out[i]);
+  return out;
+}
+template <typename DT, typename T>
+std::vector<DT> convert_pairs(const std::vector<T>& v);
+template <>
+std::vector<float2> convert_pairs<float2, double>(const std::vector<double>& v) {
+  std::vector<float2> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) to_dev(v[i], out[i], 0);
+  return out;
+}
+template <>
+std::vector<float4> convert_pairs<float4, cplx>(const std::vector<cplx>& v) {
+  std::vector<float4> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) to_dev(v[i], out[i]);
+  return out;
+}
+template <typename WT, typename T>
+std::vector<WT> convert_w(const std::vector<T>& v) {
+  if constexpr (std::is_same<WT, float2>::value && std::is_same<T, double>::value) return convert_pairs<float2>(v);
+  else if constexpr (std::is_same<WT, float4>::value) return convert_pairs<float4>(v);
+  else return convert<WT>(v);
+}
+
+template <typename T, typename DT, typename WT>
+void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh) {
   std::vector<int64_t>& fo = Lh.fo;
   std::vector<int64_t>& bo = Lh.bo;
-  static_assert(sizeof(T) == sizeof(DT), "layout");
   D.n = F.n;
   D.nnodes = (int32_t)F.nodes.size();
   D.max_depth = F.max_depth;
@@ -220,8 +266,8 @@ void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT>& D, 
   D.max_items = max_items;
   D.n_sm = h.n_sm;
   D.nodes = h.upload(nodes);
-  D.W = reinterpret_cast<DT*>(h.upload(F.W));
-  D.Dinv = reinterpret_cast<DT*>(h.upload(F.Dinv));
+  D.W = h.upload(convert_w<WT>(F.W));
+  D.Dinv = h.upload(convert<DT>(F.Dinv));
   D.rows = h.upload(F.rows);
   D.gsrc = h.upload(F.gsrc);
   D.iperm = h.upload(F.iperm);
@@ -262,21 +308,50 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
                   int dst0, double omega, int mode) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
+  if (L.prec == 1) {
+    if (h.prob.degree == 0) {
+      float* Q = static_cast<float*>(h.sQ);
+      CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.drf.iperm, S.ne, Q, h.ld_slab, h.stream));
+      CK(sn_solve_realf(L.drf, Q, static_cast<float*>(h.sZ), static_cast<float*>(h.sU), static_cast<float*>(h.sP),
+                        cnt, h.ld_slab, h.stream));
+      CK(slab_post_dg0f(Q, h.ld_slab, L.drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    } else {
+      const double inv_tau = 1.0 / L.tau;
+      const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
+      const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
+      float2* Q = static_cast<float2*>(h.sQ);
+      CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcf.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+      CK(sn_solve_cplxf(L.dcf, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
+                        static_cast<float2*>(h.sP), cnt, h.ld_slab, h.stream));
+      CK(slab_post_dg1f(Q, h.ld_slab, L.dcf.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    }
+    return;
+  }
   if (h.prob.degree == 0) {
     double* Q = static_cast<double*>(h.sQ);
-    CK(slab_pre_dg0(src, src_ld, slab0, cnt, L.dr.iperm, S.ne, Q, h.ld_slab, h.stream));
-    CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
-                     cnt, h.ld_slab, h.stream));
-    CK(slab_post_dg0(Q, h.ld_slab, L.dr.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    const int32_t* ip = L.prec == 2 ? L.drd.iperm : L.dr.iperm;
+    CK(slab_pre_dg0(src, src_ld, slab0, cnt, ip, S.ne, Q, h.ld_slab, h.stream));
+    if (L.prec == 2)
+      CK(sn_solve_real_df(L.drd, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
+                          static_cast<double*>(h.sP), cnt, h.ld_slab, h.stream));
+    else
+      CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
+                       cnt, h.ld_slab, h.stream));
+    CK(slab_post_dg0(Q, h.ld_slab, ip, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   } else {
     const double inv_tau = 1.0 / L.tau;
     const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
     const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
     double2* Q = static_cast<double2*>(h.sQ);
-    CK(slab_pre_dg1(src, src_ld, slab0, cnt, L.dc.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-    CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
-                     static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
-    CK(slab_post_dg1(Q, h.ld_slab, L.dc.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    const int32_t* ip = L.prec == 2 ? L.dcd.iperm : L.dc.iperm;
+    CK(slab_pre_dg1(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+    if (L.prec == 2)
+      CK(sn_solve_cplx_df(L.dcd, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
+                          static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
+    else
+      CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
+                       static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
+    CK(slab_post_dg1(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   }
 }
 
@@ -420,7 +495,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     return fail(ST_MG_ERR_INVALID_ARG, "n_cube must be divisible by 2^(n_space_levels-1) with coarsest >= 2");
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
-      op->nodal_jacobi_sweeps < 0)
+      op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 2)
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = (int64_t)6 * n * n * n;
   for (int64_t t = 0; t < nt; ++t)
@@ -561,6 +636,10 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   for (size_t j = 0; j < rcs.size(); ++j)
     if (rcs[j]) return fail(rcs[j] == 6 ? ST_MG_ERR_NUMERIC : ST_MG_ERR_INVALID_ARG, "factorisation: " + errs[j]);
   for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q;
+  // slab_prec 1 (FP32) leaves the coarsest level in FP64; slab_prec 2 (double-float,
+  // FP64-accurate) applies to every level
+  for (size_t l = 0; l < H.lv.size(); ++l)
+    H.lv[l].prec = (op->slab_prec == 1 && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
   if (host_only) {
     *out = h.release();
     return ST_MG_OK;
@@ -607,9 +686,19 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       for (size_t q = 0; q < nnz; ++q) { a[q] = S.M.val[q] + L.tau * S.K.val[q]; b[q] = S.M.val[q]; }
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
-      make_dev_factor(H, L.fr, L.dr, L.lists);
-      max_items = std::max<int64_t>(max_items, L.dr.max_items);
-      L.w_bytes = (int64_t)L.fr.W.size() * 8;
+      if (L.prec == 1) {
+        make_dev_factor(H, L.fr, L.drf, L.lists);
+        max_items = std::max<int64_t>(max_items, L.drf.max_items);
+        L.w_bytes = (int64_t)L.fr.W.size() * 4;
+      } else if (L.prec == 2) {
+        make_dev_factor(H, L.fr, L.drd, L.lists);
+        max_items = std::max<int64_t>(max_items, L.drd.max_items);
+        L.w_bytes = (int64_t)L.fr.W.size() * 8;
+      } else {
+        make_dev_factor(H, L.fr, L.dr, L.lists);
+        max_items = std::max<int64_t>(max_items, L.dr.max_items);
+        L.w_bytes = (int64_t)L.fr.W.size() * 8;
+      }
       max_u = std::max<int64_t>(max_u, L.fr.u_rows);
       L.fr = SupernodalFactor<double>();
     } else {
@@ -621,9 +710,19 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
       L.v2 = H.upload(c);
-      make_dev_factor(H, L.fc, L.dc, L.lists);
-      max_items = std::max<int64_t>(max_items, L.dc.max_items);
-      L.w_bytes = (int64_t)L.fc.W.size() * 16;
+      if (L.prec == 1) {
+        make_dev_factor(H, L.fc, L.dcf, L.lists);
+        max_items = std::max<int64_t>(max_items, L.dcf.max_items);
+        L.w_bytes = (int64_t)L.fc.W.size() * 8;
+      } else if (L.prec == 2) {
+        make_dev_factor(H, L.fc, L.dcd, L.lists);
+        max_items = std::max<int64_t>(max_items, L.dcd.max_items);
+        L.w_bytes = (int64_t)L.fc.W.size() * 16;
+      } else {
+        make_dev_factor(H, L.fc, L.dc, L.lists);
+        max_items = std::max<int64_t>(max_items, L.dc.max_items);
+        L.w_bytes = (int64_t)L.fc.W.size() * 16;
+      }
       max_u = std::max<int64_t>(max_u, L.fc.u_rows);
       L.fc = SupernodalFactor<cplx>();
     }
@@ -794,6 +893,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->nodal_jacobi_sweeps = 3;
   o->use_A = 1;
   o->setup_threads = 0;
+  o->slab_prec = 0;
   return ST_MG_OK;
 }
 
@@ -1123,9 +1223,15 @@ int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* 
   if (int rc = check_level(h, level)) return rc;
   const auto& L = h->lv[level];
   const bool c = h->prob.degree == 1;
-  if (macs_per_rhs) *macs_per_rhs = c ? L.dc.macs_per_rhs : L.dr.macs_per_rhs;
+  const double macs = L.prec == 1 ? (c ? L.dcf.macs_per_rhs : L.drf.macs_per_rhs)
+                     : L.prec == 2 ? (c ? L.dcd.macs_per_rhs : L.drd.macs_per_rhs)
+                                   : (c ? L.dc.macs_per_rhs : L.dr.macs_per_rhs);
+  const int dep = L.prec == 1 ? (c ? L.dcf.max_depth : L.drf.max_depth)
+                  : L.prec == 2 ? (c ? L.dcd.max_depth : L.drd.max_depth)
+                                : (c ? L.dc.max_depth : L.dr.max_depth);
+  if (macs_per_rhs) *macs_per_rhs = macs;
   if (factor_bytes) *factor_bytes = L.w_bytes;
-  if (depth) *depth = c ? L.dc.max_depth : L.dr.max_depth;
+  if (depth) *depth = dep;
   return ST_MG_OK;
 }
 

@@ -11,12 +11,22 @@
 // Nodes of one tree depth are independent, so each depth is one launch over
 // (node, row tile) x (right-hand-side tile) blocks.  The right-hand sides are the
 // slabs of the level (contiguous in each row), so every operand row is a
-// contiguous, coalesced vector.  Arithmetic is FP64 (double or double2 complex).
+// contiguous, coalesced vector.
+//
+// Arithmetic policies (template parameter P):
+//   PolNative<T>  T = double / double2 / float / float2: storage = arithmetic.
+//   PolDF / PolDFC: FP64-accurate "double-float" arithmetic for GB300, whose FP64
+//     pipe runs at 1/58 of its FP32 pipe.  W is stored as (hi, lo) FP32 pairs,
+//     right-hand sides stay FP64 in memory and are split on load, products are
+//     exact (fma error term) plus the two cross terms, and sums use the
+//     error-free two-sum (Knuth), so one multiply-add costs 12 FP32 instructions
+//     and keeps ~48 significant bits.  Epilogues (pivots, update sums) run in FP64.
 #include "device.h"
 
 namespace stmg {
 namespace {
 
+// ---------------------------------------------------------------- arithmetic
 template <typename T>
 struct Ar;
 template <>
@@ -40,56 +50,151 @@ struct Ar<double2> {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
   }
 };
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float zero() { return 0.f; }
+  static __device__ __forceinline__ void mac(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+};
+template <>
+struct Ar<float2> {
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void mac(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+  }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
+};
+
+template <typename T>
+struct PolNative {
+  using S = T;   // memory type of right-hand sides, updates, pivots
+  using WT = T;  // memory type of W
+  using A = T;   // arithmetic type
+  static __device__ __forceinline__ A zero() { return Ar<T>::zero(); }
+  static __device__ __forceinline__ A from_w(WT w) { return w; }
+  static __device__ __forceinline__ A from_s(S v) { return v; }
+  static __device__ __forceinline__ S to_s(A a) { return a; }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<T>::mac(acc, a, b); }
+};
+
+// double-float value h + l
+struct dfr {
+  float h, l;
+};
+struct dfc {
+  dfr re, im;
+};
+
+__device__ __forceinline__ dfr df_split(double v) {
+  dfr r;
+  r.h = __double2float_rn(v);
+  r.l = __double2float_rn(v - (double)r.h);
+  return r;
+}
+__device__ __forceinline__ double df_join(dfr a) { return (double)a.h + (double)a.l; }
+
+// acc += sgn * a * b (sgn = +1 or -1 folded into the first factor).
+__device__ __forceinline__ void df_mac(dfr& acc, dfr a, dfr b, float sgn) {
+  const float ah = sgn * a.h, al = sgn * a.l;
+  const float p = ah * b.h;
+  float e = fmaf(ah, b.h, -p);          // exact error of the leading product
+  e = fmaf(ah, b.l, e);
+  e = fmaf(al, b.h, e);
+  const float s = acc.h + p;            // two-sum of the leading parts
+  const float bb = s - acc.h;
+  const float t = (acc.h - (s - bb)) + (p - bb);
+  acc.l = acc.l + (t + e);
+  acc.h = s;
+}
+
+struct PolDF {
+  using S = double;
+  using WT = float2;   // (hi, lo)
+  using A = dfr;
+  static __device__ __forceinline__ A zero() { return dfr{0.f, 0.f}; }
+  static __device__ __forceinline__ A from_w(WT w) { return dfr{w.x, w.y}; }
+  static __device__ __forceinline__ A from_s(S v) { return df_split(v); }
+  static __device__ __forceinline__ S to_s(A a) { return df_join(a); }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { df_mac(acc, a, b, 1.f); }
+};
+
+struct PolDFC {
+  using S = double2;
+  using WT = float4;   // (re hi, re lo, im hi, im lo)
+  using A = dfc;
+  static __device__ __forceinline__ A zero() { return dfc{dfr{0.f, 0.f}, dfr{0.f, 0.f}}; }
+  static __device__ __forceinline__ A from_w(WT w) { return dfc{dfr{w.x, w.y}, dfr{w.z, w.w}}; }
+  static __device__ __forceinline__ A from_s(S v) { return dfc{df_split(v.x), df_split(v.y)}; }
+  static __device__ __forceinline__ S to_s(A a) { return make_double2(df_join(a.re), df_join(a.im)); }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) {
+    df_mac(acc.re, a.re, b.re, 1.f);
+    df_mac(acc.re, a.im, b.im, -1.f);
+    df_mac(acc.im, a.re, b.im, 1.f);
+    df_mac(acc.im, a.im, b.re, 1.f);
+  }
+};
 
 constexpr int BM = kSnBM;   // rows of W per block
 constexpr int BK = 16;      // depth of one shared-memory stage
 constexpr int NT = 256;     // threads: 16 x 16, micro-tile rows ty + 16 i, cols tx + 16 j
 constexpr int TM = BM / 16;
 
-template <typename T, int BN>
-__global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ nodes, const T* __restrict__ W,
-                                                   const T* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
-                                                   const int2* __restrict__ tiles, const T* __restrict__ Q,
-                                                   T* __restrict__ Z, T* __restrict__ U, int nrhs, int ld) {
+// ---------------------------------------------------------------- tiled path
+template <typename P, int BN>
+__global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ nodes,
+                                                   const typename P::WT* __restrict__ W,
+                                                   const typename P::S* __restrict__ Dinv,
+                                                   const int32_t* __restrict__ gsrc, const int2* __restrict__ tiles,
+                                                   const typename P::S* __restrict__ Q, typename P::S* __restrict__ Z,
+                                                   typename P::S* __restrict__ U, int nrhs, int ld) {
+  using S = typename P::S;
+  using A = typename P::A;
   constexpr int TN = BN / 16;
-  __shared__ T As[BK][BM];
-  __shared__ T Bs[BK][BN];
+  __shared__ A As[BK][BM];
+  __shared__ A Bs[BK][BN];
   const int2 tl = tiles[blockIdx.x];
   const DevNode nd = nodes[tl.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int row0 = tl.y * BM, c0 = blockIdx.y * BN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const T* Ws = W + nd.w_off;
+  const typename P::WT* Ws = W + nd.w_off;
   const int32_t* gs = gsrc + nd.g_off * 2;
-  T acc[TM][TN];
+  A acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = Ar<T>::zero();
+    for (int j = 0; j < TN; ++j) acc[i][j] = P::zero();
   // rows inside L11^{-1} (lower triangular) need no columns beyond the row
   const int kmax = (row0 + BM <= nc) ? (row0 + BM) : nc;
   for (int k0 = 0; k0 < kmax; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += NT) {
       const int i = t / BK, kk = t % BK;
       const int r = row0 + i, k = k0 + kk;
-      As[kk][i] = (r < m && k < nc) ? Ws[(int64_t)r * nc + k] : Ar<T>::zero();
+      As[kk][i] = (r < m && k < nc) ? P::from_w(Ws[(int64_t)r * nc + k]) : P::zero();
     }
     for (int t = threadIdx.x; t < BK * BN; t += NT) {
       const int kk = t / BN, j = t % BN;
       const int k = k0 + kk, c = c0 + j;
-      T v = Ar<T>::zero();
+      S v = Ar<S>::zero();
       if (k < nc && c < nrhs) {
         v = Q[(int64_t)(nd.col0 + k) * ld + c];
         const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
-        if (s0 >= 0) v = Ar<T>::add(v, U[(int64_t)s0 * ld + c]);
-        if (s1 >= 0) v = Ar<T>::add(v, U[(int64_t)s1 * ld + c]);
+        if (s0 >= 0) v = Ar<S>::add(v, U[(int64_t)s0 * ld + c]);
+        if (s1 >= 0) v = Ar<S>::add(v, U[(int64_t)s1 * ld + c]);
       }
-      Bs[kk][j] = v;
+      Bs[kk][j] = P::from_s(v);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[TM], b[TN];
+      A a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -97,7 +202,7 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) Ar<T>::mac(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) P::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
@@ -109,61 +214,66 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
     for (int j = 0; j < TN; ++j) {
       const int c = c0 + tx + 16 * j;
       if (c >= nrhs) continue;
+      const S v0 = P::to_s(acc[i][j]);
       if (r < nc) {
-        Z[(int64_t)(nd.col0 + r) * ld + c] = Ar<T>::mul(Dinv[nd.col0 + r], acc[i][j]);
+        Z[(int64_t)(nd.col0 + r) * ld + c] = Ar<S>::mul(Dinv[nd.col0 + r], v0);
       } else {
-        T v = acc[i][j];
+        S v = v0;
         const int s0 = gs[2 * r], s1 = gs[2 * r + 1];
-        if (s0 >= 0) v = Ar<T>::add(v, U[(int64_t)s0 * ld + c]);
-        if (s1 >= 0) v = Ar<T>::add(v, U[(int64_t)s1 * ld + c]);
+        if (s0 >= 0) v = Ar<S>::add(v, U[(int64_t)s0 * ld + c]);
+        if (s1 >= 0) v = Ar<S>::add(v, U[(int64_t)s1 * ld + c]);
         U[(int64_t)(nd.u_off + r - nc) * ld + c] = v;
       }
     }
   }
 }
 
-template <typename T, int BN>
-__global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ nodes, const T* __restrict__ W,
+template <typename P, int BN>
+__global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ nodes,
+                                                    const typename P::WT* __restrict__ W,
                                                     const int32_t* __restrict__ rows,
-                                                    const int2* __restrict__ tiles, const T* __restrict__ Z,
-                                                    T* __restrict__ X, int nrhs, int ld) {
+                                                    const int2* __restrict__ tiles,
+                                                    const typename P::S* __restrict__ Z,
+                                                    typename P::S* __restrict__ X, int nrhs, int ld) {
+  using S = typename P::S;
+  using A = typename P::A;
   constexpr int TN = BN / 16;
-  __shared__ T As[BK][BM];
-  __shared__ T Bs[BK][BN];
+  __shared__ A As[BK][BM];
+  __shared__ A Bs[BK][BN];
   const int2 tl = tiles[blockIdx.x];
   const DevNode nd = nodes[tl.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int row0 = tl.y * BM, c0 = blockIdx.y * BN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const T* Ws = W + nd.w_off;
+  const typename P::WT* Ws = W + nd.w_off;
   const int32_t* rw = rows + nd.row_off;
-  T acc[TM][TN];
+  A acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = Ar<T>::zero();
+    for (int j = 0; j < TN; ++j) acc[i][j] = P::zero();
   // W[k][i] = 0 for k < i inside L11^{-1}: start at the tile's first row
   const int kmin = (row0 / BK) * BK;
   for (int k0 = kmin; k0 < m; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += NT) {
       const int i = t % BM, kk = t / BM;
       const int r = row0 + i, k = k0 + kk;
-      As[kk][i] = (r < nc && k < m) ? Ws[(int64_t)k * nc + r] : Ar<T>::zero();
+      As[kk][i] = (r < nc && k < m) ? P::from_w(Ws[(int64_t)k * nc + r]) : P::zero();
     }
     for (int t = threadIdx.x; t < BK * BN; t += NT) {
       const int kk = t / BN, j = t % BN;
       const int k = k0 + kk, c = c0 + j;
-      T v = Ar<T>::zero();
+      S v = Ar<S>::zero();
       if (k < m && c < nrhs) {
         const int64_t src = (k < nc) ? (int64_t)(nd.col0 + k) : (int64_t)rw[k - nc];
         v = (k < nc) ? Z[src * ld + c] : X[src * ld + c];
       }
-      Bs[kk][j] = v;
+      Bs[kk][j] = P::from_s(v);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[TM], b[TN];
+      A a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -171,7 +281,7 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) Ar<T>::mac(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) P::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
@@ -182,106 +292,110 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int c = c0 + tx + 16 * j;
-      if (c < nrhs) X[(int64_t)(nd.col0 + r) * ld + c] = acc[i][j];
+      if (c < nrhs) X[(int64_t)(nd.col0 + r) * ld + c] = P::to_s(acc[i][j]);
     }
   }
 }
 
-
 // ---------------------------------------------------------------- split-K path
-// With few right-hand sides (coarse time levels have 1..16 slabs) a 64 x 32 tile
-// per block leaves most of the GPU idle and the top supernodes serialise on their
-// long K loops.  Here every item is kSkRows rows x one K chunk of kSkK columns for
-// all right-hand sides (one row per thread, NB accumulators); a second kernel sums
-// the chunks of each row in a fixed order and applies the epilogue.
+// With few right-hand sides (coarse time levels have 1..16 slabs), or at the few
+// large supernodes near the root, 64 x 32 tiles leave most of the GPU idle and the
+// top supernodes serialise on their long K loops.  Here every item is kSkRows rows
+// x one K chunk of kSkK columns x one column block of NB right-hand sides (one row
+// per thread, NB accumulators); a second kernel sums the chunks of each row in a
+// fixed order (in the memory type S) and applies the epilogue.
 constexpr int SK_THREADS = kSkRows;
 constexpr int SK_KS = 16;   // K columns staged in shared memory at a time
 
-template <typename T, int NB, bool FWD>
+template <typename P, int NB, bool FWD>
 __global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
-    const DevNode* __restrict__ nodes, const T* __restrict__ W, const int32_t* __restrict__ gsrc,
-    const int32_t* __restrict__ rows, const int4* __restrict__ items, const T* __restrict__ Q,
-    const T* __restrict__ Z, const T* __restrict__ U, const T* __restrict__ X, T* __restrict__ P, int nrhs, int ld) {
-  __shared__ T As[SK_KS][kSkRows];
-  __shared__ T Bs[SK_KS][NB];
+    const DevNode* __restrict__ nodes, const typename P::WT* __restrict__ W, const int32_t* __restrict__ gsrc,
+    const int32_t* __restrict__ rows, const int4* __restrict__ items, const typename P::S* __restrict__ Q,
+    const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U, const typename P::S* __restrict__ X,
+    typename P::S* __restrict__ Pt, int nrhs, int ld) {
+  using S = typename P::S;
+  using A = typename P::A;
+  __shared__ A As[SK_KS][kSkRows];
+  __shared__ A Bs[SK_KS][NB];
   const int4 it = items[blockIdx.x];
   const DevNode nd = nodes[it.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int r0 = it.y, k0 = it.z, k1 = it.w;
   const int tid = threadIdx.x;
   const int cb = blockIdx.y * NB;           // first right-hand side of this column block
-  const T* Ws = W + nd.w_off;
+  const typename P::WT* Ws = W + nd.w_off;
   const int32_t* gs = gsrc + nd.g_off * 2;
   const int32_t* rw = rows + nd.row_off;
-  T acc[NB];
+  A acc[NB];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) acc[j] = Ar<T>::zero();
+  for (int j = 0; j < NB; ++j) acc[j] = P::zero();
   for (int ks = k0; ks < k1; ks += SK_KS) {
     for (int t = tid; t < SK_KS * kSkRows; t += SK_THREADS) {
       int i, kk;
       if (FWD) { i = t / SK_KS; kk = t % SK_KS; }     // W row-major: k fastest
       else { i = t % kSkRows; kk = t / kSkRows; }     // W^T: row index fastest
       const int r = r0 + i, k = ks + kk;
-      T a = Ar<T>::zero();
-      if (FWD) { if (r < m && k < k1) a = Ws[(int64_t)r * nc + k]; }
-      else { if (r < nc && k < k1) a = Ws[(int64_t)k * nc + r]; }
+      A a = P::zero();
+      if (FWD) { if (r < m && k < k1) a = P::from_w(Ws[(int64_t)r * nc + k]); }
+      else { if (r < nc && k < k1) a = P::from_w(Ws[(int64_t)k * nc + r]); }
       As[kk][i] = a;
     }
     for (int t = tid; t < SK_KS * NB; t += SK_THREADS) {
       const int kk = t / NB, cl = t % NB, c = cb + cl;
       const int k = ks + kk;
-      T v = Ar<T>::zero();
+      S v = Ar<S>::zero();
       if (k < k1 && c < nrhs) {
         if (FWD) {
           v = Q[(int64_t)(nd.col0 + k) * ld + c];
           const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
-          if (s0 >= 0) v = Ar<T>::add(v, U[(int64_t)s0 * ld + c]);
-          if (s1 >= 0) v = Ar<T>::add(v, U[(int64_t)s1 * ld + c]);
+          if (s0 >= 0) v = Ar<S>::add(v, U[(int64_t)s0 * ld + c]);
+          if (s1 >= 0) v = Ar<S>::add(v, U[(int64_t)s1 * ld + c]);
         } else {
           v = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
         }
       }
-      Bs[kk][cl] = v;
+      Bs[kk][cl] = P::from_s(v);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < SK_KS; ++kk) {
-      const T a = As[kk][tid];
+      const A a = As[kk][tid];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) Ar<T>::mac(acc[j], a, Bs[kk][j]);
+      for (int j = 0; j < NB; ++j) P::mac(acc[j], a, Bs[kk][j]);
     }
     __syncthreads();
   }
-  T* out = P + (((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kSkRows + tid) * NB;
+  S* out = Pt + (((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kSkRows + tid) * NB;
 #pragma unroll
-  for (int j = 0; j < NB; ++j) out[j] = acc[j];
+  for (int j = 0; j < NB; ++j) out[j] = P::to_s(acc[j]);
 }
 
-// One block per unit (node, row0, item range): thread (row, column) sums the
-// unit's items in order, then the forward or backward epilogue.
-template <typename T, int NB, bool FWD>
+// One block per unit (node, row0, item range) and column block: thread (row,
+// column) sums the unit's items in order, then the forward or backward epilogue.
+template <typename P, int NB, bool FWD>
 __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
-    const DevNode* __restrict__ nodes, const T* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
-    const int4* __restrict__ units, int64_t item_base, int64_t n_items, const T* __restrict__ P,
-    T* __restrict__ Z, T* __restrict__ U, T* __restrict__ X, int nrhs, int ld) {
+    const DevNode* __restrict__ nodes, const typename P::S* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
+    const int4* __restrict__ units, int64_t item_base, int64_t n_items, const typename P::S* __restrict__ Pt,
+    typename P::S* __restrict__ Z, typename P::S* __restrict__ U, typename P::S* __restrict__ X, int nrhs, int ld) {
+  using S = typename P::S;
   const int4 un = units[blockIdx.x];
   const DevNode nd = nodes[un.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int i = threadIdx.x / NB, cl = threadIdx.x % NB, c = blockIdx.y * NB + cl;
   const int r = un.y + i;
   if (c >= nrhs) return;
-  const T* Pc = P + (int64_t)blockIdx.y * n_items * kSkRows * NB;
-  T acc = Ar<T>::zero();
-  for (int q = un.z; q < un.w; ++q) acc = Ar<T>::add(acc, Pc[(((int64_t)(q - item_base)) * kSkRows + i) * NB + cl]);
+  const S* Pc = Pt + (int64_t)blockIdx.y * n_items * kSkRows * NB;
+  S acc = Ar<S>::zero();
+  for (int q = un.z; q < un.w; ++q) acc = Ar<S>::add(acc, Pc[(((int64_t)(q - item_base)) * kSkRows + i) * NB + cl]);
   if (FWD) {
     if (r >= m) return;
     if (r < nc) {
-      Z[(int64_t)(nd.col0 + r) * ld + c] = Ar<T>::mul(Dinv[nd.col0 + r], acc);
+      Z[(int64_t)(nd.col0 + r) * ld + c] = Ar<S>::mul(Dinv[nd.col0 + r], acc);
     } else {
       const int32_t* gs = gsrc + nd.g_off * 2;
       const int s0 = gs[2 * r], s1 = gs[2 * r + 1];
-      if (s0 >= 0) acc = Ar<T>::add(acc, U[(int64_t)s0 * ld + c]);
-      if (s1 >= 0) acc = Ar<T>::add(acc, U[(int64_t)s1 * ld + c]);
+      if (s0 >= 0) acc = Ar<S>::add(acc, U[(int64_t)s0 * ld + c]);
+      if (s1 >= 0) acc = Ar<S>::add(acc, U[(int64_t)s1 * ld + c]);
       U[(int64_t)(nd.u_off + r - nc) * ld + c] = acc;
     }
   } else {
@@ -289,83 +403,115 @@ __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
   }
 }
 
-template <typename T, int NB>
-void skinny_depth(const DevFactor<T>& F, int d, bool fwd, T* Q, T* Z, T* U, T* P, int nrhs, int ld,
-                  cudaStream_t st) {
+template <typename P, int NB>
+void skinny_depth(const DevFactor<typename P::S, typename P::WT>& F, int d, bool fwd, typename P::S* Q,
+                  typename P::S* Z, typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
   const int64_t* io = fwd ? F.h_fs_item_off : F.h_bs_item_off;
   const int64_t* uo = fwd ? F.h_fs_unit_off : F.h_bs_unit_off;
   const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
   if (ib <= ia) return;
   const unsigned gy = (unsigned)((nrhs + NB - 1) / NB);
   if (fwd) {
-    k_sn_skinny_partial<T, NB, true><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
-        F.nodes, F.W, F.gsrc, F.rows, F.fs_items + ia, Q, Z, U, Q, P, nrhs, ld);
-    k_sn_skinny_reduce<T, NB, true><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
-        F.nodes, F.Dinv, F.gsrc, F.fs_units + ua, ia, ib - ia, P, Z, U, Q, nrhs, ld);
+    k_sn_skinny_partial<P, NB, true><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
+        F.nodes, F.W, F.gsrc, F.rows, F.fs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
+    k_sn_skinny_reduce<P, NB, true><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
+        F.nodes, F.Dinv, F.gsrc, F.fs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   } else {
-    k_sn_skinny_partial<T, NB, false><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
-        F.nodes, F.W, F.gsrc, F.rows, F.bs_items + ia, Q, Z, U, Q, P, nrhs, ld);
-    k_sn_skinny_reduce<T, NB, false><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
-        F.nodes, F.Dinv, F.gsrc, F.bs_units + ua, ia, ib - ia, P, Z, U, Q, nrhs, ld);
+    k_sn_skinny_partial<P, NB, false><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
+        F.nodes, F.W, F.gsrc, F.rows, F.bs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
+    k_sn_skinny_reduce<P, NB, false><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
+        F.nodes, F.Dinv, F.gsrc, F.bs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   }
   count_launches(2);
 }
 
-template <typename T, int NB>
-cudaError_t sn_solve_skinny(const DevFactor<T>& F, T* Q, T* Z, T* U, T* P, int nrhs, int ld, cudaStream_t st) {
-  for (int d = F.max_depth; d >= 0; --d) skinny_depth<T, NB>(F, d, true, Q, Z, U, P, nrhs, ld, st);
-  for (int d = 0; d <= F.max_depth; ++d) skinny_depth<T, NB>(F, d, false, Q, Z, U, P, nrhs, ld, st);
+template <typename P, int NB>
+cudaError_t sn_solve_skinny(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
+                            typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+  for (int d = F.max_depth; d >= 0; --d) skinny_depth<P, NB>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
+  for (int d = 0; d <= F.max_depth; ++d) skinny_depth<P, NB>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
   return cudaGetLastError();
 }
 
 // Tiled products for many right-hand sides; a depth whose tile grid would not
 // fill two waves of the GPU (the few large supernodes near the root) goes through
 // the split-K kernels instead, with NBK right-hand sides per column block.
-template <typename T, int BN, int NBK>
-cudaError_t sn_solve_impl(const DevFactor<T>& F, T* Q, T* Z, T* U, T* P, int nrhs, int ld, cudaStream_t st) {
-  if (nrhs <= 0) return cudaSuccess;
+template <typename P, int BN, int NBK>
+cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
+                           typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
   const unsigned gy = (unsigned)((nrhs + BN - 1) / BN);
   const int64_t two_waves = 2 * (int64_t)F.n_sm;
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
     if (b <= a) continue;
-    if (P && (b - a) * gy < two_waves) {
-      skinny_depth<T, NBK>(F, d, true, Q, Z, U, P, nrhs, ld, st);
+    if (Pt && (b - a) * gy < two_waves) {
+      skinny_depth<P, NBK>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
       continue;
     }
-    { k_sn_forward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc,
-                                                                       F.fwd_tiles + a, Q, Z, U, nrhs, ld); count_launches(1); }
+    k_sn_forward<P, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.fwd_tiles + a,
+                                                                     Q, Z, U, nrhs, ld);
+    count_launches(1);
   }
   for (int d = 0; d <= F.max_depth; ++d) {
     const int64_t a = F.h_bwd_off[d], b = F.h_bwd_off[d + 1];
     if (b <= a) continue;
-    if (P && (b - a) * gy < two_waves) {
-      skinny_depth<T, NBK>(F, d, false, Q, Z, U, P, nrhs, ld, st);
+    if (Pt && (b - a) * gy < two_waves) {
+      skinny_depth<P, NBK>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
       continue;
     }
-    { k_sn_backward<T, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z,
-                                                                        Q, nrhs, ld); count_launches(1); }
+    k_sn_backward<P, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z, Q,
+                                                                      nrhs, ld);
+    count_launches(1);
   }
   return cudaGetLastError();
+}
+
+// Real matrices: column blocks of 4 / 16 / 32 on the split-K path, 64-wide tiles.
+template <typename P>
+cudaError_t solve_real(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
+                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  if (Pt && nrhs <= 4) return sn_solve_skinny<P, 4>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= 16) return sn_solve_skinny<P, 16>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= kSkMaxRhsR) return sn_solve_skinny<P, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, st);
+  return sn_solve_tiled<P, 64, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, st);
+}
+// Complex matrices: column blocks of 2 / 8 / 16, 32-wide tiles.
+template <typename P>
+cudaError_t solve_cplx(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
+                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  if (Pt && nrhs <= 2) return sn_solve_skinny<P, 2>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= 8) return sn_solve_skinny<P, 8>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= kSkMaxRhsC) return sn_solve_skinny<P, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, st);
+  return sn_solve_tiled<P, 32, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, st);
 }
 
 }  // namespace
 
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,
                           cudaStream_t st) {
-  if (nrhs <= 0) return cudaSuccess;
-  if (P && nrhs <= 4) return sn_solve_skinny<double, 4>(F, Q, Z, U, P, nrhs, ld, st);
-  if (P && nrhs <= 16) return sn_solve_skinny<double, 16>(F, Q, Z, U, P, nrhs, ld, st);
-  if (P && nrhs <= kSkMaxRhsR) return sn_solve_skinny<double, kSkMaxRhsR>(F, Q, Z, U, P, nrhs, ld, st);
-  return sn_solve_impl<double, 64, kSkMaxRhsR>(F, Q, Z, U, P, nrhs, ld, st);
+  return solve_real<PolNative<double>>(F, Q, Z, U, P, nrhs, ld, st);
 }
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
                           int ld, cudaStream_t st) {
-  if (nrhs <= 0) return cudaSuccess;
-  if (P && nrhs <= 2) return sn_solve_skinny<double2, 2>(F, Q, Z, U, P, nrhs, ld, st);
-  if (P && nrhs <= 8) return sn_solve_skinny<double2, 8>(F, Q, Z, U, P, nrhs, ld, st);
-  if (P && nrhs <= kSkMaxRhsC) return sn_solve_skinny<double2, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, st);
-  return sn_solve_impl<double2, 32, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, st);
+  return solve_cplx<PolNative<double2>>(F, Q, Z, U, P, nrhs, ld, st);
+}
+cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
+                           cudaStream_t st) {
+  return solve_real<PolNative<float>>(F, Q, Z, U, P, nrhs, ld, st);
+}
+cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, float2* U, float2* P, int nrhs, int ld,
+                           cudaStream_t st) {
+  return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, st);
+}
+cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
+                             int ld, cudaStream_t st) {
+  return solve_real<PolDF>(F, Q, Z, U, P, nrhs, ld, st);
+}
+cudaError_t sn_solve_cplx_df(const DevFactor<double2, float4>& F, double2* Q, double2* Z, double2* U, double2* P,
+                             int nrhs, int ld, cudaStream_t st) {
+  return solve_cplx<PolDFC>(F, Q, Z, U, P, nrhs, ld, st);
 }
 
 }  // namespace stmg

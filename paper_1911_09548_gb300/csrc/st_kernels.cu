@@ -222,6 +222,60 @@ __global__ void k_slab_post_dg1(const double2* __restrict__ X, int ld, const int
   }
 }
 
+__global__ void k_slab_pre_dg0f(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+                                const int32_t* __restrict__ iperm, float* __restrict__ Q, int ld) {
+  const int e = blockIdx.x;
+  const double* src = r + (int64_t)e * src_ld;
+  float* dst = Q + (int64_t)iperm[e] * ld;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = (float)src[slab0 + k];
+}
+
+__global__ void k_slab_pre_dg1f(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+                                const int32_t* __restrict__ iperm, double2 c0, double2 c1,
+                                float2* __restrict__ Q, int ld) {
+  const int e = blockIdx.x;
+  const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
+  float2* dst = Q + (int64_t)iperm[e] * ld;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const double2 v = src[slab0 + k];
+    dst[k] = make_float2((float)(c0.x * v.x + c1.x * v.y), (float)(c0.y * v.x + c1.y * v.y));
+  }
+}
+
+__global__ void k_slab_post_dg0f(const float* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+                                 double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
+  const int e = blockIdx.x;
+  const float* src = X + (int64_t)iperm[e] * ld;
+  double* dst = x + (int64_t)e * dst_ld + slab0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const double v = (double)src[k];
+    if (mode == 0) dst[k] = v;
+    else dst[k] = fma(omega, v, dst[k]);
+  }
+}
+
+__global__ void k_slab_post_dg1f(const float2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+                                 double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
+                                 double omega, int mode) {
+  const int e = blockIdx.x;
+  const float2* src = X + (int64_t)iperm[e] * ld;
+  double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * dst_ld) + slab0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const float2 vf = src[k];
+    const double vx = vf.x, vy = vf.y;
+    const double u0 = 2.0 * vx;
+    const double u1 = 2.0 * (s1.x * vx - s1.y * vy);
+    if (mode == 0) {
+      dst[k] = make_double2(u0, u1);
+    } else {
+      double2 o = dst[k];
+      o.x = fma(omega, u0, o.x);
+      o.y = fma(omega, u1, o.y);
+      dst[k] = o;
+    }
+  }
+}
+
 __global__ void k_gather_perm(const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
                               double* __restrict__ Q, int ld) {
   const int v = blockIdx.x;
@@ -500,6 +554,26 @@ cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nro
 cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
   if (nrows > 0) { k_slab_post_dg1<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t slab_pre_dg0f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                          float* Q, int ld, cudaStream_t st) {
+  if (nrows > 0) { k_slab_pre_dg0f<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t slab_pre_dg1f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
+                          double2 c0, double2 c1, float2* Q, int ld, cudaStream_t st) {
+  if (nrows > 0) { k_slab_pre_dg1f<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t slab_post_dg0f(const float* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
+                           int slab0, int cnt, double omega, int mode, cudaStream_t st) {
+  if (nrows > 0) { k_slab_post_dg0f<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t slab_post_dg1f(const float2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
+                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
+  if (nrows > 0) { k_slab_post_dg1f<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,

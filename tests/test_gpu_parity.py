@@ -4,8 +4,9 @@ Cases span several tiles and ragged tails: N_t not a power of two (coarsest leve
 solved by forward substitution over an odd number of slabs), N_t beyond one
 residual pass (256 slabs), DG(0) and DG(1), a hierarchy that coarsens space
 (eq. CoarseningRule admits it), two-material coefficients, and the nodal Jacobi
-variant.  Tolerances: 1e-11 relative per V-cycle iterate (FP64 path); single
-operators to 1e-12 (they involve one factorisation solve at most).
+variant.  Tolerances: 1e-11 relative per V-cycle iterate (FP64 path, native FP64 or the
+FP64-accurate double-float slab solve); single operators to 1e-12 (they involve one
+factorisation solve at most).
 """
 import numpy as np
 import pytest
@@ -27,6 +28,10 @@ CASES = {
     "dg1_space": (8, 2, 1, 16, "unit", dict()),
     "dg0_long": (8, 1, 0, 300, "two_material", dict()),
     "dg1_jacobi": (4, 1, 1, 8, "two_material", dict(nodal_solve=1, nodal_jacobi_sweeps=3)),
+    # FP64-accurate double-float slab solve (slab_prec = 2) on the same parity bar
+    "dg1_ragged_df": (8, 1, 1, 20, "two_material", dict(nu_pre=2, nu_post=2, slab_prec=2)),
+    "dg1_space_df": (8, 2, 1, 16, "unit", dict(slab_prec=2)),
+    "dg0_long_df": (8, 1, 0, 300, "two_material", dict(slab_prec=2)),
 }
 
 
