@@ -116,6 +116,28 @@ class SpaceTimeSolver:
     def solve_host(self, f_host: np.ndarray, x_host: np.ndarray, rtol=1e-8, maxit=50):
         return B.st_mg_solve_host(self.h, f_host, x_host, rtol, maxit)
 
+    def convergence_rate(self, x0, max_iter=200, floor=1e-100):
+        """Section 5.1's power iteration: V-cycles with f = 0 from a random start; the
+        largest per-cycle reduction of the l2 norm is the rate.  Stops when the total
+        reduction falls below `floor` (the paper's 1e-100, to avoid underflow).
+        x0: device tensor (modified).  Norms come from the library's own reduction."""
+        import torch
+        f = self.zeros()
+        x = x0
+        nrm = torch.zeros(1, dtype=torch.float64, device=x.device)
+        B.st_mg_norm2_noalloc(x, x.numel(), self.stream, nrm)
+        n0 = nprev = float(nrm.item())
+        rates = []
+        for _ in range(max_iter):
+            B.st_mg_vcycle(self.h, f, x, False)
+            B.st_mg_norm2_noalloc(x, x.numel(), self.stream, nrm)
+            nx = float(nrm.item())
+            rates.append(nx / nprev)
+            nprev = nx
+            if nx == 0.0 or nx / n0 < floor:
+                break
+        return max(rates), rates
+
     def debug(self, what, space_level=0):
         return B.st_mg_debug_get(self.h, what, space_level)
 

@@ -1,0 +1,68 @@
+"""Convergence rates of the GPU path by the power iteration of Section 5.1, against the
+oracle's rates on the same operators and against what the paper reports:
+  * with spatial coarsening the plain S smoother is "completely ineffective" (rate ~ 1,
+    Section 3.1) while the hybrid SAS converges (Section 4.1);
+  * for large lambda the two-grid SAS rate is 2^-4 (Section 5.1);
+  * two materials: raising nu on one subdomain (larger local lambda) does not slow
+    the method down (Section 5.2, Table TestCase2)."""
+import numpy as np
+import pytest
+
+import st_inputs
+from helpers import oracle_mg, to_lib
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stmg():
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300
+    return paper_1911_09548_gb300
+
+
+def rate_gpu(stmg, n, nsl, nu, sigma, T, N_t, p, iters, **opts):
+    S = stmg.SpaceTimeSolver(n, nu, sigma, T, N_t, p, n_space_levels=nsl, **opts)
+    x0 = st_inputs.random_iterate((N_t, p + 1, S.n_edge), 0)
+    x = torch.from_numpy(to_lib(x0)).cuda()
+    r, rates = S.convergence_rate(x, max_iter=iters)
+    S.close()
+    return r, rates, x0
+
+
+def test_spatial_coarsening_needs_A(stmg):
+    nf, N_t = 8, 64
+    nu, sigma = st_inputs.materials(nf, "unit")
+    T = N_t / 512.0
+    r_S, rs_S, x0 = rate_gpu(stmg, nf, 2, nu, sigma, T, N_t, 0, 8, coarsen=2, max_levels=2, use_A=0)
+    r_SAS, rs_SAS, _ = rate_gpu(stmg, nf, 2, nu, sigma, T, N_t, 0, 8, coarsen=2, max_levels=2)
+    assert r_S > 0.9 and r_SAS < 0.5
+    # the oracle, same operators and start: same per-cycle reductions
+    sl, tl, mg = oracle_mg(nf, 2, nu, sigma, T, N_t, 0, coarsen=2, max_levels=2)
+    _, rs_o = mg.convergence_rate(x0, max_iter=8)
+    assert np.allclose(rs_SAS, rs_o, rtol=1e-9)
+
+
+def test_high_lambda_rate_is_two_to_minus_four(stmg):
+    nf, N_t = 8, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    r, rates, _ = rate_gpu(stmg, nf, 1, nu, sigma, 64.0, N_t, 0, 12, coarsen=1, max_levels=2)
+    assert abs(r - 2.0 ** -4) < 0.01
+
+
+def test_two_materials_rate_does_not_degrade(stmg):
+    """Table TestCase2 analogue on the Kuhn cube: nu_2 on the cubes with x > 1/2."""
+    nf, N_t = 8, 32
+    sigma = np.ones(6 * nf ** 3)
+    c = np.arange(nf ** 3)
+    right = np.repeat((c % nf) >= nf // 2, 6)
+    T = N_t * 0.25 * 3.0 / nf ** 2        # min lambda = 0.25 at level 0 -> "Full" from the top
+    out = []
+    for nu2 in (1.0, 1e2, 1e4):
+        nu = np.where(right, nu2, 1.0)
+        r, _, _ = rate_gpu(stmg, nf, 2, nu, sigma, T, N_t, 0, 10, max_levels=2)
+        out.append(r)
+    assert out[0] < 0.5
+    assert max(out[1:]) <= out[0] * 1.05     # raising the larger lambda only helps
