@@ -52,6 +52,7 @@ extern "C" {
 #define ST_MG_ERR_DIVERGED      4
 #define ST_MG_ERR_NOT_CONVERGED 5
 #define ST_MG_ERR_NUMERIC       6   /* zero pivot in a factorisation */
+#define ST_MG_ERR_TIMEOUT       7   /* a bounded device wait gave up (results of the call invalid) */
 
 typedef struct st_mg_s* st_mg_t;
 
@@ -86,7 +87,12 @@ typedef struct {
                                 as iterative refinement, Section 2.1's "sufficiently well approximated");
                                 2 double-float: the factor as FP32 (hi, lo) pairs applied with
                                 error-free FP32 products and sums (about 48 significant bits), on the
-                                FP32 pipes, which on GB300 run 58x the FP64 rate */
+                                FP32 pipes, which on GB300 run 58x the FP64 rate;
+                                3 (DG(1) only) BF16 factor on the tensor cores (tcgen05, FP32
+                                accumulation in tensor memory), coarsest level in FP64 */
+    int32_t residual_prec;   /* space-time residual arithmetic: 0 FP64; 2 double-float (x split into
+                                FP32 pairs once per call, error-free products and sums, f and r in
+                                FP64); -1 (default): FP64 when slab_prec = 0, double-float otherwise */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libstmg.so")
 
-CU_SOURCES = ["sn_kernels.cu", "st_kernels.cu", "noalloc.cu"]
+CU_SOURCES = ["sn_kernels.cu", "st_kernels.cu", "tc_kernels.cu", "noalloc.cu"]
 CPP_SOURCES = ["runtime.cpp", "mesh.cpp", "factor.cpp"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 

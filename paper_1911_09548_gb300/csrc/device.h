@@ -3,6 +3,7 @@
 // launch status (cudaGetLastError) without synchronising.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -79,6 +80,18 @@ cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float*
 cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, float2* U, float2* P, int nrhs, int ld,
                            cudaStream_t st);
 
+// BF16 factor on the tensor cores (DG(1)): W as complex BF16, right-hand sides and
+// accumulation in FP32.  Depths with enough tiles run the tcgen05 kernels (64
+// complex rows x kTcCols right-hand sides per block), the others and small nrhs
+// the split-K kernels.  err: device int set to 1 if a tensor-core wait timed out.
+constexpr int kTcCols = 128;
+cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
+                               float2* P, int nrhs, int ld, int* err, cudaStream_t st);
+cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
+                          int nrhs, int ld, int* err, cudaStream_t st);
+cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
+                           int nrhs, int ld, int* err, cudaStream_t st);
+
 // FP64-accurate double-float path (W as FP32 pairs, FP64 right-hand sides).
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
                              int ld, cudaStream_t st);
@@ -100,6 +113,13 @@ cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const doub
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
                          const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
 int residual_blocks(int nrows);
+// Double-float residual (FP64-accurate on the FP32 pipes): xs = x split into (hi, lo)
+// FP32 pairs by split_pairs, coefficient arrays as pairs; f, r and norms in FP64.
+cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st);
+cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const double* f, const float2* xs, double* r,
+                            int N_t, double* partial, int* nblocks, cudaStream_t st);
+cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
+                            const float2* xs, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
 // out[0] = sum of partial[0..n) in a fixed order.
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st);
 // out[0] = sum v^2 over n values (deterministic two-stage); partial has >= 1024 entries.

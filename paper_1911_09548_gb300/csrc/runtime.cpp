@@ -110,6 +110,7 @@ struct st_mg_s {
     int s = 0, N_t = 1;
     double tau = 1.0;
     double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;   // residual coefficients per nnz
+    float2 *p0 = nullptr, *p1 = nullptr, *p2 = nullptr;   // the same as (hi, lo) FP32 pairs
     SupernodalFactor<double> fr;
     SupernodalFactor<cplx> fc;
     DevFactor<double> dr;
@@ -118,7 +119,8 @@ struct st_mg_s {
     DevFactor<float2> dcf;
     DevFactor<double, float2> drd;                          // double-float (FP64-accurate) apply
     DevFactor<double2, float4> dcd;
-    int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float
+    DevFactor<float2, __nv_bfloat162> dcb;                  // BF16 factor on the tensor cores
+    int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
     FactorLists lists;
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
@@ -137,6 +139,9 @@ struct st_mg_s {
   double* r0 = nullptr;                 // finest residual
   double* partial = nullptr;
   double* scalar = nullptr;
+  float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
+  int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
+  bool df_residual = false;
   double2 c0{}, c1{}, s1{};             // DG(1) complex slab transformation
 
   ~st_mg_s() {
@@ -155,6 +160,7 @@ inline void to_dev(double a, double& b) { b = a; }
 inline void to_dev(const cplx& a, double2& b) { b = make_double2(a.re, a.im); }
 inline void to_dev(double a, float& b) { b = (float)a; }
 inline void to_dev(const cplx& a, float2& b) { b = make_float2((float)a.re, (float)a.im); }
+inline void to_dev(const cplx& a, __nv_bfloat162& b) { b = __floats2bfloat162_rn((float)a.re, (float)a.im); }
 // double-float pairs: hi = FP32 rounding, lo = FP32 rounding of the remainder
 inline void to_dev(double a, float2& b, int) {
   const float h = (float)a;
@@ -291,10 +297,17 @@ void op_residual(Handle& h, int l, const double* f, const double* x, double* r, 
   auto& S = h.space[L.s];
   int nb = 0;
   double* part = norm_sq_host ? h.partial : nullptr;
-  if (h.prob.degree == 0)
+  if (h.df_residual) {
+    CK(split_pairs(x, h.xsplit, L.len, h.stream));
+    if (h.prob.degree == 0)
+      CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t, part, &nb, h.stream));
+    else
+      CK(residual_dg1_df(view(S), L.p0, L.p1, L.p2, f, h.xsplit, r, L.N_t, part, &nb, h.stream));
+  } else if (h.prob.degree == 0) {
     CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t, part, &nb, h.stream));
-  else
+  } else {
     CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t, part, &nb, h.stream));
+  }
   if (norm_sq_host) {
     CK(reduce_partials(h.partial, nb, h.scalar, h.stream));
     CK(cudaMemcpyAsync(norm_sq_host, h.scalar, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
@@ -308,6 +321,17 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
                   int dst0, double omega, int mode) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
+  if (L.prec == 3) {
+    const double inv_tau = 1.0 / L.tau;
+    const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
+    const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
+    float2* Q = static_cast<float2*>(h.sQ);
+    CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+    CK(sn_solve_cplx_bf16(L.dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
+                          static_cast<float2*>(h.sP), cnt, h.ld_slab, h.tc_err, h.stream));
+    CK(slab_post_dg1f(Q, h.ld_slab, L.dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    return;
+  }
   if (L.prec == 1) {
     if (h.prob.degree == 0) {
       float* Q = static_cast<float*>(h.sQ);
@@ -495,7 +519,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     return fail(ST_MG_ERR_INVALID_ARG, "n_cube must be divisible by 2^(n_space_levels-1) with coarsest >= 2");
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
-      op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 2)
+      op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
+      (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = (int64_t)6 * n * n * n;
   for (int64_t t = 0; t < nt; ++t)
@@ -639,7 +664,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   // slab_prec 1 (FP32) leaves the coarsest level in FP64; slab_prec 2 (double-float,
   // FP64-accurate) applies to every level
   for (size_t l = 0; l < H.lv.size(); ++l)
-    H.lv[l].prec = (op->slab_prec == 1 && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
+    H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec == 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
+  H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
   if (host_only) {
     *out = h.release();
     return ST_MG_OK;
@@ -686,6 +712,10 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       for (size_t q = 0; q < nnz; ++q) { a[q] = S.M.val[q] + L.tau * S.K.val[q]; b[q] = S.M.val[q]; }
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
+      if (H.df_residual) {
+        L.p0 = H.upload(convert_pairs<float2>(a));
+        L.p1 = H.upload(convert_pairs<float2>(b));
+      }
       if (L.prec == 1) {
         make_dev_factor(H, L.fr, L.drf, L.lists);
         max_items = std::max<int64_t>(max_items, L.drf.max_items);
@@ -710,10 +740,19 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       L.v0 = H.upload(a);
       L.v1 = H.upload(b);
       L.v2 = H.upload(c);
+      if (H.df_residual) {
+        L.p0 = H.upload(convert_pairs<float2>(a));
+        L.p1 = H.upload(convert_pairs<float2>(b));
+        L.p2 = H.upload(convert_pairs<float2>(c));
+      }
       if (L.prec == 1) {
         make_dev_factor(H, L.fc, L.dcf, L.lists);
         max_items = std::max<int64_t>(max_items, L.dcf.max_items);
         L.w_bytes = (int64_t)L.fc.W.size() * 8;
+      } else if (L.prec == 3) {
+        make_dev_factor(H, L.fc, L.dcb, L.lists);
+        max_items = std::max<int64_t>(max_items, L.dcb.max_items);
+        L.w_bytes = (int64_t)L.fc.W.size() * 4;
       } else if (L.prec == 2) {
         make_dev_factor(H, L.fc, L.dcd, L.lists);
         max_items = std::max<int64_t>(max_items, L.dcd.max_items);
@@ -761,10 +800,28 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.tmp_fine = H.dalloc<double>(std::max<int64_t>(max_len_fine_tmp, 1));
   H.g1 = H.dalloc<double>(max_ne * H.q);
   H.r0 = H.dalloc<double>(H.lv[0].len);
+  if (H.df_residual) H.xsplit = H.dalloc<float2>(H.lv[0].len);
+  if (op->slab_prec == 3) {
+    H.tc_err = H.dalloc<int>(1);
+    CK(cudaMemset(H.tc_err, 0, sizeof(int)));
+  }
   H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
   H.scalar = H.dalloc<double>(1);
   CK(cudaDeviceSynchronize());
   *out = h.release();
+  return ST_MG_OK;
+}
+
+// A tensor-core block that gave up waiting leaves a flag; report it (blocking read).
+int check_tc(Handle& H) {
+  if (!H.tc_err) return ST_MG_OK;
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, H.tc_err, sizeof(int), cudaMemcpyDeviceToHost, H.stream));
+  CK(cudaStreamSynchronize(H.stream));
+  if (v) {
+    CK(cudaMemsetAsync(H.tc_err, 0, sizeof(int), H.stream));
+    return fail(ST_MG_ERR_TIMEOUT, "a tensor-core wait timed out; results of this call are invalid");
+  }
   return ST_MG_OK;
 }
 
@@ -817,6 +874,7 @@ int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit
   int status = ST_MG_OK;
   while (rel > rtol && it < maxit) {
     op_vcycle(H, 0, f, x);
+    if (int rc = check_tc(H)) return rc;
     op_residual(H, 0, f, x, H.r0, &nsq);
     rel = std::sqrt(nsq) / denom;
     ++it;
@@ -894,6 +952,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->use_A = 1;
   o->setup_threads = 0;
   o->slab_prec = 0;
+  o->residual_prec = -1;
   return ST_MG_OK;
 }
 
@@ -989,7 +1048,7 @@ int st_mg_slab_solve(st_mg_t h, int32_t level, const double* r_dev, double* y_de
   return guarded([&]() {
     const int ld = h->lv[level].N_t * h->q;
     op_slab_cols(*h, level, r_dev, ld, 0, h->lv[level].N_t, y_dev, ld, 0, 1.0, 0);
-    return ST_MG_OK;
+    return check_tc(*h);
   });
 }
 
@@ -998,7 +1057,7 @@ int st_mg_smooth_S(st_mg_t h, int32_t level, const double* f_dev, double* x_dev)
   if (int rc = check_ptrs({f_dev, x_dev})) return rc;
   return guarded([&]() {
     op_smooth_S(*h, level, f_dev, x_dev);
-    return ST_MG_OK;
+    return check_tc(*h);
   });
 }
 
@@ -1081,6 +1140,7 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
   if (int rc = check_ptrs({f_dev, x_dev})) return rc;
   return guarded([&]() {
     op_vcycle(*h, 0, f_dev, x_dev);
+    if (int rc = check_tc(*h)) return rc;
     if (rel_res_out) {
       const double fn = f_norm(*h, f_dev);
       double nsq = 0.0;
@@ -1223,10 +1283,12 @@ int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* 
   if (int rc = check_level(h, level)) return rc;
   const auto& L = h->lv[level];
   const bool c = h->prob.degree == 1;
-  const double macs = L.prec == 1 ? (c ? L.dcf.macs_per_rhs : L.drf.macs_per_rhs)
+  const double macs = L.prec == 3 ? L.dcb.macs_per_rhs
+                     : L.prec == 1 ? (c ? L.dcf.macs_per_rhs : L.drf.macs_per_rhs)
                      : L.prec == 2 ? (c ? L.dcd.macs_per_rhs : L.drd.macs_per_rhs)
                                    : (c ? L.dc.macs_per_rhs : L.dr.macs_per_rhs);
-  const int dep = L.prec == 1 ? (c ? L.dcf.max_depth : L.drf.max_depth)
+  const int dep = L.prec == 3 ? L.dcb.max_depth
+                  : L.prec == 1 ? (c ? L.dcf.max_depth : L.drf.max_depth)
                   : L.prec == 2 ? (c ? L.dcd.max_depth : L.drd.max_depth)
                                 : (c ? L.dc.max_depth : L.dr.max_depth);
   if (macs_per_rhs) *macs_per_rhs = macs;
@@ -1244,6 +1306,7 @@ const char* st_mg_strerror(int s) {
     case ST_MG_ERR_DIVERGED: return "diverged";
     case ST_MG_ERR_NOT_CONVERGED: return "not converged";
     case ST_MG_ERR_NUMERIC: return "numerical breakdown (zero pivot)";
+    case ST_MG_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
   }
 }

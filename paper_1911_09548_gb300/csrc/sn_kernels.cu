@@ -141,6 +141,18 @@ struct PolDFC {
   }
 };
 
+// BF16 factor, FP32 arithmetic (split-K path of the tensor-core solve)
+struct PolBF16C {
+  using S = float2;
+  using WT = __nv_bfloat162;
+  using A = float2;
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ A from_w(WT w) { return __bfloat1622float2(w); }
+  static __device__ __forceinline__ A from_s(S v) { return v; }
+  static __device__ __forceinline__ S to_s(A a) { return a; }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
+};
+
 constexpr int BM = kSnBM;   // rows of W per block
 constexpr int BK = 16;      // depth of one shared-memory stage
 constexpr int NT = 256;     // threads: 16 x 16, micro-tile rows ty + 16 i, cols tx + 16 j
@@ -505,6 +517,29 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
                            cudaStream_t st) {
   return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, st);
 }
+cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
+                               float2* P, int nrhs, int ld, int* err, cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  if (nrhs <= 2) return sn_solve_skinny<PolBF16C, 2>(F, Q, Z, U, P, nrhs, ld, st);
+  if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, st);
+  if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolBF16C, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, st);
+  const int64_t gy = (nrhs + kTcCols - 1) / kTcCols;
+  const int64_t two_waves = 2 * (int64_t)F.n_sm;
+  for (int d = F.max_depth; d >= 0; --d) {
+    const int64_t tiles = F.h_fwd_off[d + 1] - F.h_fwd_off[d];
+    if (tiles <= 0) continue;
+    if (tiles * gy < two_waves) skinny_depth<PolBF16C, kSkMaxRhsC>(F, d, true, Q, Z, U, P, nrhs, ld, st);
+    else sn_tc_forward(F, d, Q, Z, U, nrhs, ld, err, st);
+  }
+  for (int d = 0; d <= F.max_depth; ++d) {
+    const int64_t tiles = F.h_bwd_off[d + 1] - F.h_bwd_off[d];
+    if (tiles <= 0) continue;
+    if (tiles * gy < two_waves) skinny_depth<PolBF16C, kSkMaxRhsC>(F, d, false, Q, Z, U, P, nrhs, ld, st);
+    else sn_tc_backward(F, d, Q, Z, U, nrhs, ld, err, st);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
                              int ld, cudaStream_t st) {
   return solve_real<PolDF>(F, Q, Z, U, P, nrhs, ld, st);

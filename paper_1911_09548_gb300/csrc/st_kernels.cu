@@ -155,6 +155,155 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
   if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
 }
 
+// ---------------------------------------------------------------- double-float residual
+// FP64-accurate residual on the FP32 pipes: x is split once per call into (hi, lo)
+// FP32 pairs, matrix coefficients are stored as pairs, every product is exact
+// (fma error term) plus cross terms and every sum an error-free two-sum; the
+// accumulated pairs are joined in FP64 for the time-block combination with f.
+struct dpair {
+  float h, l;
+};
+
+__device__ __forceinline__ void dp_mac(dpair& acc, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = acc.h + p;
+  const float bb = s - acc.h;
+  const float t = (acc.h - (s - bb)) + (p - bb);
+  acc.l = acc.l + (t + e);
+  acc.h = s;
+}
+__device__ __forceinline__ double dp_join(dpair a) { return (double)a.h + (double)a.l; }
+
+__global__ void k_split_pairs(const double* __restrict__ x, float2* __restrict__ xs, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = __double2float_rn(v);
+    xs[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
+__global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, const int64_t* __restrict__ rowptr,
+                                                                    const int32_t* __restrict__ col,
+                                                                    const float2* __restrict__ m,
+                                                                    const float2* __restrict__ k0,
+                                                                    const float2* __restrict__ k1,
+                                                                    const double* __restrict__ f,
+                                                                    const float2* __restrict__ xs,
+                                                                    double* __restrict__ r, int N_t,
+                                                                    double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * RES_WARPS + warp;
+  double sq = 0.0;
+  if (row < nrows) {
+    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+    const int64_t ld = 2 * (int64_t)N_t;
+    const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
+    double2* r2 = reinterpret_cast<double2*>(r + row * ld);
+    double carry = 0.0;
+    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+      dpair A0[SPL], A1[SPL], B0[SPL], B1[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = dpair{0.f, 0.f};
+      for (int64_t q = beg; q < end; ++q) {
+        const int64_t c = col[q];
+        const float2 mv = m[q], kv0 = k0[q], kv1 = k1[q];
+        const float4* xr = reinterpret_cast<const float4*>(xs + c * ld);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const int n = n0 + 32 * j + lane;
+          if (n < N_t) {
+            const float4 v = xr[n];   // (x0 hi, x0 lo, x1 hi, x1 lo)
+            const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
+            dp_mac(A0[j], mv, x0);
+            dp_mac(A1[j], mv, x1);
+            dp_mac(B0[j], kv0, x0);
+            dp_mac(B1[j], kv1, x1);
+          }
+        }
+      }
+      double prevA = carry;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        const double a0 = dp_join(A0[j]), a1 = dp_join(A1[j]);
+        const double As = a0 + a1;
+        const double up = __shfl_up_sync(FULL, As, 1);
+        const double from31 = __shfl_sync(FULL, prevA, 31);
+        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        prevA = As;
+        const int n = n0 + 32 * j + lane;
+        if (n < N_t) {
+          const double2 fv = f2[n];
+          double2 rv;
+          rv.x = fv.x - (As + dp_join(B0[j])) + c;
+          rv.y = fv.y - ((a1 - a0) + dp_join(B1[j])) - c;
+          r2[n] = rv;
+          sq = fma(rv.x, rv.x, sq);
+          sq = fma(rv.y, rv.y, sq);
+        }
+      }
+      carry = __shfl_sync(FULL, prevA, 31);
+    }
+  }
+  if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, const int64_t* __restrict__ rowptr,
+                                                                    const int32_t* __restrict__ col,
+                                                                    const float2* __restrict__ a,
+                                                                    const float2* __restrict__ m,
+                                                                    const double* __restrict__ f,
+                                                                    const float2* __restrict__ xs,
+                                                                    double* __restrict__ r, int N_t,
+                                                                    double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * RES_WARPS + warp;
+  double sq = 0.0;
+  if (row < nrows) {
+    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+    const int64_t ld = N_t;
+    double carry = 0.0;
+    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+      dpair Ax[SPL], Mx[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = dpair{0.f, 0.f};
+      for (int64_t q = beg; q < end; ++q) {
+        const int64_t c = col[q];
+        const float2 av = a[q], mv = m[q];
+        const float2* xr = xs + c * ld;
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const int n = n0 + 32 * j + lane;
+          if (n < N_t) {
+            const float2 v = xr[n];
+            dp_mac(Ax[j], av, v);
+            dp_mac(Mx[j], mv, v);
+          }
+        }
+      }
+      double prev = carry;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        const double mx = dp_join(Mx[j]);
+        const double up = __shfl_up_sync(FULL, mx, 1);
+        const double from31 = __shfl_sync(FULL, prev, 31);
+        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        prev = mx;
+        const int n = n0 + 32 * j + lane;
+        if (n < N_t) {
+          const double rv = f[row * ld + n] - dp_join(Ax[j]) + c;
+          r[row * ld + n] = rv;
+          sq = fma(rv, rv, sq);
+        }
+      }
+      carry = __shfl_sync(FULL, prev, 31);
+    }
+  }
+  if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
+}
+
 __global__ void k_reduce_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
@@ -522,6 +671,27 @@ cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const dou
   if (nblocks) *nblocks = nb;
   if (nb > 0)
     { k_residual_dg1<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial); count_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st) {
+  if (n > 0) { k_split_pairs<<<(unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st>>>(x, xs, n); count_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const double* f, const float2* xs, double* r,
+                            int N_t, double* partial, int* nblocks, cudaStream_t st) {
+  const int nb = residual_blocks(A.nrows);
+  if (nblocks) *nblocks = nb;
+  if (nb > 0) { k_residual_dg0_df<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, xs, r, N_t, partial); count_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
+                            const float2* xs, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
+  const int nb = residual_blocks(A.nrows);
+  if (nblocks) *nblocks = nb;
+  if (nb > 0) { k_residual_dg1_df<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, xs, r, N_t, partial); count_launches(1); }
   return cudaGetLastError();
 }
 

@@ -198,7 +198,7 @@ def test_vcycle_iterates(name, lib_built):
         assert rel(from_lib(host(x), p + 1), xo) < 1e-11, it
 
 
-@pytest.mark.parametrize("name", ["dg0_two_grid", "dg1_space"])
+@pytest.mark.parametrize("name", ["dg0_two_grid", "dg1_space", "dg1_space_df"])
 def test_solve_reaches_time_stepping_solution(name, lib_built):
     S, sl, tl, mg, p = setup_case(name, lib_built)
     f = S.load(st_inputs.excitation(5))
