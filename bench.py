@@ -41,6 +41,17 @@ def smoothed_per_cycle(dofs, nu_pre, nu_post):
     return dofs * (2 * nu_pre + 2 * nu_post)
 
 
+def measured_peak(key: str) -> float:
+    """Measured peak of this machine's GB300 (MEASURED_PEAKS.json); 1938.7 TFLOP/s
+    BF16 / 6794.5 GB/s HBM, the values measured for this machine, if the file is absent."""
+    fallback = {"bf16_tflops": 1938.7, "hbm_gbs": 6794.5}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback[key]
+
+
 def reduce_max(value: float, dist=None, device="cpu") -> float:
     """Max over ranks (the slowest replica sets the job's time)."""
     import torch
@@ -300,58 +311,63 @@ def main():
         e2e_times.append(time.perf_counter() - a)
     e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
-    # mixed precision (FP32 slab apply, FP64 residual/nodal/coarsest): same workload
-    mixed = None
+    # other slab-solve precisions on the same workload: FP32 factor apply and the BF16
+    # factor on the tensor cores (residual FP64-accurate, nodal and coarsest FP64)
+    variants = {}
     if args.mixed:
         S.close()
-        del S
+        S = None
         torch.cuda.synchronize()
-        Sm = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=1)
-        fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
-        xm = Sm.zeros()
-        for _ in range(args.warmup):
-            Sm.vcycle(fm, xm)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            Sm.vcycle(fm, xm)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms_m = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
-        st_m = stmg.st_mg_factor_stats(Sm.h, 0)
-        rm = Sm.residual(fm, xm)
-        ym = Sm.zeros()
-        stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
+        for vname, prec, peak_key in (("mixed_fp32", 1, None), ("bf16_tensor", 3, "bf16_tflops")):
+            Sm = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                                      nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec)
+            fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
+            xm = Sm.zeros()
+            for _ in range(args.warmup):
+                Sm.vcycle(fm, xm)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                Sm.vcycle(fm, xm)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_m = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+            st_m = stmg.st_mg_factor_stats(Sm.h, 0)
+            rm = Sm.residual(fm, xm)
+            ym = Sm.zeros()
             stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        slab_ms_m = e0.elapsed_time(e1) / reps
-        msolve, miters, merr = [], [], []
-        for s_ in range(args.solves):
-            fs = Sm.load(st_inputs.excitation(100 + s_ + 1000 * rank))
-            xs = Sm.zeros()
             torch.cuda.synchronize()
-            a = time.perf_counter()
-            out = Sm.solve(fs, xs, rtol=1e-8, maxit=60)
+            e0.record(stream)
+            for _ in range(reps):
+                stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
+            e1.record(stream)
             torch.cuda.synchronize()
-            msolve.append(1e3 * (time.perf_counter() - a))
-            miters.append(out["iters"])
-            if s_ < len(fp64_solutions):
-                ref = fp64_solutions[s_]
-                merr.append(float(torch.linalg.vector_norm(xs - ref) / torch.linalg.vector_norm(ref)))
-        mixed = {"value": replica_value(world, per_cycle, args.steps, ms_m), "unit": UNIT,
-                 "ms_per_step": ms_m / args.steps, "slab_prec": "fp32 factor apply, fp64 residual/nodal/coarsest",
-                 "slab_solve_ms": slab_ms_m,
-                 "slab_solve_fp32_tflops": st_m["macs_per_rhs"] * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12,
+            slab_ms_m = e0.elapsed_time(e1) / reps
+            msolve, miters, merr = [], [], []
+            for s_ in range(args.solves):
+                fs = Sm.load(st_inputs.excitation(100 + s_ + 1000 * rank))
+                xs = Sm.zeros()
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                out = Sm.solve(fs, xs, rtol=1e-8, maxit=80)
+                torch.cuda.synchronize()
+                msolve.append(1e3 * (time.perf_counter() - a))
+                miters.append(out["iters"])
+                if s_ < len(fp64_solutions):
+                    ref = fp64_solutions[s_]
+                    merr.append(float(torch.linalg.vector_norm(xs - ref) / torch.linalg.vector_norm(ref)))
+            tflops = st_m["macs_per_rhs"] * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12
+            v = {"value": replica_value(world, per_cycle, args.steps, ms_m), "unit": UNIT,
+                 "ms_per_step": ms_m / args.steps, "slab_solve_ms": slab_ms_m, "slab_solve_tflops": tflops,
                  "time_to_1e-8_s": ({"p50": statistics.median(msolve) / 1e3, "n": len(msolve), "v_cycles": miters}
                                     if msolve else None),
                  "rel_err_vs_fp64_solution": merr}
-        Sm.close()
-        S = None
+            if peak_key:
+                peak = measured_peak(peak_key)
+                v["slab_solve_frac_of_bf16_peak"] = tflops / peak
+                v["bf16_peak_tflops"] = peak
+            variants[vname] = v
+            Sm.close()
 
     cpu_base = None
     if cpu_proc is not None:
@@ -385,8 +401,8 @@ def main():
         }
         if cpu_base is not None:
             line["cpu_baseline"] = cpu_base
-        if mixed is not None:
-            line["mixed"] = mixed
+        for k_, v_ in variants.items():
+            line[k_] = v_
         print(json.dumps(line))
     if S is not None:
         S.close()

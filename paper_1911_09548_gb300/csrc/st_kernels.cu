@@ -38,6 +38,7 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
 //   r0 = f0 - (A0 + A1 + B0) + c,  r1 = f1 - (A1 - A0 + B1) - c
 // where A_i = M x_i, B0 = tau K x0, B1 = (tau/3) K x1 on slab n and
 // c = (M (x0 + x1)) of slab n-1 = A0 + A1 of the previous slab.
+template <int LPR>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, const int64_t* __restrict__ rowptr,
                                                                  const int32_t* __restrict__ col,
                                                                  const double* __restrict__ m,
@@ -47,16 +48,19 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = blockIdx.x * RES_WARPS + warp;
+  // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
+  const int lane = threadIdx.x & (LPR - 1);
+  const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
   double sq = 0.0;
-  if (row < nrows) {
-    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+  {
+    // rows past the end keep the warp's shuffles uniform: empty, no loads or stores
+    const bool valid = row < nrows;
+    const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = 2 * (int64_t)N_t;
     const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
     double2* r2 = reinterpret_cast<double2*>(r + row * ld);
     double carry = 0.0;   // A0 + A1 of the slab before this pass
-    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
       double A0[SPL], A1[SPL], B0[SPL], B1[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = 0.0;
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
         const double2* xr = reinterpret_cast<const double2*>(x + c * ld);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-          const int n = n0 + 32 * j + lane;
+          const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const double2 v = xr[n];
             A0[j] = fma(mv, v.x, A0[j]);
@@ -80,12 +84,12 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
         const double As = A0[j] + A1[j];
-        const double up = __shfl_up_sync(FULL, As, 1);
-        const double from31 = __shfl_sync(FULL, prevA, 31);
+        const double up = __shfl_up_sync(FULL, As, 1, LPR);
+        const double from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
         const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prevA = As;
-        const int n = n0 + 32 * j + lane;
-        if (n < N_t) {
+        const int n = n0 + LPR * j + lane;
+        if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
           rv.x = fv.x - (As + B0[j]) + c;
@@ -95,13 +99,14 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
           sq = fma(rv.y, rv.y, sq);
         }
       }
-      carry = __shfl_sync(FULL, prevA, 31);
+      carry = __shfl_sync(FULL, prevA, LPR - 1, LPR);
     }
   }
   if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
 }
 
 // DG(0) (implicit Euler, eq. timeStepping): r_n = f_n - (M + tau K) x_n + M x_{n-1}.
+template <int LPR>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, const int64_t* __restrict__ rowptr,
                                                                  const int32_t* __restrict__ col,
                                                                  const double* __restrict__ a,
@@ -110,14 +115,17 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = blockIdx.x * RES_WARPS + warp;
+  // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
+  const int lane = threadIdx.x & (LPR - 1);
+  const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
   double sq = 0.0;
-  if (row < nrows) {
-    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+  {
+    // rows past the end keep the warp's shuffles uniform: empty, no loads or stores
+    const bool valid = row < nrows;
+    const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = N_t;
     double carry = 0.0;
-    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
       double Ax[SPL], Mx[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = 0.0;
@@ -127,7 +135,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
         const double* xr = x + c * ld;
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-          const int n = n0 + 32 * j + lane;
+          const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const double v = xr[n];
             Ax[j] = fma(av, v, Ax[j]);
@@ -138,18 +146,18 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
       double prev = carry;
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
-        const double up = __shfl_up_sync(FULL, Mx[j], 1);
-        const double from31 = __shfl_sync(FULL, prev, 31);
+        const double up = __shfl_up_sync(FULL, Mx[j], 1, LPR);
+        const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
         const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prev = Mx[j];
-        const int n = n0 + 32 * j + lane;
-        if (n < N_t) {
+        const int n = n0 + LPR * j + lane;
+        if (valid && n < N_t) {
           const double rv = f[row * ld + n] - Ax[j] + c;
           r[row * ld + n] = rv;
           sq = fma(rv, rv, sq);
         }
       }
-      carry = __shfl_sync(FULL, prev, 31);
+      carry = __shfl_sync(FULL, prev, LPR - 1, LPR);
     }
   }
   if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
@@ -185,6 +193,7 @@ __global__ void k_split_pairs(const double* __restrict__ x, float2* __restrict__
   }
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, const int64_t* __restrict__ rowptr,
                                                                     const int32_t* __restrict__ col,
                                                                     const float2* __restrict__ m,
@@ -194,16 +203,19 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
                                                                     double* __restrict__ partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = blockIdx.x * RES_WARPS + warp;
+  // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
+  const int lane = threadIdx.x & (LPR - 1);
+  const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
   double sq = 0.0;
-  if (row < nrows) {
-    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+  {
+    // rows past the end keep the warp's shuffles uniform: empty, no loads or stores
+    const bool valid = row < nrows;
+    const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = 2 * (int64_t)N_t;
     const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
     double2* r2 = reinterpret_cast<double2*>(r + row * ld);
     double carry = 0.0;
-    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
       dpair A0[SPL], A1[SPL], B0[SPL], B1[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = dpair{0.f, 0.f};
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
         const float4* xr = reinterpret_cast<const float4*>(xs + c * ld);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-          const int n = n0 + 32 * j + lane;
+          const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const float4 v = xr[n];   // (x0 hi, x0 lo, x1 hi, x1 lo)
             const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
@@ -229,12 +241,12 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
       for (int j = 0; j < SPL; ++j) {
         const double a0 = dp_join(A0[j]), a1 = dp_join(A1[j]);
         const double As = a0 + a1;
-        const double up = __shfl_up_sync(FULL, As, 1);
-        const double from31 = __shfl_sync(FULL, prevA, 31);
+        const double up = __shfl_up_sync(FULL, As, 1, LPR);
+        const double from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
         const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prevA = As;
-        const int n = n0 + 32 * j + lane;
-        if (n < N_t) {
+        const int n = n0 + LPR * j + lane;
+        if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
           rv.x = fv.x - (As + dp_join(B0[j])) + c;
@@ -244,12 +256,13 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
           sq = fma(rv.y, rv.y, sq);
         }
       }
-      carry = __shfl_sync(FULL, prevA, 31);
+      carry = __shfl_sync(FULL, prevA, LPR - 1, LPR);
     }
   }
   if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
 }
 
+template <int LPR>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, const int64_t* __restrict__ rowptr,
                                                                     const int32_t* __restrict__ col,
                                                                     const float2* __restrict__ a,
@@ -258,14 +271,17 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
                                                                     double* __restrict__ partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = blockIdx.x * RES_WARPS + warp;
+  // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
+  const int lane = threadIdx.x & (LPR - 1);
+  const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
   double sq = 0.0;
-  if (row < nrows) {
-    const int64_t beg = rowptr[row], end = rowptr[row + 1];
+  {
+    // rows past the end keep the warp's shuffles uniform: empty, no loads or stores
+    const bool valid = row < nrows;
+    const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = N_t;
     double carry = 0.0;
-    for (int n0 = 0; n0 < N_t; n0 += 32 * SPL) {
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
       dpair Ax[SPL], Mx[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = dpair{0.f, 0.f};
@@ -275,7 +291,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
         const float2* xr = xs + c * ld;
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
-          const int n = n0 + 32 * j + lane;
+          const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const float2 v = xr[n];
             dp_mac(Ax[j], av, v);
@@ -287,18 +303,18 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
         const double mx = dp_join(Mx[j]);
-        const double up = __shfl_up_sync(FULL, mx, 1);
-        const double from31 = __shfl_sync(FULL, prev, 31);
+        const double up = __shfl_up_sync(FULL, mx, 1, LPR);
+        const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
         const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prev = mx;
-        const int n = n0 + 32 * j + lane;
-        if (n < N_t) {
+        const int n = n0 + LPR * j + lane;
+        if (valid && n < N_t) {
           const double rv = f[row * ld + n] - dp_join(Ax[j]) + c;
           r[row * ld + n] = rv;
           sq = fma(rv, rv, sq);
         }
       }
-      carry = __shfl_sync(FULL, prev, 31);
+      carry = __shfl_sync(FULL, prev, LPR - 1, LPR);
     }
   }
   if (partial) block_sum_store<RES_WARPS * 32>(sq, partial + blockIdx.x);
@@ -651,26 +667,45 @@ void count_launches(int64_t n) { g_launches += n; }
 
 int residual_blocks(int nrows) { return (nrows + RES_WARPS - 1) / RES_WARPS; }
 
-cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st) {
-  { k_fp64_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-7); count_launches(1); }
-  return cudaGetLastError();
+// lanes per row: the smallest power of two whose SPL-slab passes cover N_t (<= 32)
+int lanes_per_row(int N_t) {
+  int l = 1;
+  while (l < 32 && l * SPL < N_t) l <<= 1;
+  return l;
 }
+
+#define STMG_RES_DISPATCH(KERNEL, ...)                                                              \
+  do {                                                                                              \
+    const int lpr = lanes_per_row(N_t);                                                             \
+    const int rows_per_block = RES_WARPS * (32 / lpr);                                              \
+    const int nb = (A.nrows + rows_per_block - 1) / rows_per_block;                                 \
+    if (nblocks) *nblocks = nb;                                                                     \
+    if (nb <= 0) break;                                                                             \
+    switch (lpr) {                                                                                  \
+      case 1: KERNEL<1><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
+      case 2: KERNEL<2><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
+      case 4: KERNEL<4><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
+      case 8: KERNEL<8><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
+      case 16: KERNEL<16><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                       \
+      default: KERNEL<32><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                       \
+    }                                                                                               \
+    count_launches(1);                                                                              \
+  } while (0)
 
 cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x, double* r,
                          int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  const int nb = residual_blocks(A.nrows);
-  if (nblocks) *nblocks = nb;
-  if (nb > 0)
-    { k_residual_dg0<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial); count_launches(1); }
+  STMG_RES_DISPATCH(k_residual_dg0, A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial);
   return cudaGetLastError();
 }
 
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
                          const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  const int nb = residual_blocks(A.nrows);
-  if (nblocks) *nblocks = nb;
-  if (nb > 0)
-    { k_residual_dg1<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial); count_launches(1); }
+  STMG_RES_DISPATCH(k_residual_dg1, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st) {
+  { k_fp64_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-7); count_launches(1); }
   return cudaGetLastError();
 }
 
@@ -681,17 +716,13 @@ cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st)
 
 cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const double* f, const float2* xs, double* r,
                             int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  const int nb = residual_blocks(A.nrows);
-  if (nblocks) *nblocks = nb;
-  if (nb > 0) { k_residual_dg0_df<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, a, m, f, xs, r, N_t, partial); count_launches(1); }
+  STMG_RES_DISPATCH(k_residual_dg0_df, A.nrows, A.rowptr, A.col, a, m, f, xs, r, N_t, partial);
   return cudaGetLastError();
 }
 
 cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
                             const float2* xs, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  const int nb = residual_blocks(A.nrows);
-  if (nblocks) *nblocks = nb;
-  if (nb > 0) { k_residual_dg1_df<<<nb, RES_WARPS * 32, 0, st>>>(A.nrows, A.rowptr, A.col, m, k0, k1, f, xs, r, N_t, partial); count_launches(1); }
+  STMG_RES_DISPATCH(k_residual_dg1_df, A.nrows, A.rowptr, A.col, m, k0, k1, f, xs, r, N_t, partial);
   return cudaGetLastError();
 }
 
