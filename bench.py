@@ -180,8 +180,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
-    ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 2],
-                    help="slab-solve arithmetic of the main line: 0 FP64, 2 double-float (FP64-accurate)")
+    ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
     ap.add_argument("--mode", default="bench", choices=["bench", "slab"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers)")
     args = ap.parse_args()
@@ -217,7 +217,10 @@ def main():
 
     W = WORKLOAD
     nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library captures the V-cycle into a CUDA graph on it
+    # (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     t0 = time.time()
     S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
                              nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec)

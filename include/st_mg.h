@@ -93,6 +93,10 @@ typedef struct {
     int32_t residual_prec;   /* space-time residual arithmetic: 0 FP64; 2 double-float (x split into
                                 FP32 pairs once per call, error-free products and sums, f and r in
                                 FP64); -1 (default): FP64 when slab_prec = 0, double-float otherwise */
+    int32_t use_graph;       /* 1 (default): st_mg_vcycle / st_mg_solve capture the V-cycle's fixed
+                                launch sequence into a CUDA graph once per (f, x) buffer pair and replay
+                                it (needs a non-default stream; the first call captures, later calls
+                                replay); 0: launch kernel by kernel */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
     _fields_ = [("omega", _dbl), ("nu_pre", _i32), ("nu_post", _i32), ("lambda_crit", _dbl),
                 ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
-                ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32)]
+                ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32)]
 
 
 _SIGS = {

@@ -141,10 +141,16 @@ struct st_mg_s {
   double* scalar = nullptr;
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
   int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
+  // captured V-cycle (replayed while f and x stay the same buffers)
+  cudaGraphExec_t graph_exec = nullptr;
+  const double* graph_f = nullptr;
+  double* graph_x = nullptr;
+  int64_t graph_launches = 0;
   bool df_residual = false;
   double2 c0{}, c1{}, s1{};             // DG(1) complex slab transformation
 
   ~st_mg_s() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
     for (void* p : allocs) cudaFree(p);
   }
 };
@@ -497,6 +503,41 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
   op_vcycle(h, l + 1, C.f, C.x);
   op_prolong_add(h, l, C.x, x);
   op_smooth(h, l, f, x, h.opt.nu_post);
+}
+
+// One V-cycle on the finest level.  With use_graph and a non-default stream the
+// fixed launch sequence is captured once per (f, x) pair and replayed.
+void run_vcycle(Handle& h, const double* f, double* x) {
+  if (!h.opt.use_graph || h.stream == nullptr) {
+    op_vcycle(h, 0, f, x);
+    return;
+  }
+  if (!h.graph_exec || h.graph_f != f || h.graph_x != x) {
+    if (h.graph_exec) {
+      CK(cudaGraphExecDestroy(h.graph_exec));
+      h.graph_exec = nullptr;
+    }
+    const int64_t l0 = launch_count();
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      op_vcycle(h, 0, f, x);
+    } catch (...) {
+      cudaStreamEndCapture(h.stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    CK(cudaStreamEndCapture(h.stream, &g));
+    h.graph_launches = launch_count() - l0;
+    count_launches(-h.graph_launches);     // counted when replayed
+    cudaError_t e = cudaGraphInstantiate(&h.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw CudaError{e, "cudaGraphInstantiate"};
+    h.graph_f = f;
+    h.graph_x = x;
+  }
+  CK(cudaGraphLaunch(h.graph_exec, h.stream));
+  count_launches(h.graph_launches);
 }
 
 double f_norm(Handle& h, const double* f) {
@@ -873,7 +914,7 @@ int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit
   int it = 0;
   int status = ST_MG_OK;
   while (rel > rtol && it < maxit) {
-    op_vcycle(H, 0, f, x);
+    run_vcycle(H, f, x);
     if (int rc = check_tc(H)) return rc;
     op_residual(H, 0, f, x, H.r0, &nsq);
     rel = std::sqrt(nsq) / denom;
@@ -953,6 +994,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->setup_threads = 0;
   o->slab_prec = 0;
   o->residual_prec = -1;
+  o->use_graph = 1;
   return ST_MG_OK;
 }
 
@@ -1139,7 +1181,7 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
   if (int rc = check_dev(h)) return rc;
   if (int rc = check_ptrs({f_dev, x_dev})) return rc;
   return guarded([&]() {
-    op_vcycle(*h, 0, f_dev, x_dev);
+    run_vcycle(*h, f_dev, x_dev);
     if (int rc = check_tc(*h)) return rc;
     if (rel_res_out) {
       const double fn = f_norm(*h, f_dev);

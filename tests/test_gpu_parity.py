@@ -225,3 +225,25 @@ def test_solve_host_buffers_match_device(lib_built):
     out_h = S.solve_host(fh, xh, rtol=1e-9, maxit=30)
     assert out_h["iters"] == out_d["iters"]
     assert np.array_equal(xh, host(x))       # same kernels, same order: bit-identical
+
+
+def test_graph_replay_matches_direct_launches(lib_built):
+    """A V-cycle replayed from its captured CUDA graph is bit-identical to launching
+    the same kernels one by one, and the launch counter counts replayed kernels."""
+    n, nsl, p, N_t, mat, opts = CASES["dg1_ragged"]
+    nu, sigma = st_inputs.materials(n, mat, 1)
+    side = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(side):
+        for g in (0, 1):
+            S = lib_built.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, stream=side.cuda_stream, use_graph=g, **opts)
+            f = S.load(st_inputs.excitation(12))
+            x = S.zeros()
+            c0 = lib_built.st_mg_launch_count()
+            for _ in range(3):
+                S.vcycle(f, x)
+            side.synchronize()
+            out[g] = (x.cpu().numpy(), lib_built.st_mg_launch_count() - c0)
+            S.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] > 0
