@@ -65,6 +65,10 @@ typedef struct {
     double T;                /* end time (> 0); the time interval is (0, T) */
     int32_t N_t;             /* number of time slabs on the finest level (>= 1) */
     int32_t degree;          /* DG degree in time: 0 (implicit Euler) or 1 */
+    int32_t n_batch;         /* independent problems (right-hand sides) on the same mesh, materials
+                                and time grid, solved together (0 or 1: one).  Vectors then hold
+                                v[e * (B N_t q) + b * (N_t q) + n q + i] for problem b; needs N_t a
+                                power of two (time coarsened to one slab per problem) */
 } st_mg_problem;
 
 /* Method parameters (Sections 2.1, 2.2, 4, 5). */
@@ -121,8 +125,8 @@ int st_mg_setup_host(const st_mg_problem* prob, const st_mg_options* opt, st_mg_
 
 void st_mg_destroy(st_mg_t h);
 
-/* Sizes of the finest level: interior edges, interior nodes, space-time unknowns
- * (n_edge * N_t * (degree+1)), and the number of time levels. */
+/* Sizes of the finest level: interior edges, interior nodes, space-time unknowns of
+ * all problems (n_edge * n_batch * N_t * (degree+1)), and the number of time levels. */
 int st_mg_sizes(st_mg_t h, int64_t* n_edge, int64_t* n_node, int64_t* n_dof, int32_t* n_levels);
 
 /* Time level `level` (0 = finest): its space level, slab count and step tau. */
@@ -136,6 +140,10 @@ int st_mg_level_info(st_mg_t h, int32_t level, int32_t* space_level, int32_t* N_
  * phase: host [n_modes].  f_dev: device, finest layout. */
 int st_mg_assemble_load(st_mg_t h, int32_t n_modes, const double* a, const double* k,
                         const double* phase, double* f_dev);
+/* The same for problem `batch` of a batched handle (st_mg_assemble_load = batch 0);
+ * the other problems' entries of f_dev are left untouched. */
+int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const double* a, const double* k,
+                              const double* phase, double* f_dev);
 
 /* ---- individual steps of the hot path (each on time level `level`) ---- */
 

@@ -26,7 +26,7 @@ class StMgError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n_cube", _i32), ("n_space_levels", _i32), ("nu", _P(_dbl)), ("sigma", _P(_dbl)),
-                ("T", _dbl), ("N_t", _i32), ("degree", _i32)]
+                ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32)]
 
 
 class Options(ctypes.Structure):
@@ -44,6 +44,7 @@ _SIGS = {
     "st_mg_sizes": [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i32)],
     "st_mg_level_info": [_vp, _i32, _P(_i32), _P(_i32), _P(_dbl), _P(_i64), _P(_i64)],
     "st_mg_assemble_load": [_vp, _i32, _P(_dbl), _P(_dbl), _P(_dbl), _vp],
+    "st_mg_assemble_load_batch": [_vp, _i32, _i32, _P(_dbl), _P(_dbl), _P(_dbl), _vp],
     "st_mg_residual": [_vp, _i32, _vp, _vp, _vp, _P(_dbl)],
     "st_mg_slab_solve": [_vp, _i32, _vp, _vp],
     "st_mg_smooth_S": [_vp, _i32, _vp, _vp],
@@ -125,10 +126,10 @@ def st_mg_default_options() -> Options:
     return o
 
 
-def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree):
+def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1):
     nu = np.ascontiguousarray(nu, dtype=np.float64)
     sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree)
+    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch)
     p._keep = (nu, sigma)
     return p
 
@@ -169,6 +170,14 @@ def st_mg_assemble_load(h, a, k, phase, f_dev):
     phase = np.ascontiguousarray(phase, np.float64).ravel()
     _check(lib().st_mg_assemble_load(_vp(h), len(phase), _dptr(a), _dptr(k), _dptr(phase), _vp(_addr(f_dev))),
            "st_mg_assemble_load")
+
+
+def st_mg_assemble_load_batch(h, batch, a, k, phase, f_dev):
+    a = np.ascontiguousarray(a, np.float64).ravel()
+    k = np.ascontiguousarray(k, np.float64).ravel()
+    phase = np.ascontiguousarray(phase, np.float64).ravel()
+    _check(lib().st_mg_assemble_load_batch(_vp(h), batch, len(phase), _dptr(a), _dptr(k), _dptr(phase),
+                                           _vp(_addr(f_dev))), "st_mg_assemble_load_batch")
 
 
 def st_mg_residual(h, level, f, x, r, want_norm=False):

@@ -48,7 +48,19 @@ struct DevFactor {
   int64_t* h_bs_unit_off = nullptr;
   int64_t max_items = 0;              // largest item count of one depth (partial buffer rows / kSkRows)
   int32_t n_sm = 152;                 // multiprocessors of the device (wave size of the tiled path)
+  // tensor-core split-K: per depth, items (node, row tile, k0, k1) of kTcSplitK complex
+  // columns and units (node, row tile, item_begin, item_end)
+  int4* tcf_items = nullptr;
+  int4* tcf_units = nullptr;
+  int4* tcb_items = nullptr;
+  int4* tcb_units = nullptr;
+  int64_t* h_tcf_item_off = nullptr;
+  int64_t* h_tcf_unit_off = nullptr;
+  int64_t* h_tcb_item_off = nullptr;
+  int64_t* h_tcb_unit_off = nullptr;
+  int64_t max_tc_items = 0;
 };
+constexpr int kTcSplitK = 256;      // complex K columns per tensor-core split-K item
 
 // Split-K path: rows per item, columns per item, and the largest right-hand-side
 // count it serves (complex: kSkMaxRhsC, real: kSkMaxRhsR).
@@ -86,11 +98,15 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
 // the split-K kernels.  err: device int set to 1 if a tensor-core wait timed out.
 constexpr int kTcCols = 128;
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, int nrhs, int ld, int* err, cudaStream_t st);
+                               float2* P, float2* Ptc, int nrhs, int ld, int* err, cudaStream_t st);
 cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
                           int nrhs, int ld, int* err, cudaStream_t st);
 cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
                            int nrhs, int ld, int* err, cudaStream_t st);
+// Split-K tensor-core depth: partial products of K chunks into P (max_tc_items *
+// ceil(nrhs / kTcCols) * kSnBM * kTcCols float2), then a fixed-order reduction + epilogue.
+cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
+                              float2* U, float2* P, int nrhs, int ld, int* err, cudaStream_t st);
 
 // FP64-accurate double-float path (W as FP32 pairs, FP64 right-hand sides).
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
@@ -108,18 +124,20 @@ struct CsrView {
 // r = f - L x.  DG(0): a = M + tau K, m = M.  DG(1): m = M, k0 = tau K, k1 = tau K / 3.
 // partial (nullable): one double per block with the block's sum of r^2 (deterministic
 // second stage by reduce_partials).  Returns the number of blocks via *nblocks.
+// N_t = slab columns of the call (all problems of a batch), seg = slabs per problem:
+// the history coupling is cut where a new problem starts (slab index % seg == 0).
 cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x,
-                         double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
+                         double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
-                         const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
+                         const double* x, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
 int residual_blocks(int nrows);
 // Double-float residual (FP64-accurate on the FP32 pipes): xs = x split into (hi, lo)
 // FP32 pairs by split_pairs, coefficient arrays as pairs; f, r and norms in FP64.
 cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st);
 cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const double* f, const float2* xs, double* r,
-                            int N_t, double* partial, int* nblocks, cudaStream_t st);
+                            int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
 cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
-                            const float2* xs, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st);
+                            const float2* xs, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
 // out[0] = sum of partial[0..n) in a fixed order.
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st);
 // out[0] = sum v^2 over n values (deterministic two-stage); partial has >= 1024 entries.
@@ -178,7 +196,8 @@ cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st);
 // Elementwise helpers.
 cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st);
 cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st);
-// Outer-product load f[e][n q + i] = c[n q + i] * b[e].
-cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, cudaStream_t st);
+// Outer-product load f[e * row_stride + j] = c[j] * b[e], j < ncols.
+cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, int row_stride,
+                       cudaStream_t st);
 
 }  // namespace stmg

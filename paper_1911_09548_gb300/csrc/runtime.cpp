@@ -42,7 +42,7 @@ struct CudaError {
 
 // Host-side tile and item lists of one factor (kept alive: the device view points at them).
 struct FactorLists {
-  std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu;
+  std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu, tfi, tfu, tbi, tbu;
 };
 
 #define CK(call)                                                    \
@@ -68,6 +68,7 @@ struct st_mg_s {
   double* stage_f = nullptr;           // host-buffer solve staging (allocated on first use)
   double* stage_x = nullptr;
   int q = 1;
+  int B = 1;                            // problems solved together (batch)
   std::vector<void*> allocs;
 
   template <typename T>
@@ -101,7 +102,8 @@ struct st_mg_s {
     int64_t* pxt_rowptr = nullptr; int32_t* pxt_col = nullptr; double* pxt_val = nullptr;
     SupernodalFactor<double> knF;
     DevFactor<double> kn;
-    FactorLists kn_lists;
+    DevFactor<double, float2> kn_df;      // the same factor as FP32 pairs (double-float solve)
+    FactorLists kn_lists, kn_df_lists;
     NDCoords ecoord, ncoord;
   };
   std::vector<Space> space;
@@ -140,7 +142,9 @@ struct st_mg_s {
   double* partial = nullptr;
   double* scalar = nullptr;
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
+  bool nodal_df = false;                // nodal K_n solve in double-float (every mode but FP64)
   int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
+  float2* tcP = nullptr;                // tensor-core split-K partials
   // captured V-cycle (replayed while f and x stay the same buffers)
   cudaGraphExec_t graph_exec = nullptr;
   const double* graph_f = nullptr;
@@ -277,6 +281,54 @@ void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>&
   D.h_bs_unit_off = Lh.bsu.data();
   D.max_items = max_items;
   D.n_sm = h.n_sm;
+  // tensor-core split-K items: the tiles above, each cut into kTcSplitK-wide K chunks
+  std::vector<int4> tfi, tfu, tbi, tbu;
+  Lh.tfi.assign(F.max_depth + 2, 0);
+  Lh.tfu.assign(F.max_depth + 2, 0);
+  Lh.tbi.assign(F.max_depth + 2, 0);
+  Lh.tbu.assign(F.max_depth + 2, 0);
+  int64_t max_tc = 0;
+  for (int d = 0; d <= F.max_depth; ++d) {
+    Lh.tfi[d] = (int64_t)tfi.size();
+    Lh.tfu[d] = (int64_t)tfu.size();
+    Lh.tbi[d] = (int64_t)tbi.size();
+    Lh.tbu[d] = (int64_t)tbu.size();
+    for (size_t s = 0; s < F.nodes.size(); ++s) {
+      const auto& a = F.nodes[s];
+      if (a.depth != d) continue;
+      const int m = a.nc + a.nr;
+      for (int rt = 0; rt * kSnBM < m; ++rt) {
+        const int r0 = rt * kSnBM;
+        const int kend = (r0 + kSnBM <= a.nc) ? r0 + kSnBM : a.nc;
+        const int first = (int)tfi.size();
+        for (int k0 = 0; k0 < kend; k0 += kTcSplitK)
+          tfi.push_back(make_int4((int)s, rt, k0, std::min(k0 + kTcSplitK, kend)));
+        tfu.push_back(make_int4((int)s, rt, first, (int)tfi.size()));
+      }
+      for (int rt = 0; rt * kSnBM < a.nc; ++rt) {
+        const int r0 = rt * kSnBM;
+        const int kbeg = (r0 / 32) * 32;   // the tensor-core stage width
+        const int first = (int)tbi.size();
+        for (int k0 = kbeg; k0 < m; k0 += kTcSplitK) tbi.push_back(make_int4((int)s, rt, k0, std::min(k0 + kTcSplitK, m)));
+        tbu.push_back(make_int4((int)s, rt, first, (int)tbi.size()));
+      }
+    }
+    max_tc = std::max<int64_t>(max_tc, (int64_t)tfi.size() - Lh.tfi[d]);
+    max_tc = std::max<int64_t>(max_tc, (int64_t)tbi.size() - Lh.tbi[d]);
+  }
+  Lh.tfi[F.max_depth + 1] = (int64_t)tfi.size();
+  Lh.tfu[F.max_depth + 1] = (int64_t)tfu.size();
+  Lh.tbi[F.max_depth + 1] = (int64_t)tbi.size();
+  Lh.tbu[F.max_depth + 1] = (int64_t)tbu.size();
+  D.tcf_items = h.upload(tfi);
+  D.tcf_units = h.upload(tfu);
+  D.tcb_items = h.upload(tbi);
+  D.tcb_units = h.upload(tbu);
+  D.h_tcf_item_off = Lh.tfi.data();
+  D.h_tcf_unit_off = Lh.tfu.data();
+  D.h_tcb_item_off = Lh.tbi.data();
+  D.h_tcb_unit_off = Lh.tbu.data();
+  D.max_tc_items = max_tc;
   D.nodes = h.upload(nodes);
   D.W = h.upload(convert_w<WT>(F.W));
   D.Dinv = h.upload(convert<DT>(F.Dinv));
@@ -306,13 +358,13 @@ void op_residual(Handle& h, int l, const double* f, const double* x, double* r, 
   if (h.df_residual) {
     CK(split_pairs(x, h.xsplit, L.len, h.stream));
     if (h.prob.degree == 0)
-      CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t, part, &nb, h.stream));
+      CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
     else
-      CK(residual_dg1_df(view(S), L.p0, L.p1, L.p2, f, h.xsplit, r, L.N_t, part, &nb, h.stream));
+      CK(residual_dg1_df(view(S), L.p0, L.p1, L.p2, f, h.xsplit, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
   } else if (h.prob.degree == 0) {
-    CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t, part, &nb, h.stream));
+    CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
   } else {
-    CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t, part, &nb, h.stream));
+    CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
   }
   if (norm_sq_host) {
     CK(reduce_partials(h.partial, nb, h.scalar, h.stream));
@@ -334,7 +386,7 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     float2* Q = static_cast<float2*>(h.sQ);
     CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
     CK(sn_solve_cplx_bf16(L.dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                          static_cast<float2*>(h.sP), cnt, h.ld_slab, h.tc_err, h.stream));
+                          static_cast<float2*>(h.sP), h.tcP, cnt, h.ld_slab, h.tc_err, h.stream));
     CK(slab_post_dg1f(Q, h.ld_slab, L.dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     return;
   }
@@ -391,23 +443,26 @@ void op_smooth_S(Handle& h, int l, const double* f, double* x) {
   auto& L = h.lv[l];
   double* r = level_r(h, l);
   op_residual(h, l, f, x, r, nullptr);
-  const int ld = L.N_t * h.q;
-  op_slab_cols(h, l, r, ld, 0, L.N_t, x, ld, 0, h.opt.omega, 1);
+  const int ld = L.N_t * h.B * h.q;
+  op_slab_cols(h, l, r, ld, 0, L.N_t * h.B, x, ld, 0, h.opt.omega, 1);
 }
 
 void op_grad_T(Handle& h, int l, const double* r, double* y) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  CK(grad_T(CsrView{S.nn, S.gt_rowptr, S.gt_col}, S.gt_sign_d, r, y, L.N_t * h.q, h.stream));
+  CK(grad_T(CsrView{S.nn, S.gt_rowptr, S.gt_col}, S.gt_sign_d, r, y, L.N_t * h.B * h.q, h.stream));
 }
 
 void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  const int ncols = L.N_t * h.q;
+  const int ncols = L.N_t * h.B * h.q;
   if (h.opt.nodal_solve == 0) {
     CK(gather_perm(y, ncols, S.kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
-    CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+    if (h.nodal_df)
+      CK(sn_solve_real_df(S.kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+    else
+      CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
     CK(scatter_perm(h.nQ, h.ld_nod, S.kn.iperm, S.nn, z, ncols, h.stream));
   } else {
     // damped Jacobi from z = 0, ping-pong through the nodal workspace
@@ -423,13 +478,14 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
 
 void op_time_integrate(Handle& h, int l, const double* z, double* w) {
   auto& L = h.lv[l];
-  CK(time_integrate(z, w, h.space[L.s].nn, L.N_t, h.prob.degree, h.stream));
+  // each problem's slabs of a node are one contiguous segment: nn * B independent scans
+  CK(time_integrate(z, w, h.space[L.s].nn * h.B, L.N_t, h.prob.degree, h.stream));
 }
 
 void op_grad_add(Handle& h, int l, const double* w, double* x) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  CK(grad_add(S.gtail_d, S.ghead_d, S.ne, w, x, L.N_t * h.q, h.stream));
+  CK(grad_add(S.gtail_d, S.ghead_d, S.ne, w, x, L.N_t * h.B * h.q, h.stream));
 }
 
 void op_correct_A(Handle& h, int l, const double* f, double* x) {
@@ -448,11 +504,11 @@ void op_restrict(Handle& h, int l, const double* r, double* rc) {
   auto& Sf = h.space[L.s];
   const int Nc = h.lv[l + 1].N_t;
   if (space_coarsened(h, l)) {
-    CK(time_restrict(r, h.tmp_fine, Sf.ne, Nc, h.prob.degree, h.stream));
-    CK(csr_spmm(CsrView{Sf.PxT.nrows, Sf.pxt_rowptr, Sf.pxt_col}, Sf.pxt_val, h.tmp_fine, rc, Nc * h.q, 0,
+    CK(time_restrict(r, h.tmp_fine, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
+    CK(csr_spmm(CsrView{Sf.PxT.nrows, Sf.pxt_rowptr, Sf.pxt_col}, Sf.pxt_val, h.tmp_fine, rc, Nc * h.B * h.q, 0,
                 h.stream));
   } else {
-    CK(time_restrict(r, rc, Sf.ne, Nc, h.prob.degree, h.stream));
+    CK(time_restrict(r, rc, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
   }
 }
 
@@ -461,10 +517,11 @@ void op_prolong_add(Handle& h, int l, const double* ec, double* x) {
   auto& Sf = h.space[L.s];
   const int Nc = h.lv[l + 1].N_t;
   if (space_coarsened(h, l)) {
-    CK(csr_spmm(CsrView{Sf.Px.nrows, Sf.px_rowptr, Sf.px_col}, Sf.px_val, ec, h.tmp_fine, Nc * h.q, 0, h.stream));
-    CK(time_prolong_add(h.tmp_fine, x, Sf.ne, Nc, h.prob.degree, h.stream));
+    CK(csr_spmm(CsrView{Sf.Px.nrows, Sf.px_rowptr, Sf.px_col}, Sf.px_val, ec, h.tmp_fine, Nc * h.B * h.q, 0,
+                h.stream));
+    CK(time_prolong_add(h.tmp_fine, x, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
   } else {
-    CK(time_prolong_add(ec, x, Sf.ne, Nc, h.prob.degree, h.stream));
+    CK(time_prolong_add(ec, x, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
   }
 }
 
@@ -472,9 +529,9 @@ void op_coarse_solve(Handle& h, const double* f, double* x) {
   const int l = (int)h.lv.size() - 1;
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  const int ld = L.N_t * h.q;
-  if (L.N_t == 1) {
-    op_slab_cols(h, l, f, ld, 0, 1, x, ld, 0, 1.0, 0);
+  const int ld = L.N_t * h.B * h.q;
+  if (L.N_t == 1) {   // one slab per problem: one solve over the batch
+    op_slab_cols(h, l, f, ld, 0, h.B, x, ld, 0, 1.0, 0);
     return;
   }
   for (int n = 0; n < L.N_t; ++n) {
@@ -578,6 +635,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.prob.sigma = H.sigma.data();
   H.stream = static_cast<cudaStream_t>(stream);
   H.q = pr->degree + 1;
+  H.B = pr->n_batch > 1 ? pr->n_batch : 1;
   H.host_only = host_only;
   if (!host_only) {
     CK(cudaGetDevice(&H.device));
@@ -701,7 +759,10 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   }
   for (size_t j = 0; j < rcs.size(); ++j)
     if (rcs[j]) return fail(rcs[j] == 6 ? ST_MG_ERR_NUMERIC : ST_MG_ERR_INVALID_ARG, "factorisation: " + errs[j]);
-  for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q;
+  if (H.B > 1 && H.lv.back().N_t != 1)
+    return fail(ST_MG_ERR_INVALID_ARG, "n_batch > 1 needs a hierarchy that coarsens time to one slab "
+                                       "(N_t a power of two, no max_levels cap)");
+  for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q * H.B;
   // slab_prec 1 (FP32) leaves the coarsest level in FP64; slab_prec 2 (double-float,
   // FP64-accurate) applies to every level
   for (size_t l = 0; l < H.lv.size(); ++l)
@@ -739,6 +800,10 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       S.pxt_val = H.upload(S.PxT.val);
     }
     make_dev_factor(H, S.knF, S.kn, S.kn_lists);
+    if (op->slab_prec != 0) {
+      make_dev_factor(H, S.knF, S.kn_df, S.kn_df_lists);
+      H.nodal_df = true;
+    }
     S.knF = SupernodalFactor<double>();   // host copy no longer needed
   }
   int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0, max_items = 0, max_kn_items = 0;
@@ -806,17 +871,17 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       max_u = std::max<int64_t>(max_u, L.fc.u_rows);
       L.fc = SupernodalFactor<cplx>();
     }
-    L.len = (int64_t)S.ne * L.N_t * H.q;
+    L.len = (int64_t)S.ne * L.N_t * H.q * H.B;
     if (l > 0) {
       L.f = H.dalloc<double>(L.len);
       L.x = H.dalloc<double>(L.len);
       L.r = H.dalloc<double>(L.len);
     }
     if (l + 1 < H.lv.size() && H.lv[l + 1].s != L.s)
-      max_len_fine_tmp = std::max<int64_t>(max_len_fine_tmp, (int64_t)S.ne * H.lv[l + 1].N_t * H.q);
+      max_len_fine_tmp = std::max<int64_t>(max_len_fine_tmp, (int64_t)S.ne * H.lv[l + 1].N_t * H.q * H.B);
     max_ne = std::max<int64_t>(max_ne, S.ne);
     max_nn = std::max<int64_t>(max_nn, S.nn);
-    max_nt = std::max(max_nt, L.N_t);
+    max_nt = std::max(max_nt, L.N_t * H.B);
     max_un = std::max<int64_t>(max_un, S.kn.u_rows);
   }
   const size_t esz = pr->degree == 0 ? sizeof(double) : sizeof(double2);
@@ -839,12 +904,17 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.nz = H.dalloc<double>(max_nn * H.ld_nod);
   H.nw = H.dalloc<double>(max_nn * H.ld_nod);
   H.tmp_fine = H.dalloc<double>(std::max<int64_t>(max_len_fine_tmp, 1));
-  H.g1 = H.dalloc<double>(max_ne * H.q);
+  H.g1 = H.dalloc<double>(max_ne * H.q * H.B);
   H.r0 = H.dalloc<double>(H.lv[0].len);
   if (H.df_residual) H.xsplit = H.dalloc<float2>(H.lv[0].len);
   if (op->slab_prec == 3) {
     H.tc_err = H.dalloc<int>(1);
     CK(cudaMemset(H.tc_err, 0, sizeof(int)));
+    int64_t mt = 1;
+    for (auto& L : H.lv)
+      if (L.prec == 3) mt = std::max<int64_t>(mt, L.dcb.max_tc_items);
+    const int64_t gy = (H.ld_slab + kTcCols - 1) / kTcCols;
+    H.tcP = H.dalloc<float2>(mt * gy * kSnBM * kTcCols);
   }
   H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
   H.scalar = H.dalloc<double>(1);
@@ -1036,7 +1106,13 @@ int st_mg_level_info(st_mg_t h, int32_t level, int32_t* space_level, int32_t* N_
 
 int st_mg_assemble_load(st_mg_t h, int32_t n_modes, const double* a, const double* k, const double* phase,
                         double* f_dev) {
+  return st_mg_assemble_load_batch(h, 0, n_modes, a, k, phase, f_dev);
+}
+
+int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const double* a, const double* k,
+                              const double* phase, double* f_dev) {
   if (int rc = check_dev(h)) return rc;
+  if (batch < 0 || batch >= h->B) return fail(ST_MG_ERR_INVALID_ARG, "batch index out of range");
   if (n_modes < 0 || (n_modes > 0 && (!a || !k || !phase))) return fail(ST_MG_ERR_INVALID_ARG, "bad load");
   if (int rc = check_ptrs({f_dev})) return rc;
   return guarded([&]() {
@@ -1060,7 +1136,8 @@ int st_mg_assemble_load(st_mg_t h, int32_t n_modes, const double* a, const doubl
     double* dc = H.dalloc<double>((int64_t)c.size());
     CK(cudaMemcpyAsync(db, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
     CK(cudaMemcpyAsync(dc, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
-    CK(outer_load(db, dc, f_dev, H.space[0].ne, L.N_t * H.q, H.stream));
+    const int seg = L.N_t * H.q;
+    CK(outer_load(db, dc, f_dev + (int64_t)batch * seg, H.space[0].ne, seg, seg * H.B, H.stream));
     CK(cudaStreamSynchronize(H.stream));
     // release the temporaries
     for (void* p : {static_cast<void*>(db), static_cast<void*>(dc)}) {
@@ -1088,8 +1165,9 @@ int st_mg_slab_solve(st_mg_t h, int32_t level, const double* r_dev, double* y_de
   if (int rc = check_level(h, level)) return rc;
   if (int rc = check_ptrs({r_dev, y_dev})) return rc;
   return guarded([&]() {
-    const int ld = h->lv[level].N_t * h->q;
-    op_slab_cols(*h, level, r_dev, ld, 0, h->lv[level].N_t, y_dev, ld, 0, 1.0, 0);
+    const int cols = h->lv[level].N_t * h->B;
+    const int ld = cols * h->q;
+    op_slab_cols(*h, level, r_dev, ld, 0, cols, y_dev, ld, 0, 1.0, 0);
     return check_tc(*h);
   });
 }
@@ -1269,8 +1347,8 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
   return guarded([&]() {
     Handle& H = *h;
     const auto& L = H.lv[level];
-    const int ne = H.space[L.s].ne, q = H.q, ld = L.N_t * q;
-    for (int n = 0; n < L.N_t; ++n) {
+    const int ne = H.space[L.s].ne, q = H.q, ld = L.N_t * H.B * q;
+    for (int n = 0; n < L.N_t * H.B; ++n) {
       if (q == 1) {
         std::vector<double> b(ne);
         for (int e = 0; e < ne; ++e) b[e] = r_host[(int64_t)e * ld + n];

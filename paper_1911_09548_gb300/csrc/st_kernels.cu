@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
                                                                  const double* __restrict__ f,
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
-                                                                 double* __restrict__ partial) {
+                                                                 double* __restrict__ partial, int seg) {
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -86,9 +86,10 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
         const double As = A0[j] + A1[j];
         const double up = __shfl_up_sync(FULL, As, 1, LPR);
         const double from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
-        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prevA = As;
         const int n = n0 + LPR * j + lane;
+        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
         if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
                                                                  const double* __restrict__ f,
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
-                                                                 double* __restrict__ partial) {
+                                                                 double* __restrict__ partial, int seg) {
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -148,9 +149,10 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
       for (int j = 0; j < SPL; ++j) {
         const double up = __shfl_up_sync(FULL, Mx[j], 1, LPR);
         const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
-        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prev = Mx[j];
         const int n = n0 + LPR * j + lane;
+        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
         if (valid && n < N_t) {
           const double rv = f[row * ld + n] - Ax[j] + c;
           r[row * ld + n] = rv;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
                                                                     const double* __restrict__ f,
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
-                                                                    double* __restrict__ partial) {
+                                                                    double* __restrict__ partial, int seg) {
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -243,9 +245,10 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
         const double As = a0 + a1;
         const double up = __shfl_up_sync(FULL, As, 1, LPR);
         const double from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
-        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prevA = As;
         const int n = n0 + LPR * j + lane;
+        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
         if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
                                                                     const double* __restrict__ f,
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
-                                                                    double* __restrict__ partial) {
+                                                                    double* __restrict__ partial, int seg) {
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -305,9 +308,10 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
         const double mx = dp_join(Mx[j]);
         const double up = __shfl_up_sync(FULL, mx, 1, LPR);
         const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
-        const double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prev = mx;
         const int n = n0 + LPR * j + lane;
+        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
         if (valid && n < N_t) {
           const double rv = f[row * ld + n] - dp_join(Ax[j]) + c;
           r[row * ld + n] = rv;
@@ -639,10 +643,10 @@ __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int
     b[i] = a[i];
 }
 __global__ void k_outer_load(const double* __restrict__ b, const double* __restrict__ c, double* __restrict__ f,
-                             int ncols) {
+                             int ncols, int row_stride) {
   const int e = blockIdx.x;
   const double be = b[e];
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * ncols + j] = c[j] * be;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * row_stride + j] = c[j] * be;
 }
 
 // FP64 pipe throughput probe: eight independent FMA chains per thread.
@@ -693,14 +697,14 @@ int lanes_per_row(int N_t) {
   } while (0)
 
 cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x, double* r,
-                         int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg0, A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial);
+                         int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
+  STMG_RES_DISPATCH(k_residual_dg0, A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
-                         const double* x, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg1, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial);
+                         const double* x, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
+  STMG_RES_DISPATCH(k_residual_dg1, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
@@ -715,14 +719,14 @@ cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st)
 }
 
 cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const double* f, const float2* xs, double* r,
-                            int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg0_df, A.nrows, A.rowptr, A.col, a, m, f, xs, r, N_t, partial);
+                            int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
+  STMG_RES_DISPATCH(k_residual_dg0_df, A.nrows, A.rowptr, A.col, a, m, f, xs, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
 cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
-                            const float2* xs, double* r, int N_t, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg1_df, A.nrows, A.rowptr, A.col, m, k0, k1, f, xs, r, N_t, partial);
+                            const float2* xs, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
+  STMG_RES_DISPATCH(k_residual_dg1_df, A.nrows, A.rowptr, A.col, m, k0, k1, f, xs, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
@@ -833,8 +837,9 @@ cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st) {
   if (n > 0) { k_copy<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(a, b, n); count_launches(1); }
   return cudaGetLastError();
 }
-cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, cudaStream_t st) {
-  if (nrows > 0) { k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols); count_launches(1); }
+cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, int row_stride,
+                       cudaStream_t st) {
+  if (nrows > 0) { k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols, row_stride); count_launches(1); }
   return cudaGetLastError();
 }
 

@@ -126,24 +126,36 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-template <bool FWD>
+// SPLIT = false: one (node, row tile) per block, whole K range, epilogue in place.
+// SPLIT = true: one item (node, row tile, k0, k1) per block; the FP32 partial
+// product goes to P[item, column tile] for k_sn_tc_reduce.
+template <bool FWD, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict__ nodes,
                                                       const __nv_bfloat162* __restrict__ W,
                                                       const float2* __restrict__ Dinv,
                                                       const int32_t* __restrict__ gsrc,
                                                       const int32_t* __restrict__ rows,
-                                                      const int2* __restrict__ tiles, const float2* __restrict__ Q,
+                                                      const int2* __restrict__ tiles, const int4* __restrict__ items,
+                                                      const float2* __restrict__ Q,
                                                       float2* __restrict__ Z, float2* __restrict__ U,
-                                                      float2* __restrict__ X, int nrhs, int ld, int* __restrict__ err) {
+                                                      float2* __restrict__ X, float2* __restrict__ P, int nrhs, int ld,
+                                                      int* __restrict__ err) {
   __shared__ __align__(1024) uint8_t As[A_BYTES];
   __shared__ __align__(1024) uint8_t Bs[B_BYTES];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int2 tl = tiles[blockIdx.x];
-  const DevNode nd = nodes[tl.x];
+  int node, rtile, ik0 = 0, ik1 = 0;
+  if (SPLIT) {
+    const int4 it = items[blockIdx.x];
+    node = it.x; rtile = it.y; ik0 = it.z; ik1 = it.w;
+  } else {
+    const int2 tl = tiles[blockIdx.x];
+    node = tl.x; rtile = tl.y;
+  }
+  const DevNode nd = nodes[node];
   const int nc = nd.nc, m = nd.nc + nd.nr;
-  const int row0 = tl.y * TC_ROWS, c0 = blockIdx.y * TC_N;
+  const int row0 = rtile * TC_ROWS, c0 = blockIdx.y * TC_N;
   const __nv_bfloat162* Ws = W + nd.w_off;
   const int32_t* gs = gsrc + nd.g_off * 2;
   const int32_t* rw = rows + nd.row_off;
@@ -159,7 +171,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict_
   // last row; backward rows start where L11^{-1} has its first nonzero
   const int rows_out = FWD ? m : nc;
   int kbeg, kend;
-  if (FWD) {
+  if (SPLIT) {
+    kbeg = ik0;
+    kend = ik1;
+  } else if (FWD) {
     kbeg = 0;
     kend = (row0 + TC_ROWS <= nc) ? row0 + TC_ROWS : nc;
   } else {
@@ -226,6 +241,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict_
         const float mine = __uint_as_float(v[j]);
         const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
         const int c = c0 + cb + j;
+        if (SPLIT) {
+          if (even)
+            P[(((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_ROWS + (R >> 1)) * TC_N + cb + j] =
+                make_float2(mine, other);
+          continue;
+        }
         if (!even || c >= nrhs || i >= rows_out) continue;
         const float2 y = make_float2(mine, other);
         if (FWD) {
@@ -249,15 +270,75 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict_
   if (warp == 0) tmem_dealloc(tmem);
 }
 
+// One block per (unit = node row tile, column tile): sums the unit's K-chunk
+// partials in item order, then the forward or backward epilogue.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict__ nodes,
+                                                      const float2* __restrict__ Dinv,
+                                                      const int32_t* __restrict__ gsrc,
+                                                      const int4* __restrict__ units, int64_t item_base,
+                                                      int64_t n_items, const float2* __restrict__ P,
+                                                      float2* __restrict__ Z, float2* __restrict__ U,
+                                                      float2* __restrict__ X, int nrhs, int ld) {
+  const int4 un = units[blockIdx.x];
+  const DevNode nd = nodes[un.x];
+  const int nc = nd.nc, m = nd.nc + nd.nr;
+  const int row0 = un.y * TC_ROWS, c0 = blockIdx.y * TC_N;
+  const int rows_out = FWD ? m : nc;
+  for (int t = threadIdx.x; t < TC_ROWS * TC_N; t += blockDim.x) {
+    const int il = t / TC_N, cl = t % TC_N;
+    const int i = row0 + il, c = c0 + cl;
+    if (i >= rows_out || c >= nrhs) continue;
+    float2 y = make_float2(0.f, 0.f);
+    for (int q = un.z; q < un.w; ++q)
+      y = cadd(y, P[(((int64_t)blockIdx.y * n_items + (q - item_base)) * TC_ROWS + il) * TC_N + cl]);
+    if (FWD) {
+      if (i < nc) {
+        Z[(int64_t)(nd.col0 + i) * ld + c] = cmul(Dinv[nd.col0 + i], y);
+      } else {
+        const int32_t* gs = gsrc + nd.g_off * 2;
+        const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
+        if (s0 >= 0) y = cadd(y, U[(int64_t)s0 * ld + c]);
+        if (s1 >= 0) y = cadd(y, U[(int64_t)s1 * ld + c]);
+        U[(int64_t)(nd.u_off + i - nc) * ld + c] = y;
+      }
+    } else {
+      X[(int64_t)(nd.col0 + i) * ld + c] = y;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
+                              float2* U, float2* P, int nrhs, int ld, int* err, cudaStream_t st) {
+  const int64_t* io = fwd ? F.h_tcf_item_off : F.h_tcb_item_off;
+  const int64_t* uo = fwd ? F.h_tcf_unit_off : F.h_tcb_unit_off;
+  const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
+  if (ib <= ia) return cudaSuccess;
+  const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
+  if (fwd) {
+    k_sn_tc<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
+        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcf_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
+    k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
+                                                                         ia, ib - ia, P, Z, U, Q, nrhs, ld);
+  } else {
+    k_sn_tc<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
+        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcb_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
+    k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
+                                                                          ia, ib - ia, P, Z, U, Q, nrhs, ld);
+  }
+  count_launches(2);
+  return cudaGetLastError();
+}
 
 cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
                           int nrhs, int ld, int* err, cudaStream_t st) {
   const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
   if (b > a) {
     const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
-    k_sn_tc<true><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.rows,
-                                                                       F.fwd_tiles + a, Q, Z, U, Q, nrhs, ld, err);
+    k_sn_tc<true, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(
+        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, F.fwd_tiles + a, nullptr, Q, Z, U, Q, nullptr, nrhs, ld, err);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -268,8 +349,8 @@ cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, fl
   const int64_t a = F.h_bwd_off[d], b = F.h_bwd_off[d + 1];
   if (b > a) {
     const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
-    k_sn_tc<false><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.rows,
-                                                                        F.bwd_tiles + a, Q, Z, U, Q, nrhs, ld, err);
+    k_sn_tc<false, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(
+        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, F.bwd_tiles + a, nullptr, Q, Z, U, Q, nullptr, nrhs, ld, err);
     count_launches(1);
   }
   return cudaGetLastError();

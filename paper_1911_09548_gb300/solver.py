@@ -12,8 +12,9 @@ from . import binding as B
 
 class SpaceTimeSolver:
     def __init__(self, n_cube, nu, sigma, T, N_t, degree, n_space_levels=1, stream=None, host_only=False,
-                 **options):
-        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree)
+                 n_batch=1, **options):
+        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch)
+        self.n_batch = n_batch
         self.opt = B.st_mg_default_options()
         for k, v in options.items():
             if not hasattr(self.opt, k):
@@ -48,16 +49,16 @@ class SpaceTimeSolver:
     def level_shape(self, level=0, nodal=False):
         L = self.levels[level]
         rows = L["n_node"] if nodal else L["n_edge"]
-        return (rows, L["N_t"] * self.q)
+        return (rows, self.n_batch * L["N_t"] * self.q)
 
     def zeros(self, level=0, nodal=False):
         import torch
         return torch.zeros(self.level_shape(level, nodal), dtype=torch.float64, device="cuda")
 
     # ---- C-ABI calls
-    def load(self, exc, f=None):
+    def load(self, exc, f=None, batch=0):
         f = self.zeros() if f is None else f
-        B.st_mg_assemble_load(self.h, exc["a"], exc["k"], exc["phase"], f)
+        B.st_mg_assemble_load_batch(self.h, batch, exc["a"], exc["k"], exc["phase"], f)
         return f
 
     def residual(self, f, x, r=None, level=0, want_norm=False):

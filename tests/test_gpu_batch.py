@@ -1,0 +1,89 @@
+"""Batched solves (n_batch > 1): several excitations on one mesh and time grid in one
+handle, every kernel running over all problems' slabs at once.  Each problem of the
+batch must behave exactly as if it were solved alone (the history coupling and the
+time transfers never cross problem boundaries), and reach the oracle's solution."""
+import numpy as np
+import pytest
+
+import st_inputs
+from helpers import from_lib, oracle_mg, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.spacetime import sequential_solve  # noqa: E402
+
+CASES = {
+    "dg1": (8, 1, 16, "two_material", dict(nu_pre=2, nu_post=2)),
+    "dg0": (4, 0, 16, "unit", dict()),
+    "dg1_df": (8, 1, 16, "two_material", dict(slab_prec=2)),
+    "dg1_bf16": (8, 1, 64, "two_material", dict(slab_prec=3)),
+}
+NB = 3
+
+
+@pytest.fixture(scope="module")
+def stmg():
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300
+    return paper_1911_09548_gb300
+
+
+def cols(x, b, N_t, q):
+    """Problem b's block of a batched vector (rows = edges)."""
+    return x[:, b * N_t * q:(b + 1) * N_t * q]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_batch_equals_separate_solves(stmg, name):
+    n, p, N_t, mat, opts = CASES[name]
+    q = p + 1
+    nu, sigma = st_inputs.materials(n, mat, 2)
+    SB = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, n_batch=NB, **opts)
+    fb = SB.zeros()
+    for b in range(NB):
+        SB.load(st_inputs.excitation(30 + b), f=fb, batch=b)
+    xb = SB.zeros()
+    for _ in range(2):
+        SB.vcycle(fb, xb)
+    torch.cuda.synchronize()
+    XB, FB = xb.cpu().numpy(), fb.cpu().numpy()
+    S1 = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, **opts)
+    for b in range(NB):
+        f1 = S1.load(st_inputs.excitation(30 + b))
+        assert np.array_equal(f1.cpu().numpy(), cols(FB, b, N_t, q))
+        x1 = S1.zeros()
+        for _ in range(2):
+            S1.vcycle(f1, x1)
+        torch.cuda.synchronize()
+        tol = 1e-5 if opts.get("slab_prec", 0) == 3 else 1e-12
+        assert rel(cols(XB, b, N_t, q), x1.cpu().numpy()) < tol
+    S1.close()
+    SB.close()
+
+
+@pytest.mark.parametrize("name", ["dg1", "dg0"])
+def test_batch_solve_reaches_time_stepping(stmg, name):
+    n, p, N_t, mat, opts = CASES[name]
+    q = p + 1
+    nu, sigma = st_inputs.materials(n, mat, 2)
+    SB = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, n_batch=NB, **opts)
+    fb = SB.zeros()
+    for b in range(NB):
+        SB.load(st_inputs.excitation(40 + b), f=fb, batch=b)
+    xb = SB.zeros()
+    out = SB.solve(fb, xb, rtol=1e-10, maxit=40)
+    assert out["status"] == 0
+    sl, tl, mg = oracle_mg(n, 1, nu, sigma, 1.0, N_t, p)
+    XB, FB = xb.cpu().numpy(), fb.cpu().numpy()
+    for b in range(NB):
+        xs = sequential_solve(mg.slabs[0], from_lib(cols(FB, b, N_t, q).copy(), q))
+        assert rel(from_lib(cols(XB, b, N_t, q).copy(), q), xs) < 1e-8
+    SB.close()
+
+
+def test_batch_rejects_hierarchy_without_single_slab(stmg):
+    nu, sigma = st_inputs.materials(4, "unit")
+    with pytest.raises(stmg.StMgError):
+        stmg.SpaceTimeSolver(4, nu, sigma, 1.0, 16, 0, n_batch=2, max_levels=2)
