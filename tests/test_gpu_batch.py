@@ -57,7 +57,10 @@ def test_batch_equals_separate_solves(stmg, name):
         for _ in range(2):
             S1.vcycle(f1, x1)
         torch.cuda.synchronize()
-        tol = 1e-5 if opts.get("slab_prec", 0) == 3 else 1e-12
+        # BF16: batched and single runs split K differently (different column-tile
+        # counts), and a last-bit FP32 difference can flip a later BF16 rounding of an
+        # intermediate (2^-8 relative), so they agree to BF16 level only
+        tol = 2e-3 if opts.get("slab_prec", 0) == 3 else 1e-12
         assert rel(cols(XB, b, N_t, q), x1.cpu().numpy()) < tol
     S1.close()
     SB.close()
