@@ -218,6 +218,15 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
  * library are bound by this pipe, so it is the roof their efficiency is quoted against. */
 int st_mg_probe_fp64(st_mg_t h, double* tflops);
 
+/* Per-problem l2 norms of a finest-level vector of a batched handle (e.g. r from
+ * st_mg_residual): norms_host[b] = ||v_b||_2 for b < n_batch, deterministic order
+ * (blocking).  Lets a caller stop or replace problems of a batch independently. */
+int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host);
+
+/* Zero problem `batch`'s entries of a finest-level vector (e.g. to start a new problem
+ * in a freed slot of a batch while the other problems keep iterating). */
+int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);
 

@@ -62,6 +62,8 @@ _SIGS = {
     "st_mg_debug_get": [_vp, _i32, _i32, _vp, _P(_i64)],
     "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
     "st_mg_probe_fp64": [_vp, _P(_dbl)],
+    "st_mg_batch_norms": [_vp, _vp, _P(_dbl)],
+    "st_mg_batch_zero": [_vp, _i32, _vp],
     "st_mg_launch_count": [_P(_i64)],
     "st_mg_factor_stats": [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)],
     "st_mg_norm2_noalloc": [_vp, _i64, _vp, _vp],
@@ -265,6 +267,16 @@ def st_mg_probe_fp64(h) -> float:
     t = _dbl()
     _check(lib().st_mg_probe_fp64(_vp(h), ctypes.byref(t)), "st_mg_probe_fp64")
     return t.value
+
+
+def st_mg_batch_norms(h, v_dev, n_batch):
+    out = np.zeros(n_batch)
+    _check(lib().st_mg_batch_norms(_vp(h), _vp(_addr(v_dev)), _dptr(out)), "st_mg_batch_norms")
+    return out
+
+
+def st_mg_batch_zero(h, batch, v_dev):
+    _check(lib().st_mg_batch_zero(_vp(h), batch, _vp(_addr(v_dev))), "st_mg_batch_zero")
 
 
 def st_mg_launch_count() -> int:

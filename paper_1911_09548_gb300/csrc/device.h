@@ -59,7 +59,20 @@ struct DevFactor {
   int64_t* h_tcb_item_off = nullptr;
   int64_t* h_tcb_unit_off = nullptr;
   int64_t max_tc_items = 0;
+  // pipelined tensor-core path: the factor blocks pre-laid-out as 16 KiB tiles in the
+  // shared-memory operand format (forward and transposed), per-node tile metadata and,
+  // per depth, the (node, k stage) list of right-hand-side tiles to assemble
+  uint8_t* tw_f = nullptr;            // forward A tiles
+  uint8_t* tw_b = nullptr;            // backward A tiles
+  int4* tnode = nullptr;              // per node: (fwd tile base, fwd k stages, bwd tile base, bwd k stages)
+  int2* tpre = nullptr;               // per node: prefix of k stages over its depth (fwd, bwd)
+  int2* tas_f = nullptr;              // per depth: (node, k stage) pairs
+  int2* tas_b = nullptr;
+  int64_t* h_tas_f_off = nullptr;
+  int64_t* h_tas_b_off = nullptr;
+  int64_t max_stage_tiles = 0;        // largest per-depth sum of k stages (fwd or bwd)
 };
+constexpr int kTcTileBytes = 16384;   // one operand tile: 128 real rows x 64 real K of BF16
 constexpr int kTcSplitK = 256;      // complex K columns per tensor-core split-K item
 
 // Split-K path: rows per item, columns per item, and the largest right-hand-side
@@ -98,11 +111,16 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
 // the split-K kernels.  err: device int set to 1 if a tensor-core wait timed out.
 constexpr int kTcCols = 128;
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, float2* Ptc, int nrhs, int ld, int* err, cudaStream_t st);
+                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err, cudaStream_t st);
 cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
                           int nrhs, int ld, int* err, cudaStream_t st);
 cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
                            int nrhs, int ld, int* err, cudaStream_t st);
+// Pipelined tensor-core depth: assemble the right-hand-side tiles of the depth into
+// Bst (gy * max_stage_tiles tiles), then the products with bulk-copied operand tiles.
+cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
+                         float2* Z, float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err,
+                         cudaStream_t st);
 // Split-K tensor-core depth: partial products of K chunks into P (max_tc_items *
 // ceil(nrhs / kTcCols) * kSnBM * kTcCols float2), then a fixed-order reduction + epilogue.
 cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
@@ -191,6 +209,13 @@ cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* ou
 // Coarse forward substitution: g[e][i] = f[e][n q + i] - sum_j N_t[i][j] (M x_{n-1})_j.
 cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t,
                         int n, int degree, cudaStream_t st);
+// Per-problem sums of squares of a batched finest-level vector (v[e][b * seg + j]);
+// partial: batch_norm_scratch(nb) doubles; out: nb doubles (device).
+int batch_norm_scratch(int nb);
+cudaError_t batch_norms_sq(const double* v, int nrows, int nb, int seg, double* partial, double* out,
+                           cudaStream_t st);
+// Zero columns [offset, offset + count) of every row (row length stride).
+cudaError_t zero_cols(double* v, int nrows, int stride, int offset, int count, cudaStream_t st);
 // FP64 FMA throughput probe: blocks x 256 threads x iters x 8 FMAs (out: >= blocks doubles).
 cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st);
 // Elementwise helpers.

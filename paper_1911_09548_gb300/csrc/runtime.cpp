@@ -42,7 +42,7 @@ struct CudaError {
 
 // Host-side tile and item lists of one factor (kept alive: the device view points at them).
 struct FactorLists {
-  std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu, tfi, tfu, tbi, tbu;
+  std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu, tfi, tfu, tbi, tbu, asf, asb;
 };
 
 #define CK(call)                                                    \
@@ -145,6 +145,9 @@ struct st_mg_s {
   bool nodal_df = false;                // nodal K_n solve in double-float (every mode but FP64)
   int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
   float2* tcP = nullptr;                // tensor-core split-K partials
+  uint8_t* tcB = nullptr;               // tensor-core right-hand-side tiles of one depth
+  double* bn_partial = nullptr;         // per-problem norm scratch
+  double* bn_out = nullptr;
   // captured V-cycle (replayed while f and x stay the same buffers)
   cudaGraphExec_t graph_exec = nullptr;
   const double* graph_f = nullptr;
@@ -205,6 +208,94 @@ std::vector<WT> convert_w(const std::vector<T>& v) {
   if constexpr (std::is_same<WT, float2>::value && std::is_same<T, double>::value) return convert_pairs<float2>(v);
   else if constexpr (std::is_same<WT, float4>::value) return convert_pairs<float4>(v);
   else return convert<WT>(v);
+}
+
+// byte offset of element (row, k) in a 128 x 64 BF16 operand tile, K-major core
+// matrices of 8 rows x 16 bytes (128 B between K-adjacent cores, 1024 B between
+// 8-row groups) -- the layout the tensor-core kernels read with one descriptor
+inline size_t tile_off(int row, int k) {
+  return (size_t)(row >> 3) * 1024 + (size_t)(k >> 3) * 128 + (size_t)(row & 7) * 16 + (size_t)(k & 7) * 2;
+}
+
+inline uint16_t bf16_bits(float v) {
+  __nv_bfloat16 b = __float2bfloat16_rn(v);
+  uint16_t u;
+  std::memcpy(&u, &b, 2);
+  return u;
+}
+
+// Tensor-core operand tiles of a complex factor: for node s, forward tile (rt, ks)
+// holds W rows 64 rt .. 64 rt + 63 and columns 32 ks .. 32 ks + 31, each complex
+// entry a + ib as the real block [[a, -b], [b, a]]; backward tile (rt, ks) holds the
+// same for W^T (rows of W^T = columns of W).  Zero outside the node's block.
+void build_tc_tiles(Handle& h, const SupernodalFactor<cplx>& F, DevFactor<float2, __nv_bfloat162>& D,
+                    FactorLists& Lh) {
+  const size_t TB = kTcTileBytes;
+  std::vector<int4> tnode(F.nodes.size());
+  std::vector<int2> tpre(F.nodes.size());
+  int64_t nf = 0, nb = 0;
+  for (size_t s = 0; s < F.nodes.size(); ++s) {
+    const auto& a = F.nodes[s];
+    const int m = a.nc + a.nr;
+    const int rtf = (m + 63) / 64, ksf = (a.nc + 31) / 32, rtb = (a.nc + 63) / 64, ksb = (m + 31) / 32;
+    tnode[s] = make_int4((int)nf, ksf, (int)nb, ksb);
+    nf += (int64_t)rtf * ksf;
+    nb += (int64_t)rtb * ksb;
+  }
+  std::vector<uint8_t> tf((size_t)nf * TB, 0), tb((size_t)nb * TB, 0);
+  auto put = [&](uint8_t* tile, int i, int k, cplx w) {
+    const uint16_t re = bf16_bits((float)w.re), im = bf16_bits((float)w.im), nim = bf16_bits(-(float)w.im);
+    std::memcpy(tile + tile_off(2 * i, 2 * k), &re, 2);
+    std::memcpy(tile + tile_off(2 * i, 2 * k + 1), &nim, 2);
+    std::memcpy(tile + tile_off(2 * i + 1, 2 * k), &im, 2);
+    std::memcpy(tile + tile_off(2 * i + 1, 2 * k + 1), &re, 2);
+  };
+  for (size_t s = 0; s < F.nodes.size(); ++s) {
+    const auto& a = F.nodes[s];
+    const int nc = a.nc, m = nc + a.nr;
+    const cplx* W = F.W.data() + a.w_off;
+    const int4 tn = tnode[s];
+    for (int r = 0; r < m; ++r)
+      for (int k = 0; k < nc; ++k) {
+        const cplx w = W[(int64_t)r * nc + k];
+        if (w.re == 0.0 && w.im == 0.0) continue;
+        uint8_t* t = tf.data() + ((size_t)tn.x + (size_t)(r / 64) * tn.y + (k / 32)) * TB;
+        put(t, r % 64, k % 32, w);
+        // backward: row k of W^T (k < nc), column r
+        uint8_t* u = tb.data() + ((size_t)tn.z + (size_t)(k / 64) * tn.w + (r / 32)) * TB;
+        put(u, k % 64, r % 32, w);
+      }
+  }
+  // per depth: prefix of k stages and the (node, k stage) assembly lists
+  std::vector<int2> asf, asb;
+  Lh.asf.assign(F.max_depth + 2, 0);
+  Lh.asb.assign(F.max_depth + 2, 0);
+  int64_t max_stage = 0;
+  for (int d = 0; d <= F.max_depth; ++d) {
+    Lh.asf[d] = (int64_t)asf.size();
+    Lh.asb[d] = (int64_t)asb.size();
+    int pf = 0, pb = 0;
+    for (size_t s = 0; s < F.nodes.size(); ++s) {
+      if (F.nodes[s].depth != d) continue;
+      tpre[s] = make_int2(pf, pb);
+      for (int ks = 0; ks < tnode[s].y; ++ks) asf.push_back(make_int2((int)s, ks));
+      for (int ks = 0; ks < tnode[s].w; ++ks) asb.push_back(make_int2((int)s, ks));
+      pf += tnode[s].y;
+      pb += tnode[s].w;
+    }
+    max_stage = std::max<int64_t>(max_stage, std::max(pf, pb));
+  }
+  Lh.asf[F.max_depth + 1] = (int64_t)asf.size();
+  Lh.asb[F.max_depth + 1] = (int64_t)asb.size();
+  D.tw_f = h.upload(tf);
+  D.tw_b = h.upload(tb);
+  D.tnode = h.upload(tnode);
+  D.tpre = h.upload(tpre);
+  D.tas_f = h.upload(asf);
+  D.tas_b = h.upload(asb);
+  D.h_tas_f_off = Lh.asf.data();
+  D.h_tas_b_off = Lh.asb.data();
+  D.max_stage_tiles = max_stage;
 }
 
 template <typename T, typename DT, typename WT>
@@ -386,7 +477,7 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     float2* Q = static_cast<float2*>(h.sQ);
     CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
     CK(sn_solve_cplx_bf16(L.dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                          static_cast<float2*>(h.sP), h.tcP, cnt, h.ld_slab, h.tc_err, h.stream));
+                          static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, h.tc_err, h.stream));
     CK(slab_post_dg1f(Q, h.ld_slab, L.dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     return;
   }
@@ -857,6 +948,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
         L.w_bytes = (int64_t)L.fc.W.size() * 8;
       } else if (L.prec == 3) {
         make_dev_factor(H, L.fc, L.dcb, L.lists);
+        build_tc_tiles(H, L.fc, L.dcb, L.lists);
         max_items = std::max<int64_t>(max_items, L.dcb.max_items);
         L.w_bytes = (int64_t)L.fc.W.size() * 4;
       } else if (L.prec == 2) {
@@ -915,7 +1007,13 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       if (L.prec == 3) mt = std::max<int64_t>(mt, L.dcb.max_tc_items);
     const int64_t gy = (H.ld_slab + kTcCols - 1) / kTcCols;
     H.tcP = H.dalloc<float2>(mt * gy * kSnBM * kTcCols);
+    int64_t ms = 1;
+    for (auto& L : H.lv)
+      if (L.prec == 3) ms = std::max<int64_t>(ms, L.dcb.max_stage_tiles);
+    H.tcB = H.dalloc<uint8_t>(ms * gy * kTcTileBytes);
   }
+  H.bn_partial = H.dalloc<double>(batch_norm_scratch(H.B));
+  H.bn_out = H.dalloc<double>(H.B);
   H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
   H.scalar = H.dalloc<double>(1);
   CK(cudaDeviceSynchronize());
@@ -1389,6 +1487,34 @@ int st_mg_probe_fp64(st_mg_t h, double* tflops) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *tflops = 2.0 * 8.0 * iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host) {
+  if (int rc = check_dev(h)) return rc;
+  if (!norms_host) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  if (int rc = check_ptrs({v_dev})) return rc;
+  return guarded([&]() {
+    Handle& H = *h;
+    const int seg = H.lv[0].N_t * H.q;
+    CK(batch_norms_sq(v_dev, H.space[0].ne, H.B, seg, H.bn_partial, H.bn_out, H.stream));
+    std::vector<double> sq(H.B);
+    CK(cudaMemcpyAsync(sq.data(), H.bn_out, H.B * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
+    CK(cudaStreamSynchronize(H.stream));
+    for (int b = 0; b < H.B; ++b) norms_host[b] = std::sqrt(sq[b]);
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev) {
+  if (int rc = check_dev(h)) return rc;
+  if (batch < 0 || batch >= h->B) return fail(ST_MG_ERR_INVALID_ARG, "batch index out of range");
+  if (int rc = check_ptrs({v_dev})) return rc;
+  return guarded([&]() {
+    Handle& H = *h;
+    const int seg = H.lv[0].N_t * H.q;
+    CK(zero_cols(v_dev, H.space[0].ne, seg * H.B, batch * seg, seg, H.stream));
     return ST_MG_OK;
   });
 }

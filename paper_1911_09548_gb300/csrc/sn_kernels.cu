@@ -518,7 +518,7 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
   return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, st);
 }
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, float2* Ptc, int nrhs, int ld, int* err, cudaStream_t st) {
+                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs <= 2) return sn_solve_skinny<PolBF16C, 2>(F, Q, Z, U, P, nrhs, ld, st);
   if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, st);
@@ -528,14 +528,12 @@ cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t tiles = F.h_fwd_off[d + 1] - F.h_fwd_off[d];
     if (tiles <= 0) continue;
-    if (tiles * gy < two_waves) sn_tc_split_depth(F, d, true, Q, Z, U, Ptc, nrhs, ld, err, st);
-    else sn_tc_forward(F, d, Q, Z, U, nrhs, ld, err, st);
+    sn_tc2_depth(F, d, true, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, err, st);
   }
   for (int d = 0; d <= F.max_depth; ++d) {
     const int64_t tiles = F.h_bwd_off[d + 1] - F.h_bwd_off[d];
     if (tiles <= 0) continue;
-    if (tiles * gy < two_waves) sn_tc_split_depth(F, d, false, Q, Z, U, Ptc, nrhs, ld, err, st);
-    else sn_tc_backward(F, d, Q, Z, U, nrhs, ld, err, st);
+    sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, err, st);
   }
   return cudaGetLastError();
 }

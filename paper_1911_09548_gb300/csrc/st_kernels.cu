@@ -649,6 +649,31 @@ __global__ void k_outer_load(const double* __restrict__ b, const double* __restr
   for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * row_stride + j] = c[j] * be;
 }
 
+// Per-problem sums of squares of a batched vector v[e][b * seg + j]: block (x, b)
+// sums rows x, x + gridDim.x, ... of problem b in a fixed order.
+__global__ void k_batch_norm_partial(const double* __restrict__ v, int nrows, int nb, int seg,
+                                     double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  double s = 0.0;
+  for (int e = blockIdx.x; e < nrows; e += gridDim.x) {
+    const double* row = v + ((int64_t)e * nb + b) * seg;
+    for (int j = threadIdx.x; j < seg; j += blockDim.x) s = fma(row[j], row[j], s);
+  }
+  block_sum_store<256>(s, partial + (int64_t)b * gridDim.x + blockIdx.x);
+}
+
+__global__ void k_batch_norm_final(const double* __restrict__ partial, int g, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < g; i += blockDim.x) s += partial[(int64_t)blockIdx.x * g + i];
+  block_sum_store<256>(s, out + blockIdx.x);
+}
+
+// v[e * stride + offset + j] = 0 for j < count (one problem's columns of a batched vector)
+__global__ void k_zero_cols(double* __restrict__ v, int nrows, int stride, int offset, int count) {
+  for (int e = blockIdx.x; e < nrows; e += gridDim.x)
+    for (int j = threadIdx.x; j < count; j += blockDim.x) v[(int64_t)e * stride + offset + j] = 0.0;
+}
+
 // FP64 pipe throughput probe: eight independent FMA chains per thread.
 __global__ void k_fp64_probe(double* out, int iters, double a, double b) {
   double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
@@ -705,6 +730,25 @@ cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const doub
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
                          const double* x, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
   STMG_RES_DISPATCH(k_residual_dg1, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial, seg);
+  return cudaGetLastError();
+}
+
+constexpr int BATCH_NORM_BLOCKS = 256;
+int batch_norm_scratch(int nb) { return nb * BATCH_NORM_BLOCKS; }
+
+cudaError_t batch_norms_sq(const double* v, int nrows, int nb, int seg, double* partial, double* out,
+                           cudaStream_t st) {
+  if (nrows <= 0 || nb <= 0) return cudaSuccess;
+  { k_batch_norm_partial<<<dim3(BATCH_NORM_BLOCKS, nb), 256, 0, st>>>(v, nrows, nb, seg, partial); count_launches(1); }
+  { k_batch_norm_final<<<nb, 256, 0, st>>>(partial, BATCH_NORM_BLOCKS, out); count_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t zero_cols(double* v, int nrows, int stride, int offset, int count, cudaStream_t st) {
+  if (nrows > 0 && count > 0) {
+    k_zero_cols<<<(unsigned)std::min(nrows, 4096), 128, 0, st>>>(v, nrows, stride, offset, count);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ constexpr int A_BYTES = TC_M * 2 * TC_KC * 2;   // 16 KiB
 constexpr int B_BYTES = TC_N * 2 * TC_KC * 2;   // 16 KiB
 constexpr uint32_t CORE_K = 128;          // bytes between K-adjacent core matrices
 constexpr uint32_t CORE_MN = 1024;        // bytes between 8-row groups (8 cores along K)
-constexpr int WAIT_LIMIT = 1 << 26;
+constexpr int WAIT_LIMIT = 1 << 20;       // try_wait rounds before a wait gives up (well under a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -308,7 +308,274 @@ __global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict_
   }
 }
 
+// ---------------------------------------------------------------- pipelined path
+// The factor's operand tiles are stored in global memory already in the shared-memory
+// layout above (16 KiB per 64 complex rows x 32 complex K), so a stage is two 16 KiB
+// cp.async.bulk copies (factor tile and right-hand-side tile) completing on an
+// mbarrier; TC2_STAGES stages are in flight.  Thread 0 produces (bulk copies),
+// thread 32 issues the MMAs and frees a stage by tcgen05.commit on its "empty"
+// barrier; all four warps run the epilogue.
+
+constexpr int TC2_STAGES = 3;
+constexpr int TC2_SMEM = TC2_STAGES * 2 * kTcTileBytes + 1024;   // + alignment slack
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes));
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Right-hand-side tiles of one depth: item (node, k stage) x column tile ->
+// tile gy * pre(node) + ct * kstages(node) + ks of Bst, the (Re, Im) pairs of the
+// gathered right-hand side (forward: Q + children's update rows; backward: z of the
+// node's columns, x of its below-structure rows) rounded to BF16 in operand layout.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__ nodes,
+                                                     const int32_t* __restrict__ gsrc,
+                                                     const int32_t* __restrict__ rows,
+                                                     const int4* __restrict__ tnode, const int2* __restrict__ tpre,
+                                                     const int2* __restrict__ items, const float2* __restrict__ Q,
+                                                     const float2* __restrict__ Z, const float2* __restrict__ U,
+                                                     const float2* __restrict__ X, uint8_t* __restrict__ Bst, int nrhs,
+                                                     int ld) {
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, ks = it.y, ct = blockIdx.y, gy = gridDim.y;
+  const DevNode nd = nodes[s];
+  const int nc = nd.nc, m = nc + nd.nr;
+  const int4 tn = tnode[s];
+  const int nks = FWD ? tn.y : tn.w;
+  const int pre = FWD ? tpre[s].x : tpre[s].y;
+  uint8_t* tile = Bst + ((int64_t)gy * pre + (int64_t)ct * nks + ks) * kTcTileBytes;
+  const int32_t* gs = gsrc + nd.g_off * 2;
+  const int32_t* rw = rows + nd.row_off;
+  const int kend = FWD ? nc : m;
+  for (int t = threadIdx.x; t < TC_N * TC_KC; t += blockDim.x) {
+    const int kk = t / TC_N, cl = t % TC_N;
+    const int k = ks * TC_KC + kk, c = ct * TC_N + cl;
+    float2 g = make_float2(0.f, 0.f);
+    if (k < kend && c < nrhs) {
+      if (FWD) {
+        g = Q[(int64_t)(nd.col0 + k) * ld + c];
+        const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
+        if (s0 >= 0) g = cadd(g, U[(int64_t)s0 * ld + c]);
+        if (s1 >= 0) g = cadd(g, U[(int64_t)s1 * ld + c]);
+      } else {
+        g = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
+      }
+    }
+    put_g(tile, cl, kk, g);
+  }
+}
+
+// SPLIT = false: grid over (node, row tile) tiles, whole K range; SPLIT = true: grid
+// over (node, row tile, k0, k1) items (k0, k1 multiples of 32 complex), partial
+// products to P for k_sn_tc_reduce.
+template <bool FWD, bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict__ nodes,
+                                                       const uint8_t* __restrict__ TW,
+                                                       const int4* __restrict__ tnode, const int2* __restrict__ tpre,
+                                                       const uint8_t* __restrict__ Bst,
+                                                       const float2* __restrict__ Dinv,
+                                                       const int32_t* __restrict__ gsrc,
+                                                       const int2* __restrict__ tiles, const int4* __restrict__ items,
+                                                       float2* __restrict__ Z, float2* __restrict__ U,
+                                                       float2* __restrict__ X, float2* __restrict__ P, int nrhs, int ld,
+                                                       int* __restrict__ err) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full[TC2_STAGES], empty[TC2_STAGES], done;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  int node, rtile, ik0 = 0, ik1 = 0;
+  if (SPLIT) {
+    const int4 it = items[blockIdx.x];
+    node = it.x; rtile = it.y; ik0 = it.z; ik1 = it.w;
+  } else {
+    const int2 tl = tiles[blockIdx.x];
+    node = tl.x; rtile = tl.y;
+  }
+  const DevNode nd = nodes[node];
+  const int nc = nd.nc, m = nc + nd.nr;
+  const int row0 = rtile * TC_ROWS, c0 = blockIdx.y * TC_N, ct = blockIdx.y, gy = gridDim.y;
+  const int4 tn = tnode[node];
+  const int nks = FWD ? tn.y : tn.w;
+  const int pre = FWD ? tpre[node].x : tpre[node].y;
+  const uint8_t* atiles = TW + ((int64_t)(FWD ? tn.x : tn.z) + (int64_t)rtile * nks) * kTcTileBytes;
+  const uint8_t* btiles = Bst + ((int64_t)gy * pre + (int64_t)ct * nks) * kTcTileBytes;
+  // k stages: forward rows inside L11^{-1} stop at the tile's last row; backward
+  // rows start at the first nonzero of L11^{-1} (stage 2 rtile)
+  int ks0, ks1;
+  if (SPLIT) {
+    ks0 = ik0 / TC_KC;
+    ks1 = (ik1 + TC_KC - 1) / TC_KC;
+  } else if (FWD) {
+    ks0 = 0;
+    ks1 = ((row0 + TC_ROWS <= nc ? row0 + TC_ROWS : nc) + TC_KC - 1) / TC_KC;
+  } else {
+    ks0 = row0 / TC_KC;
+    ks1 = nks;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < TC2_STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncwarp();
+  if (warp == 0) tmem_alloc(&tmem_slot);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const int nst = ks1 - ks0;
+  bool ok = true;
+  if (tid == 0) {
+    // producer: stage i waits until the MMAs that used its buffers have completed
+    for (int i = 0; i < nst && ok; ++i) {
+      const int slot = i % TC2_STAGES;
+      const uint32_t ph = (uint32_t)((i / TC2_STAGES) & 1);
+      if (!mbar_wait(&empty[slot], ph ^ 1u)) { ok = false; break; }
+      uint8_t* a = base + slot * 2 * kTcTileBytes;
+      mbar_arrive_tx(&full[slot], 2 * kTcTileBytes);
+      bulk_g2s(smem_u32(a), atiles + (int64_t)(ks0 + i) * kTcTileBytes, kTcTileBytes, &full[slot]);
+      bulk_g2s(smem_u32(a + kTcTileBytes), btiles + (int64_t)(ks0 + i) * kTcTileBytes, kTcTileBytes, &full[slot]);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    for (int i = 0; i < nst && ok; ++i) {
+      const int slot = i % TC2_STAGES;
+      const uint32_t ph = (uint32_t)((i / TC2_STAGES) & 1);
+      if (!mbar_wait(&full[slot], ph)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint8_t* a = base + slot * 2 * kTcTileBytes;
+#pragma unroll
+      for (int s4 = 0; s4 < (2 * TC_KC) / 16; ++s4) {
+        const uint64_t ad = smem_desc(smem_u32(a) + s4 * 2 * CORE_K);
+        const uint64_t bd = smem_desc(smem_u32(a + kTcTileBytes) + s4 * 2 * CORE_K);
+        const uint32_t acc = (i == 0 && s4 == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&empty[slot])));
+    }
+    if (ok) asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&done)));
+  }
+  // everyone waits for the last MMA (a failed producer/issuer sets the flag instead)
+  if (!ok) atomicExch(err, 1);
+  const bool mine = (nst > 0) && mbar_wait(&done, 0);
+  const bool fin = __syncthreads_and(mine) != 0;   // block-uniform: the TMEM loads are warp-collective
+  if (!fin && nst > 0 && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (fin) {
+    const int R = warp * 32 + lane;
+    const int i = row0 + (R >> 1);
+    const bool even = (R & 1) == 0;
+    const int rows_out = FWD ? m : nc;
+    for (int cb = 0; cb < TC_N; cb += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float mine = __uint_as_float(v[j]);
+        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+        const int c = c0 + cb + j;
+        if (SPLIT) {
+          if (even)
+            P[(((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_ROWS + (R >> 1)) * TC_N + cb + j] =
+                make_float2(mine, other);
+          continue;
+        }
+        if (!even || c >= nrhs || i >= rows_out) continue;
+        const float2 y = make_float2(mine, other);
+        if (FWD) {
+          if (i < nc) {
+            Z[(int64_t)(nd.col0 + i) * ld + c] = cmul(Dinv[nd.col0 + i], y);
+          } else {
+            float2 u = y;
+            const int32_t* gs = gsrc + nd.g_off * 2;
+            const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
+            if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
+            if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
+            U[(int64_t)(nd.u_off + i - nc) * ld + c] = u;
+          }
+        } else {
+          X[(int64_t)(nd.col0 + i) * ld + c] = y;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem);
+}
+
 }  // namespace
+
+cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
+                         float2* Z, float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err,
+                         cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sn_tc2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    attr_set = true;
+  }
+  const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
+  const int64_t* ao = fwd ? F.h_tas_f_off : F.h_tas_b_off;
+  const int64_t aa = ao[d], ab = ao[d + 1];
+  if (ab <= aa) return cudaSuccess;
+  if (fwd)
+    k_tc_assemble<true><<<dim3((unsigned)(ab - aa), gy), 256, 0, st>>>(F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
+                                                                        F.tas_f + aa, Q, Z, U, Q, Bst, nrhs, ld);
+  else
+    k_tc_assemble<false><<<dim3((unsigned)(ab - aa), gy), 256, 0, st>>>(F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
+                                                                         F.tas_b + aa, Q, Z, U, Q, Bst, nrhs, ld);
+  count_launches(1);
+  const uint8_t* TW = fwd ? F.tw_f : F.tw_b;
+  if (!split) {
+    const int64_t* to = fwd ? F.h_fwd_off : F.h_bwd_off;
+    const int64_t a = to[d], b = to[d + 1];
+    const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;
+    if (fwd)
+      k_sn_tc2<true, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st>>>(
+          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
+    else
+      k_sn_tc2<false, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st>>>(
+          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
+    count_launches(1);
+  } else {
+    const int64_t* io = fwd ? F.h_tcf_item_off : F.h_tcb_item_off;
+    const int64_t* uo = fwd ? F.h_tcf_unit_off : F.h_tcb_unit_off;
+    const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
+    const int4* its = (fwd ? F.tcf_items : F.tcb_items) + ia;
+    if (fwd) {
+      k_sn_tc2<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
+          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
+      k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
+                                                                           ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
+    } else {
+      k_sn_tc2<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
+          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
+      k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
+                                                                            ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
+    }
+    count_launches(2);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
                               float2* U, float2* P, int nrhs, int ld, int* err, cudaStream_t st) {
