@@ -169,6 +169,103 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ serving
+SERVE_SPACE_LEVELS = {4: 2, 8: 2, 16: 3, 24: 3}
+
+
+def run_serve(args):
+    """Request-loop benchmark: Poisson streams of solve requests over several meshes,
+    N_t, DG degrees and conductivity scales (st_inputs.request_stream), each solved to
+    a 1e-8 relative residual by the library's server (continuous batching, factor
+    cache, mixed-precision slab apply).  Latency = completion (solution on the host)
+    - arrival.  A warm-up pass first builds every class the streams use (factorisations
+    excluded from latencies; classes stay resident while the memory budget allows)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    import st_inputs
+
+    rates = [float(v) for v in args.serve_rates.split(",")]
+    meshes = [int(v) for v in args.serve_meshes.split(",")]
+    nt_lo, nt_hi = (int(v) for v in args.serve_nt.split(","))
+    nu_c = 2
+    srv = stmg.SpaceTimeServer(slots=args.serve_slots, slab_prec=args.serve_prec, nu=nu_c, max_cycles=60)
+    for n in meshes:
+        srv.register(n, SERVE_SPACE_LEVELS[n], *st_inputs.materials(n, "two_material", 0))
+    streams = [st_inputs.request_stream(args.serve_requests, r, seed=i, meshes=meshes, nt_range=(nt_lo, nt_hi))
+               for i, r in enumerate(rates)]
+
+    def submit(q, t_arr=0.0):
+        return srv.submit(q["n_cube"], q["degree"], q["N_t"], 1.0 / q["N_t"], q["sigma_scale"],
+                          st_inputs.excitation(q["seed"] % 100000), 1e-8, t_arr)
+
+    # warm-up: one request per class (mesh, degree, N_t, tau / s)
+    t0 = time.monotonic()
+    seen = {}
+    for st_ in streams:
+        for q in st_:
+            seen.setdefault((q["n_cube"], q["degree"], q["N_t"], q["N_t"] * q["sigma_scale"]), q)
+    for q in seen.values():
+        submit(q)
+    srv.run_until_idle()
+    warm_s = time.monotonic() - t0
+    stw = srv.stats()
+
+    rows = []
+    for rate, stream in zip(rates, streams):
+        s0 = srv.stats()
+        lat, cyc, bad = [], [], 0
+        i, done, max_q = 0, 0, 0
+        t_start = time.monotonic()
+        while done < len(stream):
+            now = time.monotonic()
+            while i < len(stream) and t_start + stream[i]["t"] <= now:
+                submit(stream[i], t_start + stream[i]["t"])
+                i += 1
+            st_ = srv.stats()
+            max_q = max(max_q, st_["queued"])
+            if st_["queued"] + st_["active"] + st_["building"] == 0:
+                if i < len(stream):
+                    time.sleep(max(0.0, t_start + stream[i]["t"] - time.monotonic()))
+                continue
+            for rid in srv.step():
+                r = srv.result(rid, want_x=False)
+                lat.append(r["t_done"] - r["t_arrival"])
+                cyc.append(r["cycles"])
+                bad += r["status"] != 0
+                done += 1
+        dur = time.monotonic() - (t_start + stream[0]["t"])
+        s1 = srv.stats()
+        lat_s = sorted(lat)
+        smoothed = (s1["dofs_smoothed"] - s0["dofs_smoothed"]) * 4 * nu_c
+        rows.append({"offered_req_per_s": rate, "requests": len(stream), "duration_s": dur,
+                     "throughput_req_per_s": len(stream) / dur, "dofs_smoothed_per_s": smoothed / dur,
+                     "latency_p50_s": float(np.percentile(lat_s, 50)), "latency_p99_s": float(np.percentile(lat_s, 99)),
+                     "latency_max_s": lat_s[-1], "v_cycles_mean": float(np.mean(cyc)), "not_converged": bad,
+                     "max_queue": max_q, "evictions": s1["evictions"] - s0["evictions"],
+                     "deferrals": s1["deferrals"] - s0["deferrals"]})
+    stf = srv.stats()
+    srv.close()
+    line = {"metric": "served solves to 1e-8 relative residual: throughput and p50/p99 latency", "unit": "s",
+            "mode": "serve", "data": "synthetic",
+            "config": {"meshes": meshes, "N_t": f"powers of two in [{nt_lo}, {nt_hi}]", "degrees": [0, 1],
+                       "sigma_scale": "log-uniform [0.1, 10] rounded to a power of two", "tau": "1 / N_t",
+                       "slots_per_class": args.serve_slots, "slab_prec": args.serve_prec,
+                       "cycle": f"V({nu_c},{nu_c})", "rtol": 1e-8,
+                       "latency": "arrival to solution on the host (pageable copy)"},
+            "warmup": {"classes": len(seen), "seconds": warm_s, "cache_entries": stw["cache_entries"],
+                       "cache_bytes": stw["cache_bytes"], "cache_hits": stw["cache_hits"],
+                       "cache_misses": stw["cache_misses"]},
+            "rates": rows,
+            "final": {"classes": stf["classes"], "class_bytes": stf["class_bytes"], "cache_bytes": stf["cache_bytes"]}}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -182,11 +279,20 @@ def main():
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
                     help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
-    ap.add_argument("--mode", default="bench", choices=["bench", "slab"],
-                    help="slab: set up the workload, run two finest-level slab solves and exit (for profilers)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve"],
+                    help="slab: set up the workload, run two finest-level slab solves and exit (for profilers); "
+                         "serve: the request-loop benchmark (Poisson streams, p50/p99 latency)")
+    ap.add_argument("--serve-rates", default="0.5,2,10", help="offered request rates (req/s), one stream each")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
+    ap.add_argument("--serve-meshes", default="8,16,24")
+    ap.add_argument("--serve-nt", default="64,2048", help="N_t range (powers of two)")
+    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-prec", type=int, default=3, choices=[0, 1, 2, 3])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import multiprocessing as mp
 

@@ -101,6 +101,10 @@ typedef struct {
                                 launch sequence into a CUDA graph once per (f, x) buffer pair and replay
                                 it (needs a non-default stream; the first call captures, later calls
                                 replay); 0: launch kernel by kernel */
+    int32_t factor_cache;    /* 1: take slab and K_n factors from, and leave new ones in, the
+                                process-wide factor cache (key: device, mesh, space level, materials,
+                                DG degree, tau, precision), so handles that share a mesh and a tau
+                                share one device copy; 0 (default): the handle owns its factors */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,
@@ -115,6 +119,16 @@ int st_mg_default_options(st_mg_options* opt);
  * default stream) used by every later call.  Host work (assembly and the sparse
  * factorisations) runs on setup_threads threads.  On success *out owns all of it. */
 int st_mg_setup(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out);
+
+/* st_mg_setup in two phases, for callers that build handles off their critical path.
+ * st_mg_setup_begin does the host work (meshes, assembly, coarsening decisions,
+ * factorisations, factor-cache lookups) and touches no device memory, so it may run
+ * on any host thread that has made the target device current; the handle it returns
+ * accepts only st_mg_setup_finish and st_mg_destroy.  st_mg_setup_finish uploads and
+ * sizes the workspaces (device current = the handle's device; it synchronises the
+ * legacy default stream).  st_mg_setup = begin + finish.  No counterpart in the paper. */
+int st_mg_setup_begin(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out);
+int st_mg_setup_finish(st_mg_t h);
 
 /* Host-only variant of st_mg_setup for inspecting the setup without a GPU: builds
  * the meshes, matrices, hierarchy and factors on the host and allocates no device
@@ -218,6 +232,12 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
  * library are bound by this pipe, so it is the roof their efficiency is quoted against. */
 int st_mg_probe_fp64(st_mg_t h, double* tflops);
 
+/* One V-cycle on x (as st_mg_vcycle, graph replay included) followed by the finest
+ * residual r = f - L x, both queued on the handle's stream with no host wait.  A
+ * tensor-core wait that timed out during it is reported by the next st_mg_batch_norms
+ * (or any blocking call that checks).  For pipelines that overlap several handles. */
+int st_mg_vcycle_residual_async(st_mg_t h, const double* f_dev, double* x_dev, double* r_dev);
+
 /* Per-problem l2 norms of a finest-level vector of a batched handle (e.g. r from
  * st_mg_residual): norms_host[b] = ||v_b||_2 for b < n_batch, deterministic order
  * (blocking).  Lets a caller stop or replace problems of a batch independently. */
@@ -226,6 +246,21 @@ int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host);
 /* Zero problem `batch`'s entries of a finest-level vector (e.g. to start a new problem
  * in a freed slot of a batch while the other problems keep iterating). */
 int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev);
+
+/* Device bytes of a handle: own_bytes = its buffers (vectors, workspaces, meshes);
+ * factor_bytes = the slab and K_n factors it references (shared with other handles
+ * when they came from the factor cache). */
+int st_mg_memory(st_mg_t h, int64_t* own_bytes, int64_t* factor_bytes);
+
+/* Factor cache (st_mg_options.factor_cache, no counterpart in the paper: a serving
+ * structure).  Stats: device bytes of all resident entries, the number of entries,
+ * how many of them some live handle uses, and lookup hits and misses so far.  Any
+ * pointer may be NULL. */
+int st_mg_cache_stats(int64_t* bytes, int32_t* entries, int32_t* in_use, int64_t* hits, int64_t* misses);
+
+/* Evict least-recently-used entries that no live handle uses until the cache holds at
+ * most max_bytes (0: every unused entry).  *bytes_after (may be NULL) = what remains. */
+int st_mg_cache_trim(int64_t max_bytes, int64_t* bytes_after);
 
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);

@@ -33,13 +33,39 @@ class Options(ctypes.Structure):
     _fields_ = [("omega", _dbl), ("nu_pre", _i32), ("nu_post", _i32), ("lambda_crit", _dbl),
                 ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
-                ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32)]
+                ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32),
+                ("factor_cache", _i32)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("slots", _i32), ("mem_budget", _i64), ("max_cycles", _i32), ("slab_prec", _i32), ("nu", _i32),
+                ("omega", _dbl), ("setup_threads", _i32), ("keep_x", _i32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_cube", _i32), ("degree", _i32), ("N_t", _i32), ("tau", _dbl), ("sigma_scale", _dbl),
+                ("n_modes", _i32), ("a", _P(_dbl)), ("k", _P(_dbl)), ("phase", _P(_dbl)), ("rtol", _dbl),
+                ("t_arrival", _dbl)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", _i64), ("state", _i32), ("status", _i32), ("cycles", _i32), ("rel_res", _dbl),
+                ("t_arrival", _dbl), ("t_admit", _dbl), ("t_done", _dbl), ("n_edge", _i64), ("n_values", _i64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("queued", _i64), ("active", _i64),
+                ("classes", _i32), ("building", _i32), ("class_bytes", _i64), ("cache_bytes", _i64),
+                ("cache_entries", _i32), ("cache_hits", _i64), ("cache_misses", _i64), ("vcycles", _i64),
+                ("slot_cycles", _i64), ("dofs_smoothed", _i64), ("evictions", _i64), ("deferrals", _i64)]
 
 
 _SIGS = {
     "st_mg_default_options": [_P(Options)],
     "st_mg_setup": [_P(Problem), _P(Options), _vp, _P(_vp)],
     "st_mg_setup_host": [_P(Problem), _P(Options), _P(_vp)],
+    "st_mg_setup_begin": [_P(Problem), _P(Options), _vp, _P(_vp)],
+    "st_mg_setup_finish": [_vp],
     "st_mg_destroy": [_vp],
     "st_mg_sizes": [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i32)],
     "st_mg_level_info": [_vp, _i32, _P(_i32), _P(_i32), _P(_dbl), _P(_i64), _P(_i64)],
@@ -63,10 +89,22 @@ _SIGS = {
     "st_mg_debug_host_slab_solve": [_vp, _i32, _P(_dbl), _P(_dbl)],
     "st_mg_probe_fp64": [_vp, _P(_dbl)],
     "st_mg_batch_norms": [_vp, _vp, _P(_dbl)],
+    "st_mg_vcycle_residual_async": [_vp, _vp, _vp, _vp],
+    "st_mg_memory": [_vp, _P(_i64), _P(_i64)],
+    "st_mg_cache_stats": [_P(_i64), _P(_i32), _P(_i32), _P(_i64), _P(_i64)],
+    "st_mg_cache_trim": [_i64, _P(_i64)],
     "st_mg_batch_zero": [_vp, _i32, _vp],
     "st_mg_launch_count": [_P(_i64)],
     "st_mg_factor_stats": [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)],
     "st_mg_norm2_noalloc": [_vp, _i64, _vp, _vp],
+    "st_mg_server_default_options": [_P(ServerOptions)],
+    "st_mg_server_create": [_P(ServerOptions), _P(_vp)],
+    "st_mg_server_set_materials": [_vp, _i32, _i32, _P(_dbl), _P(_dbl)],
+    "st_mg_server_submit": [_vp, _P(Request), _P(_i64)],
+    "st_mg_server_step": [_vp, _P(_i64), _i32, _P(_i32)],
+    "st_mg_server_result": [_vp, _i64, _P(Result), _P(_dbl), _i64, _i32],
+    "st_mg_server_stats_get": [_vp, _P(ServerStats)],
+    "st_mg_server_destroy": [_vp],
     "st_mg_strerror": [ctypes.c_int],
     "st_mg_last_error": [],
 }
@@ -85,7 +123,7 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_char_p if name in ("st_mg_strerror", "st_mg_last_error") else (
-                None if name == "st_mg_destroy" else ctypes.c_int)
+                None if name in ("st_mg_destroy", "st_mg_server_destroy") else ctypes.c_int)
         _lib = L
     return _lib
 
@@ -279,6 +317,25 @@ def st_mg_batch_zero(h, batch, v_dev):
     _check(lib().st_mg_batch_zero(_vp(h), batch, _vp(_addr(v_dev))), "st_mg_batch_zero")
 
 
+def st_mg_memory(h):
+    own, fac = _i64(0), _i64(0)
+    _check(lib().st_mg_memory(_vp(h), ctypes.byref(own), ctypes.byref(fac)), "st_mg_memory")
+    return own.value, fac.value
+
+
+def st_mg_cache_stats():
+    b, e, u, hi, mi = _i64(0), _i32(0), _i32(0), _i64(0), _i64(0)
+    _check(lib().st_mg_cache_stats(ctypes.byref(b), ctypes.byref(e), ctypes.byref(u), ctypes.byref(hi),
+                                   ctypes.byref(mi)), "st_mg_cache_stats")
+    return {"bytes": b.value, "entries": e.value, "in_use": u.value, "hits": hi.value, "misses": mi.value}
+
+
+def st_mg_cache_trim(max_bytes=0):
+    after = _i64(0)
+    _check(lib().st_mg_cache_trim(max_bytes, ctypes.byref(after)), "st_mg_cache_trim")
+    return after.value
+
+
 def st_mg_launch_count() -> int:
     c = _i64()
     _check(lib().st_mg_launch_count(ctypes.byref(c)), "st_mg_launch_count")
@@ -299,3 +356,60 @@ def st_mg_norm2_noalloc(v_dev, n, stream, norm_dev):
 
 def st_mg_strerror(status: int) -> str:
     return lib().st_mg_strerror(status).decode()
+
+
+# ----------------------------------------------------------------- request loop (st_mg_serve.h)
+def st_mg_server_default_options() -> ServerOptions:
+    o = ServerOptions()
+    _check(lib().st_mg_server_default_options(ctypes.byref(o)), "st_mg_server_default_options")
+    return o
+
+
+def st_mg_server_create(opt: ServerOptions) -> int:
+    h = _vp()
+    _check(lib().st_mg_server_create(ctypes.byref(opt), ctypes.byref(h)), "st_mg_server_create")
+    return h.value
+
+
+def st_mg_server_set_materials(srv, n_cube, n_space_levels, nu, sigma):
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    _check(lib().st_mg_server_set_materials(_vp(srv), n_cube, n_space_levels, _dptr(nu), _dptr(sigma)),
+           "st_mg_server_set_materials")
+
+
+def st_mg_server_submit(srv, n_cube, degree, N_t, tau, sigma_scale, exc, rtol, t_arrival=0.0) -> int:
+    a = np.ascontiguousarray(exc["a"], np.float64).ravel()
+    k = np.ascontiguousarray(exc["k"], np.float64).ravel()
+    ph = np.ascontiguousarray(exc["phase"], np.float64).ravel()
+    r = Request(n_cube, degree, N_t, float(tau), float(sigma_scale), len(ph), _dptr(a), _dptr(k), _dptr(ph),
+                float(rtol), float(t_arrival))
+    i = _i64()
+    _check(lib().st_mg_server_submit(_vp(srv), ctypes.byref(r), ctypes.byref(i)), "st_mg_server_submit")
+    return i.value
+
+
+def st_mg_server_step(srv, cap=4096):
+    ids = np.zeros(cap, dtype=np.int64)
+    n = _i32()
+    _check(lib().st_mg_server_step(_vp(srv), ids.ctypes.data_as(_P(_i64)), cap, ctypes.byref(n)),
+           "st_mg_server_step")
+    return [int(v) for v in ids[:min(n.value, cap)]]
+
+
+def st_mg_server_result(srv, rid, x_out: np.ndarray | None = None, release=False):
+    r = Result()
+    cap = 0 if x_out is None else x_out.size
+    _check(lib().st_mg_server_result(_vp(srv), rid, ctypes.byref(r), None if x_out is None else _dptr(x_out), cap,
+                                     1 if release else 0), "st_mg_server_result")
+    return {f: getattr(r, f) for f, _ in Result._fields_}
+
+
+def st_mg_server_stats_get(srv):
+    s = ServerStats()
+    _check(lib().st_mg_server_stats_get(_vp(srv), ctypes.byref(s)), "st_mg_server_stats_get")
+    return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+
+def st_mg_server_destroy(srv):
+    lib().st_mg_server_destroy(_vp(srv))

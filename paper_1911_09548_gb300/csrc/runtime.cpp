@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -57,6 +58,134 @@ namespace stmg {
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace stmg
 
+namespace {
+// Device allocations freed together: a handle's own buffers, or one cached factor.
+struct DevArena {
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int n_sm = 152;
+  DevArena() = default;
+  DevArena(const DevArena&) = delete;
+  DevArena& operator=(const DevArena&) = delete;
+  ~DevArena() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename T>
+  T* dalloc(int64_t count) {
+    void* p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
+    allocs.push_back(p);
+    bytes += count * (int64_t)sizeof(T);
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* d = dalloc<T>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  }
+  // free one temporary allocation of count elements of T early
+  template <typename T>
+  void release(T* p, int64_t count) {
+    auto it = std::find(allocs.begin(), allocs.end(), static_cast<void*>(p));
+    if (it == allocs.end()) return;
+    allocs.erase(it);
+    bytes -= std::max<int64_t>(count, 1) * (int64_t)sizeof(T);
+    cudaFree(p);
+  }
+};
+
+// Device factor of one time level's slab matrix (every slab of a level shares it,
+// Section 2.1) in that level's precision.  Read-only once built, so handles with the
+// same mesh, materials, DG degree, tau and precision can share one.
+struct SlabFactor {
+  DevArena mem;
+  DevFactor<double> dr;
+  DevFactor<double2> dc;
+  DevFactor<float> drf;                                   // mixed precision (FP32 apply)
+  DevFactor<float2> dcf;
+  DevFactor<double, float2> drd;                          // double-float (FP64-accurate) apply
+  DevFactor<double2, float4> dcd;
+  DevFactor<float2, __nv_bfloat162> dcb;                  // BF16 factor on the tensor cores
+  FactorLists lists;
+  int64_t w_bytes = 0;                                   // device bytes of the factor blocks
+  int64_t u_rows = 0, max_items = 0, max_tc_items = 0, max_stage_tiles = 0;
+};
+
+// Device factor of one space level's nodal matrix K_n (exact auxiliary solve, Section 4).
+struct NodalFactor {
+  DevArena mem;
+  DevFactor<double> kn;
+  DevFactor<double, float2> kn_df;                        // the same factor as FP32 pairs
+  FactorLists kn_lists, kn_df_lists;
+  int64_t u_rows = 0, max_items = 0;
+};
+
+// Process-wide cache of device factors, keyed by everything that determines them
+// (device, mesh, space level, materials, DG degree, tau, precision).  Entries stay
+// resident until st_mg_cache_trim evicts them; a handle holds a reference to each
+// entry it uses, so an entry in use is never evicted.
+struct FactorCache {
+  struct Entry {
+    std::shared_ptr<SlabFactor> slab;
+    std::shared_ptr<NodalFactor> nodal;
+    int64_t last_use = 0;
+    int64_t bytes() const { return slab ? slab->mem.bytes : nodal ? nodal->mem.bytes : 0; }
+    long refs() const { return slab ? slab.use_count() : nodal ? nodal.use_count() : 0; }
+  };
+  std::mutex mu;
+  std::map<std::string, Entry> map;
+  int64_t tick = 0, hits = 0, misses = 0;
+};
+// never destroyed: at process exit the device memory goes with the context
+FactorCache& factor_cache() {
+  static FactorCache* c = new FactorCache();
+  return *c;
+}
+
+void cache_put(const std::string& key, std::shared_ptr<SlabFactor> sf, std::shared_ptr<NodalFactor> nf) {
+  auto& C = factor_cache();
+  std::lock_guard<std::mutex> g(C.mu);
+  auto& e = C.map[key];
+  if (sf) e.slab = sf;
+  if (nf) e.nodal = nf;
+  e.last_use = ++C.tick;
+}
+
+// Second look at the device phase: an entry some other handle left since this handle's
+// host phase looked counts as a hit; otherwise this handle builds it (a miss).  Every
+// factor a handle uses is thus counted once, as a hit or as a miss.
+template <typename T>
+std::shared_ptr<T> cache_recheck(const std::string& key) {
+  auto& C = factor_cache();
+  std::lock_guard<std::mutex> g(C.mu);
+  auto it = C.map.find(key);
+  std::shared_ptr<T> p;
+  if (it != C.map.end()) {
+    if constexpr (std::is_same<T, SlabFactor>::value) p = it->second.slab;
+    else p = it->second.nodal;
+  }
+  if (p) {
+    it->second.last_use = ++C.tick;
+    ++C.hits;
+  } else {
+    ++C.misses;
+  }
+  return p;
+}
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+}  // namespace
+
 struct st_mg_s {
   st_mg_problem prob{};
   st_mg_options opt{};
@@ -69,23 +198,16 @@ struct st_mg_s {
   double* stage_x = nullptr;
   int q = 1;
   int B = 1;                            // problems solved together (batch)
-  std::vector<void*> allocs;
+  DevArena mem;                         // the handle's own device buffers
+  uint64_t mat_hash = 0;                // of (n_cube, nu, sigma): the factor cache's material key
+  bool use_cache = false;               // factors from / into the process-wide cache
+  bool pending_upload = false;          // host phase done (st_mg_setup_begin), device phase not yet
+  std::vector<std::string> lkey, skey;  // cache keys per time level / space level
 
   template <typename T>
-  T* dalloc(int64_t count) {
-    void* p = nullptr;
-    if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
-    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
-    allocs.push_back(p);
-    return static_cast<T*>(p);
-  }
+  T* dalloc(int64_t count) { return mem.dalloc<T>(count); }
   template <typename T>
-  T* upload(const std::vector<T>& v) {
-    T* d = dalloc<T>((int64_t)v.size());
-    if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return d;
-  }
+  T* upload(const std::vector<T>& v) { return mem.upload(v); }
 
   struct Space {
     KuhnMesh mesh;
@@ -100,10 +222,8 @@ struct st_mg_s {
     int64_t* kn_rowptr = nullptr; int32_t* kn_col = nullptr; double* kn_val = nullptr; double* kn_dinv = nullptr;
     int64_t* px_rowptr = nullptr; int32_t* px_col = nullptr; double* px_val = nullptr;
     int64_t* pxt_rowptr = nullptr; int32_t* pxt_col = nullptr; double* pxt_val = nullptr;
-    SupernodalFactor<double> knF;
-    DevFactor<double> kn;
-    DevFactor<double, float2> kn_df;      // the same factor as FP32 pairs (double-float solve)
-    FactorLists kn_lists, kn_df_lists;
+    SupernodalFactor<double> knF;         // host factor (released after upload)
+    std::shared_ptr<NodalFactor> nf;      // device factor (own, or shared through the cache)
     NDCoords ecoord, ncoord;
   };
   std::vector<Space> space;
@@ -113,20 +233,12 @@ struct st_mg_s {
     double tau = 1.0;
     double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;   // residual coefficients per nnz
     float2 *p0 = nullptr, *p1 = nullptr, *p2 = nullptr;   // the same as (hi, lo) FP32 pairs
-    SupernodalFactor<double> fr;
+    SupernodalFactor<double> fr;                            // host factors (released after upload)
     SupernodalFactor<cplx> fc;
-    DevFactor<double> dr;
-    DevFactor<double2> dc;
-    DevFactor<float> drf;                                   // mixed precision (FP32 apply)
-    DevFactor<float2> dcf;
-    DevFactor<double, float2> drd;                          // double-float (FP64-accurate) apply
-    DevFactor<double2, float4> dcd;
-    DevFactor<float2, __nv_bfloat162> dcb;                  // BF16 factor on the tensor cores
+    std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
     int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
-    FactorLists lists;
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
-    int64_t w_bytes = 0;                                   // device bytes of the slab factor blocks
   };
   std::vector<Level> lv;
 
@@ -158,7 +270,6 @@ struct st_mg_s {
 
   ~st_mg_s() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
-    for (void* p : allocs) cudaFree(p);
   }
 };
 
@@ -228,7 +339,7 @@ inline uint16_t bf16_bits(float v) {
 // holds W rows 64 rt .. 64 rt + 63 and columns 32 ks .. 32 ks + 31, each complex
 // entry a + ib as the real block [[a, -b], [b, a]]; backward tile (rt, ks) holds the
 // same for W^T (rows of W^T = columns of W).  Zero outside the node's block.
-void build_tc_tiles(Handle& h, const SupernodalFactor<cplx>& F, DevFactor<float2, __nv_bfloat162>& D,
+void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<float2, __nv_bfloat162>& D,
                     FactorLists& Lh) {
   const size_t TB = kTcTileBytes;
   std::vector<int4> tnode(F.nodes.size());
@@ -299,7 +410,7 @@ void build_tc_tiles(Handle& h, const SupernodalFactor<cplx>& F, DevFactor<float2
 }
 
 template <typename T, typename DT, typename WT>
-void make_dev_factor(Handle& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh) {
+void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh) {
   std::vector<int64_t>& fo = Lh.fo;
   std::vector<int64_t>& bo = Lh.bo;
   D.n = F.n;
@@ -475,40 +586,40 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
     const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
     float2* Q = static_cast<float2*>(h.sQ);
-    CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-    CK(sn_solve_cplx_bf16(L.dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
+    CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+    CK(sn_solve_cplx_bf16(L.fac->dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
                           static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, h.tc_err, h.stream));
-    CK(slab_post_dg1f(Q, h.ld_slab, L.dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+    CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     return;
   }
   if (L.prec == 1) {
     if (h.prob.degree == 0) {
       float* Q = static_cast<float*>(h.sQ);
-      CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.drf.iperm, S.ne, Q, h.ld_slab, h.stream));
-      CK(sn_solve_realf(L.drf, Q, static_cast<float*>(h.sZ), static_cast<float*>(h.sU), static_cast<float*>(h.sP),
+      CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.fac->drf.iperm, S.ne, Q, h.ld_slab, h.stream));
+      CK(sn_solve_realf(L.fac->drf, Q, static_cast<float*>(h.sZ), static_cast<float*>(h.sU), static_cast<float*>(h.sP),
                         cnt, h.ld_slab, h.stream));
-      CK(slab_post_dg0f(Q, h.ld_slab, L.drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+      CK(slab_post_dg0f(Q, h.ld_slab, L.fac->drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     } else {
       const double inv_tau = 1.0 / L.tau;
       const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
       const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
       float2* Q = static_cast<float2*>(h.sQ);
-      CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.dcf.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-      CK(sn_solve_cplxf(L.dcf, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
+      CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcf.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+      CK(sn_solve_cplxf(L.fac->dcf, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
                         static_cast<float2*>(h.sP), cnt, h.ld_slab, h.stream));
-      CK(slab_post_dg1f(Q, h.ld_slab, L.dcf.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+      CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcf.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     }
     return;
   }
   if (h.prob.degree == 0) {
     double* Q = static_cast<double*>(h.sQ);
-    const int32_t* ip = L.prec == 2 ? L.drd.iperm : L.dr.iperm;
+    const int32_t* ip = L.prec == 2 ? L.fac->drd.iperm : L.fac->dr.iperm;
     CK(slab_pre_dg0(src, src_ld, slab0, cnt, ip, S.ne, Q, h.ld_slab, h.stream));
     if (L.prec == 2)
-      CK(sn_solve_real_df(L.drd, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
+      CK(sn_solve_real_df(L.fac->drd, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
                           static_cast<double*>(h.sP), cnt, h.ld_slab, h.stream));
     else
-      CK(sn_solve_real(L.dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
+      CK(sn_solve_real(L.fac->dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
                        cnt, h.ld_slab, h.stream));
     CK(slab_post_dg0(Q, h.ld_slab, ip, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   } else {
@@ -516,13 +627,13 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
     const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
     double2* Q = static_cast<double2*>(h.sQ);
-    const int32_t* ip = L.prec == 2 ? L.dcd.iperm : L.dc.iperm;
+    const int32_t* ip = L.prec == 2 ? L.fac->dcd.iperm : L.fac->dc.iperm;
     CK(slab_pre_dg1(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
     if (L.prec == 2)
-      CK(sn_solve_cplx_df(L.dcd, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
+      CK(sn_solve_cplx_df(L.fac->dcd, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
                           static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
     else
-      CK(sn_solve_cplx(L.dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
+      CK(sn_solve_cplx(L.fac->dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
                        static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
     CK(slab_post_dg1(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   }
@@ -549,12 +660,12 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
   auto& S = h.space[L.s];
   const int ncols = L.N_t * h.B * h.q;
   if (h.opt.nodal_solve == 0) {
-    CK(gather_perm(y, ncols, S.kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
+    CK(gather_perm(y, ncols, S.nf->kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
     if (h.nodal_df)
-      CK(sn_solve_real_df(S.kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+      CK(sn_solve_real_df(S.nf->kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
     else
-      CK(sn_solve_real(S.kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
-    CK(scatter_perm(h.nQ, h.ld_nod, S.kn.iperm, S.nn, z, ncols, h.stream));
+      CK(sn_solve_real(S.nf->kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+    CK(scatter_perm(h.nQ, h.ld_nod, S.nf->kn.iperm, S.nn, z, ncols, h.stream));
   } else {
     // damped Jacobi from z = 0, ping-pong through the nodal workspace
     const int64_t n = (int64_t)S.nn * ncols;
@@ -807,7 +918,55 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.c1 = make_double2(0.0, -1.5 / r2);
   H.s1 = make_double2(1.0, r2);
 
-  // ---- factorisations (all levels concurrently)
+  // slab_prec 1 (FP32) and 3 (BF16) leave the coarsest level in FP64; slab_prec 2
+  // (double-float, FP64-accurate) applies to every level
+  for (size_t l = 0; l < H.lv.size(); ++l)
+    H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec == 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
+  H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
+  H.nodal_df = op->slab_prec != 0;
+
+  // ---- factor cache: take every factor an earlier handle left resident
+  H.use_cache = op->factor_cache != 0 && !host_only;
+  auto& lkey = H.lkey;
+  auto& skey = H.skey;
+  lkey.assign(H.lv.size(), std::string());
+  skey.assign(H.space.size(), std::string());
+  if (H.use_cache) {
+    uint64_t mh = fnv1a(1469598103934665603ull, &n, sizeof(n));
+    mh = fnv1a(mh, H.nu.data(), H.nu.size() * sizeof(double));
+    H.mat_hash = fnv1a(mh, H.sigma.data(), H.sigma.size() * sizeof(double));
+    char buf[192];
+    for (size_t l = 0; l < H.lv.size(); ++l) {
+      const auto& L = H.lv[l];
+      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d tau%a mat%016llx", H.device, n, L.s,
+                    pr->degree, L.prec, L.tau, (unsigned long long)H.mat_hash);
+      lkey[l] = buf;
+    }
+    for (size_t sl = 0; sl < H.space.size(); ++sl) {
+      std::snprintf(buf, sizeof buf, "nodal dev%d n%d s%d df%d mat%016llx", H.device, n, (int)sl, H.nodal_df ? 1 : 0,
+                    (unsigned long long)H.mat_hash);
+      skey[sl] = buf;
+    }
+    auto& C = factor_cache();
+    std::lock_guard<std::mutex> g(C.mu);
+    for (size_t l = 0; l < H.lv.size(); ++l) {
+      auto it = C.map.find(lkey[l]);
+      if (it != C.map.end() && it->second.slab) {
+        H.lv[l].fac = it->second.slab;
+        it->second.last_use = ++C.tick;
+        ++C.hits;
+      }
+    }
+    for (size_t sl = 0; sl < H.space.size(); ++sl) {
+      auto it = C.map.find(skey[sl]);
+      if (it != C.map.end() && it->second.nodal) {
+        H.space[sl].nf = it->second.nodal;
+        it->second.last_use = ++C.tick;
+        ++C.hits;
+      }
+    }
+  }
+  // ---- factorisations (all levels concurrently; cached ones skipped)
   const int nthr = hw_threads(op->setup_threads);
   std::vector<std::string> errs(H.lv.size() + H.space.size());
   std::vector<int> rcs(errs.size(), 0);
@@ -828,6 +987,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
         if (j < (int)H.lv.size()) {
           auto& L = H.lv[j];
           auto& S = H.space[L.s];
+          if (L.fac) continue;
           if (pr->degree == 0) {
             std::vector<double> v(S.M.val.size());
             for (size_t q = 0; q < v.size(); ++q) v[q] = S.M.val[q] + L.tau * S.K.val[q];
@@ -840,6 +1000,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
           }
         } else {
           auto& S = H.space[j - H.lv.size()];
+          if (S.nf) continue;
           rcs[j] = factor_nd_threads(S.Kn, S.Kn.val, S.ncoord, 48, S.knF, errs[j], inner);
         }
       }
@@ -854,17 +1015,26 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     return fail(ST_MG_ERR_INVALID_ARG, "n_batch > 1 needs a hierarchy that coarsens time to one slab "
                                        "(N_t a power of two, no max_levels cap)");
   for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q * H.B;
-  // slab_prec 1 (FP32) leaves the coarsest level in FP64; slab_prec 2 (double-float,
-  // FP64-accurate) applies to every level
-  for (size_t l = 0; l < H.lv.size(); ++l)
-    H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec == 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
-  H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
-  if (host_only) {
-    *out = h.release();
-    return ST_MG_OK;
-  }
+  H.pending_upload = !host_only;
+  *out = h.release();
+  return ST_MG_OK;
+}
 
-  // ---- upload
+// Device phase of the setup: upload meshes, matrices and factors (taking cache entries
+// that appeared since the host phase), size the workspaces.
+int setup_device(Handle& H) {
+  const st_mg_problem* pr = &H.prob;
+  const st_mg_options* op = &H.opt;
+  const auto& lkey = H.lkey;
+  const auto& skey = H.skey;
+  if (H.use_cache) {
+    for (size_t l = 0; l < H.lv.size(); ++l)
+      if (!H.lv[l].fac)
+        if (auto f = cache_recheck<SlabFactor>(lkey[l])) H.lv[l].fac = f;
+    for (size_t sl = 0; sl < H.space.size(); ++sl)
+      if (!H.space[sl].nf)
+        if (auto f = cache_recheck<NodalFactor>(skey[sl])) H.space[sl].nf = f;
+  }
   for (auto& S : H.space) {
     S.rowptr = H.upload(S.M.rowptr);
     S.col = H.upload(S.M.col);
@@ -890,15 +1060,20 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       S.pxt_col = H.upload(S.PxT.col);
       S.pxt_val = H.upload(S.PxT.val);
     }
-    make_dev_factor(H, S.knF, S.kn, S.kn_lists);
-    if (op->slab_prec != 0) {
-      make_dev_factor(H, S.knF, S.kn_df, S.kn_df_lists);
-      H.nodal_df = true;
+    if (!S.nf) {
+      auto N = std::make_shared<NodalFactor>();
+      N->mem.n_sm = H.n_sm;
+      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists);
+      if (H.nodal_df) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists);
+      N->u_rows = N->kn.u_rows;
+      N->max_items = N->kn.max_items;
+      S.nf = N;
+      if (H.use_cache) cache_put(skey[&S - H.space.data()], nullptr, N);
     }
     S.knF = SupernodalFactor<double>();   // host copy no longer needed
   }
   int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0, max_items = 0, max_kn_items = 0;
-  for (auto& S : H.space) max_kn_items = std::max<int64_t>(max_kn_items, S.kn.max_items);
+  for (auto& S : H.space) max_kn_items = std::max<int64_t>(max_kn_items, S.nf->kn.max_items);
   int max_nt = 1;
   for (size_t l = 0; l < H.lv.size(); ++l) {
     auto& L = H.lv[l];
@@ -913,21 +1088,29 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
         L.p0 = H.upload(convert_pairs<float2>(a));
         L.p1 = H.upload(convert_pairs<float2>(b));
       }
-      if (L.prec == 1) {
-        make_dev_factor(H, L.fr, L.drf, L.lists);
-        max_items = std::max<int64_t>(max_items, L.drf.max_items);
-        L.w_bytes = (int64_t)L.fr.W.size() * 4;
-      } else if (L.prec == 2) {
-        make_dev_factor(H, L.fr, L.drd, L.lists);
-        max_items = std::max<int64_t>(max_items, L.drd.max_items);
-        L.w_bytes = (int64_t)L.fr.W.size() * 8;
-      } else {
-        make_dev_factor(H, L.fr, L.dr, L.lists);
-        max_items = std::max<int64_t>(max_items, L.dr.max_items);
-        L.w_bytes = (int64_t)L.fr.W.size() * 8;
+      if (!L.fac) {
+        auto F = std::make_shared<SlabFactor>();
+        F->mem.n_sm = H.n_sm;
+        if (L.prec == 1) {
+          make_dev_factor(F->mem, L.fr, F->drf, F->lists);
+          F->max_items = F->drf.max_items;
+          F->w_bytes = (int64_t)L.fr.W.size() * 4;
+        } else if (L.prec == 2) {
+          make_dev_factor(F->mem, L.fr, F->drd, F->lists);
+          F->max_items = F->drd.max_items;
+          F->w_bytes = (int64_t)L.fr.W.size() * 8;
+        } else {
+          make_dev_factor(F->mem, L.fr, F->dr, F->lists);
+          F->max_items = F->dr.max_items;
+          F->w_bytes = (int64_t)L.fr.W.size() * 8;
+        }
+        F->u_rows = L.fr.u_rows;
+        L.fac = F;
+        if (H.use_cache) cache_put(lkey[l], F, nullptr);
       }
-      max_u = std::max<int64_t>(max_u, L.fr.u_rows);
       L.fr = SupernodalFactor<double>();
+      max_items = std::max<int64_t>(max_items, L.fac->max_items);
+      max_u = std::max<int64_t>(max_u, L.fac->u_rows);
     } else {
       for (size_t q = 0; q < nnz; ++q) {
         a[q] = S.M.val[q];
@@ -942,26 +1125,36 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
         L.p1 = H.upload(convert_pairs<float2>(b));
         L.p2 = H.upload(convert_pairs<float2>(c));
       }
-      if (L.prec == 1) {
-        make_dev_factor(H, L.fc, L.dcf, L.lists);
-        max_items = std::max<int64_t>(max_items, L.dcf.max_items);
-        L.w_bytes = (int64_t)L.fc.W.size() * 8;
-      } else if (L.prec == 3) {
-        make_dev_factor(H, L.fc, L.dcb, L.lists);
-        build_tc_tiles(H, L.fc, L.dcb, L.lists);
-        max_items = std::max<int64_t>(max_items, L.dcb.max_items);
-        L.w_bytes = (int64_t)L.fc.W.size() * 4;
-      } else if (L.prec == 2) {
-        make_dev_factor(H, L.fc, L.dcd, L.lists);
-        max_items = std::max<int64_t>(max_items, L.dcd.max_items);
-        L.w_bytes = (int64_t)L.fc.W.size() * 16;
-      } else {
-        make_dev_factor(H, L.fc, L.dc, L.lists);
-        max_items = std::max<int64_t>(max_items, L.dc.max_items);
-        L.w_bytes = (int64_t)L.fc.W.size() * 16;
+      if (!L.fac) {
+        auto F = std::make_shared<SlabFactor>();
+        F->mem.n_sm = H.n_sm;
+        if (L.prec == 1) {
+          make_dev_factor(F->mem, L.fc, F->dcf, F->lists);
+          F->max_items = F->dcf.max_items;
+          F->w_bytes = (int64_t)L.fc.W.size() * 8;
+        } else if (L.prec == 3) {
+          make_dev_factor(F->mem, L.fc, F->dcb, F->lists);
+          build_tc_tiles(F->mem, L.fc, F->dcb, F->lists);
+          F->max_items = F->dcb.max_items;
+          F->max_tc_items = F->dcb.max_tc_items;
+          F->max_stage_tiles = F->dcb.max_stage_tiles;
+          F->w_bytes = (int64_t)L.fc.W.size() * 4;
+        } else if (L.prec == 2) {
+          make_dev_factor(F->mem, L.fc, F->dcd, F->lists);
+          F->max_items = F->dcd.max_items;
+          F->w_bytes = (int64_t)L.fc.W.size() * 16;
+        } else {
+          make_dev_factor(F->mem, L.fc, F->dc, F->lists);
+          F->max_items = F->dc.max_items;
+          F->w_bytes = (int64_t)L.fc.W.size() * 16;
+        }
+        F->u_rows = L.fc.u_rows;
+        L.fac = F;
+        if (H.use_cache) cache_put(lkey[l], F, nullptr);
       }
-      max_u = std::max<int64_t>(max_u, L.fc.u_rows);
       L.fc = SupernodalFactor<cplx>();
+      max_items = std::max<int64_t>(max_items, L.fac->max_items);
+      max_u = std::max<int64_t>(max_u, L.fac->u_rows);
     }
     L.len = (int64_t)S.ne * L.N_t * H.q * H.B;
     if (l > 0) {
@@ -974,7 +1167,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     max_ne = std::max<int64_t>(max_ne, S.ne);
     max_nn = std::max<int64_t>(max_nn, S.nn);
     max_nt = std::max(max_nt, L.N_t * H.B);
-    max_un = std::max<int64_t>(max_un, S.kn.u_rows);
+    max_un = std::max<int64_t>(max_un, S.nf->kn.u_rows);
   }
   const size_t esz = pr->degree == 0 ? sizeof(double) : sizeof(double2);
   H.ld_slab = max_nt;
@@ -1004,20 +1197,21 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     CK(cudaMemset(H.tc_err, 0, sizeof(int)));
     int64_t mt = 1;
     for (auto& L : H.lv)
-      if (L.prec == 3) mt = std::max<int64_t>(mt, L.dcb.max_tc_items);
+      if (L.prec == 3) mt = std::max<int64_t>(mt, L.fac->max_tc_items);
     const int64_t gy = (H.ld_slab + kTcCols - 1) / kTcCols;
     H.tcP = H.dalloc<float2>(mt * gy * kSnBM * kTcCols);
     int64_t ms = 1;
     for (auto& L : H.lv)
-      if (L.prec == 3) ms = std::max<int64_t>(ms, L.dcb.max_stage_tiles);
+      if (L.prec == 3) ms = std::max<int64_t>(ms, L.fac->max_stage_tiles);
     H.tcB = H.dalloc<uint8_t>(ms * gy * kTcTileBytes);
   }
   H.bn_partial = H.dalloc<double>(batch_norm_scratch(H.B));
   H.bn_out = H.dalloc<double>(H.B);
   H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
   H.scalar = H.dalloc<double>(1);
-  CK(cudaDeviceSynchronize());
-  *out = h.release();
+  // the uploads above ran on the legacy default stream
+  CK(cudaStreamSynchronize(cudaStreamLegacy));
+  H.pending_upload = false;
   return ST_MG_OK;
 }
 
@@ -1051,6 +1245,7 @@ int guarded(Fn fn) {
 int check_dev(st_mg_t h) {
   if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
   if (h->host_only) return fail(ST_MG_ERR_INVALID_ARG, "handle was built by st_mg_setup_host (no device state)");
+  if (h->pending_upload) return fail(ST_MG_ERR_INVALID_ARG, "setup not finished (st_mg_setup_finish)");
   return ST_MG_OK;
 }
 
@@ -1163,11 +1358,31 @@ int st_mg_default_options(st_mg_options* o) {
   o->slab_prec = 0;
   o->residual_prec = -1;
   o->use_graph = 1;
+  o->factor_cache = 0;
   return ST_MG_OK;
 }
 
 int st_mg_setup(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out) {
+  if (int rc = st_mg_setup_begin(prob, opt, stream, out)) return rc;
+  if (int rc = st_mg_setup_finish(*out)) {
+    st_mg_destroy(*out);
+    *out = nullptr;
+    return rc;
+  }
+  return ST_MG_OK;
+}
+
+int st_mg_setup_begin(const st_mg_problem* prob, const st_mg_options* opt, void* stream, st_mg_t* out) {
   return guarded([&]() { return do_setup(prob, opt, stream, out, false); });
+}
+
+int st_mg_setup_finish(st_mg_t h) {
+  if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
+  if (!h->pending_upload) return fail(ST_MG_ERR_INVALID_ARG, "handle is not waiting for st_mg_setup_finish");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+    return fail(ST_MG_ERR_INVALID_ARG, "st_mg_setup_finish must run with the handle's device current");
+  return guarded([&]() { return setup_device(*h); });
 }
 
 int st_mg_setup_host(const st_mg_problem* prob, const st_mg_options* opt, st_mg_t* out) {
@@ -1176,7 +1391,7 @@ int st_mg_setup_host(const st_mg_problem* prob, const st_mg_options* opt, st_mg_
 
 void st_mg_destroy(st_mg_t h) {
   if (!h) return;
-  if (!h->host_only) cudaStreamSynchronize(h->stream);
+  if (!h->host_only && !h->pending_upload) cudaStreamSynchronize(h->stream);
   delete h;
 }
 
@@ -1237,12 +1452,8 @@ int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const d
     const int seg = L.N_t * H.q;
     CK(outer_load(db, dc, f_dev + (int64_t)batch * seg, H.space[0].ne, seg, seg * H.B, H.stream));
     CK(cudaStreamSynchronize(H.stream));
-    // release the temporaries
-    for (void* p : {static_cast<void*>(db), static_cast<void*>(dc)}) {
-      auto it = std::find(H.allocs.begin(), H.allocs.end(), p);
-      if (it != H.allocs.end()) H.allocs.erase(it);
-      cudaFree(p);
-    }
+    H.mem.release(db, (int64_t)b.size());
+    H.mem.release(dc, (int64_t)c.size());
     return ST_MG_OK;
   });
 }
@@ -1365,6 +1576,16 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
       op_residual(*h, 0, f_dev, x_dev, h->r0, &nsq);
       *rel_res_out = std::sqrt(nsq) / (fn > 0 ? fn : 1.0);
     }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_vcycle_residual_async(st_mg_t h, const double* f_dev, double* x_dev, double* r_dev) {
+  if (int rc = check_dev(h)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
+  return guarded([&]() {
+    run_vcycle(*h, f_dev, x_dev);
+    op_residual(*h, 0, f_dev, x_dev, r_dev, nullptr);
     return ST_MG_OK;
   });
 }
@@ -1502,6 +1723,7 @@ int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host) {
     std::vector<double> sq(H.B);
     CK(cudaMemcpyAsync(sq.data(), H.bn_out, H.B * sizeof(double), cudaMemcpyDeviceToHost, H.stream));
     CK(cudaStreamSynchronize(H.stream));
+    if (int rc = check_tc(H)) return rc;
     for (int b = 0; b < H.B; ++b) norms_host[b] = std::sqrt(sq[b]);
     return ST_MG_OK;
   });
@@ -1519,6 +1741,63 @@ int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev) {
   });
 }
 
+int st_mg_memory(st_mg_t h, int64_t* own_bytes, int64_t* factor_bytes) {
+  if (int rc = check_dev(h)) return rc;
+  int64_t fb = 0;
+  std::vector<const void*> seen;
+  auto add = [&](const void* p, int64_t b) {
+    if (!p || std::find(seen.begin(), seen.end(), p) != seen.end()) return;
+    seen.push_back(p);
+    fb += b;
+  };
+  for (auto& L : h->lv) add(L.fac.get(), L.fac ? L.fac->mem.bytes : 0);
+  for (auto& S : h->space) add(S.nf.get(), S.nf ? S.nf->mem.bytes : 0);
+  if (own_bytes) *own_bytes = h->mem.bytes;
+  if (factor_bytes) *factor_bytes = fb;
+  return ST_MG_OK;
+}
+
+int st_mg_cache_stats(int64_t* bytes, int32_t* entries, int32_t* in_use, int64_t* hits, int64_t* misses) {
+  auto& C = factor_cache();
+  std::lock_guard<std::mutex> g(C.mu);
+  int64_t b = 0;
+  int32_t u = 0;
+  for (auto& kv : C.map) {
+    b += kv.second.bytes();
+    if (kv.second.refs() > 1) ++u;
+  }
+  if (bytes) *bytes = b;
+  if (entries) *entries = (int32_t)C.map.size();
+  if (in_use) *in_use = u;
+  if (hits) *hits = C.hits;
+  if (misses) *misses = C.misses;
+  return ST_MG_OK;
+}
+
+int st_mg_cache_trim(int64_t max_bytes, int64_t* bytes_after) {
+  if (max_bytes < 0) return fail(ST_MG_ERR_INVALID_ARG, "max_bytes < 0");
+  auto& C = factor_cache();
+  std::vector<FactorCache::Entry> drop;   // freed after the lock is released
+  int64_t total = 0;
+  {
+    std::lock_guard<std::mutex> g(C.mu);
+    for (auto& kv : C.map) total += kv.second.bytes();
+    while (total > max_bytes) {
+      auto victim = C.map.end();
+      for (auto it = C.map.begin(); it != C.map.end(); ++it)
+        if (it->second.refs() == 1 && (victim == C.map.end() || it->second.last_use < victim->second.last_use))
+          victim = it;
+      if (victim == C.map.end()) break;   // everything left is in use
+      total -= victim->second.bytes();
+      drop.push_back(std::move(victim->second));
+      C.map.erase(victim);
+    }
+  }
+  drop.clear();
+  if (bytes_after) *bytes_after = total;
+  return ST_MG_OK;
+}
+
 int st_mg_launch_count(int64_t* count) {
   if (!count) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *count = launch_count();
@@ -1529,16 +1808,16 @@ int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* 
   if (int rc = check_level(h, level)) return rc;
   const auto& L = h->lv[level];
   const bool c = h->prob.degree == 1;
-  const double macs = L.prec == 3 ? L.dcb.macs_per_rhs
-                     : L.prec == 1 ? (c ? L.dcf.macs_per_rhs : L.drf.macs_per_rhs)
-                     : L.prec == 2 ? (c ? L.dcd.macs_per_rhs : L.drd.macs_per_rhs)
-                                   : (c ? L.dc.macs_per_rhs : L.dr.macs_per_rhs);
-  const int dep = L.prec == 3 ? L.dcb.max_depth
-                  : L.prec == 1 ? (c ? L.dcf.max_depth : L.drf.max_depth)
-                  : L.prec == 2 ? (c ? L.dcd.max_depth : L.drd.max_depth)
-                                : (c ? L.dc.max_depth : L.dr.max_depth);
+  const double macs = L.prec == 3 ? L.fac->dcb.macs_per_rhs
+                     : L.prec == 1 ? (c ? L.fac->dcf.macs_per_rhs : L.fac->drf.macs_per_rhs)
+                     : L.prec == 2 ? (c ? L.fac->dcd.macs_per_rhs : L.fac->drd.macs_per_rhs)
+                                   : (c ? L.fac->dc.macs_per_rhs : L.fac->dr.macs_per_rhs);
+  const int dep = L.prec == 3 ? L.fac->dcb.max_depth
+                  : L.prec == 1 ? (c ? L.fac->dcf.max_depth : L.fac->drf.max_depth)
+                  : L.prec == 2 ? (c ? L.fac->dcd.max_depth : L.fac->drd.max_depth)
+                                : (c ? L.fac->dc.max_depth : L.fac->dr.max_depth);
   if (macs_per_rhs) *macs_per_rhs = macs;
-  if (factor_bytes) *factor_bytes = L.w_bytes;
+  if (factor_bytes) *factor_bytes = L.fac->w_bytes;
   if (depth) *depth = dep;
   return ST_MG_OK;
 }

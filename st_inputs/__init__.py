@@ -15,6 +15,13 @@ J on the unit cube); the concrete recipe is ours:
       k_m uniform in {1,2,3}^3, phi_m ~ U(0, 2 pi),  g(t) = sin(pi t / T) + 1,
     returned as its parameters (a, k, phase); each side evaluates J itself.
 
+  * request_stream(n, rate, seed, meshes, nt_range, degrees): a Poisson stream of
+    solve requests (the serving workload): exponential inter-arrival gaps of mean
+    1/rate; per request a mesh uniform over `meshes`, N_t uniform over the powers of
+    two in nt_range, a DG degree uniform over `degrees`, a conductivity scale s drawn
+    log-uniform in [0.1, 10] and rounded to the nearest power of two (so that tau / s
+    stays on one power-of-two ladder per mesh and degree), and an excitation seed.
+
 Random streams: numpy Generator(PCG64(seed)).
 """
 from __future__ import annotations
@@ -52,3 +59,17 @@ def random_iterate(shape, seed: int = 0):
     """Uniform [0, 1) values, e.g. the random start of the power iteration (Section 5.1)."""
     rng = np.random.Generator(np.random.PCG64(20_000 + seed))
     return rng.uniform(0.0, 1.0, size=shape)
+
+
+def request_stream(n: int, rate: float, seed: int = 0, meshes=(8, 16, 24), nt_range=(64, 2048), degrees=(0, 1)):
+    rng = np.random.Generator(np.random.PCG64(30_000 + seed))
+    nts = [1 << k for k in range(int(np.log2(nt_range[0])), int(np.log2(nt_range[1])) + 1)]
+    gaps = rng.exponential(1.0 / rate, size=n)
+    out = []
+    t = 0.0
+    for i in range(n):
+        t += gaps[i]
+        s = 2.0 ** np.round(np.log2(10.0 ** rng.uniform(-1.0, 1.0)))
+        out.append({"t": float(t), "n_cube": int(rng.choice(meshes)), "N_t": int(rng.choice(nts)),
+                    "degree": int(rng.choice(degrees)), "sigma_scale": float(s), "seed": int(rng.integers(0, 1 << 30))})
+    return out

@@ -24,9 +24,10 @@ def B():
 
 
 def test_exports_every_declared_symbol(B):
-    header = open(os.path.join(ROOT, "include", "st_mg.h")).read()
+    inc = os.path.join(ROOT, "include")
+    header = "".join(open(os.path.join(inc, h)).read() for h in sorted(os.listdir(inc)) if h.endswith(".h"))
     declared = set(re.findall(r"\b(st_mg_\w+)\s*\(", header))
-    assert len(declared) >= 20
+    assert len(declared) >= 45
     L = B.lib()
     for name in declared:
         assert hasattr(L, name), name
@@ -101,3 +102,14 @@ def test_host_setup_matches_oracle(B, n, nsl, p, coarsen):
         yo = mg.slabs[lvl].solve(from_lib(r, p + 1))
         assert rel(from_lib(y, p + 1), yo) < 1e-13
     S.close()
+
+
+def test_server_options_validated(B):
+    o = B.st_mg_server_default_options()
+    assert (o.slots, o.max_cycles, o.slab_prec, o.nu, o.omega, o.keep_x) == (4, 50, 3, 2, 0.5, 1)
+    for field, bad in (("slots", 0), ("max_cycles", 0), ("slab_prec", 4), ("omega", 0.0), ("mem_budget", -1)):
+        o = B.st_mg_server_default_options()
+        setattr(o, field, bad)
+        with pytest.raises(B.StMgError) as e:
+            B.st_mg_server_create(o)
+        assert e.value.status == 1
