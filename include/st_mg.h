@@ -86,14 +86,16 @@ typedef struct {
     int32_t use_A;           /* 1: hybrid smoother with A; 0: plain S only */
     int32_t setup_threads;   /* host threads for the factorisations; 0 = all cores */
     int32_t slab_prec;       /* slab-solve arithmetic: 0 FP64; 1 mixed: the FP64 factor rounded to
-                                FP32 and applied in FP32 on every level but the coarsest (residual,
-                                factorisation, nodal and coarsest solves stay FP64; the V-cycle acts
-                                as iterative refinement, Section 2.1's "sufficiently well approximated");
+                                FP32 and applied in FP32 on every level but the coarsest (residual
+                                FP64-accurate, factorisation and coarsest solve FP64, nodal K_n solve
+                                FP32; the V-cycle acts as iterative refinement, Section 2.1's
+                                "sufficiently well approximated");
                                 2 double-float: the factor as FP32 (hi, lo) pairs applied with
                                 error-free FP32 products and sums (about 48 significant bits), on the
                                 FP32 pipes, which on GB300 run 58x the FP64 rate;
                                 3 (DG(1) only) BF16 factor on the tensor cores (tcgen05, FP32
-                                accumulation in tensor memory), coarsest level in FP64 */
+                                accumulation in tensor memory), coarsest level in FP64, nodal K_n
+                                solve FP32 as in 1.  Mode 2 solves K_n in double-float, mode 0 in FP64 */
     int32_t residual_prec;   /* space-time residual arithmetic: 0 FP64; 2 double-float (x split into
                                 FP32 pairs once per call, error-free products and sums, f and r in
                                 FP64); -1 (default): FP64 when slab_prec = 0, double-float otherwise */

@@ -187,6 +187,11 @@ cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nr
                         cudaStream_t st);
 cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                          cudaStream_t st);
+// the same with an FP32 workspace (FP32 nodal solve)
+cudaError_t gather_perm_f(const double* y, int ncols, const int32_t* iperm, int nrows, float* Q, int ld,
+                          cudaStream_t st);
+cudaError_t scatter_perm_f(const float* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
+                           cudaStream_t st);
 
 // y[v][j] = sum over incident interior edges of G[e][v] r[e][j]  (G^T, node-major CSR,
 // gt_sign = +1 head / -1 tail).

@@ -15,9 +15,13 @@
 //   W_s = [ L11^{-1} ; -L21 L11^{-1} ]   (row-major, (nc + nr) x nc)
 // which turns both triangular sweeps on the GPU into dense products.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <functional>
+#include <mutex>
 #include <thread>
+#include <type_traits>
 
 #include "host.h"
 
@@ -34,98 +38,245 @@ inline cplx mul(cplx a, cplx b) { return a * b; }
 inline bool isfin(double a) { return std::isfinite(a); }
 inline bool isfin(cplx a) { return std::isfinite(a.re) && std::isfinite(a.im); }
 
-// y[i] -= a[i] * t  for i in [0, n)
-inline void axpy_sub(double* y, const double* a, double t, int64_t n) {
-  for (int64_t i = 0; i < n; ++i) y[i] -= a[i] * t;
-}
-inline void axpy_sub(cplx* y, const cplx* a, cplx t, int64_t n) {
-  double* yd = reinterpret_cast<double*>(y);
-  const double* ad = reinterpret_cast<const double*>(a);
-  const double tr = t.re, ti = t.im;
-  for (int64_t i = 0; i < n; ++i) {
-    const double ar = ad[2 * i], ai = ad[2 * i + 1];
-    yd[2 * i] -= ar * tr - ai * ti;
-    yd[2 * i + 1] -= ar * ti + ai * tr;
+// ---------------------------------------------------------------- thread pool
+// Fixed set of worker threads; run(n, fn) executes fn(0..n-1) on the workers and the
+// calling thread (dynamic scheduling by an atomic counter) and returns when all are done.
+class Pool {
+ public:
+  explicit Pool(int nthreads) {
+    for (int t = 1; t < nthreads; ++t) th_.emplace_back([this]() { loop(); });
   }
-}
-// y[i] -= a0[i]*t0 + a1[i]*t1 + a2[i]*t2 + a3[i]*t3
-inline void axpy4_sub(double* y, const double* a0, const double* a1, const double* a2, const double* a3,
-                      double t0, double t1, double t2, double t3, int64_t n) {
-  for (int64_t i = 0; i < n; ++i) y[i] -= a0[i] * t0 + a1[i] * t1 + a2[i] * t2 + a3[i] * t3;
-}
-inline void axpy4_sub(cplx* y, const cplx* a0, const cplx* a1, const cplx* a2, const cplx* a3, cplx t0,
-                      cplx t1, cplx t2, cplx t3, int64_t n) {
-  double* yd = reinterpret_cast<double*>(y);
-  const double* p0 = reinterpret_cast<const double*>(a0);
-  const double* p1 = reinterpret_cast<const double*>(a1);
-  const double* p2 = reinterpret_cast<const double*>(a2);
-  const double* p3 = reinterpret_cast<const double*>(a3);
-  for (int64_t i = 0; i < n; ++i) {
-    const int64_t r = 2 * i, m = 2 * i + 1;
-    yd[r] -= (p0[r] * t0.re - p0[m] * t0.im) + (p1[r] * t1.re - p1[m] * t1.im) +
-             (p2[r] * t2.re - p2[m] * t2.im) + (p3[r] * t3.re - p3[m] * t3.im);
-    yd[m] -= (p0[r] * t0.im + p0[m] * t0.re) + (p1[r] * t1.im + p1[m] * t1.re) +
-             (p2[r] * t2.im + p2[m] * t2.re) + (p3[r] * t3.im + p3[m] * t3.re);
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  int size() const { return (int)th_.size() + 1; }
+  void run(int64_t n, const std::function<void(int64_t)>& fn) {
+    if (n <= 0) return;
+    if (th_.empty() || n == 1) {
+      for (int64_t i = 0; i < n; ++i) fn(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_.store(0);
+      busy_ = (int)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [this]() { return busy_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work() {
+    for (;;) {
+      const int64_t i = next_.fetch_add(1);
+      if (i >= n_) return;
+      (*fn_)(i);
+    }
+  }
+  void loop() {
+    int64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&]() { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+      }
+      work();
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        if (--busy_ == 0) done_cv_.notify_one();
+      }
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int64_t)>* fn_ = nullptr;
+  int64_t n_ = 0, gen_ = 0;
+  std::atomic<int64_t> next_{0};
+  int busy_ = 0;
+  bool stop_ = false;
+};
+
+// run fn(0..n-1) on the pool, or serially when pool is null
+inline void pfor(Pool* pool, int64_t n, const std::function<void(int64_t)>& fn) {
+  if (pool) {
+    pool->run(n, fn);
+  } else {
+    for (int64_t i = 0; i < n; ++i) fn(i);
   }
 }
 
-template <typename Fn>
-void parallel_for(int64_t n, int nthreads, Fn fn) {
-  if (nthreads <= 1 || n < 2) {
-    for (int64_t i = 0; i < n; ++i) fn(i);
-    return;
+// ---------------------------------------------------------------- dense kernels
+// C[r + c ldc] -= sum_{k<K} A[r + k lda] * B[k bk + c bc] on an R x CC register tile.
+template <int R, int CC>
+inline void mk_sub(const double* A, int64_t lda, const double* B, int64_t bk, int64_t bc, double* C, int64_t ldc,
+                   int64_t K) {
+  double acc[CC][R] = {};
+  for (int64_t k = 0; k < K; ++k) {
+    const double* a = A + k * lda;
+    for (int c = 0; c < CC; ++c) {
+      const double b = B[k * bk + c * bc];
+      for (int r = 0; r < R; ++r) acc[c][r] += a[r] * b;
+    }
   }
-  std::vector<std::thread> th;
-  const int nt = (int)std::min<int64_t>(nthreads, n);
-  for (int t = 0; t < nt; ++t)
-    th.emplace_back([&, t]() {
-      for (int64_t i = t; i < n; i += nt) fn(i);
-    });
-  for (auto& x : th) x.join();
+  for (int c = 0; c < CC; ++c)
+    for (int r = 0; r < R; ++r) C[r + c * ldc] -= acc[c][r];
 }
+template <int R, int CC>
+inline void mk_sub(const cplx* A, int64_t lda, const cplx* B, int64_t bk, int64_t bc, cplx* C, int64_t ldc,
+                   int64_t K) {
+  double ar[CC][R] = {}, ai[CC][R] = {};
+  for (int64_t k = 0; k < K; ++k) {
+    const double* a = reinterpret_cast<const double*>(A + k * lda);
+    double xr[R], xi[R];
+    for (int r = 0; r < R; ++r) {
+      xr[r] = a[2 * r];
+      xi[r] = a[2 * r + 1];
+    }
+    for (int c = 0; c < CC; ++c) {
+      const cplx b = B[k * bk + c * bc];
+      for (int r = 0; r < R; ++r) {
+        ar[c][r] += xr[r] * b.re - xi[r] * b.im;
+        ai[c][r] += xr[r] * b.im + xi[r] * b.re;
+      }
+    }
+  }
+  for (int c = 0; c < CC; ++c) {
+    double* cc = reinterpret_cast<double*>(C + c * ldc);
+    for (int r = 0; r < R; ++r) {
+      cc[2 * r] -= ar[c][r];
+      cc[2 * r + 1] -= ai[c][r];
+    }
+  }
+}
+// the same for an arbitrary (small) tile
+template <typename T>
+inline void mk_sub_any(const T* A, int64_t lda, const T* B, int64_t bk, int64_t bc, T* C, int64_t ldc, int64_t M,
+                       int64_t N, int64_t K) {
+  for (int64_t c = 0; c < N; ++c)
+    for (int64_t r = 0; r < M; ++r) {
+      T acc(0.0);
+      for (int64_t k = 0; k < K; ++k) acc = acc + A[r + k * lda] * B[k * bk + c * bc];
+      C[r + c * ldc] = C[r + c * ldc] - acc;
+    }
+}
+
+// C (M x N, column-major ldc) -= A (M x K, column-major lda) * B, B(k, c) = B[k bk + c bc].
+// Serial; callers split the columns across threads.
+template <typename T>
+void gemm_sub(const T* A, int64_t lda, const T* B, int64_t bk, int64_t bc, T* C, int64_t ldc, int64_t M,
+              int64_t N, int64_t K) {
+  constexpr int R = 8;
+  constexpr int CC = std::is_same<T, cplx>::value ? 2 : 4;
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  int64_t r0 = 0;
+  for (; r0 + R <= M; r0 += R) {
+    int64_t c0 = 0;
+    for (; c0 + CC <= N; c0 += CC) mk_sub<R, CC>(A + r0, lda, B + c0 * bc, bk, bc, C + r0 + c0 * ldc, ldc, K);
+    if (c0 < N) mk_sub_any(A + r0, lda, B + c0 * bc, bk, bc, C + r0 + c0 * ldc, ldc, (int64_t)R, N - c0, K);
+  }
+  if (r0 < M) mk_sub_any(A + r0, lda, B, bk, bc, C + r0, ldc, M - r0, N, K);
+}
+
+constexpr int64_t kPanel = 64;   // panel width of the blocked LDL^T
+constexpr int64_t kColGroup = 16;   // columns per parallel task
 
 // Partial LDL^T of the dense front F (m x m, column-major, lower triangle valid):
 // eliminate the first nc columns; afterwards F[:, :nc] holds L (unit diagonal
 // implied) below the diagonal and D on it, F[nc:, nc:] the Schur complement.
+// Blocked right-looking: per panel of kPanel columns the diagonal block is factored
+// column by column, the rows below it in parallel row chunks, then the trailing
+// lower triangle is updated with W = L_panel D_panel as register-tiled products.
 template <typename T>
-bool front_ldlt(T* F, int64_t m, int64_t nc, int nthreads) {
-  const int64_t NB = 32;
-  for (int64_t kb = 0; kb < nc; kb += NB) {
-    const int64_t ke = std::min(kb + NB, nc);
+bool front_ldlt(T* F, int64_t m, int64_t nc, Pool* pool) {
+  std::vector<T> Wt;
+  for (int64_t kb = 0; kb < nc; kb += kPanel) {
+    const int64_t ke = std::min(kb + kPanel, nc), K = ke - kb;
+    // diagonal block rows kb..ke-1 of the panel (left-looking inside the panel)
     for (int64_t k = kb; k < ke; ++k) {
       T* colk = F + k * m;
       for (int64_t j = kb; j < k; ++j) {
         const T t = mul(F[j * m + j], F[j * m + k]);   // D_j * L_kj
-        axpy_sub(colk + k, F + j * m + k, t, m - k);
+        for (int64_t i = k; i < ke; ++i) colk[i] = colk[i] - F[j * m + i] * t;
       }
       const T d = colk[k];
       if (!(absv(d) > 0.0) || !isfin(d)) return false;
       const T di = inv(d);
-      for (int64_t i = k + 1; i < m; ++i) colk[i] = mul(colk[i], di);
+      for (int64_t i = k + 1; i < ke; ++i) colk[i] = mul(colk[i], di);
     }
-    // trailing update of columns ke..m-1 with the panel kb..ke-1
-    const int64_t ncols = m - ke;
-    auto update_col = [&](int64_t cc) {
-      const int64_t c = ke + cc;
-      T* colc = F + c * m;
-      int64_t j = kb;
-      for (; j + 4 <= ke; j += 4) {
-        const T t0 = mul(F[j * m + j], F[j * m + c]);
-        const T t1 = mul(F[(j + 1) * m + j + 1], F[(j + 1) * m + c]);
-        const T t2 = mul(F[(j + 2) * m + j + 2], F[(j + 2) * m + c]);
-        const T t3 = mul(F[(j + 3) * m + j + 3], F[(j + 3) * m + c]);
-        axpy4_sub(colc + c, F + j * m + c, F + (j + 1) * m + c, F + (j + 2) * m + c, F + (j + 3) * m + c,
-                  t0, t1, t2, t3, m - c);
+    // rows below the diagonal block, in independent row chunks
+    const int64_t rows = m - ke, chunk = 256;
+    pfor(rows > chunk ? pool : nullptr, (rows + chunk - 1) / chunk, [&](int64_t ci) {
+      const int64_t r0 = ke + ci * chunk, r1 = std::min(m, r0 + chunk);
+      for (int64_t k = kb; k < ke; ++k) {
+        T* colk = F + k * m;
+        for (int64_t j = kb; j < k; ++j) {
+          const T t = mul(F[j * m + j], F[j * m + k]);
+          const T* colj = F + j * m;
+          for (int64_t i = r0; i < r1; ++i) colk[i] = colk[i] - colj[i] * t;
+        }
+        const T di = inv(colk[k]);
+        for (int64_t i = r0; i < r1; ++i) colk[i] = mul(colk[i], di);
       }
-      for (; j < ke; ++j) {
-        const T t = mul(F[j * m + j], F[j * m + c]);
-        axpy_sub(colc + c, F + j * m + c, t, m - c);
-      }
-    };
-    const int nt = (ncols * (m - ke) > 200000) ? nthreads : 1;
-    parallel_for(ncols, nt, update_col);
+    });
+    // trailing update: F[r][c] -= sum_k L[r][k] D_k L[c][k] for c >= ke, r >= c
+    const int64_t P = m - ke;
+    if (P <= 0) continue;
+    Wt.resize((size_t)(K * P));
+    for (int64_t k = 0; k < K; ++k) {
+      const T d = F[(kb + k) * m + kb + k];
+      const T* lk = F + (kb + k) * m + ke;
+      T* w = Wt.data() + k * P;
+      for (int64_t c = 0; c < P; ++c) w[c] = mul(d, lk[c]);
+    }
+    const int64_t ngroups = (P + kColGroup - 1) / kColGroup;
+    pfor(P * P > 4096 ? pool : nullptr, ngroups, [&](int64_t g) {
+      const int64_t c0 = ke + g * kColGroup, c1 = std::min(m, c0 + kColGroup);
+      gemm_sub(F + kb * m + c0, m, Wt.data() + (c0 - ke), P, 1, F + c0 * m + c0, m, m - c0, c1 - c0, K);
+    });
   }
   return true;
+}
+
+// X = L11^{-1} (nc x nc, column-major) for the unit lower triangle L11 of the front:
+// forward substitution on groups of kColGroup columns, blocked by kPanel rows.
+template <typename T>
+void tri_inverse(const T* F, int64_t m, int64_t nc, T* X, Pool* pool) {
+  const int64_t ngroups = (nc + kColGroup - 1) / kColGroup;
+  pfor(nc > 128 ? pool : nullptr, ngroups, [&](int64_t g) {
+    const int64_t j0 = g * kColGroup, j1 = std::min(nc, j0 + kColGroup), N = j1 - j0;
+    for (int64_t j = j0; j < j1; ++j) {
+      T* x = X + j * nc;
+      std::fill(x, x + nc, T(0.0));
+      x[j] = T(1.0);
+    }
+    for (int64_t b0 = (j0 / kPanel) * kPanel; b0 < nc; b0 += kPanel) {
+      const int64_t b1 = std::min(nc, b0 + kPanel);
+      for (int64_t k = b0; k < b1; ++k) {
+        const T* lk = F + k * m;
+        for (int64_t c = 0; c < N; ++c) {
+          T* x = X + (j0 + c) * nc;
+          const T xk = x[k];
+          for (int64_t i = k + 1; i < b1; ++i) x[i] = x[i] - lk[i] * xk;
+        }
+      }
+      if (b1 < nc)
+        gemm_sub(F + b0 * m + b1, m, X + j0 * nc + b0, 1, nc, X + j0 * nc + b1, nc, nc - b1, N, b1 - b0);
+    }
+  });
 }
 
 struct NDNode {
@@ -282,13 +433,20 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
     }
   }
 
-  // ---------------- numeric multifrontal factorisation
+  // ---------------- numeric multifrontal factorisation, one tree depth at a time
+  // (supernodes of one depth are independent; deep depths run one supernode per
+  // thread, the few large fronts near the root use all threads inside the front)
   std::vector<std::vector<T>> upd(nn);
-  std::vector<T> front, Linv;
-  for (int s = 0; s < nn; ++s) {
+  std::vector<std::vector<int>> by_depth(F.max_depth + 1);
+  for (int s = 0; s < nn; ++s) by_depth[F.nodes[s].depth].push_back(s);
+  const int nthr = std::max(1, nthreads);
+  Pool pool(nthr);
+  std::vector<char> bad(nn, 0);
+
+  auto factor_node = [&](int s, Pool* inner) {
     const auto& nd = F.nodes[s];
     const int64_t nc = nd.nc, nr = nd.nr, m = nc + nr;
-    front.assign(m * m, T(0.0));
+    std::vector<T> front((size_t)(m * m), T(0.0));
     for (int64_t jl = 0; jl < nc; ++jl) {
       const int32_t j = F.perm[nd.col0 + jl];
       for (int64_t q = A.rowptr[j]; q < A.rowptr[j + 1]; ++q) {
@@ -313,38 +471,47 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
         }
       std::vector<T>().swap(upd[ch]);
     }
-    if (!front_ldlt(front.data(), m, nc, nthreads)) {
-      err = "zero or non-finite pivot in LDL^T";
-      return 6;
+    if (!front_ldlt(front.data(), m, nc, inner)) {
+      bad[s] = 1;
+      return;
     }
     if (nr > 0) {
-      upd[s].assign(nr * nr, T(0.0));
+      upd[s].assign((size_t)(nr * nr), T(0.0));
       for (int64_t b = 0; b < nr; ++b)
         for (int64_t a = b; a < nr; ++a) upd[s][b * nr + a] = front[(nc + b) * m + nc + a];
     }
     for (int64_t k = 0; k < nc; ++k) F.Dinv[nd.col0 + k] = inv(front[k * m + k]);
-    // Linv = L11^{-1} (unit lower), column-major nc x nc
-    Linv.assign(nc * nc, T(0.0));
-    parallel_for(nc, nc > 256 ? nthreads : 1, [&](int64_t j) {
-      T* x = Linv.data() + j * nc;
-      x[j] = T(1.0);
-      for (int64_t k = j; k < nc; ++k) {
-        const T xk = x[k];
-        axpy_sub(x + k + 1, front.data() + k * m + k + 1, xk, nc - k - 1);
-      }
-    });
-    // W top = Linv (row-major), W bottom = -L21 Linv
+    // X = L11^{-1}; W top = X (row-major lower), W bottom = -L21 X
+    std::vector<T> X((size_t)(nc * nc));
+    tri_inverse(front.data(), m, nc, X.data(), inner);
     T* W = F.W.data() + nd.w_off;
     for (int64_t i = 0; i < nc; ++i)
-      for (int64_t j = 0; j <= i; ++j) W[i * nc + j] = Linv[j * nc + i];
-    if (nr > 0)
-      parallel_for(nc, nr * nc > 100000 ? nthreads : 1, [&](int64_t j) {
-        // column j of -L21 Linv = -sum_{k>=j} Linv[k][j] * L21[:, k]
-        std::vector<T> acc(nr, T(0.0));
-        const T* lj = Linv.data() + j * nc;
-        for (int64_t k = j; k < nc; ++k) axpy_sub(acc.data(), front.data() + k * m + nc, T(0.0) - lj[k], nr);
-        for (int64_t r = 0; r < nr; ++r) W[(nc + r) * nc + j] = T(0.0) - acc[r];
+      for (int64_t j = 0; j <= i; ++j) W[i * nc + j] = X[j * nc + i];
+    if (nr > 0) {
+      std::vector<T> Tb((size_t)(nr * nc), T(0.0));   // column-major nr x nc
+      const int64_t ngroups = (nc + kColGroup - 1) / kColGroup;
+      pfor(nr * nc > 16384 ? inner : nullptr, ngroups, [&](int64_t g) {
+        const int64_t j0 = g * kColGroup, j1 = std::min(nc, j0 + kColGroup);
+        gemm_sub(front.data() + j0 * m + nc, m, X.data() + j0 * nc + j0, 1, nc, Tb.data() + j0 * nr, nr, nr,
+                 j1 - j0, nc - j0);
       });
+      for (int64_t r = 0; r < nr; ++r)
+        for (int64_t j = 0; j < nc; ++j) W[(nc + r) * nc + j] = Tb[j * nr + r];
+    }
+  };
+
+  for (int d = F.max_depth; d >= 0; --d) {
+    const auto& lst = by_depth[d];
+    if ((int)lst.size() >= nthr || nthr == 1) {
+      pool.run((int64_t)lst.size(), [&](int64_t i) { factor_node(lst[i], nullptr); });
+    } else {
+      for (int s : lst) factor_node(s, &pool);
+    }
+    for (int s : lst)
+      if (bad[s]) {
+        err = "zero or non-finite pivot in LDL^T";
+        return 6;
+      }
   }
   return 0;
 }

@@ -119,7 +119,8 @@ struct NodalFactor {
   DevArena mem;
   DevFactor<double> kn;
   DevFactor<double, float2> kn_df;                        // the same factor as FP32 pairs
-  FactorLists kn_lists, kn_df_lists;
+  DevFactor<float> kn_f;                                  // the same factor rounded to FP32
+  FactorLists kn_lists, kn_df_lists, kn_f_lists;
   int64_t u_rows = 0, max_items = 0;
 };
 
@@ -254,7 +255,7 @@ struct st_mg_s {
   double* partial = nullptr;
   double* scalar = nullptr;
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
-  bool nodal_df = false;                // nodal K_n solve in double-float (every mode but FP64)
+  int nodal_prec = 0;                   // nodal K_n solve: 0 FP64, 1 FP32 (slab_prec 1, 3), 2 double-float
   int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
   float2* tcP = nullptr;                // tensor-core split-K partials
   uint8_t* tcB = nullptr;               // tensor-core right-hand-side tiles of one depth
@@ -661,7 +662,17 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
   const int ncols = L.N_t * h.B * h.q;
   if (h.opt.nodal_solve == 0) {
     CK(gather_perm(y, ncols, S.nf->kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
-    if (h.nodal_df)
+    if (h.nodal_prec == 1) {
+      // FP32 (a preconditioner step of the mixed-precision modes): float views of the
+      // double workspaces
+      float* Qf = reinterpret_cast<float*>(h.nQ);
+      CK(gather_perm_f(y, ncols, S.nf->kn.iperm, S.nn, Qf, h.ld_nod, h.stream));
+      CK(sn_solve_realf(S.nf->kn_f, Qf, reinterpret_cast<float*>(h.nZ), reinterpret_cast<float*>(h.nU),
+                        reinterpret_cast<float*>(h.nP), ncols, h.ld_nod, h.stream));
+      CK(scatter_perm_f(Qf, h.ld_nod, S.nf->kn.iperm, S.nn, z, ncols, h.stream));
+      return;
+    }
+    if (h.nodal_prec == 2)
       CK(sn_solve_real_df(S.nf->kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
     else
       CK(sn_solve_real(S.nf->kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
@@ -923,7 +934,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   for (size_t l = 0; l < H.lv.size(); ++l)
     H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec == 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
   H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
-  H.nodal_df = op->slab_prec != 0;
+  H.nodal_prec = op->slab_prec == 0 ? 0 : op->slab_prec == 2 ? 2 : 1;
 
   // ---- factor cache: take every factor an earlier handle left resident
   H.use_cache = op->factor_cache != 0 && !host_only;
@@ -943,7 +954,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       lkey[l] = buf;
     }
     for (size_t sl = 0; sl < H.space.size(); ++sl) {
-      std::snprintf(buf, sizeof buf, "nodal dev%d n%d s%d df%d mat%016llx", H.device, n, (int)sl, H.nodal_df ? 1 : 0,
+      std::snprintf(buf, sizeof buf, "nodal dev%d n%d s%d np%d mat%016llx", H.device, n, (int)sl, H.nodal_prec,
                     (unsigned long long)H.mat_hash);
       skey[sl] = buf;
     }
@@ -971,8 +982,9 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   std::vector<std::string> errs(H.lv.size() + H.space.size());
   std::vector<int> rcs(errs.size(), 0);
   {
+    // one factorisation at a time, each with every thread (tree and front parallelism)
     const int njobs = (int)errs.size();
-    const int inner = std::max(1, nthr / std::max(1, njobs));
+    const int inner = nthr;
     std::vector<std::thread> jobs;
     std::mutex mu;
     int next = 0;
@@ -1005,8 +1017,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
         }
       }
     };
-    const int nw = std::min(nthr, njobs);
-    for (int t = 0; t < nw; ++t) jobs.emplace_back(worker);
+    jobs.emplace_back(worker);
     for (auto& t : jobs) t.join();
   }
   for (size_t j = 0; j < rcs.size(); ++j)
@@ -1064,7 +1075,8 @@ int setup_device(Handle& H) {
       auto N = std::make_shared<NodalFactor>();
       N->mem.n_sm = H.n_sm;
       make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists);
-      if (H.nodal_df) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists);
+      if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists);
+      if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists);
       N->u_rows = N->kn.u_rows;
       N->max_items = N->kn.max_items;
       S.nf = N;

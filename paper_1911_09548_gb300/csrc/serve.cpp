@@ -246,6 +246,18 @@ int finish_class(Server& S, Class& c) {
 }
 
 int step(Server& S, std::vector<int64_t>& done) {
+  // nothing on the device but builds in progress: wait a little for one of them
+  // rather than return at once (a caller looping on step would spin against the
+  // factorisation threads)
+  {
+    bool occupied = false;
+    Class* building = nullptr;
+    for (auto& kv : S.cls) {
+      occupied = occupied || kv.second->occupied() > 0;
+      if (!kv.second->ready && kv.second->build.valid()) building = kv.second.get();
+    }
+    if (!occupied && building) building->build.wait_for(std::chrono::milliseconds(5));
+  }
   // (1) class builds whose host phase finished
   std::vector<std::string> failed;
   for (auto& kv : S.cls) {

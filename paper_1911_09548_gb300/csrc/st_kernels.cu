@@ -11,7 +11,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RES_WARPS = 8;   // rows (warps) per block of the residual kernels
-constexpr int SPL = 8;         // slabs per lane per pass (32 * SPL slabs per pass)
+constexpr int SPL = 8;         // slabs per lane per pass (32 * SPL slabs per pass), FP64 kernels
+constexpr int SPL_DF = 2;      // the same for the double-float kernels (4 pairs of accumulators per
+                               // slab: fewer slabs per pass keep enough warps resident)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -217,16 +219,16 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
     const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
     double2* r2 = reinterpret_cast<double2*>(r + row * ld);
     double carry = 0.0;
-    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
-      dpair A0[SPL], A1[SPL], B0[SPL], B1[SPL];
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL_DF) {
+      dpair A0[SPL_DF], A1[SPL_DF], B0[SPL_DF], B1[SPL_DF];
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = dpair{0.f, 0.f};
+      for (int j = 0; j < SPL_DF; ++j) A0[j] = A1[j] = B0[j] = B1[j] = dpair{0.f, 0.f};
       for (int64_t q = beg; q < end; ++q) {
         const int64_t c = col[q];
         const float2 mv = m[q], kv0 = k0[q], kv1 = k1[q];
         const float4* xr = reinterpret_cast<const float4*>(xs + c * ld);
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) {
+        for (int j = 0; j < SPL_DF; ++j) {
           const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const float4 v = xr[n];   // (x0 hi, x0 lo, x1 hi, x1 lo)
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
       }
       double prevA = carry;
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) {
+      for (int j = 0; j < SPL_DF; ++j) {
         const double a0 = dp_join(A0[j]), a1 = dp_join(A1[j]);
         const double As = a0 + a1;
         const double up = __shfl_up_sync(FULL, As, 1, LPR);
@@ -284,16 +286,16 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
     const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = N_t;
     double carry = 0.0;
-    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
-      dpair Ax[SPL], Mx[SPL];
+    for (int n0 = 0; n0 < N_t; n0 += LPR * SPL_DF) {
+      dpair Ax[SPL_DF], Mx[SPL_DF];
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = dpair{0.f, 0.f};
+      for (int j = 0; j < SPL_DF; ++j) Ax[j] = Mx[j] = dpair{0.f, 0.f};
       for (int64_t q = beg; q < end; ++q) {
         const int64_t c = col[q];
         const float2 av = a[q], mv = m[q];
         const float2* xr = xs + c * ld;
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) {
+        for (int j = 0; j < SPL_DF; ++j) {
           const int n = n0 + LPR * j + lane;
           if (n < N_t) {
             const float2 v = xr[n];
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
       }
       double prev = carry;
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) {
+      for (int j = 0; j < SPL_DF; ++j) {
         const double mx = dp_join(Mx[j]);
         const double up = __shfl_up_sync(FULL, mx, 1, LPR);
         const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
@@ -445,20 +447,22 @@ __global__ void k_slab_post_dg1f(const float2* __restrict__ X, int ld, const int
   }
 }
 
+template <typename TQ>
 __global__ void k_gather_perm(const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
-                              double* __restrict__ Q, int ld) {
+                              TQ* __restrict__ Q, int ld) {
   const int v = blockIdx.x;
   const double* src = y + (int64_t)v * ncols;
-  double* dst = Q + (int64_t)iperm[v] * ld;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = src[j];
+  TQ* dst = Q + (int64_t)iperm[v] * ld;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = (TQ)src[j];
 }
 
-__global__ void k_scatter_perm(const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+template <typename TQ>
+__global__ void k_scatter_perm(const TQ* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                double* __restrict__ z, int ncols) {
   const int v = blockIdx.x;
-  const double* src = X + (int64_t)iperm[v] * ld;
+  const TQ* src = X + (int64_t)iperm[v] * ld;
   double* dst = z + (int64_t)v * ncols;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = src[j];
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = (double)src[j];
 }
 
 // y = G^T r: warp per node, lanes over the time columns.
@@ -827,12 +831,22 @@ cudaError_t slab_post_dg1f(const float2* X, int ld, const int32_t* iperm, int nr
 }
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
                         cudaStream_t st) {
-  if (nrows > 0) { k_gather_perm<<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_gather_perm<double><<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                          cudaStream_t st) {
-  if (nrows > 0) { k_scatter_perm<<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
+  if (nrows > 0) { k_scatter_perm<double><<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t gather_perm_f(const double* y, int ncols, const int32_t* iperm, int nrows, float* Q, int ld,
+                          cudaStream_t st) {
+  if (nrows > 0) { k_gather_perm<float><<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t scatter_perm_f(const float* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
+                           cudaStream_t st) {
+  if (nrows > 0) { k_scatter_perm<float><<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {

@@ -270,8 +270,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict_
   if (warp == 0) tmem_dealloc(tmem);
 }
 
-// One block per (unit = node row tile, column tile): sums the unit's K-chunk
-// partials in item order, then the forward or backward epilogue.
+// One block per (unit = node row tile, column tile, group of TC_RED_ROWS rows): sums
+// the unit's K-chunk partials in item order, then the forward or backward epilogue.
+constexpr int TC_RED_ROWS = 8;
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict__ nodes,
                                                       const float2* __restrict__ Dinv,
@@ -285,8 +286,9 @@ __global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict_
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int row0 = un.y * TC_ROWS, c0 = blockIdx.y * TC_N;
   const int rows_out = FWD ? m : nc;
-  for (int t = threadIdx.x; t < TC_ROWS * TC_N; t += blockDim.x) {
-    const int il = t / TC_N, cl = t % TC_N;
+  // block z: rows TC_RED_ROWS z .. TC_RED_ROWS (z + 1) - 1 of the unit's row tile
+  for (int t = threadIdx.x; t < TC_RED_ROWS * TC_N; t += blockDim.x) {
+    const int il = blockIdx.z * TC_RED_ROWS + t / TC_N, cl = t % TC_N;
     const int i = row0 + il, c = c0 + cl;
     if (i >= rows_out || c >= nrhs) continue;
     float2 y = make_float2(0.f, 0.f);
@@ -318,6 +320,9 @@ __global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict_
 
 constexpr int TC2_STAGES = 3;
 constexpr int TC2_SMEM = TC2_STAGES * 2 * kTcTileBytes + 1024;   // + alignment slack
+constexpr int TC2_OS = 2 * TC_N + 2;   // floats per staged output row (epilogue)
+static_assert(TC_ROWS * TC2_OS * 4 <= TC2_STAGES * 2 * kTcTileBytes, "epilogue tile must fit the stage buffers");
+static_assert(TC_THREADS == TC_N, "epilogue maps one column per thread");
 
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes));
@@ -350,7 +355,8 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
   const int4 tn = tnode[s];
   const int nks = FWD ? tn.y : tn.w;
   const int pre = FWD ? tpre[s].x : tpre[s].y;
-  uint8_t* tile = Bst + ((int64_t)gy * pre + (int64_t)ct * nks + ks) * kTcTileBytes;
+  __shared__ __align__(16) uint8_t tile[kTcTileBytes];
+  uint8_t* out = Bst + ((int64_t)gy * pre + (int64_t)ct * nks + ks) * kTcTileBytes;
   const int32_t* gs = gsrc + nd.g_off * 2;
   const int32_t* rw = rows + nd.row_off;
   const int kend = FWD ? nc : m;
@@ -370,6 +376,11 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
     }
     put_g(tile, cl, kk, g);
   }
+  __syncthreads();
+  // the finished tile leaves in 16-byte pieces, consecutive threads consecutive pieces
+  const uint4* src = reinterpret_cast<const uint4*>(tile);
+  uint4* dst = reinterpret_cast<uint4*>(out);
+  for (int t = threadIdx.x; t < kTcTileBytes / 16; t += blockDim.x) dst[t] = src[t];
 }
 
 // SPLIT = false: grid over (node, row tile) tiles, whole K range; SPLIT = true: grid
@@ -436,6 +447,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
   const uint32_t tmem = tmem_slot;
   const int nst = ks1 - ks0;
   bool ok = true;
+  int issued = 0;   // stages whose bulk copies thread 0 has started
   if (tid == 0) {
     // producer: stage i waits until the MMAs that used its buffers have completed
     for (int i = 0; i < nst && ok; ++i) {
@@ -446,6 +458,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
       mbar_arrive_tx(&full[slot], 2 * kTcTileBytes);
       bulk_g2s(smem_u32(a), atiles + (int64_t)(ks0 + i) * kTcTileBytes, kTcTileBytes, &full[slot]);
       bulk_g2s(smem_u32(a + kTcTileBytes), btiles + (int64_t)(ks0 + i) * kTcTileBytes, kTcTileBytes, &full[slot]);
+      issued = i + 1;
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -468,50 +481,63 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty[slot])));
     }
-    if (ok) asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&done)));
+    // also after a failed wait: `done` then tracks the MMAs already issued, so that
+    // no thread frees TMEM or leaves while they run
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&done)));
   }
-  // everyone waits for the last MMA (a failed producer/issuer sets the flag instead)
+  // everyone waits for the last MMA; the result is used only if no wait failed
   if (!ok) atomicExch(err, 1);
   const bool mine = (nst > 0) && mbar_wait(&done, 0);
-  const bool fin = __syncthreads_and(mine) != 0;   // block-uniform: the TMEM loads are warp-collective
-  if (!fin && nst > 0 && tid == 0) atomicExch(err, 1);
+  const bool fin = __syncthreads_and(mine && ok) != 0;   // block-uniform: the TMEM loads are warp-collective
+  if (!fin && nst > 0 && tid == 0) {
+    atomicExch(err, 1);
+    // bulk copies still in flight land in this block's shared memory: wait for them
+    // (bounded) before the block can exit
+    for (int i = issued > TC2_STAGES ? issued - TC2_STAGES : 0; i < issued; ++i)
+      mbar_wait(&full[i % TC2_STAGES], (uint32_t)((i / TC2_STAGES) & 1));
+  }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (fin) {
+    // accumulator -> shared memory (the pipeline buffers are idle now): complex row
+    // il = R / 2 (R = TMEM lane), real part from even lanes, imaginary from odd ones;
+    // rows padded to 2 * TC_N + 2 floats so that a warp's 32 lanes hit 32 banks
+    float* Os = reinterpret_cast<float*>(base);
     const int R = warp * 32 + lane;
-    const int i = row0 + (R >> 1);
-    const bool even = (R & 1) == 0;
-    const int rows_out = FWD ? m : nc;
     for (int cb = 0; cb < TC_N; cb += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float mine = __uint_as_float(v[j]);
-        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-        const int c = c0 + cb + j;
-        if (SPLIT) {
-          if (even)
-            P[(((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_ROWS + (R >> 1)) * TC_N + cb + j] =
-                make_float2(mine, other);
-          continue;
-        }
-        if (!even || c >= nrhs || i >= rows_out) continue;
-        const float2 y = make_float2(mine, other);
-        if (FWD) {
-          if (i < nc) {
-            Z[(int64_t)(nd.col0 + i) * ld + c] = cmul(Dinv[nd.col0 + i], y);
-          } else {
-            float2 u = y;
-            const int32_t* gs = gsrc + nd.g_off * 2;
-            const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
-            if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
-            if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
-            U[(int64_t)(nd.u_off + i - nc) * ld + c] = u;
-          }
+      for (int j = 0; j < 32; ++j) Os[(R >> 1) * TC2_OS + 2 * (cb + j) + (R & 1)] = __uint_as_float(v[j]);
+    }
+  }
+  __syncthreads();
+  if (fin) {
+    // one column per thread, row by row: coalesced stores and update-row reads
+    const float* Os = reinterpret_cast<const float*>(base);
+    const int rows_out = FWD ? m : nc;
+    const int c = c0 + tid;
+    const int32_t* gs = gsrc + nd.g_off * 2;
+    for (int il = 0; il < TC_ROWS; ++il) {
+      const int i = row0 + il;
+      const float2 y = *reinterpret_cast<const float2*>(Os + il * TC2_OS + 2 * tid);
+      if (SPLIT) {
+        P[(((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_ROWS + il) * TC_N + tid] = y;
+        continue;
+      }
+      if (i >= rows_out || c >= nrhs) continue;
+      if (FWD) {
+        if (i < nc) {
+          Z[(int64_t)(nd.col0 + i) * ld + c] = cmul(Dinv[nd.col0 + i], y);
         } else {
-          X[(int64_t)(nd.col0 + i) * ld + c] = y;
+          float2 u = y;
+          const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
+          if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
+          if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
+          U[(int64_t)(nd.u_off + i - nc) * ld + c] = u;
         }
+      } else {
+        X[(int64_t)(nd.col0 + i) * ld + c] = y;
       }
     }
   }
@@ -564,12 +590,12 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool
     if (fwd) {
       k_sn_tc2<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
           F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
-      k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
+      k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
                                                                            ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
     } else {
       k_sn_tc2<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
           F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
-      k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
+      k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
                                                                             ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
     }
     count_launches(2);
@@ -587,12 +613,12 @@ cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d,
   if (fwd) {
     k_sn_tc<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
         F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcf_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
-    k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
+    k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
                                                                          ia, ib - ia, P, Z, U, Q, nrhs, ld);
   } else {
     k_sn_tc<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
         F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcb_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
-    k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
+    k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
                                                                           ia, ib - ia, P, Z, U, Q, nrhs, ld);
   }
   count_launches(2);

@@ -55,12 +55,15 @@ class SpaceTimeServer:
     def stats(self):
         return B.st_mg_server_stats_get(self.h)
 
-    def run_until_idle(self, max_steps=100000):
-        """Step until nothing is queued, building or on the device; returns finished ids."""
+    def run_until_idle(self, timeout_s=3600.0):
+        """Step until nothing is queued, building or on the device; returns finished ids.
+        (A step with only builds pending waits a few ms for them inside the library.)"""
+        import time
         done = []
-        for _ in range(max_steps):
+        t_end = time.monotonic() + timeout_s
+        while time.monotonic() < t_end:
             done += self.step()
             s = self.stats()
             if s["queued"] == 0 and s["active"] == 0 and s["building"] == 0:
-                break
-        return done
+                return done
+        raise TimeoutError("server not idle after %.0f s" % timeout_s)

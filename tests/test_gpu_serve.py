@@ -69,7 +69,7 @@ def serve(stmg, slab_prec, slots=2, mem_budget=0, waves=(WAVE1, WAVE2)):
         for req in wave:
             n, p, N_t, tau, s, seed = req
             ids[srv.submit(n, p, N_t, tau, s, st_inputs.excitation(seed), RTOL)] = req
-        steps = 3 if w + 1 < len(waves) else 100000
+        steps = 3 if w + 1 < len(waves) else 1000000
         for _ in range(steps):
             for rid in srv.step():
                 results[ids[rid]] = srv.result(rid)
