@@ -103,6 +103,10 @@ typedef struct {
                                 launch sequence into a CUDA graph once per (f, x) buffer pair and replay
                                 it (needs a non-default stream; the first call captures, later calls
                                 replay); 0: launch kernel by kernel */
+    int32_t persistent_split;/* 1: slab and K_n solves with few right-hand sides (coarse time levels)
+                                run as two cooperative launches that walk every tree depth with grid
+                                barriers in between, instead of two launches per depth; 0 (default):
+                                per-depth launches (faster on GB300 at 16^3, see the design notes) */
     int32_t factor_cache;    /* 1: take slab and K_n factors from, and leave new ones in, the
                                 process-wide factor cache (key: device, mesh, space level, materials,
                                 DG degree, tau, precision), so handles that share a mesh and a tau

@@ -54,6 +54,8 @@ typedef struct {
     double omega;            /* smoother damping */
     int32_t setup_threads;   /* host threads per class build (0: all cores) */
     int32_t keep_x;          /* 1: copy every solution to the host for st_mg_server_result */
+    int32_t max_builds;      /* class builds (host phases) running at once, >= 1 (host memory and
+                                cores: each factorises on all threads) */
 } st_mg_server_options;
 
 typedef struct {

@@ -34,12 +34,12 @@ class Options(ctypes.Structure):
                 ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
                 ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32),
-                ("factor_cache", _i32)]
+                ("persistent_split", _i32), ("factor_cache", _i32)]
 
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("slots", _i32), ("mem_budget", _i64), ("max_cycles", _i32), ("slab_prec", _i32), ("nu", _i32),
-                ("omega", _dbl), ("setup_threads", _i32), ("keep_x", _i32)]
+                ("omega", _dbl), ("setup_threads", _i32), ("keep_x", _i32), ("max_builds", _i32)]
 
 
 class Request(ctypes.Structure):

@@ -42,6 +42,10 @@ struct DevFactor {
   int4* fs_units = nullptr;
   int4* bs_items = nullptr;
   int4* bs_units = nullptr;
+  const int64_t* d_fs_item_off = nullptr;   // the four offset arrays below, on the device
+  const int64_t* d_fs_unit_off = nullptr;   // (persistent split-K solve)
+  const int64_t* d_bs_item_off = nullptr;
+  const int64_t* d_bs_unit_off = nullptr;
   int64_t* h_fs_item_off = nullptr;   // host, size max_depth + 2
   int64_t* h_fs_unit_off = nullptr;
   int64_t* h_bs_item_off = nullptr;
@@ -93,44 +97,46 @@ constexpr int kSnBM = 64;
 // Q (in) is overwritten by X (out); Z and U are workspaces ([n*ld], [u_rows*ld]).
 // P is the split-K partial buffer: max_items * kSkRows * (max right-hand sides per
 // solve, rounded up to the column block) elements.  Null disables the split-K path.
+// Per-handle state of the persistent split-K slab solve: grid-barrier words
+// (arrivals, generation; zero at allocation) and the flag a bounded wait sets.
+// bar == nullptr disables the persistent launch.
+struct SkSync {
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+};
+
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,
-                          cudaStream_t st);
+                          const SkSync& sy, cudaStream_t st);
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
-                          int ld, cudaStream_t st);
+                          int ld, const SkSync& sy, cudaStream_t st);
 
 // Mixed precision: the same solve with the factor and the right-hand sides in FP32
 // (factor computed in FP64 and rounded once at setup).
 cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
-                           cudaStream_t st);
+                           const SkSync& sy, cudaStream_t st);
 cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, float2* U, float2* P, int nrhs, int ld,
-                           cudaStream_t st);
+                           const SkSync& sy, cudaStream_t st);
 
 // BF16 factor on the tensor cores (DG(1)): W as complex BF16, right-hand sides and
 // accumulation in FP32.  Depths with enough tiles run the tcgen05 kernels (64
-// complex rows x kTcCols right-hand sides per block), the others and small nrhs
-// the split-K kernels.  err: device int set to 1 if a tensor-core wait timed out.
+// complex rows x kTcCols right-hand sides per block), the others split K into
+// chunks (Ptc: max_tc_items * ceil(nrhs / kTcCols) * kSnBM * kTcCols float2); small
+// nrhs takes the CUDA-core split-K path.  sy.err: set to 1 if a bounded wait timed out.
 constexpr int kTcCols = 128;
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err, cudaStream_t st);
-cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
-                          int nrhs, int ld, int* err, cudaStream_t st);
-cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
-                           int nrhs, int ld, int* err, cudaStream_t st);
+                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
+                               cudaStream_t st);
 // Pipelined tensor-core depth: assemble the right-hand-side tiles of the depth into
 // Bst (gy * max_stage_tiles tiles), then the products with bulk-copied operand tiles.
 cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
                          float2* Z, float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err,
                          cudaStream_t st);
-// Split-K tensor-core depth: partial products of K chunks into P (max_tc_items *
-// ceil(nrhs / kTcCols) * kSnBM * kTcCols float2), then a fixed-order reduction + epilogue.
-cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
-                              float2* U, float2* P, int nrhs, int ld, int* err, cudaStream_t st);
 
 // FP64-accurate double-float path (W as FP32 pairs, FP64 right-hand sides).
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
-                             int ld, cudaStream_t st);
+                             int ld, const SkSync& sy, cudaStream_t st);
 cudaError_t sn_solve_cplx_df(const DevFactor<double2, float4>& F, double2* Q, double2* Z, double2* U, double2* P,
-                             int nrhs, int ld, cudaStream_t st);
+                             int nrhs, int ld, const SkSync& sy, cudaStream_t st);
 
 // ---- space-time kernels.  Edge-major layout v[e*ncols + n*q + i], ncols = N_t*q.
 struct CsrView {

@@ -256,7 +256,9 @@ struct st_mg_s {
   double* scalar = nullptr;
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
   int nodal_prec = 0;                   // nodal K_n solve: 0 FP64, 1 FP32 (slab_prec 1, 3), 2 double-float
-  int* tc_err = nullptr;                // set by a tensor-core block whose wait timed out
+  int* tc_err = nullptr;                // flags[0]: set by a block whose bounded wait timed out
+  int* flags = nullptr;                 // [0] wait error, [1] spare, [2..3] grid-barrier words
+  SkSync sk;                            // persistent split-K solve: barrier words + error flag
   float2* tcP = nullptr;                // tensor-core split-K partials
   uint8_t* tcB = nullptr;               // tensor-core right-hand-side tiles of one depth
   double* bn_partial = nullptr;         // per-problem norm scratch
@@ -482,6 +484,10 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
   D.h_fs_unit_off = Lh.fsu.data();
   D.h_bs_item_off = Lh.bsi.data();
   D.h_bs_unit_off = Lh.bsu.data();
+  D.d_fs_item_off = h.upload(Lh.fsi);
+  D.d_fs_unit_off = h.upload(Lh.fsu);
+  D.d_bs_item_off = h.upload(Lh.bsi);
+  D.d_bs_unit_off = h.upload(Lh.bsu);
   D.max_items = max_items;
   D.n_sm = h.n_sm;
   // tensor-core split-K items: the tiles above, each cut into kTcSplitK-wide K chunks
@@ -589,7 +595,7 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     float2* Q = static_cast<float2*>(h.sQ);
     CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
     CK(sn_solve_cplx_bf16(L.fac->dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                          static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, h.tc_err, h.stream));
+                          static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, h.sk, h.stream));
     CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     return;
   }
@@ -598,7 +604,7 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
       float* Q = static_cast<float*>(h.sQ);
       CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.fac->drf.iperm, S.ne, Q, h.ld_slab, h.stream));
       CK(sn_solve_realf(L.fac->drf, Q, static_cast<float*>(h.sZ), static_cast<float*>(h.sU), static_cast<float*>(h.sP),
-                        cnt, h.ld_slab, h.stream));
+                        cnt, h.ld_slab, h.sk, h.stream));
       CK(slab_post_dg0f(Q, h.ld_slab, L.fac->drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     } else {
       const double inv_tau = 1.0 / L.tau;
@@ -607,7 +613,7 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
       float2* Q = static_cast<float2*>(h.sQ);
       CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcf.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
       CK(sn_solve_cplxf(L.fac->dcf, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                        static_cast<float2*>(h.sP), cnt, h.ld_slab, h.stream));
+                        static_cast<float2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
       CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcf.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     }
     return;
@@ -618,10 +624,10 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     CK(slab_pre_dg0(src, src_ld, slab0, cnt, ip, S.ne, Q, h.ld_slab, h.stream));
     if (L.prec == 2)
       CK(sn_solve_real_df(L.fac->drd, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
-                          static_cast<double*>(h.sP), cnt, h.ld_slab, h.stream));
+                          static_cast<double*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
     else
       CK(sn_solve_real(L.fac->dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
-                       cnt, h.ld_slab, h.stream));
+                       cnt, h.ld_slab, h.sk, h.stream));
     CK(slab_post_dg0(Q, h.ld_slab, ip, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   } else {
     const double inv_tau = 1.0 / L.tau;
@@ -632,10 +638,10 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     CK(slab_pre_dg1(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
     if (L.prec == 2)
       CK(sn_solve_cplx_df(L.fac->dcd, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
-                          static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
+                          static_cast<double2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
     else
       CK(sn_solve_cplx(L.fac->dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
-                       static_cast<double2*>(h.sP), cnt, h.ld_slab, h.stream));
+                       static_cast<double2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
     CK(slab_post_dg1(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   }
 }
@@ -668,14 +674,14 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
       float* Qf = reinterpret_cast<float*>(h.nQ);
       CK(gather_perm_f(y, ncols, S.nf->kn.iperm, S.nn, Qf, h.ld_nod, h.stream));
       CK(sn_solve_realf(S.nf->kn_f, Qf, reinterpret_cast<float*>(h.nZ), reinterpret_cast<float*>(h.nU),
-                        reinterpret_cast<float*>(h.nP), ncols, h.ld_nod, h.stream));
+                        reinterpret_cast<float*>(h.nP), ncols, h.ld_nod, h.sk, h.stream));
       CK(scatter_perm_f(Qf, h.ld_nod, S.nf->kn.iperm, S.nn, z, ncols, h.stream));
       return;
     }
     if (h.nodal_prec == 2)
-      CK(sn_solve_real_df(S.nf->kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+      CK(sn_solve_real_df(S.nf->kn_df, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.sk, h.stream));
     else
-      CK(sn_solve_real(S.nf->kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.stream));
+      CK(sn_solve_real(S.nf->kn, h.nQ, h.nZ, h.nU, h.nP, ncols, h.ld_nod, h.sk, h.stream));
     CK(scatter_perm(h.nQ, h.ld_nod, S.nf->kn.iperm, S.nn, z, ncols, h.stream));
   } else {
     // damped Jacobi from z = 0, ping-pong through the nodal workspace
@@ -831,6 +837,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
+      (op->persistent_split != 0 && op->persistent_split != 1) ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = (int64_t)6 * n * n * n;
@@ -1204,9 +1211,12 @@ int setup_device(Handle& H) {
   H.g1 = H.dalloc<double>(max_ne * H.q * H.B);
   H.r0 = H.dalloc<double>(H.lv[0].len);
   if (H.df_residual) H.xsplit = H.dalloc<float2>(H.lv[0].len);
+  H.flags = H.dalloc<int>(4);
+  CK(cudaMemset(H.flags, 0, 4 * sizeof(int)));
+  H.tc_err = H.flags;
+  H.sk.bar = op->persistent_split ? reinterpret_cast<unsigned*>(H.flags + 2) : nullptr;
+  H.sk.err = H.flags;
   if (op->slab_prec == 3) {
-    H.tc_err = H.dalloc<int>(1);
-    CK(cudaMemset(H.tc_err, 0, sizeof(int)));
     int64_t mt = 1;
     for (auto& L : H.lv)
       if (L.prec == 3) mt = std::max<int64_t>(mt, L.fac->max_tc_items);
@@ -1234,8 +1244,10 @@ int check_tc(Handle& H) {
   CK(cudaMemcpyAsync(&v, H.tc_err, sizeof(int), cudaMemcpyDeviceToHost, H.stream));
   CK(cudaStreamSynchronize(H.stream));
   if (v) {
-    CK(cudaMemsetAsync(H.tc_err, 0, sizeof(int), H.stream));
-    return fail(ST_MG_ERR_TIMEOUT, "a tensor-core wait timed out; results of this call are invalid");
+    // clear the flag and the grid-barrier words a timed-out barrier may have left behind
+    CK(cudaMemsetAsync(H.flags, 0, 4 * sizeof(int), H.stream));
+    CK(cudaStreamSynchronize(H.stream));
+    return fail(ST_MG_ERR_TIMEOUT, "a bounded device wait timed out; results of this call are invalid");
   }
   return ST_MG_OK;
 }
@@ -1370,6 +1382,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->slab_prec = 0;
   o->residual_prec = -1;
   o->use_graph = 1;
+  o->persistent_split = 0;
   o->factor_cache = 0;
   return ST_MG_OK;
 }

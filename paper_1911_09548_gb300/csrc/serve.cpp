@@ -291,6 +291,12 @@ int step(Server& S, std::vector<int64_t>& done) {
     auto ci = S.cls.find(q.cls);
     Class* c = ci == S.cls.end() ? nullptr : ci->second.get();
     if (!c) {
+      int building = 0;
+      for (auto& kv : S.cls) building += kv.second->ready ? 0 : 1;
+      if (building >= S.opt.max_builds) {   // wait for a build slot
+        ++it;
+        continue;
+      }
       const int64_t need = estimate_bytes(S, q.n_cube, q.degree, q.N_t);
       make_room(S, need);
       bool busy = false;   // anything on the device or being built: then waiting frees memory
@@ -419,6 +425,7 @@ int st_mg_server_default_options(st_mg_server_options* o) {
   o->omega = 0.5;
   o->setup_threads = 0;
   o->keep_x = 1;
+  o->max_builds = 2;
   return ST_MG_OK;
 }
 
@@ -426,7 +433,7 @@ int st_mg_server_create(const st_mg_server_options* opt, st_mg_server_t* out) {
   if (!opt || !out) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (opt->slots < 1 || opt->mem_budget < 0 || opt->max_cycles < 1 || opt->slab_prec < 0 || opt->slab_prec > 3 ||
-      opt->nu < 0 || !(opt->omega > 0))
+      opt->nu < 0 || !(opt->omega > 0) || opt->max_builds < 1)
     return fail(ST_MG_ERR_INVALID_ARG, "invalid server options");
   auto S = std::make_unique<Server>();
   S->opt = *opt;

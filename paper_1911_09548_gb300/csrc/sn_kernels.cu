@@ -319,30 +319,40 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
 constexpr int SK_THREADS = kSkRows;
 constexpr int SK_KS = 16;   // K columns staged in shared memory at a time
 
+// One item (kSkRows rows x one K chunk) x one column block of NB right-hand sides,
+// computed by one warp (lane = row); As, Bs: the warp's shared-memory stage.  The
+// kSkRows x NB partial product goes to out (row-major).
 template <typename P, int NB, bool FWD>
-__global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
-    const DevNode* __restrict__ nodes, const typename P::WT* __restrict__ W, const int32_t* __restrict__ gsrc,
-    const int32_t* __restrict__ rows, const int4* __restrict__ items, const typename P::S* __restrict__ Q,
-    const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U, const typename P::S* __restrict__ X,
-    typename P::S* __restrict__ Pt, int nrhs, int ld) {
+__device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const typename P::WT* __restrict__ W,
+                                        const int32_t* __restrict__ gsrc, const int32_t* __restrict__ rows, int4 it,
+                                        int cb, const typename P::S* __restrict__ Q,
+                                        const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U,
+                                        const typename P::S* __restrict__ X, typename P::S* __restrict__ out,
+                                        int nrhs, int ld, typename P::A (*As)[kSkRows + 1],
+                                        typename P::A (*Bs)[NB], int lane) {
   using S = typename P::S;
   using A = typename P::A;
-  __shared__ A As[SK_KS][kSkRows];
-  __shared__ A Bs[SK_KS][NB];
-  const int4 it = items[blockIdx.x];
+  static_assert(SK_THREADS == 32, "one warp per item: warp-level synchronisation below");
+  constexpr int NA = SK_KS * kSkRows / SK_THREADS;              // factor entries per thread per stage
+  constexpr int NBL = (SK_KS * NB + SK_THREADS - 1) / SK_THREADS;   // right-hand-side entries per thread
   const DevNode nd = nodes[it.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int r0 = it.y, k0 = it.z, k1 = it.w;
-  const int tid = threadIdx.x;
-  const int cb = blockIdx.y * NB;           // first right-hand side of this column block
+  const int tid = lane;
   const typename P::WT* Ws = W + nd.w_off;
   const int32_t* gs = gsrc + nd.g_off * 2;
   const int32_t* rw = rows + nd.row_off;
   A acc[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) acc[j] = P::zero();
-  for (int ks = k0; ks < k1; ks += SK_KS) {
-    for (int t = tid; t < SK_KS * kSkRows; t += SK_THREADS) {
+  // software pipeline: the next stage's global loads are in registers while the
+  // current stage is multiplied out of shared memory
+  A ra[NA];
+  S rb[NBL];
+  auto load = [&](int ks) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int t = tid + u * SK_THREADS;
       int i, kk;
       if (FWD) { i = t / SK_KS; kk = t % SK_KS; }     // W row-major: k fastest
       else { i = t % kSkRows; kk = t / kSkRows; }     // W^T: row index fastest
@@ -350,40 +360,106 @@ __global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
       A a = P::zero();
       if (FWD) { if (r < m && k < k1) a = P::from_w(Ws[(int64_t)r * nc + k]); }
       else { if (r < nc && k < k1) a = P::from_w(Ws[(int64_t)k * nc + r]); }
-      As[kk][i] = a;
+      ra[u] = a;
     }
-    for (int t = tid; t < SK_KS * NB; t += SK_THREADS) {
-      const int kk = t / NB, cl = t % NB, c = cb + cl;
-      const int k = ks + kk;
+#pragma unroll
+    for (int u = 0; u < NBL; ++u) {
+      const int t = tid + u * SK_THREADS;
       S v = Ar<S>::zero();
-      if (k < k1 && c < nrhs) {
-        if (FWD) {
-          v = Q[(int64_t)(nd.col0 + k) * ld + c];
-          const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
-          if (s0 >= 0) v = Ar<S>::add(v, U[(int64_t)s0 * ld + c]);
-          if (s1 >= 0) v = Ar<S>::add(v, U[(int64_t)s1 * ld + c]);
-        } else {
-          v = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
+      if (t < SK_KS * NB) {
+        const int kk = t / NB, cl = t % NB, c = cb + cl;
+        const int k = ks + kk;
+        if (k < k1 && c < nrhs) {
+          if (FWD) {
+            v = Q[(int64_t)(nd.col0 + k) * ld + c];
+            const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
+            if (s0 >= 0) v = Ar<S>::add(v, U[(int64_t)s0 * ld + c]);
+            if (s1 >= 0) v = Ar<S>::add(v, U[(int64_t)s1 * ld + c]);
+          } else {
+            v = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
+          }
         }
       }
-      Bs[kk][cl] = P::from_s(v);
+      rb[u] = v;
     }
-    __syncthreads();
+  };
+  if (k0 < k1) load(k0);
+  for (int ks = k0; ks < k1; ks += SK_KS) {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int t = tid + u * SK_THREADS;
+      if (FWD) As[t % SK_KS][t / SK_KS] = ra[u];
+      else As[t / kSkRows][t % kSkRows] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NBL; ++u) {
+      const int t = tid + u * SK_THREADS;
+      if (t < SK_KS * NB) Bs[t / NB][t % NB] = P::from_s(rb[u]);
+    }
+    __syncwarp();
+    if (ks + SK_KS < k1) load(ks + SK_KS);
 #pragma unroll
     for (int kk = 0; kk < SK_KS; ++kk) {
       const A a = As[kk][tid];
 #pragma unroll
       for (int j = 0; j < NB; ++j) P::mac(acc[j], a, Bs[kk][j]);
     }
-    __syncthreads();
+    __syncwarp();
   }
-  S* out = Pt + (((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kSkRows + tid) * NB;
 #pragma unroll
-  for (int j = 0; j < NB; ++j) out[j] = P::to_s(acc[j]);
+  for (int j = 0; j < NB; ++j) out[tid * NB + j] = P::to_s(acc[j]);
 }
 
-// One block per unit (node, row0, item range) and column block: thread (row,
-// column) sums the unit's items in order, then the forward or backward epilogue.
+// The kSkRows x NB outputs of one unit (node, kSkRows rows) and column block: the
+// unit's K-chunk partials summed in item order, then the forward or backward
+// epilogue.  One warp; lane t handles outputs t, t + 32, ... (row t / NB, column t % NB).
+template <typename P, int NB, bool FWD>
+__device__ __forceinline__ void sk_unit(const DevNode* __restrict__ nodes, const typename P::S* __restrict__ Dinv,
+                                        const int32_t* __restrict__ gsrc, int4 un, int64_t item_base,
+                                        int64_t n_items, int by, const typename P::S* __restrict__ Pt,
+                                        typename P::S* __restrict__ Z, typename P::S* __restrict__ U,
+                                        typename P::S* __restrict__ X, int nrhs, int ld, int lane) {
+  using S = typename P::S;
+  const DevNode nd = nodes[un.x];
+  const int nc = nd.nc, m = nd.nc + nd.nr;
+  const S* Pc = Pt + (int64_t)by * n_items * kSkRows * NB;
+  for (int t = lane; t < kSkRows * NB; t += 32) {
+    const int i = t / NB, cl = t % NB, c = by * NB + cl;
+    const int r = un.y + i;
+    if (c >= nrhs) continue;
+    S acc = Ar<S>::zero();
+    for (int q = un.z; q < un.w; ++q) acc = Ar<S>::add(acc, Pc[(((int64_t)(q - item_base)) * kSkRows + i) * NB + cl]);
+    if (FWD) {
+      if (r >= m) continue;
+      if (r < nc) {
+        Z[(int64_t)(nd.col0 + r) * ld + c] = Ar<S>::mul(Dinv[nd.col0 + r], acc);
+      } else {
+        const int32_t* gs = gsrc + nd.g_off * 2;
+        const int s0 = gs[2 * r], s1 = gs[2 * r + 1];
+        if (s0 >= 0) acc = Ar<S>::add(acc, U[(int64_t)s0 * ld + c]);
+        if (s1 >= 0) acc = Ar<S>::add(acc, U[(int64_t)s1 * ld + c]);
+        U[(int64_t)(nd.u_off + r - nc) * ld + c] = acc;
+      }
+    } else {
+      if (r < nc) X[(int64_t)(nd.col0 + r) * ld + c] = acc;
+    }
+  }
+}
+
+template <typename P, int NB, bool FWD>
+__global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
+    const DevNode* __restrict__ nodes, const typename P::WT* __restrict__ W, const int32_t* __restrict__ gsrc,
+    const int32_t* __restrict__ rows, const int4* __restrict__ items, const typename P::S* __restrict__ Q,
+    const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U, const typename P::S* __restrict__ X,
+    typename P::S* __restrict__ Pt, int nrhs, int ld) {
+  static_assert(SK_THREADS == 32, "one warp per item: warp-level synchronisation");
+  __shared__ typename P::A As[SK_KS][kSkRows + 1];   // + 1: conflict-free stores of row-major factor rows
+  __shared__ typename P::A Bs[SK_KS][NB];
+  typename P::S* out = Pt + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kSkRows * NB;
+  sk_item<P, NB, FWD>(nodes, W, gsrc, rows, items[blockIdx.x], blockIdx.y * NB, Q, Z, U, X, out, nrhs, ld, As, Bs,
+                      threadIdx.x);
+}
+
 template <typename P, int NB, bool FWD>
 __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
     const DevNode* __restrict__ nodes, const typename P::S* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
@@ -437,9 +513,124 @@ void skinny_depth(const DevFactor<typename P::S, typename P::WT>& F, int d, bool
   count_launches(2);
 }
 
+// ---------------------------------------------------------------- persistent split-K solve
+// The whole solve (every tree depth, forward then backward) in one cooperative
+// launch: PS_WARPS warps per block, each taking (item, column block) pairs and then
+// (unit, column block) pairs grid-stride, with a grid barrier after every phase in
+// place of a kernel boundary.  Same items, partial layout, summation order and
+// epilogue as the per-depth kernels.
+constexpr int PS_WARPS = 8;
+constexpr int GRID_WAIT_LIMIT = 1 << 22;   // polls of one barrier (with a short sleep each)
+
+// Grid barrier on bar[0] (arrivals) and bar[1] (generation).  Bounded: a block that
+// gives up sets *err and returns false; the kernel then returns (its results are
+// invalid and the host reports ST_MG_ERR_TIMEOUT).  Co-residency of all blocks is
+// guaranteed by the cooperative launch.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int it = 0;
+      while (*vgen == g && it < GRID_WAIT_LIMIT) {
+        __nanosleep(32);
+        ++it;
+      }
+      if (*vgen == g) {
+        atomicExch(err, 1);
+        ok = 0;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename P, int NB, bool FWD>
+__global__ void __launch_bounds__(PS_WARPS * 32) k_sn_skinny_solve(
+    const DevNode* __restrict__ nodes, const typename P::WT* __restrict__ W, const typename P::S* __restrict__ Dinv,
+    const int32_t* __restrict__ gsrc, const int32_t* __restrict__ rows, const int4* __restrict__ items,
+    const int4* __restrict__ units, const int64_t* __restrict__ item_off, const int64_t* __restrict__ unit_off,
+    int max_depth, typename P::S* __restrict__ Q, typename P::S* __restrict__ Z, typename P::S* __restrict__ U,
+    typename P::S* __restrict__ Pt, int nrhs, int ld, unsigned* bar, int* err) {
+  using A = typename P::A;
+  extern __shared__ __align__(16) unsigned char ps_smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  A (*As)[kSkRows + 1] = reinterpret_cast<A (*)[kSkRows + 1]>(ps_smem) + (int64_t)w * SK_KS;
+  A (*Bs)[NB] = reinterpret_cast<A (*)[NB]>(ps_smem + (size_t)PS_WARPS * SK_KS * (kSkRows + 1) * sizeof(A)) +
+                (int64_t)w * SK_KS;
+  const int64_t gw = (int64_t)blockIdx.x * PS_WARPS + w, nw = (int64_t)gridDim.x * PS_WARPS;
+  const int gy = (nrhs + NB - 1) / NB;
+  for (int step = 0; step <= max_depth; ++step) {
+    const int d = FWD ? max_depth - step : step;
+    const int64_t ia = item_off[d], ni = item_off[d + 1] - ia;
+    const int64_t ua = unit_off[d], nu = unit_off[d + 1] - ua;
+    if (ni <= 0) continue;
+    for (int64_t t = gw; t < ni * gy; t += nw) {
+      const int64_t q = t % ni;
+      const int by = (int)(t / ni);
+      sk_item<P, NB, FWD>(nodes, W, gsrc, rows, items[ia + q], by * NB, Q, Z, U, Q,
+                          Pt + ((int64_t)by * ni + q) * kSkRows * NB, nrhs, ld, As, Bs, lane);
+    }
+    if (!grid_barrier(bar, err)) return;
+    for (int64_t t = gw; t < nu * gy; t += nw)
+      sk_unit<P, NB, FWD>(nodes, Dinv, gsrc, units[ua + t % nu], ia, ni, (int)(t / nu), Pt, Z, U, Q, nrhs, ld, lane);
+    if (!grid_barrier(bar, err)) return;
+  }
+}
+
 template <typename P, int NB>
 cudaError_t sn_solve_skinny(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
-                            typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+                            typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy,
+                            cudaStream_t st) {
+  if (sy.bar && sy.err && F.d_fs_item_off) {
+    // two cooperative launches (forward, backward), as many blocks as can be resident
+    static int grid[2] = {-1, -1};   // per instantiation: depends only on the kernel and the device
+    const size_t smem = (size_t)PS_WARPS * SK_KS * ((kSkRows + 1) + NB) * sizeof(typename P::A);
+    for (int dir = 0; dir < 2; ++dir) {
+      auto kern = dir == 0 ? k_sn_skinny_solve<P, NB, true> : k_sn_skinny_solve<P, NB, false>;
+      if (grid[dir] < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PS_WARPS * 32, smem);
+        if (e != cudaSuccess) return e;
+        grid[dir] = per_sm * F.n_sm;
+      }
+    }
+    if (grid[0] > 0 && grid[1] > 0) {
+      for (int dir = 0; dir < 2; ++dir) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid[dir]);
+        cfg.blockDim = dim3(PS_WARPS * 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const bool fwd = dir == 0;
+        cudaError_t e = cudaLaunchKernelEx(
+            &cfg, fwd ? k_sn_skinny_solve<P, NB, true> : k_sn_skinny_solve<P, NB, false>, F.nodes, F.W, F.Dinv,
+            F.gsrc, F.rows, fwd ? F.fs_items : F.bs_items, fwd ? F.fs_units : F.bs_units,
+            fwd ? F.d_fs_item_off : F.d_bs_item_off, fwd ? F.d_fs_unit_off : F.d_bs_unit_off, F.max_depth, Q, Z, U, Pt,
+            nrhs, ld, sy.bar, sy.err);
+        count_launches(1);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
   for (int d = F.max_depth; d >= 0; --d) skinny_depth<P, NB>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
   for (int d = 0; d <= F.max_depth; ++d) skinny_depth<P, NB>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
   return cudaGetLastError();
@@ -481,70 +672,71 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
 // Real matrices: column blocks of 4 / 16 / 32 on the split-K path, 64-wide tiles.
 template <typename P>
 cudaError_t solve_real(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
-                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
-  if (Pt && nrhs <= 4) return sn_solve_skinny<P, 4>(F, Q, Z, U, Pt, nrhs, ld, st);
-  if (Pt && nrhs <= 16) return sn_solve_skinny<P, 16>(F, Q, Z, U, Pt, nrhs, ld, st);
-  if (Pt && nrhs <= kSkMaxRhsR) return sn_solve_skinny<P, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= 4) return sn_solve_skinny<P, 4>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  if (Pt && nrhs <= 16) return sn_solve_skinny<P, 16>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  if (Pt && nrhs <= kSkMaxRhsR) return sn_solve_skinny<P, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   return sn_solve_tiled<P, 64, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, st);
 }
 // Complex matrices: column blocks of 2 / 8 / 16, 32-wide tiles.
 template <typename P>
 cudaError_t solve_cplx(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
-                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+                       typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
-  if (Pt && nrhs <= 2) return sn_solve_skinny<P, 2>(F, Q, Z, U, Pt, nrhs, ld, st);
-  if (Pt && nrhs <= 8) return sn_solve_skinny<P, 8>(F, Q, Z, U, Pt, nrhs, ld, st);
-  if (Pt && nrhs <= kSkMaxRhsC) return sn_solve_skinny<P, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, st);
+  if (Pt && nrhs <= 2) return sn_solve_skinny<P, 2>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  if (Pt && nrhs <= 8) return sn_solve_skinny<P, 8>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  if (Pt && nrhs <= kSkMaxRhsC) return sn_solve_skinny<P, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   return sn_solve_tiled<P, 32, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, st);
 }
 
 }  // namespace
 
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,
-                          cudaStream_t st) {
-  return solve_real<PolNative<double>>(F, Q, Z, U, P, nrhs, ld, st);
+                          const SkSync& sy, cudaStream_t st) {
+  return solve_real<PolNative<double>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
-                          int ld, cudaStream_t st) {
-  return solve_cplx<PolNative<double2>>(F, Q, Z, U, P, nrhs, ld, st);
+                          int ld, const SkSync& sy, cudaStream_t st) {
+  return solve_cplx<PolNative<double2>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
-                           cudaStream_t st) {
-  return solve_real<PolNative<float>>(F, Q, Z, U, P, nrhs, ld, st);
+                           const SkSync& sy, cudaStream_t st) {
+  return solve_real<PolNative<float>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, float2* U, float2* P, int nrhs, int ld,
-                           cudaStream_t st) {
-  return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, st);
+                           const SkSync& sy, cudaStream_t st) {
+  return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err, cudaStream_t st) {
+                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
+                               cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
-  if (nrhs <= 2) return sn_solve_skinny<PolBF16C, 2>(F, Q, Z, U, P, nrhs, ld, st);
-  if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, st);
-  if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolBF16C, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, st);
+  if (nrhs <= 2) return sn_solve_skinny<PolBF16C, 2>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolBF16C, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, sy, st);
   const int64_t gy = (nrhs + kTcCols - 1) / kTcCols;
   const int64_t two_waves = 2 * (int64_t)F.n_sm;
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t tiles = F.h_fwd_off[d + 1] - F.h_fwd_off[d];
     if (tiles <= 0) continue;
-    sn_tc2_depth(F, d, true, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, err, st);
+    sn_tc2_depth(F, d, true, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy.err, st);
   }
   for (int d = 0; d <= F.max_depth; ++d) {
     const int64_t tiles = F.h_bwd_off[d + 1] - F.h_bwd_off[d];
     if (tiles <= 0) continue;
-    sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, err, st);
+    sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy.err, st);
   }
   return cudaGetLastError();
 }
 
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,
-                             int ld, cudaStream_t st) {
-  return solve_real<PolDF>(F, Q, Z, U, P, nrhs, ld, st);
+                             int ld, const SkSync& sy, cudaStream_t st) {
+  return solve_real<PolDF>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_cplx_df(const DevFactor<double2, float4>& F, double2* Q, double2* Z, double2* U, double2* P,
-                             int nrhs, int ld, cudaStream_t st) {
-  return solve_cplx<PolDFC>(F, Q, Z, U, P, nrhs, ld, st);
+                             int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
+  return solve_cplx<PolDFC>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 
 }  // namespace stmg

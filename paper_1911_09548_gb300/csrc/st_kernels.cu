@@ -466,43 +466,106 @@ __global__ void k_scatter_perm(const TQ* __restrict__ X, int ld, const int32_t* 
 }
 
 // y = G^T r: warp per node, lanes over the time columns.
-__global__ void k_grad_T(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                         const int8_t* __restrict__ sgn, const double* __restrict__ r, double* __restrict__ y,
-                         int ncols) {
-  const int lane = threadIdx.x & 31;
-  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// y = G^T r: one warp per interior vertex.  The vertex's (at most 32) edges and signs
+// are staged in shared memory; each lane sums double2 column pairs over them, four
+// loads issued before their sums (the edge order of the sum is fixed).
+constexpr int GT_WARPS = 8;
+constexpr int GT_CHUNK = 64;   // column pairs per warp
+__global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col,
+                                                          const int8_t* __restrict__ sgn,
+                                                          const double* __restrict__ r, double* __restrict__ y,
+                                                          int ncols) {
+  __shared__ int s_col[GT_WARPS][32];
+  __shared__ int s_sgn[GT_WARPS][32];
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int v = blockIdx.x * GT_WARPS + wb;
   if (v >= nrows) return;
-  const int64_t beg = rowptr[v], end = rowptr[v + 1];
-  for (int j = lane; j < ncols; j += 32) {
-    double s = 0.0;
-    for (int64_t q = beg; q < end; ++q) {
-      const double rv = r[(int64_t)col[q] * ncols + j];
-      s = sgn[q] > 0 ? s + rv : s - rv;
+  const int64_t beg = rowptr[v];
+  const int nq = (int)(rowptr[v + 1] - beg);
+  if (nq > 32 || (ncols & 1)) {   // general case (not reached on Kuhn meshes: <= 14 edges per vertex)
+    if (blockIdx.y > 0) return;
+    for (int j = lane; j < ncols; j += 32) {
+      double sum = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        const double rv = r[(int64_t)col[beg + q] * ncols + j];
+        sum = sgn[beg + q] > 0 ? sum + rv : sum - rv;
+      }
+      y[(int64_t)v * ncols + j] = sum;
     }
-    y[(int64_t)v * ncols + j] = s;
+    return;
+  }
+  if (lane < nq) {
+    s_col[wb][lane] = col[beg + lane];
+    s_sgn[wb][lane] = sgn[beg + lane];
+  }
+  __syncwarp();
+  const int* cq = s_col[wb];
+  const int* sq = s_sgn[wb];
+  const int n2 = ncols >> 1;
+  const double2* r2 = reinterpret_cast<const double2*>(r);
+  double2* y2 = reinterpret_cast<double2*>(y + (int64_t)v * ncols);
+  // blockIdx.y: a chunk of GT_CHUNK column pairs (more warps in flight on long rows)
+  const int j1 = min(n2, (int)(blockIdx.y + 1) * GT_CHUNK);
+  for (int j = (int)blockIdx.y * GT_CHUNK + lane; j < j1; j += 32) {
+    double2 sum = make_double2(0.0, 0.0);
+    int q = 0;
+    for (; q + 4 <= nq; q += 4) {
+      double2 rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rv[u] = r2[(int64_t)cq[q + u] * n2 + j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool plus = sq[q + u] > 0;
+        sum.x = plus ? sum.x + rv[u].x : sum.x - rv[u].x;
+        sum.y = plus ? sum.y + rv[u].y : sum.y - rv[u].y;
+      }
+    }
+    for (; q < nq; ++q) {
+      const double2 rv = r2[(int64_t)cq[q] * n2 + j];
+      const bool plus = sq[q] > 0;
+      sum.x = plus ? sum.x + rv.x : sum.x - rv.x;
+      sum.y = plus ? sum.y + rv.y : sum.y - rv.y;
+    }
+    y2[j] = sum;
   }
 }
-
-// x += G w: G has -1 at the tail and +1 at the head of each edge.
+// x += G w: one block per interior edge, double2 column pairs.
 __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __restrict__ head,
                            const double* __restrict__ w, double* __restrict__ x, int ncols) {
   const int e = blockIdx.x;
   const int t = tail[e], h = head[e];
   double* xr = x + (int64_t)e * ncols;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
-    double d = 0.0;
-    if (h >= 0) d += w[(int64_t)h * ncols + j];
-    if (t >= 0) d -= w[(int64_t)t * ncols + j];
-    xr[j] += d;
+  if (ncols & 1) {
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+      double d = 0.0;
+      if (h >= 0) d += w[(int64_t)h * ncols + j];
+      if (t >= 0) d -= w[(int64_t)t * ncols + j];
+      xr[j] += d;
+    }
+    return;
+  }
+  const int n2 = ncols >> 1;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2* x2 = reinterpret_cast<double2*>(xr);
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) {   // (one or two iterations at 256 slabs)
+    double2 d = make_double2(0.0, 0.0);
+    if (h >= 0) {
+      const double2 a = w2[(int64_t)h * n2 + j];
+      d.x += a.x;
+      d.y += a.y;
+    }
+    if (t >= 0) {
+      const double2 b = w2[(int64_t)t * n2 + j];
+      d.x -= b.x;
+      d.y -= b.y;
+    }
+    double2 xv = x2[j];
+    xv.x += d.x;
+    xv.y += d.y;
+    x2[j] = xv;
   }
 }
-
-// w = L_t^{-1} z along the slabs of each node row (eq. AuxNodalSm).
-// DG(0): L_t = bidiag(1, -1), so w_n = sum_{j<=n} z_j (the running sum Sigma_t).
-// DG(1): K_t w_n = z_n - N_t w_{n-1} with K_t = [[1,1],[-1,1]], N_t = [[-1,-1],[1,1]]
-//   gives w_n = ((z0 - z1)/2 + e_{n-1}, (z0 + z1)/2) with the end values
-//   e_n = w_n0 + w_n1 = e_{n-1} + z0_n: a running sum of z0.
-// Warp per node: each lane sums a contiguous chunk, a warp scan gives its carry.
 __global__ void k_time_integrate(const double* __restrict__ z, double* __restrict__ w, int nrows, int N_t,
                                  int degree) {
   const int lane = threadIdx.x & 31;
@@ -850,7 +913,7 @@ cudaError_t scatter_perm_f(const float* X, int ld, const int32_t* iperm, int nro
   return cudaGetLastError();
 }
 cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {
-  if (GT.nrows > 0) { k_grad_T<<<grid1(GT.nrows, 8), 256, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols); count_launches(1); }
+  if (GT.nrows > 0) { k_grad_T<<<dim3(grid1(GT.nrows, GT_WARPS), (unsigned)std::max<int64_t>(1, grid1(ncols / 2, GT_CHUNK))), GT_WARPS * 32, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const double* w, double* x, int ncols,

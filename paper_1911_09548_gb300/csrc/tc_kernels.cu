@@ -8,12 +8,15 @@
 // w = a + ib becomes the 2x2 block [[a, -b], [b, a]] of a 128 x 2K real tile, and
 // each complex right-hand side entry g becomes the pair (Re g, Im g) along K, so
 // row 2i of the FP32 accumulator holds Re y_i and row 2i+1 holds Im y_i.
-// Operands are staged in shared memory in the K-major, no-swizzle core-matrix
-// layout (8 rows x 16 bytes per core matrix; 128 bytes between K-adjacent cores,
-// 1024 bytes between 8-row groups) and consumed by tcgen05.mma kind::f16
-// (M = 128, N = 128, K = 16 per instruction) issued by one thread; completion is
-// signalled through an mbarrier by tcgen05.commit.  Every wait is bounded: on
-// timeout the block records an error in *err and skips its epilogue.
+// Operands live in the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes
+// per core matrix; 128 bytes between K-adjacent cores, 1024 bytes between 8-row
+// groups): the factor tiles are laid out so at setup, the right-hand-side tiles by
+// k_tc_assemble once per tree depth.  k_sn_tc2 moves (factor, right-hand side) tile
+// pairs into a 3-stage shared-memory ring with cp.async.bulk, one thread issues
+// tcgen05.mma kind::f16 (M = 128, N = 128, K = 16 per instruction) and frees each
+// stage with tcgen05.commit.  Every wait is bounded: on timeout the block records an
+// error in *err, waits (bounded) for its copies and MMAs in flight and skips its
+// epilogue.
 #include <cuda_bf16.h>
 
 #include "device.h"
@@ -27,8 +30,6 @@ constexpr int TC_N = kTcCols;             // right-hand sides per block (MMA N)
 constexpr int TC_KC = 32;                 // complex K per stage (64 real = 4 MMAs of K = 16)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = TC_N;   // FP32 accumulator columns
-constexpr int A_BYTES = TC_M * 2 * TC_KC * 2;   // 16 KiB
-constexpr int B_BYTES = TC_N * 2 * TC_KC * 2;   // 16 KiB
 constexpr uint32_t CORE_K = 128;          // bytes between K-adjacent core matrices
 constexpr uint32_t CORE_MN = 1024;        // bytes between 8-row groups (8 cores along K)
 constexpr int WAIT_LIMIT = 1 << 20;       // try_wait rounds before a wait gives up (well under a second)
@@ -55,11 +56,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
-  asm volatile("fence.mbarrier_init.release.cluster;");
-}
-
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   uint32_t done = 0;
   for (int it = 0; it < WAIT_LIMIT; ++it) {
@@ -82,22 +78,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS));
 }
 
-// 4 MMAs (K = 4 x 16) of one stage; accumulate unless this is the first stage
-__device__ __forceinline__ void issue_stage(uint32_t tmem, const uint8_t* As, const uint8_t* Bs, bool first,
-                                            uint64_t* bar) {
-#pragma unroll
-  for (int s = 0; s < (2 * TC_KC) / 16; ++s) {
-    const uint64_t ad = smem_desc(smem_u32(As) + s * 2 * CORE_K);
-    const uint64_t bd = smem_desc(smem_u32(Bs) + s * 2 * CORE_K);
-    const uint32_t acc = (first && s == 0) ? 0u : 1u;
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
-  }
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -110,13 +90,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// writes the real 2x2 block of complex w at complex (i, k) of the A tile
-__device__ __forceinline__ void put_w(uint8_t* As, int i, int k, __nv_bfloat162 w) {
-  const __nv_bfloat16 re = w.x, im = w.y, nim = __hneg(w.y);
-  *reinterpret_cast<__nv_bfloat162*>(As + core_off(2 * i, 2 * k)) = __halves2bfloat162(re, nim);
-  *reinterpret_cast<__nv_bfloat162*>(As + core_off(2 * i + 1, 2 * k)) = __halves2bfloat162(im, re);
-}
-
 __device__ __forceinline__ void put_g(uint8_t* Bs, int c, int k, float2 g) {
   *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(c, 2 * k)) = __floats2bfloat162_rn(g.x, g.y);
 }
@@ -124,150 +97,6 @@ __device__ __forceinline__ void put_g(uint8_t* Bs, int c, int k, float2 g) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// SPLIT = false: one (node, row tile) per block, whole K range, epilogue in place.
-// SPLIT = true: one item (node, row tile, k0, k1) per block; the FP32 partial
-// product goes to P[item, column tile] for k_sn_tc_reduce.
-template <bool FWD, bool SPLIT>
-__global__ void __launch_bounds__(TC_THREADS) k_sn_tc(const DevNode* __restrict__ nodes,
-                                                      const __nv_bfloat162* __restrict__ W,
-                                                      const float2* __restrict__ Dinv,
-                                                      const int32_t* __restrict__ gsrc,
-                                                      const int32_t* __restrict__ rows,
-                                                      const int2* __restrict__ tiles, const int4* __restrict__ items,
-                                                      const float2* __restrict__ Q,
-                                                      float2* __restrict__ Z, float2* __restrict__ U,
-                                                      float2* __restrict__ X, float2* __restrict__ P, int nrhs, int ld,
-                                                      int* __restrict__ err) {
-  __shared__ __align__(1024) uint8_t As[A_BYTES];
-  __shared__ __align__(1024) uint8_t Bs[B_BYTES];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t tmem_slot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int node, rtile, ik0 = 0, ik1 = 0;
-  if (SPLIT) {
-    const int4 it = items[blockIdx.x];
-    node = it.x; rtile = it.y; ik0 = it.z; ik1 = it.w;
-  } else {
-    const int2 tl = tiles[blockIdx.x];
-    node = tl.x; rtile = tl.y;
-  }
-  const DevNode nd = nodes[node];
-  const int nc = nd.nc, m = nd.nc + nd.nr;
-  const int row0 = rtile * TC_ROWS, c0 = blockIdx.y * TC_N;
-  const __nv_bfloat162* Ws = W + nd.w_off;
-  const int32_t* gs = gsrc + nd.g_off * 2;
-  const int32_t* rw = rows + nd.row_off;
-  if (tid == 0) mbar_init(&bar);
-  __syncwarp();
-  if (warp == 0) tmem_alloc(&tmem_slot);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-
-  // K range in complex columns: forward rows inside L11^{-1} stop at the tile's
-  // last row; backward rows start where L11^{-1} has its first nonzero
-  const int rows_out = FWD ? m : nc;
-  int kbeg, kend;
-  if (SPLIT) {
-    kbeg = ik0;
-    kend = ik1;
-  } else if (FWD) {
-    kbeg = 0;
-    kend = (row0 + TC_ROWS <= nc) ? row0 + TC_ROWS : nc;
-  } else {
-    kbeg = (row0 / TC_KC) * TC_KC;
-    kend = m;
-  }
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int k0 = kbeg; k0 < kend; k0 += TC_KC) {
-    // A: 64 complex rows x 32 complex columns of W (forward) or W^T (backward)
-    for (int t = tid; t < TC_ROWS * TC_KC; t += TC_THREADS) {
-      int i, kk;
-      if (FWD) { i = t / TC_KC; kk = t % TC_KC; }
-      else { i = t % TC_ROWS; kk = t / TC_ROWS; }
-      const int r = row0 + i, k = k0 + kk;
-      __nv_bfloat162 w = __floats2bfloat162_rn(0.f, 0.f);
-      if (r < rows_out && k < kend) w = FWD ? Ws[(int64_t)r * nc + k] : Ws[(int64_t)k * nc + r];
-      put_w(As, i, kk, w);
-    }
-    // B: 128 right-hand sides x 32 complex K entries
-    for (int t = tid; t < TC_N * TC_KC; t += TC_THREADS) {
-      const int kk = t / TC_N, cl = t % TC_N;
-      const int k = k0 + kk, c = c0 + cl;
-      float2 g = make_float2(0.f, 0.f);
-      if (k < kend && c < nrhs) {
-        if (FWD) {
-          g = Q[(int64_t)(nd.col0 + k) * ld + c];
-          const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
-          if (s0 >= 0) g = cadd(g, U[(int64_t)s0 * ld + c]);
-          if (s1 >= 0) g = cadd(g, U[(int64_t)s1 * ld + c]);
-        } else {
-          g = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
-        }
-      }
-      put_g(Bs, cl, kk, g);
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      issue_stage(tmem, As, Bs, k0 == kbeg, &bar);
-    }
-    if (!mbar_wait(&bar, phase)) {
-      ok = false;
-      break;
-    }
-    phase ^= 1u;
-    __syncthreads();
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-  } else {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // thread = accumulator row (warp w reads TMEM lanes 32w .. 32w+31); even rows
-    // hold real parts, odd rows imaginary parts of complex row row0 + R/2
-    const int R = warp * 32 + lane;
-    const int i = row0 + (R >> 1);
-    const bool even = (R & 1) == 0;
-    for (int cb = 0; cb < TC_N; cb += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float mine = __uint_as_float(v[j]);
-        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-        const int c = c0 + cb + j;
-        if (SPLIT) {
-          if (even)
-            P[(((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * TC_ROWS + (R >> 1)) * TC_N + cb + j] =
-                make_float2(mine, other);
-          continue;
-        }
-        if (!even || c >= nrhs || i >= rows_out) continue;
-        const float2 y = make_float2(mine, other);
-        if (FWD) {
-          if (i < nc) {
-            Z[(int64_t)(nd.col0 + i) * ld + c] = cmul(Dinv[nd.col0 + i], y);
-          } else {
-            float2 u = y;
-            const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
-            if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
-            if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
-            U[(int64_t)(nd.u_off + i - nc) * ld + c] = u;
-          }
-        } else {
-          X[(int64_t)(nd.col0 + i) * ld + c] = y;
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem);
 }
 
 // One block per (unit = node row tile, column tile, group of TC_RED_ROWS rows): sums
@@ -599,52 +428,6 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool
                                                                             ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
     }
     count_launches(2);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t sn_tc_split_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, float2* Q, float2* Z,
-                              float2* U, float2* P, int nrhs, int ld, int* err, cudaStream_t st) {
-  const int64_t* io = fwd ? F.h_tcf_item_off : F.h_tcb_item_off;
-  const int64_t* uo = fwd ? F.h_tcf_unit_off : F.h_tcb_unit_off;
-  const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
-  if (ib <= ia) return cudaSuccess;
-  const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
-  if (fwd) {
-    k_sn_tc<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
-        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcf_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
-    k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
-                                                                         ia, ib - ia, P, Z, U, Q, nrhs, ld);
-  } else {
-    k_sn_tc<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, 0, st>>>(
-        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, nullptr, F.tcb_items + ia, Q, Z, U, Q, P, nrhs, ld, err);
-    k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
-                                                                          ia, ib - ia, P, Z, U, Q, nrhs, ld);
-  }
-  count_launches(2);
-  return cudaGetLastError();
-}
-
-cudaError_t sn_tc_forward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
-                          int nrhs, int ld, int* err, cudaStream_t st) {
-  const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
-  if (b > a) {
-    const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
-    k_sn_tc<true, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(
-        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, F.fwd_tiles + a, nullptr, Q, Z, U, Q, nullptr, nrhs, ld, err);
-    count_launches(1);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t sn_tc_backward(const DevFactor<float2, __nv_bfloat162>& F, int d, float2* Q, float2* Z, float2* U,
-                           int nrhs, int ld, int* err, cudaStream_t st) {
-  const int64_t a = F.h_bwd_off[d], b = F.h_bwd_off[d + 1];
-  if (b > a) {
-    const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
-    k_sn_tc<false, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, 0, st>>>(
-        F.nodes, F.W, F.Dinv, F.gsrc, F.rows, F.bwd_tiles + a, nullptr, Q, Z, U, Q, nullptr, nrhs, ld, err);
-    count_launches(1);
   }
   return cudaGetLastError();
 }

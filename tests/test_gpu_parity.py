@@ -32,6 +32,9 @@ CASES = {
     "dg1_ragged_df": (8, 1, 1, 20, "two_material", dict(nu_pre=2, nu_post=2, slab_prec=2)),
     "dg1_space_df": (8, 2, 1, 16, "unit", dict(slab_prec=2)),
     "dg0_long_df": (8, 1, 0, 300, "two_material", dict(slab_prec=2)),
+    # coarse-level solves as persistent cooperative launches (grid barriers between depths)
+    "dg1_ragged_persistent": (8, 1, 1, 20, "two_material", dict(nu_pre=2, nu_post=2, persistent_split=1)),
+    "dg0_long_df_persistent": (8, 1, 0, 300, "two_material", dict(slab_prec=2, persistent_split=1)),
 }
 
 
@@ -247,3 +250,21 @@ def test_graph_replay_matches_direct_launches(lib_built):
             S.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] > 0
+
+
+@pytest.mark.parametrize("slab_prec", [0, 1, 3])
+def test_persistent_split_matches_per_depth_launches(slab_prec, lib_built):
+    """The persistent split-K solve runs the same items, partial layout and summation
+    order as the per-depth kernels: a V-cycle must agree bit for bit."""
+    nu, sigma = st_inputs.materials(8, "two_material", 4)
+    xs = []
+    for ps in (0, 1):
+        S = lib_built.SpaceTimeSolver(8, nu, sigma, 1.0, 64, 1, nu_pre=2, nu_post=2, slab_prec=slab_prec,
+                                      persistent_split=ps)
+        f = S.load(st_inputs.excitation(6))
+        x = S.zeros()
+        for _ in range(2):
+            S.vcycle(f, x)
+        xs.append(host(x))
+        S.close()
+    assert np.array_equal(xs[0], xs[1])
