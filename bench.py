@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
+    ap.add_argument("--batch", type=int, default=8,
+                    help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
                     help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
     ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve"],
@@ -477,6 +479,45 @@ def main():
                 v["bf16_peak_tflops"] = peak
             variants[vname] = v
             Sm.close()
+
+    # batched: `batch` excitations on one handle (problem-major slab columns), BF16
+    # slab solve on the tensor cores; the same workload per problem
+    if args.mixed and args.batch > 1:
+        NB_ = args.batch
+        Sb = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=3, n_batch=NB_)
+        fb = Sb.zeros()
+        for b in range(NB_):
+            Sb.load(st_inputs.excitation(W["seed"] + 1 + b + 1000 * rank), f=fb, batch=b)
+        xb = Sb.zeros()
+        for _ in range(args.warmup):
+            Sb.vcycle(fb, xb)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            Sb.vcycle(fb, xb)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+        st_b = stmg.st_mg_factor_stats(Sb.h, 0)
+        rb_ = Sb.residual(fb, xb)
+        yb = Sb.zeros()
+        stmg.st_mg_slab_solve(Sb.h, 0, rb_, yb)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            stmg.st_mg_slab_solve(Sb.h, 0, rb_, yb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        slab_ms_b = e0.elapsed_time(e1) / reps
+        tflops_b = st_b["macs_per_rhs"] * flops_per_mac * W["N_t"] * NB_ / (slab_ms_b / 1e3) / 1e12
+        peak = measured_peak("bf16_tflops")
+        variants["bf16_tensor_batched"] = {
+            "value": replica_value(world, per_cycle * NB_, args.steps, ms_b), "unit": UNIT, "problems": NB_,
+            "ms_per_step": ms_b / args.steps, "slab_solve_ms": slab_ms_b, "slab_solve_tflops": tflops_b,
+            "slab_solve_frac_of_bf16_peak": tflops_b / peak, "bf16_peak_tflops": peak}
+        Sb.close()
+        del fb, xb, rb_, yb
 
     cpu_base = None
     if cpu_proc is not None:
