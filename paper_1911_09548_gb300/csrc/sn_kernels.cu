@@ -84,6 +84,29 @@ struct PolNative {
   static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<T>::mac(acc, a, b); }
 };
 
+// FP64 complex products with three real multiplications (Gauss): for y = sum_k a_k b_k
+// keep p = sum Re a Re b, q = sum Im a Im b, r = sum (Re a + Im a)(Re b + Im b); then
+// Re y = p - q, Im y = r - p - q.  Operands are staged as (Re, Im, Re + Im), the sums
+// formed once per staged element and reused across the whole tile, so a complex
+// multiply-add costs 3 FP64 FMAs instead of 4 on the FP64 pipe that bounds this path.
+struct c3 {
+  double x, y, z;
+};
+struct PolC3M {
+  using S = double2;
+  using WT = double2;
+  using A = c3;
+  static __device__ __forceinline__ A zero() { return c3{0.0, 0.0, 0.0}; }
+  static __device__ __forceinline__ A from_w(WT w) { return c3{w.x, w.y, w.x + w.y}; }
+  static __device__ __forceinline__ A from_s(S v) { return c3{v.x, v.y, v.x + v.y}; }
+  static __device__ __forceinline__ S to_s(A a) { return make_double2(a.x - a.y, a.z - a.x - a.y); }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.y = fma(a.y, b.y, acc.y);
+    acc.z = fma(a.z, b.z, acc.z);
+  }
+};
+
 // double-float value h + l
 struct dfr {
   float h, l;
@@ -347,7 +370,7 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
   for (int j = 0; j < NB; ++j) acc[j] = P::zero();
   // software pipeline: the next stage's global loads are in registers while the
   // current stage is multiplied out of shared memory
-  A ra[NA];
+  typename P::WT ra[NA];   // raw factor entries (converted on the way into shared memory)
   S rb[NBL];
   auto load = [&](int ks) {
 #pragma unroll
@@ -357,9 +380,9 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
       if (FWD) { i = t / SK_KS; kk = t % SK_KS; }     // W row-major: k fastest
       else { i = t % kSkRows; kk = t / kSkRows; }     // W^T: row index fastest
       const int r = r0 + i, k = ks + kk;
-      A a = P::zero();
-      if (FWD) { if (r < m && k < k1) a = P::from_w(Ws[(int64_t)r * nc + k]); }
-      else { if (r < nc && k < k1) a = P::from_w(Ws[(int64_t)k * nc + r]); }
+      typename P::WT a{};
+      if (FWD) { if (r < m && k < k1) a = Ws[(int64_t)r * nc + k]; }
+      else { if (r < nc && k < k1) a = Ws[(int64_t)k * nc + r]; }
       ra[u] = a;
     }
 #pragma unroll
@@ -388,8 +411,8 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
 #pragma unroll
     for (int u = 0; u < NA; ++u) {
       const int t = tid + u * SK_THREADS;
-      if (FWD) As[t % SK_KS][t / SK_KS] = ra[u];
-      else As[t / kSkRows][t % kSkRows] = ra[u];
+      if (FWD) As[t % SK_KS][t / SK_KS] = P::from_w(ra[u]);
+      else As[t / kSkRows][t % kSkRows] = P::from_w(ra[u]);
     }
 #pragma unroll
     for (int u = 0; u < NBL; ++u) {
@@ -698,7 +721,7 @@ cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, doub
 }
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
                           int ld, const SkSync& sy, cudaStream_t st) {
-  return solve_cplx<PolNative<double2>>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  return solve_cplx<PolC3M>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
                            const SkSync& sy, cudaStream_t st) {
