@@ -169,6 +169,47 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ convergence rates
+def run_rates(args):
+    """Two-grid convergence rates by the power iteration of Section 5.1 on the GPU:
+    'Semi-time' (time coarsening only) and 'Full' (space and time) against lambda of eq.
+    CoarseningRule (the paper's experiment E1 on the Kuhn cube 16^3 -> 8^3, DG(0),
+    nu = sigma = 1, N_t = 16, lambda varied through tau), then hybrid-smoother orderings
+    (Section 4) at a small and a large lambda."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    import st_inputs
+
+    nf, N_t = 16, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    h2 = 3.0 / nf ** 2
+
+    def rate(tau, **opts):
+        S = stmg.SpaceTimeSolver(nf, nu, sigma, tau * N_t, N_t, 0, n_space_levels=2, max_levels=2, **opts)
+        x = torch.from_numpy(st_inputs.random_iterate((S.n_edge, N_t), 0)).cuda()
+        r, _ = S.convergence_rate(x, max_iter=15)
+        S.close()
+        return r
+
+    sweep = []
+    for k in range(-12, 3, 2):
+        tau = 2.0 ** k
+        sweep.append({"tau": tau, "lambda": tau / h2, "semi_time": rate(tau, coarsen=1), "full": rate(tau, coarsen=2)})
+    orderings = {}
+    for tau in (2.0 ** -8, 1.0):
+        orderings[f"lambda={tau / h2:.3g}"] = {p: rate(tau, coarsen=1, smoother=p)
+                                                for p in ("SAS", "SA", "AS", "SSA", "ASS", "SSAS", "SSASS")}
+    print(json.dumps({"mode": "rates", "metric": "two-grid convergence rate (power iteration, Section 5.1)",
+                      "config": {"mesh": "Kuhn 16^3 -> 8^3", "degree": 0, "N_t": 16, "materials": "nu = sigma = 1",
+                                 "cycle": "two-grid, SAS unless stated"},
+                      "lambda_sweep": sweep, "orderings_semi_time": orderings}))
+    return 0
+
+
 # ------------------------------------------------------------------ serving
 SERVE_SPACE_LEVELS = {4: 2, 8: 2, 16: 3, 24: 3}
 
@@ -281,7 +322,7 @@ def main():
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
                     help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
-    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers); "
                          "serve: the request-loop benchmark (Poisson streams, p50/p99 latency)")
     ap.add_argument("--serve-rates", default="0.5,2,10", help="offered request rates (req/s), one stream each")
@@ -295,6 +336,8 @@ def main():
         return run_reference(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "rates":
+        return run_rates(args)
 
     import multiprocessing as mp
 

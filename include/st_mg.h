@@ -103,6 +103,11 @@ typedef struct {
                                 launch sequence into a CUDA graph once per (f, x) buffer pair and replay
                                 it (needs a non-default stream; the first call captures, later calls
                                 replay); 0: launch kernel by kernel */
+    char smoother[16];       /* hybrid smoother as a product of S and A in the paper's notation, read
+                                right to left (Section 4: "SA" applies A, then S), NUL-terminated, at
+                                most 15 letters: the pre-smoother applies it right to left, the
+                                post-smoother the same factors left to right.  Empty (default):
+                                S^nu_pre A S^nu_pre and S^nu_post A S^nu_post (A only if use_A) */
     int32_t persistent_split;/* 1: slab and K_n solves with few right-hand sides (coarse time levels)
                                 run as two cooperative launches that walk every tree depth with grid
                                 barriers in between, instead of two launches per depth; 0 (default):

@@ -66,15 +66,32 @@ def build_time_hierarchy(N_t, T, n_fine, n_space_levels, nu, sigma, mode="rule",
 
 class SpaceTimeMG:
     def __init__(self, space_levels, time_levels, p, omega=0.5, nu_pre=1, nu_post=1,
-                 nodal="exact", jacobi_sweeps=0, use_A=True):
+                 nodal="exact", jacobi_sweeps=0, use_A=True, pattern=""):
         self.space, self.levels, self.p = space_levels, time_levels, p
         self.use_A = use_A
+        # Section 4: a hybrid smoother written as a product of S and A, read right to
+        # left ("SA": A, then S); the post-smoother applies the same factors in the
+        # reverse order.  Empty: S^nu A S^nu with nu = nu_pre / nu_post.
+        if any(c not in "SA" for c in pattern):
+            raise ValueError(pattern)
+        self.pattern = pattern
         self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
         self.nodal, self.jacobi_sweeps = nodal, jacobi_sweeps
         self.slabs = [SlabOperator(space_levels[L.s], p, L.tau) for L in time_levels]
 
-    # one level's smoothing sequence S^k A S^k
-    def _smooth(self, li, f, x, k):
+    def _apply(self, li, f, x, op):
+        slab = self.slabs[li]
+        if op == "S":
+            return smoother_S(slab, f, x, self.omega)
+        return correction_A(slab, f, x, self.nodal, self.jacobi_sweeps)
+
+    # one level's smoothing sequence: the pattern (pre: right to left, post: left to
+    # right), else S^k A S^k
+    def _smooth(self, li, f, x, k, post=False):
+        if self.pattern:
+            for op in (self.pattern if post else self.pattern[::-1]):
+                x = self._apply(li, f, x, op)
+            return x
         slab = self.slabs[li]
         for _ in range(k):
             x = smoother_S(slab, f, x, self.omega)
@@ -103,7 +120,7 @@ class SpaceTimeMG:
         if space_coarsened:
             ec = prolong_space(self.space[self.levels[li].s].Px, ec)
         x = x + prolong_time(self.p, ec)
-        x = self._smooth(li, f, x, self.nu_post)
+        x = self._smooth(li, f, x, self.nu_post, post=True)
         return x
 
     def solve(self, f, x0=None, rtol=1e-8, maxit=50):

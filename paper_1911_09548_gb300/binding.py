@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
                 ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32),
-                ("persistent_split", _i32), ("factor_cache", _i32)]
+                ("smoother", ctypes.c_char * 16), ("persistent_split", _i32), ("factor_cache", _i32)]
 
 
 class ServerOptions(ctypes.Structure):

@@ -759,7 +759,20 @@ void op_coarse_solve(Handle& h, const double* f, double* x) {
   }
 }
 
-void op_smooth(Handle& h, int l, const double* f, double* x, int nu) {
+// Hybrid smoother of Section 4 on level l: the option's S/A product (pre-smoother:
+// right to left as a matrix product, post-smoother: the same factors in reverse), or
+// S^nu A S^nu.
+void op_smooth(Handle& h, int l, const double* f, double* x, int nu, bool post) {
+  const char* pat = h.opt.smoother;
+  const int np = (int)strnlen(pat, sizeof(h.opt.smoother));
+  if (np > 0) {
+    for (int i = 0; i < np; ++i) {
+      const char op = pat[post ? i : np - 1 - i];
+      if (op == 'S') op_smooth_S(h, l, f, x);
+      else op_correct_A(h, l, f, x);
+    }
+    return;
+  }
   for (int k = 0; k < nu; ++k) op_smooth_S(h, l, f, x);
   if (h.opt.use_A) op_correct_A(h, l, f, x);
   for (int k = 0; k < nu; ++k) op_smooth_S(h, l, f, x);
@@ -770,7 +783,7 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
     op_coarse_solve(h, f, x);
     return;
   }
-  op_smooth(h, l, f, x, h.opt.nu_pre);
+  op_smooth(h, l, f, x, h.opt.nu_pre, false);
   double* r = level_r(h, l);
   op_residual(h, l, f, x, r, nullptr);
   auto& C = h.lv[l + 1];
@@ -778,7 +791,7 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
   CK(vec_fill(C.x, C.len, 0.0, h.stream));
   op_vcycle(h, l + 1, C.f, C.x);
   op_prolong_add(h, l, C.x, x);
-  op_smooth(h, l, f, x, h.opt.nu_post);
+  op_smooth(h, l, f, x, h.opt.nu_post, true);
 }
 
 // One V-cycle on the finest level.  With use_graph and a non-default stream the
@@ -825,6 +838,15 @@ double f_norm(Handle& h, const double* f) {
 }
 
 // ---------------------------------------------------------------- setup
+// smoother pattern: NUL-terminated within the field, letters S and A only
+bool valid_pattern(const char (&p)[16]) {
+  const size_t n = strnlen(p, sizeof(p));
+  if (n >= sizeof(p)) return false;
+  for (size_t i = 0; i < n; ++i)
+    if (p[i] != 'S' && p[i] != 'A') return false;
+  return true;
+}
+
 int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_mg_t* out, bool host_only) {
   if (!pr || !op || !out) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
@@ -837,7 +859,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
-      (op->persistent_split != 0 && op->persistent_split != 1) ||
+      (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = (int64_t)6 * n * n * n;
@@ -1382,6 +1404,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->slab_prec = 0;
   o->residual_prec = -1;
   o->use_graph = 1;
+  std::memset(o->smoother, 0, sizeof(o->smoother));
   o->persistent_split = 0;
   o->factor_cache = 0;
   return ST_MG_OK;

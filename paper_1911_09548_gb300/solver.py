@@ -19,7 +19,7 @@ class SpaceTimeSolver:
         for k, v in options.items():
             if not hasattr(self.opt, k):
                 raise KeyError(k)
-            setattr(self.opt, k, v)
+            setattr(self.opt, k, v.encode() if isinstance(v, str) else v)
         self.host_only = host_only
         if host_only:
             self.h = B.st_mg_setup_host(self.prob, self.opt)

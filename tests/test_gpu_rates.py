@@ -66,3 +66,35 @@ def test_two_materials_rate_does_not_degrade(stmg):
         out.append(r)
     assert out[0] < 0.5
     assert max(out[1:]) <= out[0] * 1.05     # raising the larger lambda only helps
+
+
+def test_lambda_sweep_full_vs_semi_time(stmg):
+    """The E1 analogue on the Kuhn cube (Section 5.1 experiment, power iteration of the
+    two-grid method): Full tracks Semi-time for large lambda and deteriorates for small
+    lambda; at lambda = 1/3 the GPU rates reproduce the oracle's per-cycle reductions."""
+    nf, N_t = 8, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    r = {}
+    for tau in (2.0 ** -10, 2.0 ** -6, 1.0):
+        for coarsen in (1, 2):
+            r[tau, coarsen] = rate_gpu(stmg, nf, 2, nu, sigma, tau * N_t, N_t, 0, 15, coarsen=coarsen, max_levels=2)
+    assert r[2.0 ** -10, 2][0] > 1.5 * r[2.0 ** -10, 1][0]
+    assert abs(r[1.0, 2][0] / r[1.0, 1][0] - 1.0) < 0.1
+    assert r[2.0 ** -6, 2][0] < 0.5
+    _, rs_gpu, x0 = r[2.0 ** -6, 2]
+    sl, tl, mg = oracle_mg(nf, 2, nu, sigma, 2.0 ** -6 * N_t, N_t, 0, coarsen=2, max_levels=2)
+    _, rs_o = mg.convergence_rate(x0, max_iter=15)
+    assert np.allclose(rs_gpu, rs_o, rtol=1e-9)
+
+
+@pytest.mark.parametrize("pattern", ["SA", "SSASS"])
+def test_smoother_orderings_match_oracle(stmg, pattern):
+    """Rates of other hybrid-smoother orderings (Section 4) through the library equal the
+    oracle's, cycle by cycle."""
+    nf, N_t = 4, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    r, rs_gpu, x0 = rate_gpu(stmg, nf, 1, nu, sigma, 16 / 512.0, N_t, 0, 10, coarsen=1, max_levels=2,
+                             smoother=pattern)
+    sl, tl, mg = oracle_mg(nf, 1, nu, sigma, 16 / 512.0, N_t, 0, coarsen=1, max_levels=2, pattern=pattern)
+    _, rs_o = mg.convergence_rate(x0, max_iter=10)
+    assert np.allclose(rs_gpu, rs_o, rtol=1e-9)

@@ -114,3 +114,17 @@ def test_server_options_validated(B):
         with pytest.raises(B.StMgError) as e:
             B.st_mg_server_create(o)
         assert e.value.status == 1
+
+
+def test_smoother_pattern_validated(B):
+    nu, sigma = st_inputs.materials(4, "unit")
+    prob = B.make_problem(4, 1, nu, sigma, 1.0, 8, 0)
+    for bad in (b"SXA", b"S A"):
+        opt = B.st_mg_default_options()
+        opt.smoother = bad
+        with pytest.raises(B.StMgError) as e:
+            B.st_mg_setup_host(prob, opt)
+        assert e.value.status == 1
+    opt = B.st_mg_default_options()
+    opt.smoother = b"SSA"
+    B.st_mg_destroy(B.st_mg_setup_host(prob, opt))

@@ -361,3 +361,58 @@ def test_paper_high_lambda_rate():
     x0 = st_inputs.random_iterate((N_t, 1, sl[0].ne), 0)
     r, _ = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1).convergence_rate(x0, max_iter=12)
     assert abs(r - 2.0 ** -4) < 0.01
+
+
+def _pattern_rates(T, patterns, nf=4, N_t=16):
+    nu, sigma = st_inputs.materials(nf, "unit")
+    sl = build_space_hierarchy(nf, 1, nu, sigma)
+    tl = build_time_hierarchy(N_t, T, nf, 1, nu, sigma, mode="semi_time", max_levels=2)
+    x0 = st_inputs.random_iterate((N_t, 1, sl[0].ne), 0)
+    return {p: SpaceTimeMG(sl, tl, 0, 0.5, pattern=p).convergence_rate(x0, max_iter=30)[0] for p in patterns}
+
+
+def test_paper_section4_smoother_orderings():
+    """Section 4 (hybrid smoother): two V-cycles with SA act like one with SAS, and SSASS
+    fails to square the SAS rate at low lambda but squares it at very large lambda."""
+    lo = _pattern_rates(16 / 512.0, ("SAS", "SA", "AS", "SSASS"))    # lambda = 1/3 (tau = 1/512, h = sqrt3/4)
+    hi = _pattern_rates(16.0, ("SAS", "SA", "AS", "SSASS"))           # lambda ~ 170
+    for r in (lo, hi):
+        assert r["SAS"] < r["SA"] < 1.0
+        assert 0.5 < r["SA"] ** 2 / r["SAS"] < 1.5
+        assert r["SSASS"] < r["SAS"]
+    assert abs(hi["SA"] ** 2 / hi["SAS"] - 1.0) < 0.02
+    assert lo["SSASS"] > 1.5 * lo["SAS"] ** 2          # does not square at low lambda
+    assert abs(hi["SSASS"] / hi["SAS"] ** 2 - 1.0) < 0.1   # squares at large lambda
+    assert abs(hi["SAS"] - 2.0 ** -4) < 0.01
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+def test_pattern_reproduces_symmetric_default(nu):
+    """The pattern S^nu A S^nu written out is the default V(nu, nu) smoother exactly."""
+    nf, N_t = 4, 8
+    nu_m, sigma = st_inputs.materials(nf, "two_material", 1)
+    sl = build_space_hierarchy(nf, 1, nu_m, sigma)
+    tl = build_time_hierarchy(N_t, 1.0, nf, 1, nu_m, sigma, mode="semi_time")
+    f = spacetime_load(sl[0].mesh, st_inputs.excitation(2), 1, N_t, 1.0)
+    a = SpaceTimeMG(sl, tl, 1, 0.5, nu, nu).vcycle(f, np.zeros_like(f))
+    b = SpaceTimeMG(sl, tl, 1, 0.5, pattern="S" * nu + "A" + "S" * nu).vcycle(f, np.zeros_like(f))
+    assert np.array_equal(a, b)
+
+
+def test_paper_lambda_full_vs_semi_time():
+    """Section 4.1 / 5.1: with the hybrid smoother, coarsening in space and time ('Full')
+    behaves like coarsening in time only ('Semi-time') for large lambda and deteriorates
+    for small lambda -- the reason for the coarsening rule eq. CoarseningRule."""
+    nf, N_t = 8, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    sl = build_space_hierarchy(nf, 2, nu, sigma)
+    x0 = st_inputs.random_iterate((N_t, 1, sl[0].ne), 0)
+    rates = {}
+    for tau in (2.0 ** -10, 1.0):
+        for mode in ("semi_time", "full_top"):
+            tl = build_time_hierarchy(N_t, tau * N_t, nf, 2, nu, sigma, mode=mode, max_levels=2)
+            rates[tau, mode] = SpaceTimeMG(sl, tl, 0, 0.5, 1, 1).convergence_rate(x0, max_iter=12)[0]
+    assert coarsening_lambda(nf, 2.0 ** -10, nu, sigma) < 0.05 < 10 < coarsening_lambda(nf, 1.0, nu, sigma)
+    assert rates[2.0 ** -10, "full_top"] > 1.5 * rates[2.0 ** -10, "semi_time"]
+    assert abs(rates[1.0, "full_top"] / rates[1.0, "semi_time"] - 1.0) < 0.1
+    assert abs(rates[1.0, "semi_time"] - 2.0 ** -4) < 0.01
