@@ -174,8 +174,9 @@ def run_rates(args):
     """Two-grid convergence rates by the power iteration of Section 5.1 on the GPU:
     'Semi-time' (time coarsening only) and 'Full' (space and time) against lambda of eq.
     CoarseningRule (the paper's experiment E1 on the Kuhn cube 16^3 -> 8^3, DG(0),
-    nu = sigma = 1, N_t = 16, lambda varied through tau), then hybrid-smoother orderings
-    (Section 4) at a small and a large lambda."""
+    nu = sigma = 1, N_t = 16, lambda varied through tau; Dirichlet and, as in the
+    paper's experiment, Neumann boundaries), then hybrid-smoother orderings (Section 4)
+    at a small and a large lambda."""
     import torch
 
     torch.cuda.set_device(0)
@@ -188,8 +189,8 @@ def run_rates(args):
     nu, sigma = st_inputs.materials(nf, "unit")
     h2 = 3.0 / nf ** 2
 
-    def rate(tau, **opts):
-        S = stmg.SpaceTimeSolver(nf, nu, sigma, tau * N_t, N_t, 0, n_space_levels=2, max_levels=2, **opts)
+    def rate(tau, bc=0, **opts):
+        S = stmg.SpaceTimeSolver(nf, nu, sigma, tau * N_t, N_t, 0, n_space_levels=2, max_levels=2, bc=bc, **opts)
         x = torch.from_numpy(st_inputs.random_iterate((S.n_edge, N_t), 0)).cuda()
         r, _ = S.convergence_rate(x, max_iter=15)
         S.close()
@@ -198,7 +199,10 @@ def run_rates(args):
     sweep = []
     for k in range(-12, 3, 2):
         tau = 2.0 ** k
-        sweep.append({"tau": tau, "lambda": tau / h2, "semi_time": rate(tau, coarsen=1), "full": rate(tau, coarsen=2)})
+        row = {"tau": tau, "lambda": tau / h2}
+        for bc, name in ((0, "dirichlet"), (1, "neumann")):
+            row[name] = {"semi_time": rate(tau, coarsen=1, bc=bc), "full": rate(tau, coarsen=2, bc=bc)}
+        sweep.append(row)
     orderings = {}
     for tau in (2.0 ** -8, 1.0):
         orderings[f"lambda={tau / h2:.3g}"] = {p: rate(tau, coarsen=1, smoother=p)

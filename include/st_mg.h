@@ -20,8 +20,9 @@
  *    is the vertex chain corner, +e_a, +e_b, +e_c.  Edges are sorted vertex pairs
  *    (lo, hi), numbered lexicographically and oriented lo -> hi.  Coarser space
  *    levels are the Kuhn meshes n/2, n/4, ... (uniform refinement, Section 5.1).
- *  Boundary.  Homogeneous Dirichlet u x n = 0: unknowns are the interior edges
- *    (edges not contained in a face of the cube), in increasing edge id order.
+ *  Boundary.  Homogeneous Dirichlet u x n = 0 (default): unknowns are the interior
+ *    edges (edges not contained in a face of the cube), in increasing edge id order;
+ *    Neumann (st_mg_problem.bc = 1): all edges in edge id order.
  *  Space-time vectors (f, x, r) of a time level with N_t slabs and degree p are
  *    double arrays  v[e * (N_t*(p+1)) + n*(p+1) + i]  -- edge-major, time
  *    contiguous -- for interior edge e, slab n, time basis function i
@@ -69,6 +70,11 @@ typedef struct {
                                 and time grid, solved together (0 or 1: one).  Vectors then hold
                                 v[e * (B N_t q) + b * (N_t q) + n q + i] for problem b; needs N_t a
                                 power of two (time coarsened to one slab per problem) */
+    int32_t bc;              /* boundary condition (Section 3): 0 homogeneous Dirichlet u x n = 0 (the
+                                unknowns are the interior edges, the nodal space the interior
+                                vertices); 1 Neumann (all edges; all vertices but vertex 0, which
+                                grounds the singular nodal matrix: G annihilates constants, so the
+                                correction G z does not depend on the choice) */
 } st_mg_problem;
 
 /* Method parameters (Sections 2.1, 2.2, 4, 5). */

@@ -22,6 +22,11 @@ not through code):
     order and oriented lo -> hi;
   * an edge lies on the boundary iff both end points lie on one face plane;
     a vertex is interior iff none of its indices is 0 or n.
+Boundary conditions (Section 3 offers both): Dirichlet u x n = 0 keeps the interior
+edges and vertices as unknowns; Neumann keeps every edge, and every vertex but
+vertex 0 (the nodal matrix of the Neumann problem is singular with the constants as
+kernel; G annihilates constants, so fixing one vertex changes no correction G z).
+The flags edge_interior / vert_interior mark the unknowns in both cases.
 """
 from __future__ import annotations
 
@@ -60,8 +65,9 @@ class KuhnMesh:
 LOCAL_EDGES = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
 
 
-def kuhn_mesh(n: int) -> KuhnMesh:
-    """Build the Kuhn mesh of [0,1]^3 with n cubes per side (plain loops)."""
+def kuhn_mesh(n: int, bc: str = "dirichlet") -> KuhnMesh:
+    """Build the Kuhn mesh of [0,1]^3 with n cubes per side (plain loops); bc selects
+    the unknowns ("dirichlet" or "neumann")."""
     nv = (n + 1) ** 3
     ijk = np.zeros((nv, 3), dtype=np.int64)
     for k in range(n + 1):
@@ -105,6 +111,12 @@ def kuhn_mesh(n: int) -> KuhnMesh:
     a, b = edges[:, 0], edges[:, 1]
     same_face = ((ijk[a] == 0) & (ijk[b] == 0)) | ((ijk[a] == n) & (ijk[b] == n))
     edge_interior = ~same_face.any(axis=1)
+    if bc == "neumann":
+        edge_interior = np.ones(len(edges), dtype=bool)
+        vert_interior = np.ones(nv, dtype=bool)
+        vert_interior[0] = False
+    elif bc != "dirichlet":
+        raise ValueError(bc)
     return KuhnMesh(n, xyz, ijk, tets, edges, tet_edges, edge_interior, vert_interior)
 
 

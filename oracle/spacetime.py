@@ -58,15 +58,16 @@ class SpaceLevel:
         return self._kn_lu.solve(y)
 
 
-def build_space_hierarchy(n_fine: int, n_levels: int, nu, sigma):
-    """Space levels, finest first.  nu, sigma are per tet of the finest mesh.
+def build_space_hierarchy(n_fine: int, n_levels: int, nu, sigma, bc: str = "dirichlet"):
+    """Space levels, finest first.  nu, sigma are per tet of the finest mesh; bc is
+    "dirichlet" or "neumann" (which unknowns, see oracle.mesh).
 
     The finest matrices are assembled from the element integrals; each coarser
     level uses Galerkin products with the interpolation prolongations (the
     coefficients vary per fine tet, so re-discretisation would be ambiguous).
     """
     levels = []
-    mesh = kuhn_mesh(n_fine)
+    mesh = kuhn_mesh(n_fine, bc)
     M, K = assemble_edge_matrices(mesh, nu, sigma)
     G = discrete_gradient(mesh)
     Kn = nodal_stiffness(mesh, sigma)
@@ -74,7 +75,7 @@ def build_space_hierarchy(n_fine: int, n_levels: int, nu, sigma):
     n = n_fine
     for _ in range(1, n_levels):
         assert n % 2 == 0
-        cmesh = kuhn_mesh(n // 2)
+        cmesh = kuhn_mesh(n // 2, bc)
         fine = levels[-1]
         Px = round_dyadic(edge_prolongation(cmesh, fine.mesh))
         Pn = round_dyadic(node_prolongation(cmesh, fine.mesh))

@@ -26,7 +26,7 @@ class StMgError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("n_cube", _i32), ("n_space_levels", _i32), ("nu", _P(_dbl)), ("sigma", _P(_dbl)),
-                ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32)]
+                ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32), ("bc", _i32)]
 
 
 class Options(ctypes.Structure):
@@ -166,10 +166,10 @@ def st_mg_default_options() -> Options:
     return o
 
 
-def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1):
+def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1, bc=0):
     nu = np.ascontiguousarray(nu, dtype=np.float64)
     sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch)
+    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch, bc)
     p._keep = (nu, sigma)
     return p
 

@@ -57,7 +57,10 @@ extern const int kPerm[6][3];      // axis permutations, lexicographic
 extern const int kDir[7][3];       // edge direction codes, sorted by vertex-id offset
 extern const int kLocalEdge[6][2];
 
-void build_kuhn(int n, KuhnMesh& m);
+// bc 0: Dirichlet u x n = 0 (interior edges and vertices are the unknowns);
+// bc 1: Neumann (all edges; all vertices but vertex 0, which grounds the singular
+// nodal matrix -- G annihilates constants, so the correction G z is unchanged)
+void build_kuhn(int n, KuhnMesh& m, int bc = 0);
 
 // Whitney edge matrices on interior edges: one CSR pattern, two value arrays.
 void assemble_edge(const KuhnMesh& m, const double* nu, const double* sigma, Csr& M, Csr& K);

@@ -100,7 +100,7 @@ int64_t find_pos(const Csr& A, int32_t r, int32_t c) {
 
 }  // namespace
 
-void build_kuhn(int n, KuhnMesh& m) {
+void build_kuhn(int n, KuhnMesh& m, int bc) {
   m.n = n;
   m.nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
   m.nt = (int64_t)6 * n * n * n;
@@ -147,7 +147,10 @@ void build_kuhn(int n, KuhnMesh& m) {
   for (int v = 0; v < m.nv; ++v) {
     int i, j, k;
     m.vijk(v, i, j, k);
-    if (i > 0 && i < n && j > 0 && j < n && k > 0 && k < n) {
+    // Dirichlet: interior vertices; Neumann: all but vertex 0 (the grounded node of
+    // the singular nodal problem)
+    const bool unknown = bc == 1 ? v != 0 : (i > 0 && i < n && j > 0 && j < n && k > 0 && k < n);
+    if (unknown) {
       m.vert_iid[v] = (int32_t)m.int_verts.size();
       m.int_verts.push_back(v);
     }
@@ -161,7 +164,7 @@ void build_kuhn(int n, KuhnMesh& m) {
     bool on_face = false;
     for (int d = 0; d < 3; ++d)
       if ((a[d] == 0 && b[d] == 0) || (a[d] == n && b[d] == n)) on_face = true;
-    if (!on_face) {
+    if (!on_face || bc == 1) {   // Neumann: every edge is an unknown
       m.edge_iid[e] = (int32_t)m.int_edges.size();
       m.int_edges.push_back((int32_t)e);
     }

@@ -854,6 +854,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (n < 2 || nsl < 1 || pr->N_t < 1 || !(pr->T > 0) || (pr->degree != 0 && pr->degree != 1) || !pr->nu ||
       !pr->sigma)
     return fail(ST_MG_ERR_INVALID_ARG, "invalid problem (n_cube >= 2, n_space_levels >= 1, N_t >= 1, T > 0, degree 0|1)");
+  if (pr->bc != 0 && pr->bc != 1) return fail(ST_MG_ERR_INVALID_ARG, "bc must be 0 (Dirichlet) or 1 (Neumann)");
   if ((n >> (nsl - 1)) < 2 || (n % (1 << (nsl - 1))) != 0)
     return fail(ST_MG_ERR_INVALID_ARG, "n_cube must be divisible by 2^(n_space_levels-1) with coarsest >= 2");
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
@@ -888,7 +889,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.space.resize(nsl);
   for (int s = 0; s < nsl; ++s) {
     auto& S = H.space[s];
-    build_kuhn(n >> s, S.mesh);
+    build_kuhn(n >> s, S.mesh, pr->bc);
     S.ne = (int32_t)S.mesh.int_edges.size();
     S.nn = (int32_t)S.mesh.int_verts.size();
     gradient_pairs(S.mesh, S.gtail, S.ghead);
@@ -973,6 +974,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   skey.assign(H.space.size(), std::string());
   if (H.use_cache) {
     uint64_t mh = fnv1a(1469598103934665603ull, &n, sizeof(n));
+    mh = fnv1a(mh, &pr->bc, sizeof(pr->bc));
     mh = fnv1a(mh, H.nu.data(), H.nu.size() * sizeof(double));
     H.mat_hash = fnv1a(mh, H.sigma.data(), H.sigma.size() * sizeof(double));
     char buf[192];

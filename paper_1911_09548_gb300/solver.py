@@ -12,8 +12,8 @@ from . import binding as B
 
 class SpaceTimeSolver:
     def __init__(self, n_cube, nu, sigma, T, N_t, degree, n_space_levels=1, stream=None, host_only=False,
-                 n_batch=1, **options):
-        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch)
+                 n_batch=1, bc=0, **options):
+        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch, bc)
         self.n_batch = n_batch
         self.opt = B.st_mg_default_options()
         for k, v in options.items():

@@ -26,8 +26,8 @@ def rel(a, b):
 
 
 def oracle_mg(n, nsl, nu, sigma, T, N_t, p, coarsen=0, max_levels=0, nu_pre=1, nu_post=1, lambda_crit=0.1,
-              nodal="exact", jacobi_sweeps=0, use_A=True, omega=0.5, pattern=""):
-    sl = build_space_hierarchy(n, nsl, nu, sigma)
+              nodal="exact", jacobi_sweeps=0, use_A=True, omega=0.5, pattern="", bc=0):
+    sl = build_space_hierarchy(n, nsl, nu, sigma, bc=("dirichlet", "neumann")[bc])
     tl = build_time_hierarchy(N_t, T, n, nsl, nu, sigma, mode=MODES[coarsen], lambda_crit=lambda_crit,
                               max_levels=max_levels if max_levels > 0 else 64)
     mg = SpaceTimeMG(sl, tl, p, omega, nu_pre, nu_post, nodal=nodal, jacobi_sweeps=jacobi_sweeps, use_A=use_A,

@@ -38,6 +38,8 @@ CASES = {
     # other hybrid-smoother orderings (Section 4): "SSA" (pre A, S, S; post S, S, A), "SA"
     "dg1_ragged_SSA": (8, 1, 1, 20, "two_material", dict(smoother="SSA")),
     "dg0_two_grid_SA": (4, 1, 0, 16, "unit", dict(max_levels=2, smoother="SA")),
+    # Neumann boundary (all edges, grounded vertex 0), space coarsening on the first transition
+    "dg1_neumann_full": (8, 2, 1, 16, "two_material", dict(bc=1, coarsen=2)),
 }
 
 
@@ -63,7 +65,8 @@ def setup_case(name, lib_built):
     okw = dict(coarsen=opts.get("coarsen", 0), max_levels=opts.get("max_levels", 0),
                nu_pre=opts.get("nu_pre", 1), nu_post=opts.get("nu_post", 1),
                nodal="exact" if opts.get("nodal_solve", 0) == 0 else "jacobi",
-               jacobi_sweeps=opts.get("nodal_jacobi_sweeps", 0), pattern=opts.get("smoother", ""))
+               jacobi_sweeps=opts.get("nodal_jacobi_sweeps", 0), pattern=opts.get("smoother", ""),
+               bc=opts.get("bc", 0))
     sl, tl, mg = oracle_mg(n, nsl, nu, sigma, 1.0, N_t, p, **okw)
     assert [(L["space_level"], L["N_t"]) for L in S.levels] == [(t.s, t.N_t) for t in tl]
     _cache[name] = (S, sl, tl, mg, p)

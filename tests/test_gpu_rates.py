@@ -98,3 +98,18 @@ def test_smoother_orderings_match_oracle(stmg, pattern):
     sl, tl, mg = oracle_mg(nf, 1, nu, sigma, 16 / 512.0, N_t, 0, coarsen=1, max_levels=2, pattern=pattern)
     _, rs_o = mg.convergence_rate(x0, max_iter=10)
     assert np.allclose(rs_gpu, rs_o, rtol=1e-9)
+
+
+def test_neumann_rates(stmg):
+    """The paper's rate experiments use Neumann conditions: with them, the large-lambda
+    two-grid rate is again 2^-4, Full matches Semi-time there, and the GPU reproduces the
+    oracle cycle by cycle."""
+    nf, N_t = 8, 16
+    nu, sigma = st_inputs.materials(nf, "unit")
+    r1, rs1, x0 = rate_gpu(stmg, nf, 2, nu, sigma, float(N_t), N_t, 0, 12, coarsen=1, max_levels=2, bc=1)
+    r2, _, _ = rate_gpu(stmg, nf, 2, nu, sigma, float(N_t), N_t, 0, 12, coarsen=2, max_levels=2, bc=1)
+    assert abs(r1 - 2.0 ** -4) < 0.01
+    assert abs(r2 / r1 - 1.0) < 0.1
+    sl, tl, mg = oracle_mg(nf, 2, nu, sigma, float(N_t), N_t, 0, coarsen=1, max_levels=2, bc=1)
+    _, rs_o = mg.convergence_rate(x0, max_iter=12)
+    assert np.allclose(rs1, rs_o, rtol=1e-9)

@@ -55,12 +55,13 @@ def test_invalid_arguments_rejected(B):
     assert B.st_mg_strerror(5) == "not converged"
 
 
-@pytest.mark.parametrize("n,nsl,p,coarsen", [(4, 1, 0, 0), (8, 2, 1, 2)])
-def test_host_setup_matches_oracle(B, n, nsl, p, coarsen):
+@pytest.mark.parametrize("n,nsl,p,coarsen,bc", [(4, 1, 0, 0, 0), (8, 2, 1, 2, 0), (4, 2, 1, 2, 1)])
+def test_host_setup_matches_oracle(B, n, nsl, p, coarsen, bc):
+    """bc = 1: Neumann (all edges; vertex 0 grounds the nodal matrix)."""
     from paper_1911_09548_gb300 import SpaceTimeSolver
     nu, sigma = st_inputs.materials(n, "two_material", 3)
-    S = SpaceTimeSolver(n, nu, sigma, 1.0, 8, p, n_space_levels=nsl, host_only=True, coarsen=coarsen)
-    sl, tl, mg = oracle_mg(n, nsl, nu, sigma, 1.0, 8, p, coarsen=coarsen)
+    S = SpaceTimeSolver(n, nu, sigma, 1.0, 8, p, n_space_levels=nsl, host_only=True, coarsen=coarsen, bc=bc)
+    sl, tl, mg = oracle_mg(n, nsl, nu, sigma, 1.0, 8, p, coarsen=coarsen, bc=bc)
     assert [(L["space_level"], L["N_t"]) for L in S.levels] == [(t.s, t.N_t) for t in tl]
     for s in range(nsl):
         m = sl[s].mesh

@@ -416,3 +416,35 @@ def test_paper_lambda_full_vs_semi_time():
     assert rates[2.0 ** -10, "full_top"] > 1.5 * rates[2.0 ** -10, "semi_time"]
     assert abs(rates[1.0, "full_top"] / rates[1.0, "semi_time"] - 1.0) < 0.1
     assert abs(rates[1.0, "semi_time"] - 2.0 ** -4) < 0.01
+
+
+def test_neumann_spaces():
+    """Neumann boundary (Section 3): every edge is an unknown; the nodal space drops one
+    vertex (the constants are the kernel of the singular nodal matrix).  curl grad = 0,
+    G^T M G = K_n, rank K = N_e - (N_v - 1), K_n SPD, and P_x G_c = G_f P_n."""
+    n = 3
+    m = kuhn_mesh(n, "neumann")
+    assert len(m.interior_edges) == len(m.edges) and len(m.interior_verts) == (n + 1) ** 3 - 1
+    nu, sigma = st_inputs.materials(n, "two_material", 1)
+    M, K = assemble_edge_matrices(m, nu, sigma)
+    G = discrete_gradient(m)
+    Kn = nodal_stiffness(m, sigma)
+    assert abs(K @ G).max() < 1e-12 and abs(G.T @ M @ G - Kn).max() < 1e-12
+    assert np.linalg.matrix_rank(K.toarray()) == M.shape[0] - G.shape[1]
+    assert np.linalg.eigvalsh(Kn.toarray()).min() > 0
+    sl = build_space_hierarchy(4, 2, *st_inputs.materials(4, "unit"), bc="neumann")
+    assert abs(sl[0].Px @ sl[1].G - sl[0].G @ sl[0].Pn).max() == 0
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_neumann_direct_solve_equals_time_stepping(p):
+    nu, sigma = st_inputs.materials(3, "two_material", 2)
+    sl = build_space_hierarchy(3, 1, nu, sigma, bc="neumann")
+    N_t, T = 6, 0.5
+    tl = build_time_hierarchy(N_t, T, 3, 1, nu, sigma, mode="semi_time", max_levels=1)
+    slab = SlabOperator(sl[0], p, tl[0].tau)
+    f = spacetime_load(sl[0].mesh, st_inputs.excitation(4), p, N_t, T)
+    x_seq = sequential_solve(slab, f)
+    L = spacetime_matrix(sl[0], p, tl[0].tau, N_t)
+    x_dir = spla.spsolve(L.tocsc(), f.reshape(-1)).reshape(f.shape)
+    assert np.abs(x_seq - x_dir).max() < 1e-10 * np.abs(x_dir).max()
