@@ -216,6 +216,7 @@ def run_rates(args):
 
 # ------------------------------------------------------------------ serving
 SERVE_SPACE_LEVELS = {4: 2, 8: 2, 16: 3, 24: 3}
+SERVE_EDGES = {4: 316, 8: 3032, 16: 26416, 24: 91656}   # interior edges of the Kuhn meshes
 
 
 def run_serve(args):
@@ -235,14 +236,23 @@ def run_serve(args):
     import st_inputs
 
     rates = [float(v) for v in args.serve_rates.split(",")]
-    meshes = [int(v) for v in args.serve_meshes.split(",")]
+    meshes = [24] if args.serve_burst > 0 else [int(v) for v in args.serve_meshes.split(",")]
     nt_lo, nt_hi = (int(v) for v in args.serve_nt.split(","))
     nu_c = 2
     srv = stmg.SpaceTimeServer(slots=args.serve_slots, slab_prec=args.serve_prec, nu=nu_c, max_cycles=60)
     for n in meshes:
         srv.register(n, SERVE_SPACE_LEVELS[n], *st_inputs.materials(n, "two_material", 0))
-    streams = [st_inputs.request_stream(args.serve_requests, r, seed=i, meshes=meshes, nt_range=(nt_lo, nt_hi))
-               for i, r in enumerate(rates)]
+    if args.serve_burst > 0:
+        # every request arrives at once (offered rate: unbounded)
+        rates = [float("inf")]
+        burst = st_inputs.request_stream(args.serve_burst, 1e9, seed=7, meshes=(24,), nt_range=(128, 1024),
+                                         degrees=(1,))
+        for q in burst:
+            q["t"], q["sigma_scale"] = 0.0, 1.0
+        streams = [burst]
+    else:
+        streams = [st_inputs.request_stream(args.serve_requests, r, seed=i, meshes=meshes, nt_range=(nt_lo, nt_hi))
+                   for i, r in enumerate(rates)]
 
     def submit(q, t_arr=0.0):
         return srv.submit(q["n_cube"], q["degree"], q["N_t"], 1.0 / q["N_t"], q["sigma_scale"],
@@ -284,10 +294,12 @@ def run_serve(args):
                 bad += r["status"] != 0
                 done += 1
         dur = time.monotonic() - (t_start + stream[0]["t"])
+        n_dofs = sum(SERVE_EDGES.get(q["n_cube"], 0) * q["N_t"] * (q["degree"] + 1) for q in stream)
         s1 = srv.stats()
         lat_s = sorted(lat)
         smoothed = (s1["dofs_smoothed"] - s0["dofs_smoothed"]) * 4 * nu_c
-        rows.append({"offered_req_per_s": rate, "requests": len(stream), "duration_s": dur,
+        rows.append({"offered_req_per_s": rate if rate != float("inf") else "all at t = 0",
+                     "requests": len(stream), "duration_s": dur, "space_time_dofs": n_dofs,
                      "throughput_req_per_s": len(stream) / dur, "dofs_smoothed_per_s": smoothed / dur,
                      "latency_p50_s": float(np.percentile(lat_s, 50)), "latency_p99_s": float(np.percentile(lat_s, 99)),
                      "latency_max_s": lat_s[-1], "v_cycles_mean": float(np.mean(cyc)), "not_converged": bad,
@@ -297,7 +309,10 @@ def run_serve(args):
     srv.close()
     line = {"metric": "served solves to 1e-8 relative residual: throughput and p50/p99 latency", "unit": "s",
             "mode": "serve", "data": "synthetic",
-            "config": {"meshes": meshes, "N_t": f"powers of two in [{nt_lo}, {nt_hi}]", "degrees": [0, 1],
+            "config": {"meshes": meshes, "burst": args.serve_burst,
+                       "N_t": (f"powers of two in [{nt_lo}, {nt_hi}]" if args.serve_burst == 0 else
+                               "uniform over {128, 256, 512, 1024}"),
+                       "degrees": [0, 1] if args.serve_burst == 0 else [1],
                        "sigma_scale": "log-uniform [0.1, 10] rounded to a power of two", "tau": "1 / N_t",
                        "slots_per_class": args.serve_slots, "slab_prec": args.serve_prec,
                        "cycle": f"V({nu_c},{nu_c})", "rtol": 1e-8,
@@ -335,6 +350,9 @@ def main():
     ap.add_argument("--serve-nt", default="64,2048", help="N_t range (powers of two)")
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--serve-prec", type=int, default=3, choices=[0, 1, 2, 3])
+    ap.add_argument("--serve-burst", type=int, default=0,
+                    help="instead of Poisson streams: this many requests at once on the 24^3 mesh, N_t uniform "
+                         "over {128, 256, 512, 1024}, DG(1) (the batching workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -160,3 +160,26 @@ def test_factor_cache_shares_levels(stmg):
         S.close()
     assert B.st_mg_cache_stats()["in_use"] == 0
     assert B.st_mg_cache_trim(0) == 0
+
+
+def test_request_failures_reported(stmg):
+    """A request that reaches max_cycles comes back ST_MG_ERR_NOT_CONVERGED (5) with its
+    last iterate; invalid submissions are rejected at submit time."""
+    srv = stmg.SpaceTimeServer(slots=2, slab_prec=0, nu=1, max_cycles=2)
+    srv.register(4, 2, *mats(4))
+    exc = st_inputs.excitation(1)
+    rid = srv.submit(4, 1, 16, 1 / 16, 1.0, exc, 1e-12)
+    done = {}
+    for _ in range(100000):
+        for d in srv.step():
+            done[d] = srv.result(d)
+        if rid in done:
+            break
+    r = done[rid]
+    assert r["status"] == 5 and r["cycles"] == 2 and 1e-12 < r["rel_res"] < 1.0
+    B = stmg.binding
+    for args in ((8, 1, 16, 1 / 16, 1.0), (4, 2, 16, 1 / 16, 1.0), (4, 1, 12, 1 / 16, 1.0),
+                 (4, 1, 16, -1.0, 1.0), (4, 1, 16, 1 / 16, 0.0)):
+        with pytest.raises(B.StMgError):
+            srv.submit(*args, exc, 1e-8)   # unregistered mesh, degree, N_t, tau, sigma scale
+    srv.close()
