@@ -35,6 +35,10 @@ WORKLOAD = dict(name="kuhn16_dg1_Nt256_V22", n=16, N_t=256, degree=1, T=1.0, nu_
 METRIC = "space-time DoFs smoothed/s"
 UNIT = "DoF/s"
 CPU_SAMPLE_SLABS = 16
+# DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
+# this workload, from one ncu capture (profiles/sn_slab_solve_kuhn16_dg1_fp64_traffic.md);
+# set to None when those kernels change
+SLAB_SOLVE_TRAFFIC_FP64 = 1.766e9
 
 
 def smoothed_per_cycle(dofs, nu_pre, nu_post):
@@ -605,8 +609,11 @@ def main():
                                  "v_cycles": solve_iters} if solve_ms else None),
             "setup_s": setup_s,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak, "traffic": None,
-                         "kernel": "supernodal slab solve, finest level (k_sn_forward/backward, split-K near the root)",
+                         "frac": achieved / fp64_peak,
+                         "traffic": SLAB_SOLVE_TRAFFIC_FP64 if args.slab_prec == 0 else None,
+                         "kernel": ("supernodal slab solve, finest level (k_sn_forward/backward, split-K near the "
+                                    "root; complex products with three real multiplications)"),
+                         "achieved_counts": "algorithmic flop: 8 per complex multiply-add of the factor",
                          "peak_source": "FP64 FMA throughput measured in this run (st_mg_probe_fp64)",
                          "ms_per_launch_group": slab_ms},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n_dof * 8,
