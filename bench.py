@@ -341,6 +341,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="tiled / split-K thresholds chosen per level by timing at setup")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
@@ -400,7 +402,9 @@ def main():
     torch.cuda.set_stream(stream)
     t0 = time.time()
     S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                             nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec)
+                             nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec,
+                             autotune=args.autotune)
+    split_waves = [stmg.st_mg_split_waves(S.h, l) for l in range(S.n_levels)]
     setup_s = time.time() - t0
     n_levels, n_dof = S.n_levels, S.n_dof
     f = S.load(st_inputs.excitation(W["seed"] + rank))
@@ -500,7 +504,8 @@ def main():
         torch.cuda.synchronize()
         for vname, prec, peak_key in (("mixed_fp32", 1, None), ("bf16_tensor", 3, "bf16_tflops")):
             Sm = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                                      nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec)
+                                      nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec,
+                                      autotune=args.autotune)
             fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
             xm = Sm.zeros()
             for _ in range(args.warmup):
@@ -554,7 +559,8 @@ def main():
     if args.mixed and args.batch > 1:
         NB_ = args.batch
         Sb = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=3, n_batch=NB_)
+                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=3, n_batch=NB_,
+                                  autotune=args.autotune)
         fb = Sb.zeros()
         for b in range(NB_):
             Sb.load(st_inputs.excitation(W["seed"] + 1 + b + 1000 * rank), f=fb, batch=b)
@@ -604,6 +610,7 @@ def main():
             "config": {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
                        "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": n_levels,
                        "dofs": n_dof, "parallelism": f"replicas x{world}",
+                       "split_waves_per_level": split_waves, "autotune": bool(args.autotune),
                        "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),

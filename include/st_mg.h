@@ -122,6 +122,11 @@ typedef struct {
                                 process-wide factor cache (key: device, mesh, space level, materials,
                                 DG degree, tau, precision), so handles that share a mesh and a tau
                                 share one device copy; 0 (default): the handle owns its factors */
+    int32_t autotune;        /* 1: at setup, time each time level's slab solve for several tiled /
+                                split-K thresholds (a tree depth whose tiles fill fewer than w waves
+                                of the SMs runs split-K; w in {0, 1, 2, 4, 8}) and keep the fastest
+                                per level (results change at rounding level, by the summation order
+                                of the chosen kernels); 0 (default): w = 2 */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,
@@ -278,6 +283,10 @@ int st_mg_cache_stats(int64_t* bytes, int32_t* entries, int32_t* in_use, int64_t
 /* Evict least-recently-used entries that no live handle uses until the cache holds at
  * most max_bytes (0: every unused entry).  *bytes_after (may be NULL) = what remains. */
 int st_mg_cache_trim(int64_t max_bytes, int64_t* bytes_after);
+
+/* Tiled / split-K threshold of a time level's slab solve, in waves of SMs (2 unless
+ * st_mg_options.autotune chose another). */
+int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves);
 
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("coarsen", _i32), ("max_levels", _i32), ("min_coarse_slabs", _i32),
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
                 ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32),
-                ("smoother", ctypes.c_char * 16), ("persistent_split", _i32), ("factor_cache", _i32)]
+                ("smoother", ctypes.c_char * 16), ("persistent_split", _i32), ("factor_cache", _i32),
+                ("autotune", _i32)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -91,6 +92,7 @@ _SIGS = {
     "st_mg_batch_norms": [_vp, _vp, _P(_dbl)],
     "st_mg_vcycle_residual_async": [_vp, _vp, _vp, _vp],
     "st_mg_memory": [_vp, _P(_i64), _P(_i64)],
+    "st_mg_split_waves": [_vp, _i32, _P(_i32)],
     "st_mg_cache_stats": [_P(_i64), _P(_i32), _P(_i32), _P(_i64), _P(_i64)],
     "st_mg_cache_trim": [_i64, _P(_i64)],
     "st_mg_batch_zero": [_vp, _i32, _vp],
@@ -315,6 +317,12 @@ def st_mg_batch_norms(h, v_dev, n_batch):
 
 def st_mg_batch_zero(h, batch, v_dev):
     _check(lib().st_mg_batch_zero(_vp(h), batch, _vp(_addr(v_dev))), "st_mg_batch_zero")
+
+
+def st_mg_split_waves(h, level):
+    w = _i32(0)
+    _check(lib().st_mg_split_waves(_vp(h), level, ctypes.byref(w)), "st_mg_split_waves")
+    return w.value
 
 
 def st_mg_memory(h):

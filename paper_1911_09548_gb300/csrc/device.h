@@ -97,12 +97,14 @@ constexpr int kSnBM = 64;
 // Q (in) is overwritten by X (out); Z and U are workspaces ([n*ld], [u_rows*ld]).
 // P is the split-K partial buffer: max_items * kSkRows * (max right-hand sides per
 // solve, rounded up to the column block) elements.  Null disables the split-K path.
-// Per-handle state of the persistent split-K slab solve: grid-barrier words
-// (arrivals, generation; zero at allocation) and the flag a bounded wait sets.
-// bar == nullptr disables the persistent launch.
+// Per-handle solve state: grid-barrier words of the persistent split-K solve
+// (arrivals, generation; zero at allocation; bar == nullptr disables the persistent
+// launch), the flag a bounded wait sets, and the tiled/split-K threshold.
 struct SkSync {
   unsigned* bar = nullptr;
   int* err = nullptr;
+  int split_waves = 2;   // a tree depth runs split-K when its tiles fill fewer than this many
+                         // waves of the SMs (setup may tune it per level)
 };
 
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,

@@ -238,6 +238,7 @@ struct st_mg_s {
     SupernodalFactor<cplx> fc;
     std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
     int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
+    int split_waves = 2;                                    // tiled / split-K threshold (autotuned)
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
   };
@@ -582,39 +583,61 @@ void op_residual(Handle& h, int l, const double* f, const double* x, double* r, 
   }
 }
 
+// The slab factor of level l applied to cnt permuted columns of the workspace Q
+// (in place), in the level's arithmetic.
+void level_solve(Handle& h, int l, int cnt) {
+  auto& L = h.lv[l];
+  SkSync sk = h.sk;
+  sk.split_waves = L.split_waves;
+  if (L.prec == 3) {
+    CK(sn_solve_cplx_bf16(L.fac->dcb, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
+                          static_cast<float2*>(h.sU), static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, sk,
+                          h.stream));
+  } else if (L.prec == 1) {
+    if (h.prob.degree == 0)
+      CK(sn_solve_realf(L.fac->drf, static_cast<float*>(h.sQ), static_cast<float*>(h.sZ), static_cast<float*>(h.sU),
+                        static_cast<float*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+    else
+      CK(sn_solve_cplxf(L.fac->dcf, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
+                        static_cast<float2*>(h.sU), static_cast<float2*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+  } else if (h.prob.degree == 0) {
+    if (L.prec == 2)
+      CK(sn_solve_real_df(L.fac->drd, static_cast<double*>(h.sQ), static_cast<double*>(h.sZ),
+                          static_cast<double*>(h.sU), static_cast<double*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+    else
+      CK(sn_solve_real(L.fac->dr, static_cast<double*>(h.sQ), static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
+                       static_cast<double*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+  } else {
+    if (L.prec == 2)
+      CK(sn_solve_cplx_df(L.fac->dcd, static_cast<double2*>(h.sQ), static_cast<double2*>(h.sZ),
+                          static_cast<double2*>(h.sU), static_cast<double2*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+    else
+      CK(sn_solve_cplx(L.fac->dc, static_cast<double2*>(h.sQ), static_cast<double2*>(h.sZ),
+                       static_cast<double2*>(h.sU), static_cast<double2*>(h.sP), cnt, h.ld_slab, sk, h.stream));
+  }
+}
+
 // Slab solve on slabs [slab0, slab0+cnt) of src (row length src_ld doubles) into dst
 // (row length dst_ld) at slab dst0: mode 0 assign, mode 1 dst += omega * A^{-1} src.
 void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, int cnt, double* dst, int dst_ld,
                   int dst0, double omega, int mode) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  if (L.prec == 3) {
-    const double inv_tau = 1.0 / L.tau;
-    const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
-    const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
-    float2* Q = static_cast<float2*>(h.sQ);
-    CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcb.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-    CK(sn_solve_cplx_bf16(L.fac->dcb, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                          static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, h.sk, h.stream));
-    CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcb.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
-    return;
-  }
-  if (L.prec == 1) {
+  const double inv_tau = 1.0 / L.tau;
+  const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
+  const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
+  if (L.prec == 1 || L.prec == 3) {   // FP32 workspace
     if (h.prob.degree == 0) {
       float* Q = static_cast<float*>(h.sQ);
       CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.fac->drf.iperm, S.ne, Q, h.ld_slab, h.stream));
-      CK(sn_solve_realf(L.fac->drf, Q, static_cast<float*>(h.sZ), static_cast<float*>(h.sU), static_cast<float*>(h.sP),
-                        cnt, h.ld_slab, h.sk, h.stream));
+      level_solve(h, l, cnt);
       CK(slab_post_dg0f(Q, h.ld_slab, L.fac->drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     } else {
-      const double inv_tau = 1.0 / L.tau;
-      const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
-      const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
+      const int32_t* ip = L.prec == 3 ? L.fac->dcb.iperm : L.fac->dcf.iperm;
       float2* Q = static_cast<float2*>(h.sQ);
-      CK(slab_pre_dg1f(src, src_ld, slab0, cnt, L.fac->dcf.iperm, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-      CK(sn_solve_cplxf(L.fac->dcf, Q, static_cast<float2*>(h.sZ), static_cast<float2*>(h.sU),
-                        static_cast<float2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
-      CK(slab_post_dg1f(Q, h.ld_slab, L.fac->dcf.iperm, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
+      CK(slab_pre_dg1f(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+      level_solve(h, l, cnt);
+      CK(slab_post_dg1f(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     }
     return;
   }
@@ -622,26 +645,13 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
     double* Q = static_cast<double*>(h.sQ);
     const int32_t* ip = L.prec == 2 ? L.fac->drd.iperm : L.fac->dr.iperm;
     CK(slab_pre_dg0(src, src_ld, slab0, cnt, ip, S.ne, Q, h.ld_slab, h.stream));
-    if (L.prec == 2)
-      CK(sn_solve_real_df(L.fac->drd, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU),
-                          static_cast<double*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
-    else
-      CK(sn_solve_real(L.fac->dr, Q, static_cast<double*>(h.sZ), static_cast<double*>(h.sU), static_cast<double*>(h.sP),
-                       cnt, h.ld_slab, h.sk, h.stream));
+    level_solve(h, l, cnt);
     CK(slab_post_dg0(Q, h.ld_slab, ip, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   } else {
-    const double inv_tau = 1.0 / L.tau;
-    const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
-    const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
     double2* Q = static_cast<double2*>(h.sQ);
     const int32_t* ip = L.prec == 2 ? L.fac->dcd.iperm : L.fac->dc.iperm;
     CK(slab_pre_dg1(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
-    if (L.prec == 2)
-      CK(sn_solve_cplx_df(L.fac->dcd, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
-                          static_cast<double2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
-    else
-      CK(sn_solve_cplx(L.fac->dc, Q, static_cast<double2*>(h.sZ), static_cast<double2*>(h.sU),
-                       static_cast<double2*>(h.sP), cnt, h.ld_slab, h.sk, h.stream));
+    level_solve(h, l, cnt);
     CK(slab_post_dg1(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
   }
 }
@@ -861,6 +871,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
+      (op->autotune != 0 && op->autotune != 1) ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = (int64_t)6 * n * n * n;
@@ -1062,6 +1073,44 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   return ST_MG_OK;
 }
 
+// Tiled / split-K threshold per time level: each candidate is timed on two slab solves
+// of the level's full column count (after one untimed solve), on the handle's stream,
+// with the slab workspace as input (the values do not affect the time).  Levels whose
+// solve runs split-K throughout (few right-hand sides) have nothing to choose.
+void autotune_split(Handle& H) {
+  const int cand[] = {0, 1, 2, 4, 8};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (size_t l = 0; l < H.lv.size(); ++l) {
+    auto& L = H.lv[l];
+    const int cnt = L.N_t * H.B;
+    const int skinny_max = (H.prob.degree == 0) ? kSkMaxRhsR : kSkMaxRhsC;
+    if (cnt <= skinny_max) continue;
+    float best = 0.f;
+    int best_w = L.split_waves;
+    for (int w : cand) {
+      L.split_waves = w;
+      level_solve(H, (int)l, cnt);
+      CK(cudaEventRecord(e0, H.stream));
+      for (int rep = 0; rep < 2; ++rep) level_solve(H, (int)l, cnt);
+      CK(cudaEventRecord(e1, H.stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (best == 0.f || ms < best) {
+        best = ms;
+        best_w = w;
+      }
+    }
+    L.split_waves = best_w;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timed solves may have left the bounded-wait flag set only through a real timeout
+  CK(cudaStreamSynchronize(H.stream));
+}
+
 // Device phase of the setup: upload meshes, matrices and factors (taking cache entries
 // that appeared since the host phase), size the workspaces.
 int setup_device(Handle& H) {
@@ -1258,6 +1307,7 @@ int setup_device(Handle& H) {
   // the uploads above ran on the legacy default stream
   CK(cudaStreamSynchronize(cudaStreamLegacy));
   H.pending_upload = false;
+  if (op->autotune) autotune_split(H);
   return ST_MG_OK;
 }
 
@@ -1409,6 +1459,7 @@ int st_mg_default_options(st_mg_options* o) {
   std::memset(o->smoother, 0, sizeof(o->smoother));
   o->persistent_split = 0;
   o->factor_cache = 0;
+  o->autotune = 0;
   return ST_MG_OK;
 }
 
@@ -1851,6 +1902,13 @@ int st_mg_cache_trim(int64_t max_bytes, int64_t* bytes_after) {
 int st_mg_launch_count(int64_t* count) {
   if (!count) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *count = launch_count();
+  return ST_MG_OK;
+}
+
+int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves) {
+  if (int rc = check_level(h, level)) return rc;
+  if (!waves) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  *waves = h->lv[level].split_waves;
   return ST_MG_OK;
 }
 

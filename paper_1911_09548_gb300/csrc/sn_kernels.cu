@@ -664,9 +664,10 @@ cudaError_t sn_solve_skinny(const DevFactor<typename P::S, typename P::WT>& F, t
 // the split-K kernels instead, with NBK right-hand sides per column block.
 template <typename P, int BN, int NBK>
 cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
-                           typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+                           typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy,
+                           cudaStream_t st) {
   const unsigned gy = (unsigned)((nrhs + BN - 1) / BN);
-  const int64_t two_waves = 2 * (int64_t)F.n_sm;
+  const int64_t two_waves = (int64_t)sy.split_waves * F.n_sm;
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
     if (b <= a) continue;
@@ -700,7 +701,7 @@ cudaError_t solve_real(const DevFactor<typename P::S, typename P::WT>& F, typena
   if (Pt && nrhs <= 4) return sn_solve_skinny<P, 4>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= 16) return sn_solve_skinny<P, 16>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= kSkMaxRhsR) return sn_solve_skinny<P, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
-  return sn_solve_tiled<P, 64, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, st);
+  return sn_solve_tiled<P, 64, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
 }
 // Complex matrices: column blocks of 2 / 8 / 16, 32-wide tiles.
 template <typename P>
@@ -710,7 +711,7 @@ cudaError_t solve_cplx(const DevFactor<typename P::S, typename P::WT>& F, typena
   if (Pt && nrhs <= 2) return sn_solve_skinny<P, 2>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= 8) return sn_solve_skinny<P, 8>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= kSkMaxRhsC) return sn_solve_skinny<P, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
-  return sn_solve_tiled<P, 32, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, st);
+  return sn_solve_tiled<P, 32, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
 }
 
 }  // namespace
@@ -739,7 +740,7 @@ cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float
   if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, sy, st);
   if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolBF16C, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, sy, st);
   const int64_t gy = (nrhs + kTcCols - 1) / kTcCols;
-  const int64_t two_waves = 2 * (int64_t)F.n_sm;
+  const int64_t two_waves = (int64_t)sy.split_waves * F.n_sm;
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t tiles = F.h_fwd_off[d + 1] - F.h_fwd_off[d];
     if (tiles <= 0) continue;

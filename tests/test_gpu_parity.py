@@ -40,6 +40,8 @@ CASES = {
     "dg0_two_grid_SA": (4, 1, 0, 16, "unit", dict(max_levels=2, smoother="SA")),
     # Neumann boundary (all edges, grounded vertex 0), space coarsening on the first transition
     "dg1_neumann_full": (8, 2, 1, 16, "two_material", dict(bc=1, coarsen=2)),
+    # tiled / split-K thresholds chosen per level by timing at setup
+    "dg1_long_autotune": (8, 1, 1, 128, "two_material", dict(nu_pre=2, nu_post=2, autotune=1)),
 }
 
 
@@ -274,3 +276,9 @@ def test_persistent_split_matches_per_depth_launches(slab_prec, lib_built):
         xs.append(host(x))
         S.close()
     assert np.array_equal(xs[0], xs[1])
+
+
+def test_autotune_choices_valid(lib_built):
+    S, sl, tl, mg, p = setup_case("dg1_long_autotune", lib_built)
+    ws = [lib_built.st_mg_split_waves(S.h, l) for l in range(S.n_levels)]
+    assert all(w in (0, 1, 2, 4, 8) for w in ws)
