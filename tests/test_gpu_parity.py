@@ -40,6 +40,11 @@ CASES = {
     "dg0_two_grid_SA": (4, 1, 0, 16, "unit", dict(max_levels=2, smoother="SA")),
     # Neumann boundary (all edges, grounded vertex 0), space coarsening on the first transition
     "dg1_neumann_full": (8, 2, 1, 16, "two_material", dict(bc=1, coarsen=2)),
+    # degenerate hierarchies: one slab (the V-cycle is the exact coarse solve), the smallest
+    # Kuhn mesh (2^3 cubes), a prime number of slabs (no time coarsening at all)
+    "dg1_single_slab": (4, 1, 1, 1, "two_material", dict()),
+    "dg0_n2": (2, 1, 0, 8, "unit", dict()),
+    "dg1_prime": (4, 1, 1, 7, "two_material", dict()),
     # tiled / split-K thresholds chosen per level by timing at setup
     "dg1_long_autotune": (8, 1, 1, 128, "two_material", dict(nu_pre=2, nu_post=2, autotune=1)),
 }
