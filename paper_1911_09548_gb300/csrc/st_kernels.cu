@@ -340,45 +340,55 @@ __global__ void k_norm_partial(const double* __restrict__ v, int64_t n, double* 
   block_sum_store<256>(s, partial + blockIdx.x);
 }
 
-__global__ void k_slab_pre_dg0(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+constexpr int SLAB_ROWS = 4;   // rows (one per warp) per block of the permutation / transform kernels
+
+__global__ void k_slab_pre_dg0(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                const int32_t* __restrict__ iperm, double* __restrict__ Q, int ld) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double* src = r + (int64_t)e * src_ld;
   double* dst = Q + (int64_t)iperm[e] * ld;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = src[slab0 + k];
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) dst[k] = src[slab0 + k];
 }
 
-__global__ void k_slab_pre_dg1(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+__global__ void k_slab_pre_dg1(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                const int32_t* __restrict__ iperm, double2 c0, double2 c1,
                                double2* __restrict__ Q, int ld) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
   double2* dst = Q + (int64_t)iperm[e] * ld;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double2 v = src[slab0 + k];
     dst[k] = make_double2(c0.x * v.x + c1.x * v.y, c0.y * v.x + c1.y * v.y);
   }
 }
 
-__global__ void k_slab_post_dg0(const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+__global__ void k_slab_post_dg0(int nrows, const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                 double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double* src = X + (int64_t)iperm[e] * ld;
   double* dst = x + (int64_t)e * dst_ld + slab0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double v = src[k];
     if (mode == 0) dst[k] = v;
     else dst[k] = fma(omega, v, dst[k]);
   }
 }
 
-__global__ void k_slab_post_dg1(const double2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+__global__ void k_slab_post_dg1(int nrows, const double2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                 double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
                                 double omega, int mode) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double2* src = X + (int64_t)iperm[e] * ld;
   double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * dst_ld) + slab0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double2 v = src[k];
     const double u0 = 2.0 * v.x;
     const double u1 = 2.0 * (s1.x * v.x - s1.y * v.y);
@@ -393,45 +403,53 @@ __global__ void k_slab_post_dg1(const double2* __restrict__ X, int ld, const int
   }
 }
 
-__global__ void k_slab_pre_dg0f(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+__global__ void k_slab_pre_dg0f(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                 const int32_t* __restrict__ iperm, float* __restrict__ Q, int ld) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double* src = r + (int64_t)e * src_ld;
   float* dst = Q + (int64_t)iperm[e] * ld;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = (float)src[slab0 + k];
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) dst[k] = (float)src[slab0 + k];
 }
 
-__global__ void k_slab_pre_dg1f(const double* __restrict__ r, int src_ld, int slab0, int cnt,
+__global__ void k_slab_pre_dg1f(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                 const int32_t* __restrict__ iperm, double2 c0, double2 c1,
                                 float2* __restrict__ Q, int ld) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
   float2* dst = Q + (int64_t)iperm[e] * ld;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double2 v = src[slab0 + k];
     dst[k] = make_float2((float)(c0.x * v.x + c1.x * v.y), (float)(c0.y * v.x + c1.y * v.y));
   }
 }
 
-__global__ void k_slab_post_dg0f(const float* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+__global__ void k_slab_post_dg0f(int nrows, const float* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                  double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const float* src = X + (int64_t)iperm[e] * ld;
   double* dst = x + (int64_t)e * dst_ld + slab0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double v = (double)src[k];
     if (mode == 0) dst[k] = v;
     else dst[k] = fma(omega, v, dst[k]);
   }
 }
 
-__global__ void k_slab_post_dg1f(const float2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+__global__ void k_slab_post_dg1f(int nrows, const float2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                  double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
                                  double omega, int mode) {
-  const int e = blockIdx.x;
+  const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (e >= nrows) return;
   const float2* src = X + (int64_t)iperm[e] * ld;
   double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * dst_ld) + slab0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+#pragma unroll 4
+  for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const float2 vf = src[k];
     const double vx = vf.x, vy = vf.y;
     const double u0 = 2.0 * vx;
@@ -448,21 +466,25 @@ __global__ void k_slab_post_dg1f(const float2* __restrict__ X, int ld, const int
 }
 
 template <typename TQ>
-__global__ void k_gather_perm(const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
+__global__ void k_gather_perm(int nrows, const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
                               TQ* __restrict__ Q, int ld) {
-  const int v = blockIdx.x;
+  const int v = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (v >= nrows) return;
   const double* src = y + (int64_t)v * ncols;
   TQ* dst = Q + (int64_t)iperm[v] * ld;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = (TQ)src[j];
+#pragma unroll 4
+  for (int j = threadIdx.x & 31; j < ncols; j += 32) dst[j] = (TQ)src[j];
 }
 
 template <typename TQ>
-__global__ void k_scatter_perm(const TQ* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
+__global__ void k_scatter_perm(int nrows, const TQ* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                double* __restrict__ z, int ncols) {
-  const int v = blockIdx.x;
+  const int v = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
+  if (v >= nrows) return;
   const TQ* src = X + (int64_t)iperm[v] * ld;
   double* dst = z + (int64_t)v * ncols;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) dst[j] = (double)src[j];
+#pragma unroll 4
+  for (int j = threadIdx.x & 31; j < ncols; j += 32) dst[j] = (double)src[j];
 }
 
 // y = G^T r: warp per node, lanes over the time columns.
@@ -854,62 +876,62 @@ cudaError_t norm2_sq(const double* v, int64_t n, double* partial, double* out, c
 
 cudaError_t slab_pre_dg0(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg0<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_slab_pre_dg0<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg1(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double2 c0, double2 c1, double2* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg1<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_slab_pre_dg1<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
                           int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg0<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { k_slab_post_dg0<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg1<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { k_slab_post_dg1<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg0f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                           float* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg0f<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_slab_pre_dg0f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg1f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                           double2 c0, double2 c1, float2* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg1f<<<nrows, 128, 0, st>>>(r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_slab_pre_dg1f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg0f(const float* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
                            int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg0f<<<nrows, 128, 0, st>>>(X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { k_slab_post_dg0f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg1f(const float2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                            int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg1f<<<nrows, 128, 0, st>>>(X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { k_slab_post_dg1f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
                         cudaStream_t st) {
-  if (nrows > 0) { k_gather_perm<double><<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_gather_perm<double><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                          cudaStream_t st) {
-  if (nrows > 0) { k_scatter_perm<double><<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
+  if (nrows > 0) { k_scatter_perm<double><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm_f(const double* y, int ncols, const int32_t* iperm, int nrows, float* Q, int ld,
                           cudaStream_t st) {
-  if (nrows > 0) { k_gather_perm<float><<<nrows, 128, 0, st>>>(y, ncols, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { k_gather_perm<float><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm_f(const float* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                            cudaStream_t st) {
-  if (nrows > 0) { k_scatter_perm<float><<<nrows, 128, 0, st>>>(X, ld, iperm, z, ncols); count_launches(1); }
+  if (nrows > 0) { k_scatter_perm<float><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {
