@@ -4,7 +4,8 @@ The case has enough slabs (N_t = 1024, 8 column blocks of 128) that the deep
 tree depths run the tcgen05 kernels and the top ones the split-K kernels.  The
 BF16 factor is a preconditioner-quality inverse: its error is BF16-sized (checked
 against the oracle's exact slab solve), and the V-cycle still converges to the
-FP64 solution because residual, nodal correction and coarsest solve stay FP64."""
+FP64 solution because the residual is FP64-accurate and the coarsest solve FP64
+(the nodal correction runs in FP32)."""
 import numpy as np
 import pytest
 

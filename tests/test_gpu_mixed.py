@@ -1,6 +1,7 @@
 """Mixed-precision slab solve (slab_prec = 1): the FP64 factor is rounded to FP32 and
-applied in FP32; residual, nodal correction and coarsest solve stay FP64, so the
-V-cycle iteration refines to the FP64 solution.  Checked against the oracle: the
+applied in FP32; the residual is FP64-accurate (double-float) and the coarsest
+solve FP64, so the V-cycle iteration refines to the FP64 solution (the nodal
+correction, an inner part of the preconditioner, runs in FP32).  Checked against the oracle: the
 FP32 slab apply to FP32 accuracy, and the final solution to 1e-8 relative."""
 import numpy as np
 import pytest
