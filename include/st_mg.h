@@ -95,7 +95,7 @@ typedef struct {
                                 FP32 and applied in FP32 on every level but the coarsest (residual
                                 FP64-accurate, factorisation and coarsest solve FP64, nodal K_n solve
                                 FP32; the V-cycle acts as iterative refinement, Section 2.1's
-                                "sufficiently well approximated");
+                                premise that the slab inverse need only be approximated well);
                                 2 double-float: the factor as FP32 (hi, lo) pairs applied with
                                 error-free FP32 products and sums (about 48 significant bits), on the
                                 FP32 pipes, which on GB300 run 58x the FP64 rate;

@@ -1,6 +1,6 @@
 """Convergence rates of the GPU path by the power iteration of Section 5.1, against the
 oracle's rates on the same operators and against what the paper reports:
-  * with spatial coarsening the plain S smoother is "completely ineffective" (rate ~ 1,
+  * with spatial coarsening the plain S smoother does not converge (rate ~ 1,
     Section 3.1) while the hybrid SAS converges (Section 4.1);
   * for large lambda the two-grid SAS rate is 2^-4 (Section 5.1);
   * two materials: raising nu on one subdomain (larger local lambda) does not slow
