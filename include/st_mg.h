@@ -265,6 +265,14 @@ int st_mg_vcycle_residual_async(st_mg_t h, const double* f_dev, double* x_dev, d
  * (blocking).  Lets a caller stop or replace problems of a batch independently. */
 int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host);
 
+/* The same per-problem sums of squares ||v_b||^2, queued on the handle's stream into
+ * norms_sq_dev (device, n_batch doubles) with no host wait. */
+int st_mg_batch_norms_async(st_mg_t h, const double* v_dev, double* norms_sq_dev);
+
+/* Blocking: ST_MG_ERR_TIMEOUT if a bounded device wait of earlier work on the handle's
+ * stream gave up (the flag is then cleared), else ST_MG_OK. */
+int st_mg_check(st_mg_t h);
+
 /* Zero problem `batch`'s entries of a finest-level vector (e.g. to start a new problem
  * in a freed slot of a batch while the other problems keep iterating). */
 int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev);

@@ -17,17 +17,20 @@
  * the process-wide factor cache keyed by (mesh, space level, degree, tau / s 2^l,
  * precision), so classes that differ only in N_t share their factors.
  *
- * Continuous batching.  st_mg_server_step (1) finishes class builds whose host
- * phase (st_mg_setup_begin, run on a worker thread) is done, (2) admits queued
- * requests into free slots of their class -- load assembled into the slot, iterate
- * zeroed -- creating a class when the device-memory budget allows (evicting idle
- * classes and unused cached factors first), (3) queues one V-cycle plus residual on
- * every class with an occupied slot, each class on its own CUDA stream so their work
- * overlaps on the device, then (4) reads each class's per-slot residual norms and
- * retires slots that reached rtol (or max_cycles): the solution is copied to the
- * host, the slot zeroed and freed for the next request.  A problem's iterates do not
- * depend on the other slots of its batch (the batched operators act on each
- * problem's columns separately), so a result is the same alone and in the mix.
+ * Continuous batching.  Every class runs its own pipeline of V-cycles on its own
+ * CUDA stream; st_mg_server_step, without waiting for classes still on the device,
+ * (1) finishes class builds whose host phase (st_mg_setup_begin, run on a worker
+ * thread) is done, (2) collects the classes whose V-cycle has finished (per-slot
+ * residual norms, copied to pinned memory behind the cycle) and retires slots that
+ * reached rtol or max_cycles -- the solution is copied to the host, the slot zeroed
+ * and freed, (3) admits queued requests into free slots of idle classes -- load
+ * assembled into the slot, iterate zeroed -- creating a class when the device-memory
+ * budget allows (evicting idle classes and unused cached factors first), and (4)
+ * queues the next V-cycle, residual and norms of every idle class with occupied
+ * slots.  Small classes thus advance at their own pace beside large ones.  A
+ * problem's iterates do not depend on the other slots of its batch (the batched
+ * operators act on each problem's columns separately), so a result is the same alone
+ * and in the mix.
  *
  * The server is driven by one host thread (it is not thread safe); it uses the
  * device that was current at st_mg_server_create.
@@ -110,8 +113,9 @@ int st_mg_server_set_materials(st_mg_server_t srv, int32_t n_cube, int32_t n_spa
 int st_mg_server_submit(st_mg_server_t srv, const st_mg_request* req, int64_t* id);
 
 /* One scheduling round (see above).  The ids of requests finished in it go to
- * done_ids[0 .. min(*n_done, cap)); *n_done = how many finished.  Blocks until the
- * round's V-cycles are done. */
+ * done_ids[0 .. min(*n_done, cap)); *n_done = how many finished.  When no class has
+ * finished and none could start, it polls for a few milliseconds before returning, so
+ * a caller may loop on it. */
 int st_mg_server_step(st_mg_server_t srv, int64_t* done_ids, int32_t cap, int32_t* n_done);
 
 /* State of a request.  When it is done, x_host (may be NULL) receives min(x_cap,

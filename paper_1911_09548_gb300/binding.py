@@ -91,6 +91,8 @@ _SIGS = {
     "st_mg_probe_fp64": [_vp, _P(_dbl)],
     "st_mg_batch_norms": [_vp, _vp, _P(_dbl)],
     "st_mg_vcycle_residual_async": [_vp, _vp, _vp, _vp],
+    "st_mg_batch_norms_async": [_vp, _vp, _vp],
+    "st_mg_check": [_vp],
     "st_mg_memory": [_vp, _P(_i64), _P(_i64)],
     "st_mg_split_waves": [_vp, _i32, _P(_i32)],
     "st_mg_cache_stats": [_P(_i64), _P(_i32), _P(_i32), _P(_i64), _P(_i64)],

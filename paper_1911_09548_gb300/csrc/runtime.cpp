@@ -86,15 +86,6 @@ struct DevArena {
     if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     return d;
   }
-  // free one temporary allocation of count elements of T early
-  template <typename T>
-  void release(T* p, int64_t count) {
-    auto it = std::find(allocs.begin(), allocs.end(), static_cast<void*>(p));
-    if (it == allocs.end()) return;
-    allocs.erase(it);
-    bytes -= std::max<int64_t>(count, 1) * (int64_t)sizeof(T);
-    cudaFree(p);
-  }
 };
 
 // Device factor of one time level's slab matrix (every slab of a level shares it,
@@ -262,6 +253,8 @@ struct st_mg_s {
   SkSync sk;                            // persistent split-K solve: barrier words + error flag
   float2* tcP = nullptr;                // tensor-core split-K partials
   uint8_t* tcB = nullptr;               // tensor-core right-hand-side tiles of one depth
+  double* load_b = nullptr;             // load assembly staging: space part [n_edge], time part [N_t q]
+  double* load_c = nullptr;
   double* bn_partial = nullptr;         // per-problem norm scratch
   double* bn_out = nullptr;
   // captured V-cycle (replayed while f and x stay the same buffers)
@@ -1300,6 +1293,8 @@ int setup_device(Handle& H) {
       if (L.prec == 3) ms = std::max<int64_t>(ms, L.fac->max_stage_tiles);
     H.tcB = H.dalloc<uint8_t>(ms * gy * kTcTileBytes);
   }
+  H.load_b = H.dalloc<double>(H.space[0].ne);
+  H.load_c = H.dalloc<double>((int64_t)H.lv[0].N_t * H.q);
   H.bn_partial = H.dalloc<double>(batch_norm_scratch(H.B));
   H.bn_out = H.dalloc<double>(H.B);
   H.partial = H.dalloc<double>(std::max(std::max(1024, 8 * H.n_sm), residual_blocks((int)max_ne)));
@@ -1546,15 +1541,15 @@ int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const d
         c[(size_t)n * H.q] += L.tau * gw[p] * g;
         if (H.q == 2) c[(size_t)n * 2 + 1] += L.tau * gw[p] * g * (2.0 * gx[p] - 1.0);
       }
-    double* db = H.dalloc<double>((int64_t)b.size());
-    double* dc = H.dalloc<double>((int64_t)c.size());
+    // staging buffers of the handle (no allocation here: a cudaFree would wait for
+    // every stream of the device)
+    double* db = H.load_b;
+    double* dc = H.load_c;
     CK(cudaMemcpyAsync(db, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
     CK(cudaMemcpyAsync(dc, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
     const int seg = L.N_t * H.q;
     CK(outer_load(db, dc, f_dev + (int64_t)batch * seg, H.space[0].ne, seg, seg * H.B, H.stream));
     CK(cudaStreamSynchronize(H.stream));
-    H.mem.release(db, (int64_t)b.size());
-    H.mem.release(dc, (int64_t)c.size());
     return ST_MG_OK;
   });
 }
@@ -1828,6 +1823,22 @@ int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host) {
     for (int b = 0; b < H.B; ++b) norms_host[b] = std::sqrt(sq[b]);
     return ST_MG_OK;
   });
+}
+
+int st_mg_batch_norms_async(st_mg_t h, const double* v_dev, double* norms_sq_dev) {
+  if (int rc = check_dev(h)) return rc;
+  if (int rc = check_ptrs({v_dev})) return rc;
+  if (!norms_sq_dev) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    Handle& H = *h;
+    CK(batch_norms_sq(v_dev, H.space[0].ne, H.B, H.lv[0].N_t * H.q, H.bn_partial, norms_sq_dev, H.stream));
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_check(st_mg_t h) {
+  if (int rc = check_dev(h)) return rc;
+  return guarded([&]() { return check_tc(*h); });
 }
 
 int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev) {

@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -74,7 +75,10 @@ struct Class {
   int64_t est_bytes = 0, bytes = 0;
   int64_t last_use = 0;
   std::vector<int64_t> slot;              // request id per slot, -1 free
-  bool launched = false;
+  bool in_flight = false;                 // a V-cycle + residual norms queued, not yet collected
+  cudaEvent_t ev = nullptr;               // recorded after the norms' copy to the host
+  double* norms_dev = nullptr;            // per-slot squared residual norms (device)
+  double* norms_host = nullptr;           // the same, pinned host copy
   int occupied() const {
     int c = 0;
     for (int64_t v : slot) c += v >= 0;
@@ -135,9 +139,13 @@ void free_class(Class& c) {
   }
   if (c.h) st_mg_destroy(c.h);
   c.h = nullptr;
-  for (double* p : {c.f, c.x, c.r})
+  for (double* p : {c.f, c.x, c.r, c.norms_dev})
     if (p) cudaFree(p);
-  c.f = c.x = c.r = nullptr;
+  c.f = c.x = c.r = c.norms_dev = nullptr;
+  if (c.norms_host) cudaFreeHost(c.norms_host);
+  c.norms_host = nullptr;
+  if (c.ev) cudaEventDestroy(c.ev);
+  c.ev = nullptr;
   if (c.stream) cudaStreamDestroy(c.stream);
   c.stream = nullptr;
 }
@@ -236,6 +244,12 @@ int finish_class(Server& S, Class& c) {
     }
     if (cudaMemsetAsync(*p, 0, (size_t)c.len * sizeof(double), c.stream) != cudaSuccess) return ST_MG_ERR_CUDA;
   }
+  if (cudaMalloc(&c.norms_dev, c.slot.size() * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&c.norms_host, c.slot.size() * sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming) != cudaSuccess) {
+    c.build_err = "per-class norm buffers";
+    return ST_MG_ERR_OOM;
+  }
   int64_t own = 0, fac = 0;
   st_mg_memory(c.h, &own, &fac);
   c.bytes = own + 3 * c.len * (int64_t)sizeof(double);
@@ -284,7 +298,49 @@ int step(Server& S, std::vector<int64_t>& done) {
   }
   if (class_usage(S) + cache_bytes() > S.opt.mem_budget) make_room(S, 0);
 
-  // (2) admission, first come first served within each class
+  // (2) collect the classes whose V-cycle has finished: per-slot residual norms,
+  // retire slots that reached rtol or max_cycles
+  bool progressed = false;
+  for (auto& kv : S.cls) {
+    Class& c = *kv.second;
+    if (!c.in_flight) continue;
+    const cudaError_t q = cudaEventQuery(c.ev);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return fail(ST_MG_ERR_CUDA, cudaGetErrorString(q));
+    c.in_flight = false;
+    progressed = true;
+    if (int rc = st_mg_check(c.h)) return rc;
+    ++S.st.vcycles;
+    for (size_t b = 0; b < c.slot.size(); ++b) {
+      if (c.slot[b] < 0) continue;
+      Request& q2 = S.req[c.slot[b]];
+      ++q2.cycles;
+      ++S.st.slot_cycles;
+      S.st.dofs_smoothed += c.ne * c.seg;
+      q2.rel = std::sqrt(c.norms_host[b]) / q2.fnorm;
+      int status = -1;
+      if (!std::isfinite(q2.rel)) status = ST_MG_ERR_DIVERGED;
+      else if (q2.rel <= q2.rtol) status = ST_MG_OK;
+      else if (q2.cycles >= S.opt.max_cycles) status = ST_MG_ERR_NOT_CONVERGED;
+      if (status < 0) continue;
+      if (S.opt.keep_x) {
+        q2.x.resize((size_t)q2.n_values);
+        const size_t w = (size_t)c.seg * sizeof(double);
+        if (cudaMemcpy2DAsync(q2.x.data(), w, c.x + (int64_t)b * c.seg, w * c.slot.size(), w, (size_t)c.ne,
+                              cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+            cudaStreamSynchronize(c.stream) != cudaSuccess)
+          return fail(ST_MG_ERR_CUDA, "copy of a solution to the host");
+      }
+      if (int rc = st_mg_batch_zero(c.h, (int)b, c.f)) return rc;
+      if (int rc = st_mg_batch_zero(c.h, (int)b, c.x)) return rc;
+      c.slot[b] = -1;
+      finish_request(S, q2, status, done);
+    }
+    c.last_use = ++S.tick;
+  }
+
+  // (3) admission into free slots of idle classes, first come first served within a
+  // class; new classes when the memory budget allows
   std::vector<Class*> admitted;
   for (auto it = S.queue.begin(); it != S.queue.end();) {
     Request& q = S.req[*it];
@@ -311,7 +367,7 @@ int step(Server& S, std::vector<int64_t>& done) {
       ++it;
       continue;
     }
-    if (!c->ready) {
+    if (!c->ready || c->in_flight) {   // a class's vectors change only between its V-cycles
       ++it;
       continue;
     }
@@ -335,7 +391,7 @@ int step(Server& S, std::vector<int64_t>& done) {
     if (std::find(admitted.begin(), admitted.end(), c) == admitted.end()) admitted.push_back(c);
     it = S.queue.erase(it);
   }
-  // ||f_b|| of the newly admitted problems
+  // ||f_b|| of the newly admitted problems (their classes are idle)
   std::vector<double> norms;
   for (Class* c : admitted) {
     norms.assign(c->slot.size(), 0.0);
@@ -354,48 +410,35 @@ int step(Server& S, std::vector<int64_t>& done) {
     }
   }
 
-  // (3) one V-cycle + residual on every class with occupied slots, each on its stream
+  // (4) every idle class with occupied slots starts its next V-cycle at once: V-cycle,
+  // finest residual, per-slot norms, their copy to the host and an event, all queued
+  // on the class's stream -- classes advance independently of one another
   for (auto& kv : S.cls) {
     Class& c = *kv.second;
-    c.launched = false;
-    if (!c.ready || c.occupied() == 0) continue;
+    if (!c.ready || c.in_flight || c.occupied() == 0) continue;
     if (int rc = st_mg_vcycle_residual_async(c.h, c.f, c.x, c.r)) return rc;
-    c.launched = true;
+    if (int rc = st_mg_batch_norms_async(c.h, c.r, c.norms_dev)) return rc;
+    if (cudaMemcpyAsync(c.norms_host, c.norms_dev, c.slot.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        c.stream) != cudaSuccess ||
+        cudaEventRecord(c.ev, c.stream) != cudaSuccess)
+      return fail(ST_MG_ERR_CUDA, "queueing a class V-cycle");
+    c.in_flight = true;
+    progressed = true;
   }
 
-  // (4) per-slot residual norms; retire converged slots
-  for (auto& kv : S.cls) {
-    Class& c = *kv.second;
-    if (!c.launched) continue;
-    norms.assign(c.slot.size(), 0.0);
-    if (int rc = st_mg_batch_norms(c.h, c.r, norms.data())) return rc;
-    ++S.st.vcycles;
-    for (size_t b = 0; b < c.slot.size(); ++b) {
-      if (c.slot[b] < 0) continue;
-      Request& q = S.req[c.slot[b]];
-      ++q.cycles;
-      ++S.st.slot_cycles;
-      S.st.dofs_smoothed += c.ne * c.seg;
-      q.rel = norms[b] / q.fnorm;
-      int status = -1;
-      if (!std::isfinite(q.rel)) status = ST_MG_ERR_DIVERGED;
-      else if (q.rel <= q.rtol) status = ST_MG_OK;
-      else if (q.cycles >= S.opt.max_cycles) status = ST_MG_ERR_NOT_CONVERGED;
-      if (status < 0) continue;
-      if (S.opt.keep_x) {
-        q.x.resize((size_t)q.n_values);
-        const size_t w = (size_t)c.seg * sizeof(double);
-        if (cudaMemcpy2DAsync(q.x.data(), w, c.x + (int64_t)b * c.seg, w * c.slot.size(), w, (size_t)c.ne,
-                              cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
-            cudaStreamSynchronize(c.stream) != cudaSuccess)
-          return fail(ST_MG_ERR_CUDA, "copy of a solution to the host");
-      }
-      if (int rc = st_mg_batch_zero(c.h, (int)b, c.f)) return rc;
-      if (int rc = st_mg_batch_zero(c.h, (int)b, c.x)) return rc;
-      c.slot[b] = -1;
-      finish_request(S, q, status, done);
+  // (5) nothing finished and nothing started: wait (briefly, polling) for the first
+  // class to finish, so that a caller looping on step does not spin
+  if (!progressed) {
+    for (int it = 0; it < 200; ++it) {
+      bool any = false, ready = false;
+      for (auto& kv : S.cls)
+        if (kv.second->in_flight) {
+          any = true;
+          if (cudaEventQuery(kv.second->ev) != cudaErrorNotReady) ready = true;
+        }
+      if (!any || ready) break;
+      std::this_thread::sleep_for(std::chrono::microseconds(25));
     }
-    c.last_use = ++S.tick;
   }
   return ST_MG_OK;
 }
