@@ -173,6 +173,51 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ precision (config 3)
+def run_precision(args):
+    """The mixed-precision workload: Kuhn 16^3, two materials, T = 1, N_t = 1024, DG(1),
+    V(2,2), solved to a 1e-8 relative residual with the slab factor in FP64, FP32 and BF16
+    (tensor cores); V-cycle counts, times, and the relative error of each final solution
+    against the FP64 one."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    import st_inputs
+
+    n, N_t = 16, 1024
+    nu, sigma = st_inputs.materials(n, "two_material", 0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rows, ref = {}, None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16_tensor", 3)):
+        S = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, 1, nu_pre=2, nu_post=2, stream=stream.cuda_stream,
+                                 slab_prec=prec, autotune=args.autotune)
+        f = S.load(st_inputs.excitation(0))
+        x = S.zeros()
+        S.solve(f, x, rtol=1e-8, maxit=60)          # warm-up (graph capture), discarded
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = S.solve(f, x, rtol=1e-8, maxit=60)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ref is None:
+            ref = x.clone()
+        err = float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+        rows[name] = {"time_to_1e-8_s": dt, "v_cycles": out["iters"], "rel_res": out["rel_res"],
+                      "ms_per_v_cycle": 1e3 * dt / max(out["iters"], 1), "rel_err_vs_fp64_solution": err}
+        S.close()
+    print(json.dumps({"mode": "precision", "metric": "time to 1e-8 relative residual, mixed vs FP64",
+                      "config": {"mesh": "Kuhn 16^3, 26416 interior edges", "N_t": N_t, "degree": 1,
+                                 "dofs": 26416 * N_t * 2, "cycle": "V(2,2)", "materials": "two_material",
+                                 "autotune": bool(args.autotune)},
+                      "results": rows}))
+    return 0
+
+
 # ------------------------------------------------------------------ convergence rates
 def run_rates(args):
     """Two-grid convergence rates by the power iteration of Section 5.1 on the GPU:
@@ -343,11 +388,14 @@ def main():
     ap.add_argument("--mixed", type=int, default=1, help="also measure the mixed-precision slab solve")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="tiled / split-K thresholds chosen per level by timing at setup")
+    ap.add_argument("--split-waves", default="",
+                    help="comma-separated tiled / split-K threshold per time level, set after setup "
+                         "(repeats an autotuned run's choice, e.g. under a profiler)")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
                     help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
-    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates", "precision"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers); "
                          "serve: the request-loop benchmark (Poisson streams, p50/p99 latency)")
     ap.add_argument("--serve-rates", default="0.5,2,10", help="offered request rates (req/s), one stream each")
@@ -366,6 +414,8 @@ def main():
         return run_serve(args)
     if args.mode == "rates":
         return run_rates(args)
+    if args.mode == "precision":
+        return run_precision(args)
 
     import multiprocessing as mp
 
@@ -404,6 +454,9 @@ def main():
     S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
                              nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec,
                              autotune=args.autotune)
+    if args.split_waves:
+        for l, w in enumerate(int(v) for v in args.split_waves.split(",")):
+            stmg.st_mg_set_split_waves(S.h, l, w)
     split_waves = [stmg.st_mg_split_waves(S.h, l) for l in range(S.n_levels)]
     setup_s = time.time() - t0
     n_levels, n_dof = S.n_levels, S.n_dof
@@ -437,11 +490,13 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_vcycles")   # lets a profiler select these launches
     ev0.record(stream)
     for _ in range(args.steps):
         S.vcycle(f, x)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     launches = stmg.st_mg_launch_count() - launches0
@@ -613,7 +668,8 @@ def main():
             "config": {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
                        "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": n_levels,
                        "dofs": n_dof, "parallelism": f"replicas x{world}",
-                       "split_waves_per_level": split_waves, "autotune": bool(args.autotune),
+                       "split_waves_per_level": split_waves,
+                       "autotune": "given" if args.split_waves else bool(args.autotune),
                        "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),

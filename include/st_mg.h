@@ -296,6 +296,11 @@ int st_mg_cache_trim(int64_t max_bytes, int64_t* bytes_after);
  * st_mg_options.autotune chose another). */
 int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves);
 
+/* Set that threshold (waves in [0, 64]; 0 = tiled at every depth that has any tile),
+ * e.g. to repeat the choice an earlier autotuned run made.  Drops the captured V-cycle
+ * graph, which the next V-cycle re-captures.  ST_MG_ERR_INVALID_ARG outside the range. */
+int st_mg_set_split_waves(st_mg_t h, int32_t level, int32_t waves);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);
 

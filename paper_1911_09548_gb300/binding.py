@@ -95,6 +95,7 @@ _SIGS = {
     "st_mg_check": [_vp],
     "st_mg_memory": [_vp, _P(_i64), _P(_i64)],
     "st_mg_split_waves": [_vp, _i32, _P(_i32)],
+    "st_mg_set_split_waves": [_vp, _i32, _i32],
     "st_mg_cache_stats": [_P(_i64), _P(_i32), _P(_i32), _P(_i64), _P(_i64)],
     "st_mg_cache_trim": [_i64, _P(_i64)],
     "st_mg_batch_zero": [_vp, _i32, _vp],
@@ -325,6 +326,10 @@ def st_mg_split_waves(h, level):
     w = _i32(0)
     _check(lib().st_mg_split_waves(_vp(h), level, ctypes.byref(w)), "st_mg_split_waves")
     return w.value
+
+
+def st_mg_set_split_waves(h, level, waves):
+    _check(lib().st_mg_set_split_waves(_vp(h), level, waves), "st_mg_set_split_waves")
 
 
 def st_mg_memory(h):

@@ -1923,6 +1923,17 @@ int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves) {
   return ST_MG_OK;
 }
 
+int st_mg_set_split_waves(st_mg_t h, int32_t level, int32_t waves) {
+  if (int rc = check_level(h, level)) return rc;
+  if (waves < 0 || waves > 64) return fail(ST_MG_ERR_INVALID_ARG, "split waves outside [0, 64]");
+  h->lv[level].split_waves = waves;
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  return ST_MG_OK;
+}
+
 int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* factor_bytes, int32_t* depth) {
   if (int rc = check_level(h, level)) return rc;
   const auto& L = h->lv[level];

@@ -287,3 +287,29 @@ def test_autotune_choices_valid(lib_built):
     S, sl, tl, mg, p = setup_case("dg1_long_autotune", lib_built)
     ws = [lib_built.st_mg_split_waves(S.h, l) for l in range(S.n_levels)]
     assert all(w in (0, 1, 2, 4, 8) for w in ws)
+
+
+def test_split_waves_set_between_graph_replays(lib_built):
+    """Thresholds set after the V-cycle graph was captured (all tiled, then all split-K)
+    take effect on the next V-cycle: each iterate still matches the oracle."""
+    n, nsl, p, N_t, mat, opts = CASES["dg1_long_autotune"]
+    _, sl, tl, mg, _ = setup_case("dg1_long_autotune", lib_built)
+    nu, sigma = st_inputs.materials(n, mat, 1)
+    stream = torch.cuda.Stream()
+    S = lib_built.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, nu_pre=2, nu_post=2, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        f = S.load(st_inputs.excitation(6))
+        x = S.zeros()
+    for bad in (-1, 65):
+        with pytest.raises(lib_built.StMgError) as e:
+            lib_built.st_mg_set_split_waves(S.h, 0, bad)
+        assert e.value.status == 1
+    fo = from_lib(host(f), p + 1)
+    xo = np.zeros_like(fo)
+    for waves in (2, 0, 64):
+        for l in range(S.n_levels):
+            lib_built.st_mg_set_split_waves(S.h, l, waves)
+        S.vcycle(f, x)
+        xo = mg.vcycle(fo, xo)
+        assert rel(from_lib(host(x), p + 1), xo) < 1e-11, waves
+    S.close()

@@ -129,3 +129,17 @@ def test_smoother_pattern_validated(B):
     opt = B.st_mg_default_options()
     opt.smoother = b"SSA"
     B.st_mg_destroy(B.st_mg_setup_host(prob, opt))
+
+
+
+def test_split_waves_setter_needs_device_state(B):
+    """The tiled / split-K threshold is device state: host-only handles reject both calls."""
+    nu, sigma = st_inputs.materials(4, "unit")
+    h = B.st_mg_setup_host(B.make_problem(4, 1, nu, sigma, 1.0, 8, 1), B.st_mg_default_options())
+    try:
+        for call in (lambda: B.st_mg_split_waves(h, 0), lambda: B.st_mg_set_split_waves(h, 0, 8)):
+            with pytest.raises(B.StMgError) as e:
+                call()
+            assert e.value.status == 1
+    finally:
+        B.st_mg_destroy(h)
