@@ -7,8 +7,9 @@ CPU-baseline leg may import it; the product path never does.
 The paper discretises the eddy-current problem on a tetrahedral mesh with
 lowest-order Nedelec (edge) elements (Section 3, eq. EddyCurrent) and refines the
 mesh uniformly to build the spatial hierarchy (Section 5.1).  The paper's
-two-tetrahedron start mesh is not specified further, so the oracle uses the
-Kuhn (Freudenthal) cube mesh, whose uniform refinement is again a Kuhn mesh.
+two-tetrahedron start mesh is not specified further, so the benchmark workloads use
+the Kuhn (Freudenthal) cube mesh, whose uniform refinement is again a Kuhn mesh;
+general start meshes and their red refinement are at the end of this file.
 
 Conventions (shared with the C library through the published problem statement,
 not through code):
@@ -147,3 +148,126 @@ def fine_tet_parents(coarse_n: int) -> np.ndarray:
     fine = kuhn_mesh(2 * coarse_n)
     bc = tet_barycentres(fine)
     return np.array([locate_point(coarse_n, b) for b in bc], dtype=np.int64)
+
+
+# ----------------------------------------------------------------- general tet meshes
+# Section 5.1 builds the spatial hierarchy by uniform refinement of a coarse start mesh.
+# Besides the Kuhn cube meshes the oracle takes any conforming tetrahedral mesh and
+# refines it with the red refinement of J. Bey (Computing 55, 1995): every tet is cut
+# into its four corner tets and four tets around one diagonal of the inner octahedron.
+# Conventions (shared with the C library through the published problem statement):
+#   * a tet keeps the vertex order it is given in; edges are the sorted vertex pairs,
+#     numbered lexicographically and oriented lo -> hi, as for Kuhn meshes;
+#   * refinement keeps the coarse vertex ids and gives the midpoint of coarse edge e the
+#     id nv + e; child k of coarse tet t is tet 8 t + k, with vertex lists (x_ij = the
+#     midpoint of the parent's local vertices i and j, in the parent's vertex order)
+#       k=0 (x0, x01, x02, x03)  k=1 (x01, x1, x12, x13)  k=2 (x02, x12, x2, x23)
+#       k=3 (x03, x13, x23, x3)  k=4 (x01, x02, x03, x13) k=5 (x01, x02, x12, x13)
+#       k=6 (x02, x03, x13, x23) k=7 (x02, x12, x13, x23)
+#   * the boundary is the set of faces that belong to one tet only; Dirichlet keeps the
+#     edges and vertices that lie on no boundary face, Neumann keeps every edge and every
+#     vertex but vertex 0.
+
+@dataclass
+class TetMesh:
+    xyz: np.ndarray            # (nv, 3) float64
+    tets: np.ndarray           # (nt, 4) int64, as given / as refined
+    edges: np.ndarray          # (ne, 2) int64 sorted vertex pairs, lexicographic
+    tet_edges: np.ndarray      # (nt, 6) int64 edge ids of the local edges LOCAL_EDGES
+    edge_interior: np.ndarray  # (ne,) bool: unknowns
+    vert_interior: np.ndarray  # (nv,) bool: unknowns
+    parent: np.ndarray | None = None   # (nt,) coarse tet of every tet of a refined mesh
+    n: int = 0                 # 0: not a Kuhn mesh
+
+    @property
+    def interior_edges(self) -> np.ndarray:
+        return np.nonzero(self.edge_interior)[0]
+
+    @property
+    def interior_verts(self) -> np.ndarray:
+        return np.nonzero(self.vert_interior)[0]
+
+    @property
+    def longest_edge(self) -> np.ndarray:
+        """h_T of eq. CoarseningRule read as the diameter of T (its longest edge)."""
+        P = self.xyz[self.tets]
+        return np.max([np.linalg.norm(P[:, a] - P[:, b], axis=1) for a, b in LOCAL_EDGES], axis=0)
+
+
+TET_FACES = [(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)]
+BEY_CHILDREN = [  # entries: parent-local vertex i (int) or midpoint (i, j)
+    (0, (0, 1), (0, 2), (0, 3)),
+    ((0, 1), 1, (1, 2), (1, 3)),
+    ((0, 2), (1, 2), 2, (2, 3)),
+    ((0, 3), (1, 3), (2, 3), 3),
+    ((0, 1), (0, 2), (0, 3), (1, 3)),
+    ((0, 1), (0, 2), (1, 2), (1, 3)),
+    ((0, 2), (0, 3), (1, 3), (2, 3)),
+    ((0, 2), (1, 2), (1, 3), (2, 3)),
+]
+
+
+def tet_mesh(xyz, tets, bc: str = "dirichlet", parent=None) -> TetMesh:
+    """Edges, local edge ids and unknowns of a conforming tetrahedral mesh (plain loops)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    pairs = set()
+    for t in tets:
+        for a, b in LOCAL_EDGES:
+            pairs.add(tuple(sorted((int(t[a]), int(t[b])))))
+    edges = np.array(sorted(pairs), dtype=np.int64).reshape(-1, 2)
+    index = {(int(a), int(b)): e for e, (a, b) in enumerate(edges)}
+    tet_edges = np.zeros((len(tets), 6), dtype=np.int64)
+    for t, tv in enumerate(tets):
+        for le, (a, b) in enumerate(LOCAL_EDGES):
+            tet_edges[t, le] = index[tuple(sorted((int(tv[a]), int(tv[b]))))]
+    count = {}
+    for tv in tets:
+        for f in TET_FACES:
+            key = tuple(sorted(int(tv[i]) for i in f))
+            count[key] = count.get(key, 0) + 1
+    bverts, bedges = set(), set()
+    for key, c in count.items():
+        if c == 1:
+            bverts.update(key)
+            for i, j in ((0, 1), (0, 2), (1, 2)):
+                bedges.add(index[(key[i], key[j])])
+    nv = len(xyz)
+    if bc == "dirichlet":
+        vert_interior = np.array([v not in bverts for v in range(nv)], dtype=bool)
+        edge_interior = np.array([e not in bedges for e in range(len(edges))], dtype=bool)
+    elif bc == "neumann":
+        vert_interior = np.ones(nv, dtype=bool)
+        vert_interior[0] = False
+        edge_interior = np.ones(len(edges), dtype=bool)
+    else:
+        raise ValueError(bc)
+    return TetMesh(xyz, tets, edges, tet_edges, edge_interior, vert_interior,
+                   None if parent is None else np.asarray(parent, dtype=np.int64))
+
+
+def refine_uniform(mesh: TetMesh, bc: str = "dirichlet") -> TetMesh:
+    """One red refinement (conventions above)."""
+    nv = len(mesh.xyz)
+    index = {(int(a), int(b)): e for e, (a, b) in enumerate(mesh.edges)}
+    mids = 0.5 * (mesh.xyz[mesh.edges[:, 0]] + mesh.xyz[mesh.edges[:, 1]])
+    xyz = np.concatenate([mesh.xyz, mids])
+    tets, parent = [], []
+    for t, tv in enumerate(mesh.tets):
+        def vid(s):
+            if isinstance(s, int):
+                return int(tv[s])
+            i, j = s
+            return nv + index[tuple(sorted((int(tv[i]), int(tv[j]))))]
+        for child in BEY_CHILDREN:
+            tets.append([vid(s) for s in child])
+            parent.append(t)
+    return tet_mesh(xyz, np.array(tets, dtype=np.int64), bc, parent)
+
+
+def refine_times(xyz, tets, n_refine: int, bc: str = "dirichlet"):
+    """Meshes [coarse, refined once, ..., refined n_refine times]."""
+    out = [tet_mesh(xyz, tets, bc)]
+    for _ in range(n_refine):
+        out.append(refine_uniform(out[-1], bc))
+    return out

@@ -43,8 +43,16 @@ def coarsening_lambda(n_space: int, tau: float, nu, sigma) -> float:
     return float(np.min(np.asarray(nu) / np.asarray(sigma)) * tau / h ** 2)
 
 
+def coarsening_lambda_mesh(h_anc, tau: float, nu, sigma) -> float:
+    """lambda of eq. CoarseningRule on a general mesh: h_anc[t] is the longest edge of the
+    tet of that level containing finest tet t, nu and sigma are per finest tet."""
+    return float(np.min(np.asarray(nu) / (np.asarray(sigma) * np.asarray(h_anc) ** 2)) * tau)
+
+
 def build_time_hierarchy(N_t, T, n_fine, n_space_levels, nu, sigma, mode="rule",
-                         lambda_crit=0.1, min_coarse_slabs=1, max_levels=64):
+                         lambda_crit=0.1, min_coarse_slabs=1, max_levels=64, h_levels=None):
+    """n_fine: Kuhn cubes per side of the finest mesh; on a general mesh h_levels[s] gives,
+    per finest tet, the longest edge of its ancestor on space level s (n_fine unused)."""
     levels = [TimeLevel(0, N_t, T / N_t)]
     while len(levels) < max_levels:
         cur = levels[-1]
@@ -53,7 +61,9 @@ def build_time_hierarchy(N_t, T, n_fine, n_space_levels, nu, sigma, mode="rule",
         n_cur = n_fine >> cur.s
         can_space = cur.s + 1 < n_space_levels
         if mode == "rule":
-            coarsen = can_space and coarsening_lambda(n_cur, cur.tau, nu, sigma) >= lambda_crit
+            lam = (coarsening_lambda(n_cur, cur.tau, nu, sigma) if h_levels is None
+                   else coarsening_lambda_mesh(h_levels[cur.s], cur.tau, nu, sigma))
+            coarsen = can_space and lam >= lambda_crit
         elif mode == "semi_time":
             coarsen = False
         elif mode == "full_top":

@@ -25,9 +25,10 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .mesh import KuhnMesh, kuhn_mesh
+from .mesh import KuhnMesh, kuhn_mesh, refine_times
 from .fem import assemble_edge_matrices, discrete_gradient, nodal_stiffness
-from .transfer import edge_prolongation, node_prolongation, round_dyadic
+from .transfer import (edge_prolongation, edge_prolongation_nested, node_prolongation,
+                       node_prolongation_nested, round_dyadic)
 from .timeblocks import time_blocks, time_prolongation_block
 
 NODAL_JACOBI_WEIGHT = 2.0 / 3.0  # damping of the nodal Jacobi variant (our constant)
@@ -87,6 +88,37 @@ def build_space_hierarchy(n_fine: int, n_levels: int, nu, sigma, bc: str = "diri
         levels.append(SpaceLevel(cmesh, Mc, Kc, Gc, Knc))
         n //= 2
     return levels
+
+
+def build_space_hierarchy_mesh(xyz, tets, n_refine: int, n_levels: int, nu, sigma, bc: str = "dirichlet"):
+    """Space levels, finest first, of a general start mesh (xyz, tets) refined n_refine
+    times (oracle.mesh conventions); nu, sigma per tet of the finest mesh.  Matrices as in
+    build_space_hierarchy: assembled on the finest mesh, Galerkin below it."""
+    assert 1 <= n_levels <= n_refine + 1
+    meshes = refine_times(xyz, tets, n_refine, bc)[::-1]     # finest first
+    mesh = meshes[0]
+    M, K = assemble_edge_matrices(mesh, nu, sigma)
+    levels = [SpaceLevel(mesh, M, K, discrete_gradient(mesh), nodal_stiffness(mesh, sigma))]
+    for s in range(1, n_levels):
+        cmesh, fine = meshes[s], levels[-1]
+        Px = round_dyadic(edge_prolongation_nested(cmesh, fine.mesh))
+        Pn = round_dyadic(node_prolongation_nested(cmesh, fine.mesh))
+        fine.Px, fine.Pn = Px, Pn
+        levels.append(SpaceLevel(cmesh, (Px.T @ fine.M @ Px).tocsr(), (Px.T @ fine.K @ Px).tocsr(),
+                                 discrete_gradient(cmesh), (Pn.T @ fine.Kn @ Pn).tocsr()))
+    return levels
+
+
+def ancestor_longest_edge(levels) -> list:
+    """Per space level s: for every finest tet, the longest edge of its ancestor on level s
+    (h_T of eq. CoarseningRule on the coarser mesh; nu, sigma stay per finest tet)."""
+    out = []
+    anc = np.arange(len(levels[0].mesh.tets))
+    for s, L in enumerate(levels):
+        if s > 0:
+            anc = levels[s - 1].mesh.parent[anc]
+        out.append(L.mesh.longest_edge[anc])
+    return out
 
 
 class SlabOperator:

@@ -61,3 +61,50 @@ def round_dyadic(P: sp.csr_matrix, bits: int = 20) -> sp.csr_matrix:
     Q.data = np.round(Q.data * (1 << bits)) / (1 << bits)
     Q.eliminate_zeros()
     return Q
+
+
+def _first_tet_of(items_of_tet: np.ndarray, n_items: int) -> np.ndarray:
+    """For every item (edge or vertex) the first tet, in tet order, that has it."""
+    first = np.full(n_items, -1, dtype=np.int64)
+    for t in range(len(items_of_tet)):
+        for i in items_of_tet[t]:
+            if first[i] < 0:
+                first[i] = t
+    return first
+
+
+def edge_prolongation_nested(coarse, fine) -> sp.csr_matrix:
+    """P_x between a mesh and its red refinement (fine.parent gives each fine tet's coarse
+    tet): the same line integral of the coarse Whitney function as above, evaluated in the
+    parent of a fine tet that contains the fine edge."""
+    first = _first_tet_of(fine.tet_edges, len(fine.edges))
+    rows, cols, vals = [], [], []
+    for f, (a, b) in enumerate(fine.edges):
+        xa, xb = fine.xyz[a], fine.xyz[b]
+        mid = 0.5 * (xa + xb)
+        t = int(fine.parent[first[f]])
+        for le in range(6):
+            v = float(np.dot(whitney_field(coarse, t, le, mid), xb - xa))
+            if abs(v) > 1e-13:
+                rows.append(f)
+                cols.append(coarse.tet_edges[t, le])
+                vals.append(v)
+    P = sp.coo_matrix((vals, (rows, cols)), shape=(len(fine.edges), len(coarse.edges))).tocsr()
+    P.sum_duplicates()
+    return P[fine.interior_edges][:, coarse.interior_edges].tocsr()
+
+
+def node_prolongation_nested(coarse, fine) -> sp.csr_matrix:
+    """P1 interpolation between a mesh and its red refinement."""
+    first = _first_tet_of(fine.tets, len(fine.xyz))
+    rows, cols, vals = [], [], []
+    for v, x in enumerate(fine.xyz):
+        t = int(fine.parent[first[v]])
+        lam = barycentric(coarse, t, x)
+        for i in range(4):
+            if abs(lam[i]) > 1e-13:
+                rows.append(v)
+                cols.append(coarse.tets[t, i])
+                vals.append(lam[i])
+    P = sp.coo_matrix((vals, (rows, cols)), shape=(len(fine.xyz), len(coarse.xyz))).tocsr()
+    return P[fine.interior_verts][:, coarse.interior_verts].tocsr()

@@ -3,7 +3,7 @@ import numpy as np
 
 import st_inputs
 from oracle.multigrid import SpaceTimeMG, build_time_hierarchy
-from oracle.spacetime import build_space_hierarchy
+from oracle.spacetime import ancestor_longest_edge, build_space_hierarchy, build_space_hierarchy_mesh
 
 MODES = {0: "rule", 1: "semi_time", 2: "full_top"}
 
@@ -32,6 +32,16 @@ def oracle_mg(n, nsl, nu, sigma, T, N_t, p, coarsen=0, max_levels=0, nu_pre=1, n
                               max_levels=max_levels if max_levels > 0 else 64)
     mg = SpaceTimeMG(sl, tl, p, omega, nu_pre, nu_post, nodal=nodal, jacobi_sweeps=jacobi_sweeps, use_A=use_A,
                      pattern=pattern)
+    return sl, tl, mg
+
+
+def oracle_mg_mesh(xyz, tets, n_refine, nsl, nu, sigma, T, N_t, p, coarsen=0, max_levels=0, nu_pre=1, nu_post=1,
+                   lambda_crit=0.1, nodal="exact", jacobi_sweeps=0, omega=0.5, pattern="", bc=0):
+    """oracle_mg on a general start mesh refined n_refine times (nu, sigma per finest tet)."""
+    sl = build_space_hierarchy_mesh(xyz, tets, n_refine, nsl, nu, sigma, bc=("dirichlet", "neumann")[bc])
+    tl = build_time_hierarchy(N_t, T, 0, nsl, nu, sigma, mode=MODES[coarsen], lambda_crit=lambda_crit,
+                              max_levels=max_levels if max_levels > 0 else 64, h_levels=ancestor_longest_edge(sl))
+    mg = SpaceTimeMG(sl, tl, p, omega, nu_pre, nu_post, nodal=nodal, jacobi_sweeps=jacobi_sweeps, pattern=pattern)
     return sl, tl, mg
 
 
