@@ -20,8 +20,10 @@
  *    is the vertex chain corner, +e_a, +e_b, +e_c.  Edges are sorted vertex pairs
  *    (lo, hi), numbered lexicographically and oriented lo -> hi.  Coarser space
  *    levels are the Kuhn meshes n/2, n/4, ... (uniform refinement, Section 5.1).
+ *    Alternatively (st_mg_problem.mesh) a general start mesh refined uniformly; its
+ *    conventions are given with st_mg_mesh below; edges are numbered the same way.
  *  Boundary.  Homogeneous Dirichlet u x n = 0 (default): unknowns are the interior
- *    edges (edges not contained in a face of the cube), in increasing edge id order;
+ *    edges (edges not contained in a boundary face), in increasing edge id order;
  *    Neumann (st_mg_problem.bc = 1): all edges in edge id order.
  *  Space-time vectors (f, x, r) of a time level with N_t slabs and degree p are
  *    double arrays  v[e * (N_t*(p+1)) + n*(p+1) + i]  -- edge-major, time
@@ -57,12 +59,34 @@ extern "C" {
 
 typedef struct st_mg_s* st_mg_t;
 
+/* A general start mesh (Section 5.1: the spatial hierarchy comes from uniform refinement
+ * of a coarse tetrahedral mesh).  Host arrays, read during setup only (the handle copies
+ * what it needs).  The mesh must be conforming (a face belongs to one or two tets) with
+ * tets of non-zero volume.  Each refinement is the red refinement of J. Bey (Computing 55,
+ * 1995): coarse vertex ids are kept; the midpoint of coarse edge e (edges = sorted vertex
+ * pairs numbered lexicographically) gets id n_vert + e; child k of coarse tet t is tet
+ * 8 t + k with vertices, in terms of the parent's vertex order x0..x3 and midpoints x_ij:
+ *   k=0 (x0,x01,x02,x03)   k=1 (x01,x1,x12,x13)  k=2 (x02,x12,x2,x23)   k=3 (x03,x13,x23,x3)
+ *   k=4 (x01,x02,x03,x13)  k=5 (x01,x02,x12,x13) k=6 (x02,x03,x13,x23)  k=7 (x02,x12,x13,x23)
+ * The boundary is the set of faces of one tet only; with bc = 0 the unknowns are the edges
+ * and vertices on no boundary face. */
+typedef struct {
+    int32_t n_vert;          /* vertices of the start mesh (>= 4) */
+    int32_t n_tet;           /* tets of the start mesh (>= 1) */
+    const double* xyz;       /* host [n_vert * 3] coordinates */
+    const int32_t* tet;      /* host [n_tet * 4] vertex ids in [0, n_vert), distinct per tet */
+    int32_t n_refine;        /* refinements to the finest mesh (0 .. 8; n_tet 8^n_refine <= 2^28) */
+} st_mg_mesh;
+
 /* Problem statement (Section 3, eq. EddyCurrent; Section 2.1 time stepping). */
 typedef struct {
-    int32_t n_cube;          /* cubes per side of the finest Kuhn mesh (>= 2, even if n_space_levels > 1) */
-    int32_t n_space_levels;  /* nested meshes n_cube, n_cube/2, ... available for coarsening (>= 1) */
-    const double* nu;        /* host [6 n_cube^3] reluctivity 1/mu per finest tet, > 0 */
-    const double* sigma;     /* host [6 n_cube^3] conductivity per finest tet, > 0 */
+    int32_t n_cube;          /* cubes per side of the finest Kuhn mesh (>= 2, even if n_space_levels > 1);
+                                ignored when mesh is given */
+    int32_t n_space_levels;  /* nested meshes n_cube, n_cube/2, ... (or the finest general mesh and its
+                                n_space_levels - 1 coarser ancestors, <= n_refine + 1) for coarsening (>= 1) */
+    const double* nu;        /* host [n_tet] reluctivity 1/mu per finest tet, > 0 (n_tet = 6 n_cube^3, or
+                                mesh->n_tet 8^n_refine in the child order above) */
+    const double* sigma;     /* host [n_tet] conductivity per finest tet, > 0 */
     double T;                /* end time (> 0); the time interval is (0, T) */
     int32_t N_t;             /* number of time slabs on the finest level (>= 1) */
     int32_t degree;          /* DG degree in time: 0 (implicit Euler) or 1 */
@@ -75,6 +99,8 @@ typedef struct {
                                 vertices); 1 Neumann (all edges; all vertices but vertex 0, which
                                 grounds the singular nodal matrix: G annihilates constants, so the
                                 correction G z does not depend on the choice) */
+    const st_mg_mesh* mesh;  /* NULL: the Kuhn mesh of the unit cube with n_cube cubes per side;
+                                else a general start mesh refined mesh->n_refine times */
 } st_mg_problem;
 
 /* Method parameters (Sections 2.1, 2.2, 4, 5). */

@@ -24,9 +24,14 @@ class StMgError(RuntimeError):
         self.status = status
 
 
+class Mesh(ctypes.Structure):
+    _fields_ = [("n_vert", _i32), ("n_tet", _i32), ("xyz", _P(_dbl)), ("tet", _P(_i32)), ("n_refine", _i32)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("n_cube", _i32), ("n_space_levels", _i32), ("nu", _P(_dbl)), ("sigma", _P(_dbl)),
-                ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32), ("bc", _i32)]
+                ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32), ("bc", _i32),
+                ("mesh", _P(Mesh))]
 
 
 class Options(ctypes.Structure):
@@ -171,11 +176,21 @@ def st_mg_default_options() -> Options:
     return o
 
 
-def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1, bc=0):
+def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1, bc=0, mesh=None):
+    """mesh: None (Kuhn mesh with n_cube cubes per side) or (xyz, tets, n_refine), a general
+    start mesh refined n_refine times (n_cube is then ignored)."""
     nu = np.ascontiguousarray(nu, dtype=np.float64)
     sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch, bc)
-    p._keep = (nu, sigma)
+    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch, bc, None)
+    keep = [nu, sigma]
+    if mesh is not None:
+        xyz, tets, n_refine = mesh
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        m = Mesh(len(xyz), len(tets), _dptr(xyz), tets.ctypes.data_as(_P(_i32)), int(n_refine))
+        p.mesh = ctypes.pointer(m)
+        keep += [xyz, tets, m]
+    p._keep = keep
     return p
 
 

@@ -6,11 +6,12 @@
 // Re mu > 0 (complex symmetric with SPD real part, so elimination without
 // pivoting is stable), K_n (real SPD).
 //
-// Ordering: geometric nested dissection on the integer "min corner" of each
-// unknown (tail vertex of an edge, the vertex itself for a node).  Splitting the
-// set at plane c of axis a into {m_a < c}, {m_a == c} (separator), {m_a > c}
-// separates the matrix graph, because unknowns couple only inside a common cube
-// and the two outer sets touch disjoint layers of cubes.  Each separator (and
+// Ordering: nested dissection guided by the positions of the unknowns (edge
+// midpoints, vertices).  A set is cut in two by position along one axis, and the
+// separator is the smaller of the two one-sided boundaries of the cut in the matrix
+// graph (the unknowns of one part coupled to the other), which leaves the rest of
+// the two parts uncoupled; the axis and the cut position (between 35% and 65% of the
+// set) are chosen to make that separator smallest.  Each separator (and
 // each leaf box) is one supernode; the factor is stored per supernode as
 //   W_s = [ L11^{-1} ; -L21 L11^{-1} ]   (row-major, (nc + nr) x nc)
 // which turns both triangular sweeps on the GPU into dense products.
@@ -295,30 +296,94 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
   F.n = n;
   // ---------------- nested dissection tree (recursive, built bottom-up in postorder)
   std::vector<NDNode> tree;
+  std::vector<int8_t> side(n, -1);
+  std::vector<int32_t> rank(n, -1);
   std::function<int(std::vector<int32_t>&, int)> build = [&](std::vector<int32_t>& idx, int depth) -> int {
     NDNode node;
     node.depth = depth;
-    int axis = -1;
-    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
-    for (int32_t i : idx) {
-      const int32_t c[3] = {co.x[i], co.y[i], co.z[i]};
-      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], c[d]); hi[d] = std::max(hi[d], c[d]); }
-    }
-    if ((int)idx.size() > leaf_max) {
-      int best = 1;
-      for (int d = 0; d < 3; ++d)
-        if (hi[d] - lo[d] > best) { best = hi[d] - lo[d]; axis = d; }
-      if (best < 2) axis = -1;
-    }
-    if (axis < 0) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const std::vector<double>* cv3[3] = {&co.rx, &co.ry, &co.rz};
+    for (int32_t i : idx)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], (*cv3[d])[i]);
+        hi[d] = std::max(hi[d], (*cv3[d])[i]);
+      }
+    if ((int)idx.size() <= leaf_max || (hi[0] <= lo[0] && hi[1] <= lo[1] && hi[2] <= lo[2])) {
       node.cols = idx;
       tree.push_back(node);
       return (int)tree.size() - 1;
     }
-    const std::vector<int32_t>& cv = axis == 0 ? co.x : axis == 1 ? co.y : co.z;
-    const int32_t cut = (lo[axis] + hi[axis]) / 2;
-    std::vector<int32_t> L, S, R;
-    for (int32_t i : idx) (cv[i] < cut ? L : cv[i] == cut ? S : R).push_back(i);
+    // Candidate cuts: each axis, the first h unknowns in coordinate order on one side,
+    // h / |idx| in [0.35, 0.65].  With rank[i] the position of i in that order and
+    // lo_nb / hi_nb the lowest / highest rank among i's neighbours in the set, i < h lies
+    // on the boundary of the lower part iff hi_nb[i] >= h, and i >= h on the boundary of
+    // the upper part iff lo_nb[i] < h; the cut with the smallest boundary wins.
+    const int64_t m = (int64_t)idx.size();
+    size_t best_sep = SIZE_MAX;
+    int best_axis = -1;
+    int64_t best_h = 0;
+    std::vector<int32_t> best_ord;
+    std::vector<int32_t> ord(idx);
+    std::vector<int32_t> lo_nb(m), hi_nb(m), cnt_lo(m + 1), cnt_hi(m + 1);
+    for (int axis = 0; axis < 3; ++axis) {
+      if (!(hi[axis] > lo[axis])) continue;
+      const std::vector<double>& cv = *cv3[axis];
+      ord = idx;
+      std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return cv[a] < cv[b] || (cv[a] == cv[b] && a < b); });
+      for (int64_t q = 0; q < m; ++q) rank[ord[q]] = (int32_t)q;
+      for (int64_t q = 0; q < m; ++q) {
+        const int32_t i = ord[q];
+        int32_t l = (int32_t)q, h = (int32_t)q;
+        for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+          const int32_t r = rank[A.col[e]];
+          if (r >= 0) { l = std::min(l, r); h = std::max(h, r); }
+        }
+        lo_nb[q] = l;
+        hi_nb[q] = h;
+      }
+      // boundary sizes for every h at once: lower part {q < h: hi_nb[q] >= h},
+      // upper part {q >= h: lo_nb[q] < h}, by difference arrays over h
+      std::fill(cnt_lo.begin(), cnt_lo.end(), 0);
+      std::fill(cnt_hi.begin(), cnt_hi.end(), 0);
+      for (int64_t q = 0; q < m; ++q) {
+        if (hi_nb[q] > q) { cnt_lo[q + 1]++; cnt_lo[hi_nb[q] + 1]--; }       // h in (q, hi_nb]
+        if (lo_nb[q] < q) { cnt_hi[lo_nb[q] + 1]++; cnt_hi[q + 1]--; }       // h in (lo_nb, q]
+      }
+      int64_t run_lo = 0, run_hi = 0;
+      for (int64_t h = 0; h <= m; ++h) {
+        run_lo += cnt_lo[h];
+        run_hi += cnt_hi[h];
+        if (20 * h < 7 * m || 20 * h > 13 * m) continue;
+        const size_t sep = (size_t)std::min(run_lo, run_hi);
+        if (sep < best_sep) { best_sep = sep; best_axis = axis; best_h = h; best_ord = ord; }
+      }
+      for (int32_t i : idx) rank[i] = -1;
+    }
+    if (best_axis < 0) {
+      node.cols = idx;
+      tree.push_back(node);
+      return (int)tree.size() - 1;
+    }
+    for (int64_t q = 0; q < m; ++q) side[best_ord[q]] = q < best_h ? 0 : 1;
+    std::vector<int32_t> bnd[2], rest[2];
+    for (int32_t i : idx) {
+      bool cut = false;
+      for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1] && !cut; ++q) {
+        const int8_t sj = side[A.col[q]];
+        cut = sj >= 0 && sj != side[i];
+      }
+      (cut ? bnd : rest)[side[i]].push_back(i);
+    }
+    for (int32_t i : idx) side[i] = -1;
+    // separator: the smaller boundary; its side keeps only its interior
+    const int sep = bnd[0].size() <= bnd[1].size() ? 0 : 1;
+    std::vector<int32_t> L = rest[sep], R = rest[1 - sep], S = bnd[sep];
+    R.insert(R.end(), bnd[1 - sep].begin(), bnd[1 - sep].end());
+    if (S.empty()) {                     // halves not coupled: any single unknown separates
+      std::vector<int32_t>& from = R.empty() ? L : R;
+      S.push_back(from.back());
+      from.pop_back();
+    }
     int nch = 0;
     int ch[2] = {-1, -1};
     if (!L.empty()) ch[nch++] = build(L, depth + 1);
@@ -326,9 +391,6 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
     node.child[0] = ch[0];
     node.child[1] = ch[1];
     node.cols = S;
-    if (S.empty()) {  // cannot happen for lattice coordinates with range >= 2; keep a valid tree anyway
-      node.cols.clear();
-    }
     tree.push_back(node);
     return (int)tree.size() - 1;
   };

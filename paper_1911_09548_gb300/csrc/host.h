@@ -34,15 +34,19 @@ struct Csr {
   int64_t nnz() const { return (int64_t)col.size(); }
 };
 
-// Kuhn mesh of [0,1]^3 with n cubes per side (conventions in include/st_mg.h).
-struct KuhnMesh {
-  int n = 0;
+// Tetrahedral mesh: the Kuhn mesh of [0,1]^3 with n cubes per side, or (n == 0) a
+// general mesh given by coordinates, possibly a red refinement of a coarser one
+// (conventions in include/st_mg.h).
+struct TetMesh {
+  int n = 0;                               // Kuhn cubes per side; 0 for a general mesh
   int64_t nv = 0, ne = 0, nt = 0;
   std::vector<int32_t> edge_lo, edge_hi;   // [ne]
   std::vector<int32_t> tet_vert;           // [nt*4] chain order
   std::vector<int32_t> tet_edge;           // [nt*6] local edges (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
-  std::vector<int32_t> tet_perm;           // [nt] axis permutation index 0..5
-  std::vector<int32_t> edge_of;            // [nv*7] edge id from vertex lo in direction code d, or -1
+  std::vector<int32_t> tet_perm;           // [nt] axis permutation index 0..5 (Kuhn)
+  std::vector<int32_t> edge_of;            // [nv*7] edge id from vertex lo in direction code d, or -1 (Kuhn)
+  std::vector<double> xyz;                 // [nv*3] coordinates (general meshes)
+  std::vector<int32_t> parent;             // [nt] tet of the mesh this one refines, or empty
   std::vector<int32_t> edge_iid;           // [ne] interior index or -1
   std::vector<int32_t> int_edges;          // interior index -> edge id
   std::vector<int32_t> vert_iid;           // [nv] interior index or -1
@@ -60,18 +64,29 @@ extern const int kLocalEdge[6][2];
 // bc 0: Dirichlet u x n = 0 (interior edges and vertices are the unknowns);
 // bc 1: Neumann (all edges; all vertices but vertex 0, which grounds the singular
 // nodal matrix -- G annihilates constants, so the correction G z is unchanged)
-void build_kuhn(int n, KuhnMesh& m, int bc = 0);
+void build_kuhn(int n, TetMesh& m, int bc = 0);
+// General mesh from coordinates and tets (vertex order kept).  Returns 0, or 1 with a
+// message in err for an invalid mesh (index out of range, repeated vertex, zero volume,
+// a face shared by more than two tets).
+int build_general(int32_t nv, const double* xyz, int64_t nt, const int32_t* tets, int bc, TetMesh& m,
+                  std::string& err);
+// Red refinement of a general mesh (child k of tet t is tet 8 t + k; include/st_mg.h).
+void refine_red(const TetMesh& coarse, int bc, TetMesh& fine);
+// Longest edge of every tet (h_T of the coarsening rule).
+std::vector<double> longest_edges(const TetMesh& m);
+// Coordinates of every vertex (Kuhn or general).
+void vertex_xyz(const TetMesh& m, int64_t v, double x[3]);
 
 // Whitney edge matrices on interior edges: one CSR pattern, two value arrays.
-void assemble_edge(const KuhnMesh& m, const double* nu, const double* sigma, Csr& M, Csr& K);
+void assemble_edge(const TetMesh& m, const double* nu, const double* sigma, Csr& M, Csr& K);
 // P1 stiffness of div(sigma grad) on interior nodes.
-void assemble_nodal(const KuhnMesh& m, const double* sigma, Csr& Kn);
+void assemble_nodal(const TetMesh& m, const double* sigma, Csr& Kn);
 // Discrete gradient on interior unknowns as (tail, head) interior node ids (-1 = boundary).
-void gradient_pairs(const KuhnMesh& m, std::vector<int32_t>& tail, std::vector<int32_t>& head);
+void gradient_pairs(const TetMesh& m, std::vector<int32_t>& tail, std::vector<int32_t>& head);
 // Interpolation prolongation of Whitney functions, coarse (n) -> fine (2n), interior edges.
-void edge_prolongation(const KuhnMesh& coarse, const KuhnMesh& fine, Csr& P);
+void edge_prolongation(const TetMesh& coarse, const TetMesh& fine, Csr& P);
 // Space load b_e = int curl psi . w_e (4-point rule per tet), interior edges.
-void space_load(const KuhnMesh& m, int n_modes, const double* a, const double* k,
+void space_load(const TetMesh& m, int n_modes, const double* a, const double* k,
                 const double* phase, std::vector<double>& b);
 
 // Sparse helpers.
@@ -117,8 +132,8 @@ struct SupernodalFactor {
   double flops_apply_per_rhs = 0;       // multiply-adds (real or complex) of one forward+backward per rhs
 };
 
-struct NDCoords {                        // integer "min corner" of each unknown
-  std::vector<int32_t> x, y, z;
+struct NDCoords {                        // position of each unknown (edge midpoint, vertex)
+  std::vector<double> rx, ry, rz;
 };
 
 // Factor A (pattern Csr with values given separately as T) with ND ordering from

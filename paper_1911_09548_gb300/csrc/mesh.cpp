@@ -1,6 +1,13 @@
-// Kuhn meshes, Whitney (lowest-order Nedelec) and P1 assembly, discrete gradient,
-// spatial prolongation and the space part of the load (Section 3 and eq. AuxNodalSm
-// of the paper; uniform refinement as in Section 5.1).
+// Kuhn and general tetrahedral meshes, Whitney (lowest-order Nedelec) and P1 assembly,
+// discrete gradient, spatial prolongation and the space part of the load (Section 3 and
+// eq. AuxNodalSm of the paper; uniform refinement as in Section 5.1).
+//
+// General meshes take the element geometry from the coordinates: with the rows
+// r_k = x_k - x_0 (k = 1..3) and det = r_1 . (r_2 x r_3),
+//   grad lam_1 = (r_2 x r_3) / det, grad lam_2 = (r_3 x r_1) / det,
+//   grad lam_3 = (r_1 x r_2) / det, grad lam_0 = -(sum of the others), |T| = |det| / 6,
+// and a local edge (i, j) whose global orientation is j -> i (vertex id of j lower)
+// carries the Whitney function with the opposite sign.
 //
 // Every Kuhn tet of permutation (a,b,c) in a cube of side h is the chain
 //   v0 = corner, v1 = v0 + h e_a, v2 = v1 + h e_b, v3 = v2 + h e_c,
@@ -10,6 +17,7 @@
 // increase along the chain, so the global orientation lo -> hi of a local edge
 // (i, j), i < j, is i -> j and the Whitney function is lam_i grad lam_j - lam_j grad lam_i.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <numeric>
 
@@ -98,9 +106,211 @@ int64_t find_pos(const Csr& A, int32_t r, int32_t c) {
   return (it != e && *it == c) ? (int64_t)(it - A.col.begin()) : -1;
 }
 
+// Barycentric gradients g and volume of tet t of a general mesh; returns det.
+double general_grads(const TetMesh& m, int64_t t, double g[4][3], double& vol) {
+  const int32_t* tv = &m.tet_vert[t * 4];
+  double r[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) r[k][d] = m.xyz[(int64_t)tv[k + 1] * 3 + d] - m.xyz[(int64_t)tv[0] * 3 + d];
+  double c12[3], c20[3], c01[3];
+  cross3(r[1], r[2], c12);
+  cross3(r[2], r[0], c20);
+  cross3(r[0], r[1], c01);
+  const double det = dot3(r[0], c12);
+  for (int d = 0; d < 3; ++d) {
+    g[1][d] = c12[d] / det;
+    g[2][d] = c20[d] / det;
+    g[3][d] = c01[d] / det;
+    g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+  }
+  vol = std::fabs(det) / 6.0;
+  return det;
+}
+
+// +1 if local edge le of tet t is oriented i -> j globally (kLocalEdge order), else -1.
+inline double edge_sign(const TetMesh& m, int64_t t, int le) {
+  return m.tet_vert[t * 4 + kLocalEdge[le][0]] < m.tet_vert[t * 4 + kLocalEdge[le][1]] ? 1.0 : -1.0;
+}
+
+// Local Whitney matrices (coefficient 1, times |T|) of a general tet, orientation included.
+void general_element(const TetMesh& m, int64_t t, double Me[6][6], double Ke[6][6]) {
+  double g[4][3], vol;
+  general_grads(m, t, g, vol);
+  auto I = [](int s, int u) { return (s == u ? 2.0 : 1.0) / 20.0; };
+  for (int e = 0; e < 6; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int i = kLocalEdge[e][0], j = kLocalEdge[e][1];
+      const int k = kLocalEdge[f][0], l = kLocalEdge[f][1];
+      const double sg = edge_sign(m, t, e) * edge_sign(m, t, f) * vol;
+      Me[e][f] = sg * (I(i, k) * dot3(g[j], g[l]) - I(i, l) * dot3(g[j], g[k]) - I(j, k) * dot3(g[i], g[l]) +
+                       I(j, l) * dot3(g[i], g[k]));
+      double ce[3], cf[3];
+      cross3(g[i], g[j], ce);
+      cross3(g[k], g[l], cf);
+      Ke[e][f] = sg * 4.0 * dot3(ce, cf);
+    }
+}
+
+// Children of the red refinement: parent-local vertex i (< 4) or midpoint code 4 + le of
+// local edge le = (i, j) in kLocalEdge order.
+const int kRedChild[8][4] = {
+    {0, 4 + 0, 4 + 1, 4 + 2},          // (x0,  x01, x02, x03)
+    {4 + 0, 1, 4 + 3, 4 + 4},          // (x01, x1,  x12, x13)
+    {4 + 1, 4 + 3, 2, 4 + 5},          // (x02, x12, x2,  x23)
+    {4 + 2, 4 + 4, 4 + 5, 3},          // (x03, x13, x23, x3)
+    {4 + 0, 4 + 1, 4 + 2, 4 + 4},      // (x01, x02, x03, x13)
+    {4 + 0, 4 + 1, 4 + 3, 4 + 4},      // (x01, x02, x12, x13)
+    {4 + 1, 4 + 2, 4 + 4, 4 + 5},      // (x02, x03, x13, x23)
+    {4 + 1, 4 + 3, 4 + 4, 4 + 5},      // (x02, x12, x13, x23)
+};
+
+// Barycentric coordinates, in the parent, of a child vertex code (exact dyadics).
+void code_lambda(int code, double lam[4]) {
+  for (int v = 0; v < 4; ++v) lam[v] = 0.0;
+  if (code < 4) {
+    lam[code] = 1.0;
+  } else {
+    lam[kLocalEdge[code - 4][0]] = 0.5;
+    lam[kLocalEdge[code - 4][1]] = 0.5;
+  }
+}
+
 }  // namespace
 
-void build_kuhn(int n, KuhnMesh& m, int bc) {
+void vertex_xyz(const TetMesh& m, int64_t v, double x[3]) {
+  if (m.n > 0) {
+    int i, j, k;
+    m.vijk((int)v, i, j, k);
+    x[0] = (double)i / m.n; x[1] = (double)j / m.n; x[2] = (double)k / m.n;
+  } else {
+    for (int d = 0; d < 3; ++d) x[d] = m.xyz[v * 3 + d];
+  }
+}
+
+std::vector<double> longest_edges(const TetMesh& m) {
+  std::vector<double> h(m.nt, 0.0);
+  for (int64_t t = 0; t < m.nt; ++t)
+    for (int le = 0; le < 6; ++le) {
+      double a[3], b[3];
+      vertex_xyz(m, m.tet_vert[t * 4 + kLocalEdge[le][0]], a);
+      vertex_xyz(m, m.tet_vert[t * 4 + kLocalEdge[le][1]], b);
+      const double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      h[t] = std::max(h[t], std::sqrt(dot3(d, d)));
+    }
+  return h;
+}
+
+int build_general(int32_t nv, const double* xyz, int64_t nt, const int32_t* tets, int bc, TetMesh& m,
+                  std::string& err) {
+  m = TetMesh();
+  m.n = 0;
+  m.nv = nv;
+  m.nt = nt;
+  m.xyz.assign(xyz, xyz + (int64_t)nv * 3);
+  m.tet_vert.assign(tets, tets + nt * 4);
+  for (int64_t q = 0; q < nt * 4; ++q)
+    if (m.tet_vert[q] < 0 || m.tet_vert[q] >= nv) { err = "mesh: vertex id out of range"; return 1; }
+  for (int64_t t = 0; t < nt; ++t) {
+    const int32_t* tv = &m.tet_vert[t * 4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (tv[a] == tv[b]) { err = "mesh: repeated vertex in a tet"; return 1; }
+    double g[4][3], vol, hmax = 0.0;
+    general_grads(m, t, g, vol);
+    for (int le = 0; le < 6; ++le) {
+      double d[3];
+      for (int s = 0; s < 3; ++s)
+        d[s] = m.xyz[(int64_t)tv[kLocalEdge[le][1]] * 3 + s] - m.xyz[(int64_t)tv[kLocalEdge[le][0]] * 3 + s];
+      hmax = std::max(hmax, std::sqrt(dot3(d, d)));
+    }
+    if (!(vol > 1e-12 * hmax * hmax * hmax) || !std::isfinite(vol)) { err = "mesh: tet of zero volume"; return 1; }
+  }
+  // edges: sorted vertex pairs, lexicographic
+  std::vector<std::pair<int32_t, int32_t>> ed;
+  ed.reserve(nt * 6);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int le = 0; le < 6; ++le) {
+      const int32_t a = m.tet_vert[t * 4 + kLocalEdge[le][0]], b = m.tet_vert[t * 4 + kLocalEdge[le][1]];
+      ed.emplace_back(std::min(a, b), std::max(a, b));
+    }
+  std::sort(ed.begin(), ed.end());
+  ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+  m.ne = (int64_t)ed.size();
+  m.edge_lo.resize(m.ne);
+  m.edge_hi.resize(m.ne);
+  for (int64_t e = 0; e < m.ne; ++e) { m.edge_lo[e] = ed[e].first; m.edge_hi[e] = ed[e].second; }
+  auto edge_id = [&](int32_t a, int32_t b) -> int32_t {
+    const std::pair<int32_t, int32_t> key(std::min(a, b), std::max(a, b));
+    return (int32_t)(std::lower_bound(ed.begin(), ed.end(), key) - ed.begin());
+  };
+  m.tet_edge.resize(nt * 6);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int le = 0; le < 6; ++le)
+      m.tet_edge[t * 6 + le] = edge_id(m.tet_vert[t * 4 + kLocalEdge[le][0]], m.tet_vert[t * 4 + kLocalEdge[le][1]]);
+  // boundary = faces of one tet only
+  std::vector<std::array<int32_t, 3>> faces;
+  faces.reserve(nt * 4);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int skip = 0; skip < 4; ++skip) {
+      std::array<int32_t, 3> f;
+      int c = 0;
+      for (int v = 0; v < 4; ++v)
+        if (v != skip) f[c++] = m.tet_vert[t * 4 + v];
+      std::sort(f.begin(), f.end());
+      faces.push_back(f);
+    }
+  std::sort(faces.begin(), faces.end());
+  std::vector<char> bvert(nv, 0), bedge(m.ne, 0);
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i;
+    while (j < faces.size() && faces[j] == faces[i]) ++j;
+    if (j - i > 2) { err = "mesh: a face is shared by more than two tets"; return 1; }
+    if (j - i == 1) {
+      const auto& f = faces[i];
+      for (int a = 0; a < 3; ++a) bvert[f[a]] = 1;
+      bedge[edge_id(f[0], f[1])] = bedge[edge_id(f[0], f[2])] = bedge[edge_id(f[1], f[2])] = 1;
+    }
+    i = j;
+  }
+  m.vert_iid.assign(nv, -1);
+  for (int32_t v = 0; v < nv; ++v)
+    if (bc == 1 ? v != 0 : !bvert[v]) {
+      m.vert_iid[v] = (int32_t)m.int_verts.size();
+      m.int_verts.push_back(v);
+    }
+  m.edge_iid.assign(m.ne, -1);
+  for (int64_t e = 0; e < m.ne; ++e)
+    if (bc == 1 || !bedge[e]) {
+      m.edge_iid[e] = (int32_t)m.int_edges.size();
+      m.int_edges.push_back((int32_t)e);
+    }
+  return 0;
+}
+
+void refine_red(const TetMesh& c, int bc, TetMesh& f) {
+  const int32_t nv = (int32_t)(c.nv + c.ne);
+  std::vector<double> xyz((int64_t)nv * 3);
+  for (int64_t v = 0; v < c.nv; ++v) vertex_xyz(c, v, &xyz[v * 3]);
+  for (int64_t e = 0; e < c.ne; ++e) {
+    double a[3], b[3];
+    vertex_xyz(c, c.edge_lo[e], a);
+    vertex_xyz(c, c.edge_hi[e], b);
+    for (int d = 0; d < 3; ++d) xyz[(c.nv + e) * 3 + d] = 0.5 * (a[d] + b[d]);
+  }
+  std::vector<int32_t> tets(c.nt * 32);
+  for (int64_t t = 0; t < c.nt; ++t)
+    for (int k = 0; k < 8; ++k)
+      for (int v = 0; v < 4; ++v) {
+        const int code = kRedChild[k][v];
+        tets[(t * 8 + k) * 4 + v] = code < 4 ? c.tet_vert[t * 4 + code] : (int32_t)(c.nv + c.tet_edge[t * 6 + code - 4]);
+      }
+  std::string err;
+  build_general(nv, xyz.data(), c.nt * 8, tets.data(), bc, f, err);   // children of a valid mesh are valid
+  f.parent.resize(f.nt);
+  for (int64_t t = 0; t < f.nt; ++t) f.parent[t] = (int32_t)(t / 8);
+}
+
+void build_kuhn(int n, TetMesh& m, int bc) {
   m.n = n;
   m.nv = (int64_t)(n + 1) * (n + 1) * (n + 1);
   m.nt = (int64_t)6 * n * n * n;
@@ -171,7 +381,7 @@ void build_kuhn(int n, KuhnMesh& m, int bc) {
   }
 }
 
-void assemble_edge(const KuhnMesh& m, const double* nu, const double* sigma, Csr& M, Csr& K) {
+void assemble_edge(const TetMesh& m, const double* nu, const double* sigma, Csr& M, Csr& K) {
   const int32_t ni = (int32_t)m.int_edges.size();
   std::vector<std::pair<int32_t, int32_t>> pr;
   pr.reserve(m.nt * 36);
@@ -186,6 +396,24 @@ void assemble_edge(const KuhnMesh& m, const double* nu, const double* sigma, Csr
     }
   pattern_from_pairs(pr, ni, ni, M);
   K = M;
+  if (m.n == 0) {
+    for (int64_t t = 0; t < m.nt; ++t) {
+      double Me[6][6], Ke[6][6];
+      general_element(m, t, Me, Ke);
+      for (int e = 0; e < 6; ++e) {
+        const int32_t r = m.edge_iid[m.tet_edge[t * 6 + e]];
+        if (r < 0) continue;
+        for (int f = 0; f < 6; ++f) {
+          const int32_t c = m.edge_iid[m.tet_edge[t * 6 + f]];
+          if (c < 0) continue;
+          const int64_t q = find_pos(M, r, c);
+          M.val[q] += sigma[t] * Me[e][f];
+          K.val[q] += nu[t] * Ke[e][f];
+        }
+      }
+    }
+    return;
+  }
   const double h = 1.0 / m.n;
   const RefMats& R = ref();
   for (int64_t t = 0; t < m.nt; ++t) {
@@ -206,7 +434,7 @@ void assemble_edge(const KuhnMesh& m, const double* nu, const double* sigma, Csr
   }
 }
 
-void assemble_nodal(const KuhnMesh& m, const double* sigma, Csr& Kn) {
+void assemble_nodal(const TetMesh& m, const double* sigma, Csr& Kn) {
   const int32_t ni = (int32_t)m.int_verts.size();
   std::vector<std::pair<int32_t, int32_t>> pr;
   for (int64_t t = 0; t < m.nt; ++t)
@@ -219,11 +447,17 @@ void assemble_nodal(const KuhnMesh& m, const double* sigma, Csr& Kn) {
       }
     }
   pattern_from_pairs(pr, ni, ni, Kn);
-  const double h = 1.0 / m.n;
+  const double h = m.n > 0 ? 1.0 / m.n : 0.0;
   for (int64_t t = 0; t < m.nt; ++t) {
-    double g[4][3];
-    unit_gradients(m.tet_perm[t], g);
-    const double s = sigma[t] * h / 6.0;
+    double g[4][3], s;
+    if (m.n > 0) {
+      unit_gradients(m.tet_perm[t], g);
+      s = sigma[t] * h / 6.0;
+    } else {
+      double vol;
+      general_grads(m, t, g, vol);
+      s = sigma[t] * vol;
+    }
     for (int a = 0; a < 4; ++a) {
       const int32_t r = m.vert_iid[m.tet_vert[t * 4 + a]];
       if (r < 0) continue;
@@ -236,7 +470,7 @@ void assemble_nodal(const KuhnMesh& m, const double* sigma, Csr& Kn) {
   }
 }
 
-void gradient_pairs(const KuhnMesh& m, std::vector<int32_t>& tail, std::vector<int32_t>& head) {
+void gradient_pairs(const TetMesh& m, std::vector<int32_t>& tail, std::vector<int32_t>& head) {
   tail.resize(m.int_edges.size());
   head.resize(m.int_edges.size());
   for (size_t i = 0; i < m.int_edges.size(); ++i) {
@@ -265,13 +499,54 @@ Csr gradient_csr(const std::vector<int32_t>& tail, const std::vector<int32_t>& h
 // direction d, the midpoint in coarse lattice units is (2P + d)/4; inside the
 // coarse tet containing it, P[f, (i,j)] = (lam_i (g_j . d) - lam_j (g_i . d)) / 2,
 // the line integral of the coarse Whitney function along f (exact: it is linear).
-void edge_prolongation(const KuhnMesh& coarse, const KuhnMesh& fine, Csr& P) {
+//
+// General meshes (fine = red refinement of coarse): the fine edge lies in the parent T of
+// the first fine tet that has it; the barycentric coordinates in T of the fine vertices
+// are exact dyadics (kRedChild), and since grad lam . (x_hi - x_lo) = lam(x_hi) - lam(x_lo)
+// the entry for the coarse edge i -> j of T is
+//   lam_i(mid) (lam_j(hi) - lam_j(lo)) - lam_j(mid) (lam_i(hi) - lam_i(lo)),
+// no geometry needed.
+void edge_prolongation(const TetMesh& coarse, const TetMesh& fine, Csr& P) {
   const int n = coarse.n;
   P.nrows = (int32_t)fine.int_edges.size();
   P.ncols = (int32_t)coarse.int_edges.size();
   P.rowptr.assign(P.nrows + 1, 0);
   P.col.clear();
   P.val.clear();
+  if (fine.n == 0) {
+    std::vector<int64_t> first(fine.ne, -1);   // t * 6 + le of the first fine tet with the edge
+    for (int64_t t = 0; t < fine.nt; ++t)
+      for (int le = 0; le < 6; ++le)
+        if (first[fine.tet_edge[t * 6 + le]] < 0) first[fine.tet_edge[t * 6 + le]] = t * 6 + le;
+    for (int32_t r = 0; r < P.nrows; ++r) {
+      const int32_t e = fine.int_edges[r];
+      const int64_t t = first[e] / 6;
+      const int le = (int)(first[e] % 6);
+      const int64_t T = fine.parent[t];
+      const int k = (int)(t - 8 * T);
+      int ca = kRedChild[k][kLocalEdge[le][0]], cb = kRedChild[k][kLocalEdge[le][1]];
+      if (fine.tet_vert[t * 4 + kLocalEdge[le][0]] > fine.tet_vert[t * 4 + kLocalEdge[le][1]]) std::swap(ca, cb);
+      double lo[4], hi[4], mid[4];
+      code_lambda(ca, lo);
+      code_lambda(cb, hi);
+      for (int v = 0; v < 4; ++v) mid[v] = 0.5 * (lo[v] + hi[v]);
+      std::vector<std::pair<int32_t, double>> row;
+      for (int ce = 0; ce < 6; ++ce) {
+        int i = kLocalEdge[ce][0], j = kLocalEdge[ce][1];
+        if (coarse.tet_vert[T * 4 + i] > coarse.tet_vert[T * 4 + j]) std::swap(i, j);
+        const double v = mid[i] * (hi[j] - lo[j]) - mid[j] * (hi[i] - lo[i]);
+        const int32_t c = coarse.edge_iid[coarse.tet_edge[T * 6 + ce]];
+        if (v != 0.0 && c >= 0) row.emplace_back(c, v);
+      }
+      std::sort(row.begin(), row.end());
+      for (auto& cv : row) {
+        P.col.push_back(cv.first);
+        P.val.push_back(cv.second);
+      }
+      P.rowptr[r + 1] = (int64_t)P.col.size();
+    }
+    return;
+  }
   for (int32_t r = 0; r < P.nrows; ++r) {
     const int32_t e = fine.int_edges[r];
     int a[3], b[3];
@@ -311,23 +586,23 @@ void edge_prolongation(const KuhnMesh& coarse, const KuhnMesh& fine, Csr& P) {
   }
 }
 
-void space_load(const KuhnMesh& m, int n_modes, const double* a, const double* k, const double* phase,
+void space_load(const TetMesh& m, int n_modes, const double* a, const double* k, const double* phase,
                 std::vector<double>& b) {
   b.assign(m.int_edges.size(), 0.0);
-  const double h = 1.0 / m.n;
+  const double h = m.n > 0 ? 1.0 / m.n : 1.0;   // general meshes: g are true gradients
   const double sq5 = std::sqrt(5.0);
   const double al = (5.0 + 3.0 * sq5) / 20.0, be = (5.0 - sq5) / 20.0;
   std::vector<double> kxa(3 * n_modes);
   for (int md = 0; md < n_modes; ++md) cross3(k + 3 * md, a + 3 * md, &kxa[3 * md]);
-  const double vol = h * h * h / 6.0;
   for (int64_t t = 0; t < m.nt; ++t) {
-    double g[4][3], X[4][3];
-    unit_gradients(m.tet_perm[t], g);
-    for (int v = 0; v < 4; ++v) {
-      int i, j, kk;
-      m.vijk(m.tet_vert[t * 4 + v], i, j, kk);
-      X[v][0] = i * h; X[v][1] = j * h; X[v][2] = kk * h;
+    double g[4][3], X[4][3], vol;
+    if (m.n > 0) {
+      unit_gradients(m.tet_perm[t], g);
+      vol = h * h * h / 6.0;
+    } else {
+      general_grads(m, t, g, vol);
     }
+    for (int v = 0; v < 4; ++v) vertex_xyz(m, m.tet_vert[t * 4 + v], X[v]);
     for (int q = 0; q < 4; ++q) {
       double lam[4] = {be, be, be, be};
       lam[q] = al;
@@ -343,8 +618,9 @@ void space_load(const KuhnMesh& m, int n_modes, const double* a, const double* k
         const int32_t r = m.edge_iid[m.tet_edge[t * 6 + le]];
         if (r < 0) continue;
         const int i = kLocalEdge[le][0], j = kLocalEdge[le][1];
+        const double sg = m.n > 0 ? 1.0 : edge_sign(m, t, le);
         double w[3];
-        for (int s = 0; s < 3; ++s) w[s] = (lam[i] * g[j][s] - lam[j] * g[i][s]) / h;
+        for (int s = 0; s < 3; ++s) w[s] = sg * (lam[i] * g[j][s] - lam[j] * g[i][s]) / h;
         b[r] += vol / 4.0 * dot3(jx, w);
       }
     }

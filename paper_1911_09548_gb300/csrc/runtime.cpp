@@ -202,7 +202,7 @@ struct st_mg_s {
   T* upload(const std::vector<T>& v) { return mem.upload(v); }
 
   struct Space {
-    KuhnMesh mesh;
+    TetMesh mesh;
     Csr M, K, Kn, Px, PxT, GT;            // Px: prolongation from space level s+1 to s
     std::vector<int32_t> gtail, ghead;
     std::vector<int8_t> gt_sign;
@@ -853,13 +853,21 @@ bool valid_pattern(const char (&p)[16]) {
 int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_mg_t* out, bool host_only) {
   if (!pr || !op || !out) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  const int n = pr->n_cube, nsl = pr->n_space_levels;
-  if (n < 2 || nsl < 1 || pr->N_t < 1 || !(pr->T > 0) || (pr->degree != 0 && pr->degree != 1) || !pr->nu ||
+  const st_mg_mesh* gm = pr->mesh;
+  const int n = gm ? 0 : pr->n_cube, nsl = pr->n_space_levels;
+  if ((!gm && n < 2) || nsl < 1 || pr->N_t < 1 || !(pr->T > 0) || (pr->degree != 0 && pr->degree != 1) || !pr->nu ||
       !pr->sigma)
     return fail(ST_MG_ERR_INVALID_ARG, "invalid problem (n_cube >= 2, n_space_levels >= 1, N_t >= 1, T > 0, degree 0|1)");
   if (pr->bc != 0 && pr->bc != 1) return fail(ST_MG_ERR_INVALID_ARG, "bc must be 0 (Dirichlet) or 1 (Neumann)");
-  if ((n >> (nsl - 1)) < 2 || (n % (1 << (nsl - 1))) != 0)
+  if (gm) {
+    if (gm->n_vert < 4 || gm->n_tet < 1 || !gm->xyz || !gm->tet || gm->n_refine < 0 || gm->n_refine > 8 ||
+        nsl > gm->n_refine + 1 || ((int64_t)gm->n_tet << (3 * gm->n_refine)) > ((int64_t)1 << 28))
+      return fail(ST_MG_ERR_INVALID_ARG,
+                  "invalid mesh (n_vert >= 4, n_tet >= 1, 0 <= n_refine <= 8, n_tet 8^n_refine <= 2^28, "
+                  "n_space_levels <= n_refine + 1)");
+  } else if ((n >> (nsl - 1)) < 2 || (n % (1 << (nsl - 1))) != 0) {
     return fail(ST_MG_ERR_INVALID_ARG, "n_cube must be divisible by 2^(n_space_levels-1) with coarsest >= 2");
+  }
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
@@ -867,7 +875,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       (op->autotune != 0 && op->autotune != 1) ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
-  const int64_t nt = (int64_t)6 * n * n * n;
+  const int64_t nt = gm ? ((int64_t)gm->n_tet << (3 * gm->n_refine)) : (int64_t)6 * n * n * n;
   for (int64_t t = 0; t < nt; ++t)
     if (!(pr->nu[t] > 0) || !(pr->sigma[t] > 0) || !std::isfinite(pr->nu[t]) || !std::isfinite(pr->sigma[t]))
       return fail(ST_MG_ERR_INVALID_ARG, "nu and sigma must be positive and finite");
@@ -880,6 +888,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.sigma.assign(pr->sigma, pr->sigma + nt);
   H.prob.nu = H.nu.data();
   H.prob.sigma = H.sigma.data();
+  H.prob.mesh = nullptr;   // the caller's mesh is read during this call only
   H.stream = static_cast<cudaStream_t>(stream);
   H.q = pr->degree + 1;
   H.B = pr->n_batch > 1 ? pr->n_batch : 1;
@@ -889,23 +898,37 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     CK(cudaDeviceGetAttribute(&H.n_sm, cudaDevAttrMultiProcessorCount, H.device));
   }
 
-  // ---- space hierarchy
+  // ---- space hierarchy (level 0 finest)
   H.space.resize(nsl);
+  if (gm) {
+    std::vector<TetMesh> chain(gm->n_refine + 1);   // start mesh, refined once, ...
+    std::string err;
+    if (build_general(gm->n_vert, gm->xyz, gm->n_tet, gm->tet, pr->bc, chain[0], err))
+      return fail(ST_MG_ERR_INVALID_ARG, err);
+    for (int r = 1; r <= gm->n_refine; ++r) refine_red(chain[r - 1], pr->bc, chain[r]);
+    for (int s = 0; s < nsl; ++s) H.space[s].mesh = std::move(chain[gm->n_refine - s]);
+  }
   for (int s = 0; s < nsl; ++s) {
     auto& S = H.space[s];
-    build_kuhn(n >> s, S.mesh, pr->bc);
+    if (!gm) build_kuhn(n >> s, S.mesh, pr->bc);
     S.ne = (int32_t)S.mesh.int_edges.size();
     S.nn = (int32_t)S.mesh.int_verts.size();
+    if (S.ne < 1 || S.nn < 1)
+      return fail(ST_MG_ERR_INVALID_ARG, "a space level has no interior edge or no interior vertex (refine more)");
     gradient_pairs(S.mesh, S.gtail, S.ghead);
+    // positions that guide the nested-dissection orderings: edge midpoints, vertices
     for (int32_t e : S.mesh.int_edges) {
-      int i, j, k;
-      S.mesh.vijk(S.mesh.edge_lo[e], i, j, k);
-      S.ecoord.x.push_back(i); S.ecoord.y.push_back(j); S.ecoord.z.push_back(k);
+      double a[3], b[3];
+      vertex_xyz(S.mesh, S.mesh.edge_lo[e], a);
+      vertex_xyz(S.mesh, S.mesh.edge_hi[e], b);
+      S.ecoord.rx.push_back(0.5 * (a[0] + b[0]));
+      S.ecoord.ry.push_back(0.5 * (a[1] + b[1]));
+      S.ecoord.rz.push_back(0.5 * (a[2] + b[2]));
     }
     for (int32_t v : S.mesh.int_verts) {
-      int i, j, k;
-      S.mesh.vijk(v, i, j, k);
-      S.ncoord.x.push_back(i); S.ncoord.y.push_back(j); S.ncoord.z.push_back(k);
+      double a[3];
+      vertex_xyz(S.mesh, v, a);
+      S.ncoord.rx.push_back(a[0]); S.ncoord.ry.push_back(a[1]); S.ncoord.rz.push_back(a[2]);
     }
   }
   assemble_edge(H.space[0].mesh, H.nu.data(), H.sigma.data(), H.space[0].M, H.space[0].K);
@@ -926,9 +949,18 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     for (size_t q = 0; q < S.GT.val.size(); ++q) S.gt_sign[q] = S.GT.val[q] > 0 ? 1 : -1;
   }
 
-  // ---- time hierarchy (eq. CoarseningRule with h_T = sqrt(3)/n for every Kuhn tet)
+  // ---- time hierarchy (eq. CoarseningRule).  Kuhn: h_T = sqrt(3)/n for every tet;
+  // general meshes: h_T = the longest edge of the level-s ancestor of each finest tet
+  // (tet t >> 3s), the minimum taken over the finest tets.
   double min_ratio = INFINITY;
   for (int64_t t = 0; t < nt; ++t) min_ratio = std::min(min_ratio, H.nu[t] / H.sigma[t]);
+  std::vector<double> min_ratio_h2(nsl, INFINITY);
+  if (gm)
+    for (int s = 0; s < nsl; ++s) {
+      const std::vector<double> h = longest_edges(H.space[s].mesh);
+      for (int64_t t = 0; t < nt; ++t)
+        min_ratio_h2[s] = std::min(min_ratio_h2[s], H.nu[t] / (H.sigma[t] * h[t >> (3 * s)] * h[t >> (3 * s)]));
+    }
   {
     Handle::Level L0;
     L0.s = 0;
@@ -943,8 +975,12 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     const bool can_space = cur.s + 1 < nsl;
     bool coarsen = false;
     if (op->coarsen == 0) {
-      const double hT = std::sqrt(3.0) / (double)(n >> cur.s);
-      coarsen = can_space && (min_ratio * cur.tau / (hT * hT) >= op->lambda_crit);
+      if (gm) {
+        coarsen = can_space && (min_ratio_h2[cur.s] * cur.tau >= op->lambda_crit);
+      } else {
+        const double hT = std::sqrt(3.0) / (double)(n >> cur.s);
+        coarsen = can_space && (min_ratio * cur.tau / (hT * hT) >= op->lambda_crit);
+      }
     } else if (op->coarsen == 2) {
       coarsen = can_space && H.lv.size() == 1;
     }
@@ -979,6 +1015,11 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (H.use_cache) {
     uint64_t mh = fnv1a(1469598103934665603ull, &n, sizeof(n));
     mh = fnv1a(mh, &pr->bc, sizeof(pr->bc));
+    if (gm) {   // the start mesh and its refinement count
+      mh = fnv1a(mh, &gm->n_refine, sizeof(gm->n_refine));
+      mh = fnv1a(mh, gm->xyz, (size_t)gm->n_vert * 3 * sizeof(double));
+      mh = fnv1a(mh, gm->tet, (size_t)gm->n_tet * 4 * sizeof(int32_t));
+    }
     mh = fnv1a(mh, H.nu.data(), H.nu.size() * sizeof(double));
     H.mat_hash = fnv1a(mh, H.sigma.data(), H.sigma.size() * sizeof(double));
     char buf[192];

@@ -12,8 +12,10 @@ from . import binding as B
 
 class SpaceTimeSolver:
     def __init__(self, n_cube, nu, sigma, T, N_t, degree, n_space_levels=1, stream=None, host_only=False,
-                 n_batch=1, bc=0, **options):
-        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch, bc)
+                 n_batch=1, bc=0, mesh=None, **options):
+        """n_cube: Kuhn cubes per side, or mesh = (xyz, tets, n_refine) for a general start mesh
+        refined n_refine times (n_cube ignored; nu, sigma per finest tet, child k of tet t = 8 t + k)."""
+        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch, bc, mesh)
         self.n_batch = n_batch
         self.opt = B.st_mg_default_options()
         for k, v in options.items():

@@ -143,3 +143,61 @@ def test_split_waves_setter_needs_device_state(B):
             assert e.value.status == 1
     finally:
         B.st_mg_destroy(h)
+
+
+@pytest.mark.parametrize("kind,n_refine,nsl,p,bc", [("two_tet", 3, 2, 1, 0), ("cube5", 3, 2, 0, 0),
+                                                    ("kuhn2_jitter", 2, 2, 1, 1)])
+def test_general_mesh_setup_matches_oracle(B, kind, n_refine, nsl, p, bc):
+    """General start mesh refined uniformly: meshes, unknowns, matrices, P_x (bit-exact:
+    dyadic) and the slab factors agree with the oracle's independent construction."""
+    from helpers import oracle_mg_mesh
+    from paper_1911_09548_gb300 import SpaceTimeSolver
+    xyz, tets = st_inputs.start_mesh(kind, 0)
+    nt = len(tets) * 8 ** n_refine
+    nu, sigma = st_inputs.materials_tets(nt, "two_material", 1)
+    S = SpaceTimeSolver(0, nu, sigma, 1.0, 8, p, n_space_levels=nsl, host_only=True, coarsen=2, bc=bc,
+                        mesh=(xyz, tets, n_refine))
+    sl, tl, mg = oracle_mg_mesh(xyz, tets, n_refine, nsl, nu, sigma, 1.0, 8, p, coarsen=2, bc=bc)
+    assert [(L["space_level"], L["N_t"]) for L in S.levels] == [(t.s, t.N_t) for t in tl]
+    for s in range(nsl):
+        m = sl[s].mesh
+        assert np.array_equal(S.debug(1, s).reshape(-1, 2), m.edges)
+        assert np.array_equal(S.debug(2, s), m.interior_edges)
+        assert np.array_equal(S.debug(3, s), m.interior_verts)
+        M = sl[s].M.tocsr(); M.sort_indices()
+        K = sl[s].K.tocsr(); K.sort_indices()
+        rp, cols = S.debug(4, s), S.debug(5, s)
+        Ml = sp.csr_matrix((S.debug(6, s), cols, rp), shape=M.shape)
+        Kl = sp.csr_matrix((S.debug(7, s), cols, rp), shape=K.shape)
+        assert abs(Ml - M).max() <= 1e-13 * abs(M).max()
+        assert abs(Kl - K).max() <= 1e-13 * abs(K).max()
+        Kn = sl[s].Kn.tocsr()
+        knl = sp.csr_matrix((S.debug(11, s), S.debug(10, s), S.debug(9, s)), shape=Kn.shape)
+        assert abs(knl - Kn).max() <= 1e-12 * abs(Kn).max()
+    P = sl[0].Px
+    assert np.array_equal(S.debug(12), P.indptr) and np.array_equal(S.debug(13), P.indices)
+    assert np.array_equal(S.debug(14), P.data)
+    rng = np.random.default_rng(0)
+    for lvl, L in enumerate(S.levels):
+        r = rng.normal(size=(L["n_edge"], L["N_t"] * (p + 1)))
+        assert rel(from_lib(S.host_slab_solve(r, lvl), p + 1), mg.slabs[lvl].solve(from_lib(r, p + 1))) < 1e-12
+    S.close()
+
+
+def test_general_mesh_rejected_when_invalid(B):
+    xyz, tets = st_inputs.start_mesh("two_tet", 0)
+    opt = B.st_mg_default_options()
+    nu, sigma = st_inputs.materials_tets(2 * 8 ** 3, "unit")
+    for bad_tets, n_refine, nsl in ((np.array([[0, 1, 2, 2], [0, 1, 2, 4]]), 3, 1),     # repeated vertex
+                                    (np.array([[0, 1, 2, 7], [0, 1, 2, 4]]), 3, 1),     # id out of range
+                                    (tets, 3, 5),                                       # too many levels
+                                    (tets, 1, 1)):                                      # no interior unknowns
+        n = len(bad_tets) * 8 ** n_refine
+        prob = B.make_problem(0, nsl, nu[:n], sigma[:n], 1.0, 4, 0, mesh=(xyz, bad_tets, n_refine))
+        with pytest.raises(B.StMgError) as e:
+            B.st_mg_setup_host(prob, opt)
+        assert e.value.status == 1
+    flat = xyz.copy(); flat[3] = [0.5, 0.5, 0.0]                                          # zero volume
+    prob = B.make_problem(0, 1, nu, sigma, 1.0, 4, 0, mesh=(flat, tets, 3))
+    with pytest.raises(B.StMgError):
+        B.st_mg_setup_host(prob, opt)
