@@ -37,8 +37,9 @@ UNIT = "DoF/s"
 CPU_SAMPLE_SLABS = 16
 # DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
 # this workload, from one ncu capture (profiles/sn_slab_solve_kuhn16_dg1_fp64_traffic.md);
-# set to None when those kernels change
-SLAB_SOLVE_TRAFFIC_FP64 = 2.626e9
+# set to None when those kernels or the factor they read change (the factor of the current
+# nested-dissection ordering has not been captured yet)
+SLAB_SOLVE_TRAFFIC_FP64 = None
 
 
 def smoothed_per_cycle(dofs, nu_pre, nu_post):
@@ -391,6 +392,8 @@ def main():
     ap.add_argument("--split-waves", default="",
                     help="comma-separated tiled / split-K threshold per time level, set after setup "
                          "(repeats an autotuned run's choice, e.g. under a profiler)")
+    ap.add_argument("--nd-leaf", type=int, default=0,
+                    help="largest leaf of the slab matrices' nested dissection (0: the library default)")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
@@ -453,7 +456,7 @@ def main():
     t0 = time.time()
     S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
                              nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec,
-                             autotune=args.autotune)
+                             autotune=args.autotune, nd_leaf=args.nd_leaf)
     if args.split_waves:
         for l, w in enumerate(int(v) for v in args.split_waves.split(",")):
             stmg.st_mg_set_split_waves(S.h, l, w)
@@ -466,12 +469,21 @@ def main():
     if args.mode == "slab":
         r = S.residual(f, x)
         y = S.zeros()
+        stmg.st_mg_slab_solve(S.h, 0, r, y)
         torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("slab_solves")   # lets a profiler select these launches
+        e0.record(stream)
         for _ in range(2):
             stmg.st_mg_slab_solve(S.h, 0, r, y)
+        e1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
+        st = stmg.st_mg_factor_stats(S.h, 0)
+        if rank == 0:
+            print(json.dumps({"mode": "slab", "slab_prec": args.slab_prec, "nd_leaf": args.nd_leaf,
+                              "slab_solve_ms": e0.elapsed_time(e1) / 2, "setup_s": setup_s,
+                              "split_waves_per_level": split_waves, **st}))
         S.close()
         return 0
 
@@ -670,7 +682,8 @@ def main():
                        "dofs": n_dof, "parallelism": f"replicas x{world}",
                        "split_waves_per_level": split_waves,
                        "autotune": "given" if args.split_waves else bool(args.autotune),
-                       "l2": "inputs larger than L2 (f, x 108 MB each; slab factors 0.27 GB per level)"},
+                       "l2": "inputs larger than L2 (129 MB): f and x %.0f MB each, finest slab factor "
+                             "%.2f GB, all read in every V-cycle" % (n_dof * 8 / 1e6, st["factor_bytes"] / 1e9)},
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),
             "setup_s": setup_s,

@@ -150,9 +150,13 @@ typedef struct {
                                 share one device copy; 0 (default): the handle owns its factors */
     int32_t autotune;        /* 1: at setup, time each time level's slab solve for several tiled /
                                 split-K thresholds (a tree depth whose tiles fill fewer than w waves
-                                of the SMs runs split-K; w in {0, 1, 2, 4, 8}) and keep the fastest
+                                of the SMs runs split-K; w in {0, 1, 2, 4, 8, 16, 32}) and keep the fastest
                                 per level (results change at rounding level, by the summation order
                                 of the chosen kernels); 0 (default): w = 2 */
+    int32_t nd_leaf;         /* nested dissection of the slab matrices stops at sets of at most this
+                                many unknowns (the leaf supernodes); 0 (default): 64.  Larger leaves
+                                mean a shallower tree (fewer dependent depths in each slab solve) and
+                                more fill */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

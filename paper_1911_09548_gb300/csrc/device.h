@@ -15,6 +15,10 @@ struct DevNode {
   int64_t w_off, row_off, u_off, g_off;
 };
 
+// Row tile height of the supernodal products (tiles are built on the host with it).
+constexpr int kSnBM = 64;
+constexpr int kSnBmFP64 = 16;   // tile rows of the FP64 factors' tiled path (DevFactor::bm)
+
 // Factor of one matrix (slab matrix of a time level, or K_n of a space level).
 // T = memory type of right-hand sides and pivots: double (real symmetric), double2
 // (complex symmetric, x = re, y = im), or float / float2 (mixed precision);
@@ -32,6 +36,7 @@ struct DevFactor {
   // per depth d: tiles [tile_off[d], tile_off[d+1]) as (node, row tile)
   int2* fwd_tiles = nullptr;
   int2* bwd_tiles = nullptr;
+  int32_t bm = kSnBM;             // rows per tile of fwd_tiles / bwd_tiles
   int64_t* h_fwd_off = nullptr;   // host arrays, size max_depth + 2
   int64_t* h_bwd_off = nullptr;
   int64_t u_rows = 0;
@@ -90,8 +95,6 @@ constexpr int kSkMaxRhsR = 32;
 int64_t launch_count();
 void count_launches(int64_t n);
 
-// Row tile height of the supernodal products (tiles are built on the host with it).
-constexpr int kSnBM = 64;
 
 // ---- supernodal solve: X = A^{-1} Q on `nrhs` columns, leading dimension ld.
 // Q (in) is overwritten by X (out); Z and U are workspaces ([n*ld], [u_rows*ld]).

@@ -407,7 +407,8 @@ void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<floa
 }
 
 template <typename T, typename DT, typename WT>
-void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh) {
+void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh,
+                     int bm = kSnBM) {
   std::vector<int64_t>& fo = Lh.fo;
   std::vector<int64_t>& bo = Lh.bo;
   D.n = F.n;
@@ -419,6 +420,7 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
     nodes[s] = DevNode{a.col0, a.nc, a.nr, 0, a.w_off, a.row_off, a.u_off, F.gather_off[s]};
   }
   std::vector<int2> ft, bt;
+  D.bm = bm;
   fo.assign(F.max_depth + 2, 0);
   bo.assign(F.max_depth + 2, 0);
   for (int d = 0; d <= F.max_depth; ++d) {
@@ -427,7 +429,7 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
     for (size_t s = 0; s < F.nodes.size(); ++s) {
       const auto& a = F.nodes[s];
       if (a.depth != d) continue;
-      const int mf = (a.nc + a.nr + kSnBM - 1) / kSnBM, mb = (a.nc + kSnBM - 1) / kSnBM;
+      const int mf = (a.nc + a.nr + bm - 1) / bm, mb = (a.nc + bm - 1) / bm;
       for (int t = 0; t < mf; ++t) ft.push_back(make_int2((int)s, t));
       for (int t = 0; t < mb; ++t) bt.push_back(make_int2((int)s, t));
     }
@@ -872,7 +874,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
-      (op->autotune != 0 && op->autotune != 1) ||
+      (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = gm ? ((int64_t)gm->n_tet << (3 * gm->n_refine)) : (int64_t)6 * n * n * n;
@@ -1025,8 +1027,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     char buf[192];
     for (size_t l = 0; l < H.lv.size(); ++l) {
       const auto& L = H.lv[l];
-      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d tau%a mat%016llx", H.device, n, L.s,
-                    pr->degree, L.prec, L.tau, (unsigned long long)H.mat_hash);
+      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d tau%a mat%016llx", H.device, n, L.s,
+                    pr->degree, L.prec, op->nd_leaf > 0 ? op->nd_leaf : 64, L.tau, (unsigned long long)H.mat_hash);
       lkey[l] = buf;
     }
     for (size_t sl = 0; sl < H.space.size(); ++sl) {
@@ -1055,6 +1057,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   }
   // ---- factorisations (all levels concurrently; cached ones skipped)
   const int nthr = hw_threads(op->setup_threads);
+  const int leaf = op->nd_leaf > 0 ? op->nd_leaf : 64;
   std::vector<std::string> errs(H.lv.size() + H.space.size());
   std::vector<int> rcs(errs.size(), 0);
   {
@@ -1079,12 +1082,12 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
           if (pr->degree == 0) {
             std::vector<double> v(S.M.val.size());
             for (size_t q = 0; q < v.size(); ++q) v[q] = S.M.val[q] + L.tau * S.K.val[q];
-            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, 64, L.fr, errs[j], inner);
+            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, leaf, L.fr, errs[j], inner);
           } else {
             const double mr = 2.0 / L.tau, mi = r2 / L.tau;   // mu = (2 + i sqrt2) / tau
             std::vector<cplx> v(S.M.val.size());
             for (size_t q = 0; q < v.size(); ++q) v[q] = cplx(S.K.val[q] + mr * S.M.val[q], mi * S.M.val[q]);
-            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, 64, L.fc, errs[j], inner);
+            rcs[j] = factor_nd_threads(S.M, v, S.ecoord, leaf, L.fc, errs[j], inner);
           }
         } else {
           auto& S = H.space[j - H.lv.size()];
@@ -1112,7 +1115,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
 // with the slab workspace as input (the values do not affect the time).  Levels whose
 // solve runs split-K throughout (few right-hand sides) have nothing to choose.
 void autotune_split(Handle& H) {
-  const int cand[] = {0, 1, 2, 4, 8};
+  const int cand[] = {0, 1, 2, 4, 8, 16, 32};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1188,7 +1191,7 @@ int setup_device(Handle& H) {
     if (!S.nf) {
       auto N = std::make_shared<NodalFactor>();
       N->mem.n_sm = H.n_sm;
-      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists);
+      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists, kSnBmFP64);
       if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists);
       if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists);
       N->u_rows = N->kn.u_rows;
@@ -1226,7 +1229,7 @@ int setup_device(Handle& H) {
           F->max_items = F->drd.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         } else {
-          make_dev_factor(F->mem, L.fr, F->dr, F->lists);
+          make_dev_factor(F->mem, L.fr, F->dr, F->lists, kSnBmFP64);
           F->max_items = F->dr.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         }
@@ -1270,7 +1273,7 @@ int setup_device(Handle& H) {
           F->max_items = F->dcd.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         } else {
-          make_dev_factor(F->mem, L.fc, F->dc, F->lists);
+          make_dev_factor(F->mem, L.fc, F->dc, F->lists, kSnBmFP64);
           F->max_items = F->dc.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         }
@@ -1496,6 +1499,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->persistent_split = 0;
   o->factor_cache = 0;
   o->autotune = 0;
+  o->nd_leaf = 0;
   return ST_MG_OK;
 }
 

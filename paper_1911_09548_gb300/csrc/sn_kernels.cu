@@ -176,13 +176,17 @@ struct PolBF16C {
   static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
 };
 
-constexpr int BM = kSnBM;   // rows of W per block
 constexpr int BK = 16;      // depth of one shared-memory stage
 constexpr int NT = 256;     // threads: 16 x 16, micro-tile rows ty + 16 i, cols tx + 16 j
-constexpr int TM = BM / 16;
 
 // ---------------------------------------------------------------- tiled path
-template <typename P, int BN>
+// BM rows of W (forward) or output rows (backward) per block, BN right-hand sides.  The
+// factor's tile lists are built for its BM (DevFactor::bm): 64 for the FP32 / BF16 /
+// double-float factors, 16 for the FP64 ones, whose kernels are bound by the FP64 pipe,
+// so that small supernodes waste few multiply-adds on padded rows and on the zero
+// triangle of L11^{-1} (shared-memory and L2 traffic per multiply-add rise, but far
+// below what that pipe's rate leaves room for).
+template <typename P, int BN, int BM>
 __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ nodes,
                                                    const typename P::WT* __restrict__ W,
                                                    const typename P::S* __restrict__ Dinv,
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
   using S = typename P::S;
   using A = typename P::A;
   constexpr int TN = BN / 16;
+  constexpr int TM = BM / 16;
   __shared__ A As[BK][BM];
   __shared__ A Bs[BK][BN];
   const int2 tl = tiles[blockIdx.x];
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
   }
 }
 
-template <typename P, int BN>
+template <typename P, int BN, int BM>
 __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ nodes,
                                                     const typename P::WT* __restrict__ W,
                                                     const int32_t* __restrict__ rows,
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
   using S = typename P::S;
   using A = typename P::A;
   constexpr int TN = BN / 16;
+  constexpr int TM = BM / 16;
   __shared__ A As[BK][BM];
   __shared__ A Bs[BK][BN];
   const int2 tl = tiles[blockIdx.x];
@@ -662,7 +668,7 @@ cudaError_t sn_solve_skinny(const DevFactor<typename P::S, typename P::WT>& F, t
 // Tiled products for many right-hand sides; a depth whose tile grid would not
 // fill two waves of the GPU (the few large supernodes near the root) goes through
 // the split-K kernels instead, with NBK right-hand sides per column block.
-template <typename P, int BN, int NBK>
+template <typename P, int BN, int NBK, int BM>
 cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
                            typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy,
                            cudaStream_t st) {
@@ -675,7 +681,7 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
       skinny_depth<P, NBK>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
       continue;
     }
-    k_sn_forward<P, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.fwd_tiles + a,
+    k_sn_forward<P, BN, BM><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.fwd_tiles + a,
                                                                      Q, Z, U, nrhs, ld);
     count_launches(1);
   }
@@ -686,7 +692,7 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
       skinny_depth<P, NBK>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
       continue;
     }
-    k_sn_backward<P, BN><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z, Q,
+    k_sn_backward<P, BN, BM><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z, Q,
                                                                       nrhs, ld);
     count_launches(1);
   }
@@ -694,35 +700,37 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
 }
 
 // Real matrices: column blocks of 4 / 16 / 32 on the split-K path, 64-wide tiles.
-template <typename P>
+template <typename P, int BM = kSnBM>
 cudaError_t solve_real(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
                        typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
   if (Pt && nrhs <= 4) return sn_solve_skinny<P, 4>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= 16) return sn_solve_skinny<P, 16>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= kSkMaxRhsR) return sn_solve_skinny<P, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
-  return sn_solve_tiled<P, 64, kSkMaxRhsR>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  return sn_solve_tiled<P, 64, kSkMaxRhsR, BM>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
 }
 // Complex matrices: column blocks of 2 / 8 / 16, 32-wide tiles.
-template <typename P>
+template <typename P, int BM = kSnBM>
 cudaError_t solve_cplx(const DevFactor<typename P::S, typename P::WT>& F, typename P::S* Q, typename P::S* Z,
                        typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
   if (Pt && nrhs <= 2) return sn_solve_skinny<P, 2>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= 8) return sn_solve_skinny<P, 8>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
   if (Pt && nrhs <= kSkMaxRhsC) return sn_solve_skinny<P, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
-  return sn_solve_tiled<P, 32, kSkMaxRhsC>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
+  return sn_solve_tiled<P, 32, kSkMaxRhsC, BM>(F, Q, Z, U, Pt, nrhs, ld, sy, st);
 }
 
 }  // namespace
 
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,
                           const SkSync& sy, cudaStream_t st) {
-  return solve_real<PolNative<double>>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  return F.bm == kSnBmFP64 ? solve_real<PolNative<double>, kSnBmFP64>(F, Q, Z, U, P, nrhs, ld, sy, st)
+                           : solve_real<PolNative<double>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_cplx(const DevFactor<double2>& F, double2* Q, double2* Z, double2* U, double2* P, int nrhs,
                           int ld, const SkSync& sy, cudaStream_t st) {
-  return solve_cplx<PolC3M>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  return F.bm == kSnBmFP64 ? solve_cplx<PolC3M, kSnBmFP64>(F, Q, Z, U, P, nrhs, ld, sy, st)
+                           : solve_cplx<PolC3M>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
 cudaError_t sn_solve_realf(const DevFactor<float>& F, float* Q, float* Z, float* U, float* P, int nrhs, int ld,
                            const SkSync& sy, cudaStream_t st) {
