@@ -154,9 +154,10 @@ typedef struct {
                                 per level (results change at rounding level, by the summation order
                                 of the chosen kernels); 0 (default): w = 2 */
     int32_t nd_leaf;         /* nested dissection of the slab matrices stops at sets of at most this
-                                many unknowns (the leaf supernodes); 0 (default): 64.  Larger leaves
-                                mean a shallower tree (fewer dependent depths in each slab solve) and
-                                more fill */
+                                many unknowns (the leaf supernodes); 0 (default): 512 with slab_prec 3
+                                (BF16 solves are bound by the latency of the tree's dependent depths),
+                                else 64 (the other solves are bound by arithmetic, so the least fill
+                                wins).  Larger leaves mean a shallower tree and more fill */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

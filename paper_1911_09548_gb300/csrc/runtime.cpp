@@ -843,6 +843,15 @@ double f_norm(Handle& h, const double* f) {
 }
 
 // ---------------------------------------------------------------- setup
+// Leaf size of the slab matrices' nested dissection.  The FP64 / FP32 / double-float
+// solves are bound by arithmetic, so small leaves (least fill) win; the BF16 tensor-core
+// solve is bound by the latency of its dependent tree depths, so it takes large leaves
+// (a shallower tree) at the price of more fill.
+int nd_leaf_of(const st_mg_options& o) {
+  if (o.nd_leaf > 0) return o.nd_leaf;
+  return o.slab_prec == 3 ? 512 : 64;
+}
+
 // smoother pattern: NUL-terminated within the field, letters S and A only
 bool valid_pattern(const char (&p)[16]) {
   const size_t n = strnlen(p, sizeof(p));
@@ -1028,7 +1037,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     for (size_t l = 0; l < H.lv.size(); ++l) {
       const auto& L = H.lv[l];
       std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d tau%a mat%016llx", H.device, n, L.s,
-                    pr->degree, L.prec, op->nd_leaf > 0 ? op->nd_leaf : 64, L.tau, (unsigned long long)H.mat_hash);
+                    pr->degree, L.prec, nd_leaf_of(*op), L.tau, (unsigned long long)H.mat_hash);
       lkey[l] = buf;
     }
     for (size_t sl = 0; sl < H.space.size(); ++sl) {
@@ -1057,7 +1066,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   }
   // ---- factorisations (all levels concurrently; cached ones skipped)
   const int nthr = hw_threads(op->setup_threads);
-  const int leaf = op->nd_leaf > 0 ? op->nd_leaf : 64;
+  const int leaf = nd_leaf_of(*op);
   std::vector<std::string> errs(H.lv.size() + H.space.size());
   std::vector<int> rcs(errs.size(), 0);
   {

@@ -232,8 +232,11 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
       Bs[kk][j] = P::from_s(v);
     }
     __syncthreads();
+    const int klim = kmax - k0;   // the stage's last K column (block-uniform)
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
+      // FP64 tiles (BM == kSnBmFP64) skip the zero-padded K columns: the FP64 pipe bounds them
+      if (BM == kSnBmFP64 && kk >= klim) break;
       A a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
@@ -312,8 +315,11 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
       Bs[kk][j] = P::from_s(v);
     }
     __syncthreads();
+    const int klim = m - k0;      // the stage's last K column (block-uniform)
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
+      // FP64 tiles (BM == kSnBmFP64) skip the zero-padded K columns: the FP64 pipe bounds them
+      if (BM == kSnBmFP64 && kk >= klim) break;
       A a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
