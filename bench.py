@@ -37,9 +37,8 @@ UNIT = "DoF/s"
 CPU_SAMPLE_SLABS = 16
 # DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
 # this workload, from one ncu capture (profiles/sn_slab_solve_kuhn16_dg1_fp64_traffic.md);
-# set to None when those kernels or the factor they read change (the factor of the current
-# nested-dissection ordering has not been captured yet)
-SLAB_SOLVE_TRAFFIC_FP64 = None
+# set to None when those kernels or the factor they read change
+SLAB_SOLVE_TRAFFIC_FP64 = 1.306e9
 
 
 def smoothed_per_cycle(dofs, nu_pre, nu_post):
