@@ -56,6 +56,35 @@ def measured_peak(key: str) -> float:
         return fallback[key]
 
 
+# FP32 FMA rate of the GB300, from its unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def roofline_of(slab_prec: int, achieved: float, fp64_peak: float, slab_ms: float) -> dict:
+    """Roofline object of the finest-level slab solve for the arithmetic it runs in."""
+    counts = "algorithmic flop: 8 per complex multiply-add of the factor"
+    if slab_prec == 3:
+        peak = measured_peak("bf16_tflops")
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "supernodal slab solve, finest level, BF16 on the tensor cores "
+                "(k_tc_assemble, k_sn_tc2, k_sn_tc_reduce)", "achieved_counts": counts + " (4 real BF16 ones)",
+                "peak_source": "measured dense BF16 peak (MEASURED_PEAKS.json)", "ms_per_launch_group": slab_ms}
+    if slab_prec in (1, 2):
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "supernodal slab solve, finest level, %s on the FP32 pipes (k_sn_forward/backward, split-K "
+                "near the root)" % ("FP32" if slab_prec == 1 else "double-float"), "achieved_counts": counts,
+                "peak_source": "FP32 FMA rate from unit counts and clock (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
+                "ms_per_launch_group": slab_ms}
+    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": SLAB_SOLVE_TRAFFIC_FP64,
+            "kernel": ("supernodal slab solve, finest level (k_sn_forward/backward, split-K near the "
+                       "root; complex products with three real multiplications)"),
+            "achieved_counts": counts,
+            "peak_source": "FP64 FMA throughput measured in this run (st_mg_probe_fp64)",
+            "ms_per_launch_group": slab_ms}
+
+
 def reduce_max(value: float, dist=None, device="cpu") -> float:
     """Max over ranks (the slowest replica sets the job's time)."""
     import torch
@@ -686,14 +715,7 @@ def main():
             "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
                                  "v_cycles": solve_iters} if solve_ms else None),
             "setup_s": setup_s,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak,
-                         "traffic": SLAB_SOLVE_TRAFFIC_FP64 if args.slab_prec == 0 else None,
-                         "kernel": ("supernodal slab solve, finest level (k_sn_forward/backward, split-K near the "
-                                    "root; complex products with three real multiplications)"),
-                         "achieved_counts": "algorithmic flop: 8 per complex multiply-add of the factor",
-                         "peak_source": "FP64 FMA throughput measured in this run (st_mg_probe_fp64)",
-                         "ms_per_launch_group": slab_ms},
+            "roofline": roofline_of(args.slab_prec, achieved, fp64_peak, slab_ms),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n_dof * 8,
                     "d2h_bytes_per_step": n_dof * 8 + 16},
             "gpu_launches": launches,
