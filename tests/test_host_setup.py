@@ -201,3 +201,29 @@ def test_general_mesh_rejected_when_invalid(B):
     prob = B.make_problem(0, 1, nu, sigma, 1.0, 4, 0, mesh=(flat, tets, 3))
     with pytest.raises(B.StMgError):
         B.st_mg_setup_host(prob, opt)
+
+
+@pytest.mark.parametrize("p,bc", [(1, 0), (0, 1)])
+def test_kuhn_mesh_as_general_mesh_matches_kuhn_path(B, p, bc):
+    """The Kuhn mesh handed in as a general mesh (coordinates and tets, no refinement) gives
+    the Kuhn path's numbering and unknowns exactly and its matrices and slab solves to
+    rounding: the general builder (face-based boundary, coordinate geometry) against the
+    Kuhn builder (lattice rules, reference element matrices)."""
+    from oracle.mesh import kuhn_mesh
+    from paper_1911_09548_gb300 import SpaceTimeSolver
+    n = 4
+    km = kuhn_mesh(n)
+    nu, sigma = st_inputs.materials(n, "two_material", 4)
+    A = SpaceTimeSolver(n, nu, sigma, 1.0, 8, p, host_only=True, bc=bc)
+    G = SpaceTimeSolver(0, nu, sigma, 1.0, 8, p, host_only=True, bc=bc, mesh=(km.xyz, km.tets, 0))
+    for what in (1, 2, 3, 4, 5, 8, 9, 10):
+        assert np.array_equal(A.debug(what, 0), G.debug(what, 0)), what
+    for what in (6, 7, 11):
+        a, g = A.debug(what, 0), G.debug(what, 0)
+        assert np.abs(a - g).max() <= 1e-13 * np.abs(a).max(), what
+    rng = np.random.default_rng(5)
+    for lvl, L in enumerate(A.levels):
+        r = rng.normal(size=(L["n_edge"], L["N_t"] * (p + 1)))
+        assert rel(G.host_slab_solve(r, lvl), A.host_slab_solve(r, lvl)) < 1e-12
+    A.close()
+    G.close()
