@@ -74,7 +74,8 @@ typedef struct {
     int32_t n_vert;          /* vertices of the start mesh (>= 4) */
     int32_t n_tet;           /* tets of the start mesh (>= 1) */
     const double* xyz;       /* host [n_vert * 3] coordinates */
-    const int32_t* tet;      /* host [n_tet * 4] vertex ids in [0, n_vert), distinct per tet */
+    const int32_t* tet;      /* host [n_tet * 4] vertex ids in [0, n_vert), distinct per tet; every
+                                vertex belongs to some tet */
     int32_t n_refine;        /* refinements to the finest mesh (0 .. 8; n_tet 8^n_refine <= 2^28) */
 } st_mg_mesh;
 

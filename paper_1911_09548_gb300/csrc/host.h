@@ -66,8 +66,8 @@ extern const int kLocalEdge[6][2];
 // nodal matrix -- G annihilates constants, so the correction G z is unchanged)
 void build_kuhn(int n, TetMesh& m, int bc = 0);
 // General mesh from coordinates and tets (vertex order kept).  Returns 0, or 1 with a
-// message in err for an invalid mesh (index out of range, repeated vertex, zero volume,
-// a face shared by more than two tets).
+// message in err for an invalid mesh (index out of range, a vertex in no tet, repeated
+// vertex, zero volume, a face shared by more than two tets).
 int build_general(int32_t nv, const double* xyz, int64_t nt, const int32_t* tets, int bc, TetMesh& m,
                   std::string& err);
 // Red refinement of a general mesh (child k of tet t is tet 8 t + k; include/st_mg.h).

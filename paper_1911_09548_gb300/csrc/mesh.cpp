@@ -208,8 +208,13 @@ int build_general(int32_t nv, const double* xyz, int64_t nt, const int32_t* tets
   m.nt = nt;
   m.xyz.assign(xyz, xyz + (int64_t)nv * 3);
   m.tet_vert.assign(tets, tets + nt * 4);
-  for (int64_t q = 0; q < nt * 4; ++q)
+  std::vector<char> used(nv, 0);
+  for (int64_t q = 0; q < nt * 4; ++q) {
     if (m.tet_vert[q] < 0 || m.tet_vert[q] >= nv) { err = "mesh: vertex id out of range"; return 1; }
+    used[m.tet_vert[q]] = 1;
+  }
+  for (int32_t v = 0; v < nv; ++v)
+    if (!used[v]) { err = "mesh: a vertex belongs to no tet"; return 1; }
   for (int64_t t = 0; t < nt; ++t) {
     const int32_t* tv = &m.tet_vert[t * 4];
     for (int a = 0; a < 4; ++a)

@@ -197,6 +197,11 @@ def test_general_mesh_rejected_when_invalid(B):
         with pytest.raises(B.StMgError) as e:
             B.st_mg_setup_host(prob, opt)
         assert e.value.status == 1
+    extra = np.vstack([xyz, [[2.0, 2.0, 2.0]]])                                         # unused vertex
+    prob = B.make_problem(0, 1, nu, sigma, 1.0, 4, 0, mesh=(extra, tets, 3))
+    with pytest.raises(B.StMgError) as e:
+        B.st_mg_setup_host(prob, opt)
+    assert e.value.status == 1
     flat = xyz.copy(); flat[3] = [0.5, 0.5, 0.0]                                          # zero volume
     prob = B.make_problem(0, 1, nu, sigma, 1.0, 4, 0, mesh=(flat, tets, 3))
     with pytest.raises(B.StMgError):
