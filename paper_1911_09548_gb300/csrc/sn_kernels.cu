@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
 
 // ---------------------------------------------------------------- split-K path
 // With few right-hand sides (coarse time levels have 1..16 slabs), or at the few
-// large supernodes near the root, 64 x 32 tiles leave most of the GPU idle and the
-// top supernodes serialise on their long K loops.  Here every item is kSkRows rows
+// large supernodes near the root, the tiles of the tiled path leave most of the GPU
+// idle and the top supernodes serialise on their long K loops.  Here every item is kSkRows rows
 // x one K chunk of kSkK columns x one column block of NB right-hand sides (one row
 // per thread, NB accumulators); a second kernel sums the chunks of each row in a
 // fixed order (in the memory type S) and applies the epilogue.
