@@ -193,6 +193,7 @@ void gemm_sub(const T* A, int64_t lda, const T* B, int64_t bk, int64_t bc, T* C,
 }
 
 constexpr int64_t kPanel = 64;   // panel width of the blocked LDL^T
+constexpr int64_t kFrontPerThread = 1000;   // largest front order factored by a single thread
 constexpr int64_t kColGroup = 16;   // columns per parallel task
 
 // Partial LDL^T of the dense front F (m x m, column-major, lower triangle valid):
@@ -496,8 +497,13 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
   }
 
   // ---------------- numeric multifrontal factorisation, one tree depth at a time
-  // (supernodes of one depth are independent; deep depths run one supernode per
-  // thread, the few large fronts near the root use all threads inside the front)
+  // (supernodes of one depth are independent; a depth with at least one supernode per
+  // thread and fronts of at most kFrontPerThread rows runs one supernode per thread,
+  // otherwise the supernodes go one after another with all threads inside each front:
+  // a large front factored by one thread streams its panels from memory and left the
+  // whole depth waiting on the slowest thread, at 1/3 of the inner-parallel rate.
+  // Either way every entry is computed in the same order, so the factor does not
+  // depend on the schedule)
   std::vector<std::vector<T>> upd(nn);
   std::vector<std::vector<int>> by_depth(F.max_depth + 1);
   for (int s = 0; s < nn; ++s) by_depth[F.nodes[s].depth].push_back(s);
@@ -564,7 +570,9 @@ int factor_nd_threads(const Csr& A, const std::vector<T>& val, const NDCoords& c
 
   for (int d = F.max_depth; d >= 0; --d) {
     const auto& lst = by_depth[d];
-    if ((int)lst.size() >= nthr || nthr == 1) {
+    int64_t mmax = 0;
+    for (int s : lst) mmax = std::max<int64_t>(mmax, (int64_t)F.nodes[s].nc + F.nodes[s].nr);
+    if (((int)lst.size() >= nthr && mmax <= kFrontPerThread) || nthr == 1) {
       pool.run((int64_t)lst.size(), [&](int64_t i) { factor_node(lst[i], nullptr); });
     } else {
       for (int s : lst) factor_node(s, &pool);
