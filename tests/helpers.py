@@ -21,8 +21,17 @@ def from_lib(v, q):
 
 
 def rel(a, b):
+    """Relative difference of a from b, the larger of the norm-wise ||a - b|| / ||b|| and
+    the element-wise max |a - b| / max |b|: a block of wrong entries that a norm would
+    average away (one bad supernode row block, one slab) still shows in the second."""
+    a = np.asarray(a)
+    b = np.asarray(b)
     nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+    mb = np.max(np.abs(b)) if b.size else 0.0
+    d = a - b
+    norm_wise = np.linalg.norm(d) / (nb if nb > 0 else 1.0)
+    elem_wise = (np.max(np.abs(d)) if d.size else 0.0) / (mb if mb > 0 else 1.0)
+    return max(norm_wise, elem_wise)
 
 
 def oracle_mg(n, nsl, nu, sigma, T, N_t, p, coarsen=0, max_levels=0, nu_pre=1, nu_post=1, lambda_crit=0.1,

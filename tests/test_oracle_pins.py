@@ -309,6 +309,56 @@ def test_space_load_constant_field():
     assert abs(u @ b - c @ c2) < 1e-13
 
 
+
+def _psi(x, exc):
+    """The excitation's vector potential psi(x) = sum_m a_m sin(pi k_m . x + phi_m), the
+    configuration's definition of the source (J = g(t) curl psi), written out here."""
+    out = np.zeros_like(x)
+    for a, k, ph in zip(exc["a"], exc["k"], exc["phase"]):
+        out += np.sin(np.pi * x @ k + ph)[:, None] * a[None, :]
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_source_space_is_curl_of_potential(seed):
+    """The source j = curl psi (Section 3 source, div-free by construction): the oracle's
+    closed form against central differences of psi at random points.  A swapped cross
+    product (j = -curl psi), a dropped pi or a wrong phase fails this."""
+    exc = st_inputs.excitation(seed)
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    x = rng.uniform(0.0, 1.0, size=(40, 3))
+    h = 1e-5
+    d = np.zeros((3, 40, 3))          # d[j] = d psi / d x_j
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        d[j] = (_psi(x + e, exc) - _psi(x - e, exc)) / (2 * h)
+    curl = np.stack([d[1][:, 2] - d[2][:, 1], d[2][:, 0] - d[0][:, 2], d[0][:, 1] - d[1][:, 0]], axis=1)
+    from oracle.load import source_space
+    j = source_space(x, exc)
+    assert np.max(np.abs(j - curl)) <= 1e-6 * np.max(np.abs(curl))
+    # and its divergence vanishes (central differences of j itself)
+    div = sum((source_space(x + h * np.eye(3)[i], exc)[:, i] - source_space(x - h * np.eye(3)[i], exc)[:, i])
+              / (2 * h) for i in range(3))
+    assert np.max(np.abs(div)) <= 1e-5 * np.max(np.abs(j)) * np.pi * 3
+
+
+def test_space_load_of_divergence_free_source_is_orthogonal_to_gradients():
+    """For div j = 0 and an interior vertex v, (G^T b)_v = int j . grad phi_v = -int div j phi_v = 0
+    (phi_v vanishes on the boundary; the gradients of the nodal basis are the columns of G in
+    the edge basis).  With the fixed degree-2 rule the identity holds up to quadrature error,
+    which must shrink under refinement (at least 4x per halving of h)."""
+    exc = st_inputs.excitation(3)
+    ratios = []
+    for n in (4, 8):
+        m = kuhn_mesh(n)
+        b = space_load(m, exc)
+        G = discrete_gradient(m)
+        gtb = G.T @ b
+        ratios.append(np.linalg.norm(gtb) / (abs(G).T @ abs(b)).max())
+    assert ratios[0] < 0.05 and ratios[1] < ratios[0] / 4, ratios
+
+
 # ---------------------------------------------------------------- multigrid
 def test_two_grid_config_small_converges_to_time_stepping():
     n, N_t = 4, 16
@@ -328,13 +378,29 @@ def test_coarsening_rule_values():
     """lambda = min(nu/sigma) tau / h_T^2 with h_T = sqrt(3)/n (longest Kuhn edge)."""
     nu, sigma = st_inputs.materials(16, "two_material", 0)
     lam = coarsening_lambda(16, 1.0 / 256, nu, sigma)
-    assert abs(lam - 1e-3 / sigma[nu < 1].max() / 256 / (3.0 / 256)) < 1e-15 or lam < 1e-4
+    assert abs(lam - 1e-3 / sigma[nu < 1].max() / 256 / (3.0 / 256)) < 1e-15
     tl = build_time_hierarchy(256, 1.0, 16, 3, nu, sigma)
     assert all(l.s == 0 for l in tl) and [l.N_t for l in tl][-1] == 1   # never coarsens space
     nu1, s1 = st_inputs.materials(16, "unit")
     tl = build_time_hierarchy(16, 1.0, 16, 3, nu1, s1)
     # lambda at level 0: (1/16) / (3/256) = 5.33 >= 0.1 -> coarsen space at once
     assert [(l.s, l.N_t) for l in tl][:3] == [(0, 16), (1, 8), (2, 4)]
+
+
+
+def test_coarsening_rule_uses_longest_tet_edge():
+    """eq. CoarseningRule with h_T the longest edge of the tet (sqrt(3)/n on every Kuhn tet,
+    the body diagonal of a cube).  Unit materials on 8^3 with tau = 0.04 h_T^2 give
+    lambda = 0.04, 0.08, 0.16 on time levels 0, 1, 2: space coarsens first when leaving
+    level 2.  The cube edge 1/n or its face diagonal as h_T (lambda 3x or 1.5x larger)
+    would coarsen space one or two levels earlier."""
+    n = 8
+    nu, sigma = st_inputs.materials(n, "unit")
+    hT2 = 3.0 / n ** 2
+    tau = 0.04 * hT2
+    tl = build_time_hierarchy(16, 16 * tau, n, 2, nu, sigma)
+    assert [(l.s, l.N_t) for l in tl][:4] == [(0, 16), (0, 8), (0, 4), (1, 2)]
+    assert abs(coarsening_lambda(n, tau, nu, sigma) - 0.04) < 1e-14
 
 
 @pytest.mark.slow
