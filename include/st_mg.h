@@ -333,6 +333,16 @@ int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves);
  * graph, which the next V-cycle re-captures.  ST_MG_ERR_INVALID_ARG outside the range. */
 int st_mg_set_split_waves(st_mg_t h, int32_t level, int32_t waves);
 
+/* How a BF16 slab factor (slab_prec 3, DG(1)) is applied on time level `level`:
+ * mode 0 (default) the tensor-core kernels (tcgen05); mode 1 the same factor on the CUDA
+ * cores with the same operand rounding -- the gathered FP32 right-hand sides rounded to
+ * BF16 where they enter each product, products and sums in FP32, every tree depth tiled
+ * -- so that the two differ only in the FP32 summation order.  Mode 1 is the element-wise
+ * reference the tensor-core kernels are tested against (eq. StandardSmoother's slab
+ * inverse in either case); it is slower.  Drops the captured V-cycle graph.
+ * ST_MG_ERR_INVALID_ARG if the level has no BF16 factor or mode is not 0 or 1. */
+int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);
 
@@ -344,23 +354,28 @@ int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* 
 
 /* Allocation-free l2 norm: norm_dev[0] = ||v||_2 for the n doubles at v_dev, queued
  * on `stream` (a cudaStream_t; NULL = legacy default stream).  The paper has no
- * counterpart; this is a library service.  It is the library's deterministic
- * two-stage norm (the solver's stopping test) for callers that cannot allocate
- * device memory at the point where they need the norm -- a control loop that must
- * not stall on cudaMalloc/cudaFree (both may synchronise the whole device), or a
- * host framework that owns the device allocator and forbids allocations by
- * libraries.  It needs no handle and calls no cudaMalloc, cudaFree or other
- * allocating routine.
- * Scratch: one partial sum per 4096 elements lives in a file-scope device array of
- * 32768 doubles (256 KiB) that every GPU which loads the library holds until the
- * process exits; hence n <= 134217728 (larger n returns ST_MG_ERR_INVALID_ARG).
+ * counterpart; this is a library service for callers that cannot allocate device
+ * memory at the point where they need the norm -- a control loop that must not stall
+ * on cudaMalloc/cudaFree (both may synchronise the whole device), or a host framework
+ * that owns the device allocator and forbids allocations by libraries.  It needs no
+ * handle and calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its reduction is its own fixed-order two-stage sum (one partial per 4096
+ * consecutive elements, then the partials in index order): deterministic for a given
+ * n, and equal to the solver's norm (st_mg_residual's) only up to rounding, since the
+ * two sum in different orders.
+ * Scratch: the partial sums live in a file-scope device array of 32768 doubles
+ * (256 KiB) that every GPU which loads the library holds until the process exits;
+ * hence n <= 134217728 (larger n returns ST_MG_ERR_INVALID_ARG before any launch).
+ * n = 0 writes 0.
  * The first call on a device, with that device current, looks the array up with
- * cudaGetSymbolAddress; make that first call before any stream capture.  Every call
- * shares the array and it keeps the last call's partial sums (each call overwrites
- * the entries it reads), so calls that overlap on the GPU (other streams, other
- * threads, before an earlier call finished) race and must be serialised by the
- * caller.  v_dev and norm_dev: device pointers, 8-byte aligned; the result is
- * written on the stream (read it after synchronising). */
+ * cudaGetSymbolAddress and keeps the address for the life of the process; make that
+ * first call before any stream capture, and do not use the entry point on a device
+ * after cudaDeviceReset (the module is then loaded anew and the kept address is
+ * stale).  Every call shares the array and it keeps the last call's partial sums
+ * (each call overwrites the entries it reads), so calls that overlap on the GPU
+ * (other streams, other threads, before an earlier call finished) race and must be
+ * serialised by the caller.  v_dev and norm_dev: device pointers, 8-byte aligned;
+ * the result is written on the stream (read it after synchronising that stream). */
 int st_mg_norm2_noalloc(const double* v_dev, int64_t n, void* stream, double* norm_dev);
 
 const char* st_mg_strerror(int status);

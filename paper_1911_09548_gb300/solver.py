@@ -123,18 +123,24 @@ class SpaceTimeSolver:
         """Section 5.1's power iteration: V-cycles with f = 0 from a random start; the
         largest per-cycle reduction of the l2 norm is the rate.  Stops when the total
         reduction falls below `floor` (the paper's 1e-100, to avoid underflow).
-        x0: device tensor (modified).  Norms come from the library's own reduction."""
+        x0: device tensor (modified).  Norms come from the handle's own deterministic
+        reduction (st_mg_batch_norms: per-handle scratch, queued on the handle's stream,
+        which the call synchronises before it returns the values; over a batch the norm
+        of the whole vector is the root of the problems' sums of squares)."""
         import torch
         f = self.zeros()
         x = x0
-        nrm = torch.zeros(1, dtype=torch.float64, device=x.device)
-        B.st_mg_norm2_noalloc(x, x.numel(), self.stream, nrm)
-        n0 = nprev = float(nrm.item())
+        # f and x0 were written on torch's current stream; the V-cycles run on the handle's
+        torch.cuda.current_stream().synchronize()
+
+        def norm(v):
+            return float(np.sqrt(np.sum(B.st_mg_batch_norms(self.h, v, self.n_batch) ** 2)))
+
+        n0 = nprev = norm(x)
         rates = []
         for _ in range(max_iter):
             B.st_mg_vcycle(self.h, f, x, False)
-            B.st_mg_norm2_noalloc(x, x.numel(), self.stream, nrm)
-            nx = float(nrm.item())
+            nx = norm(x)
             rates.append(nx / nprev)
             nprev = nx
             if nx == 0.0 or nx / n0 < floor:
