@@ -333,6 +333,40 @@ int st_mg_split_waves(st_mg_t h, int32_t level, int32_t* waves);
  * graph, which the next V-cycle re-captures.  ST_MG_ERR_INVALID_ARG outside the range. */
 int st_mg_set_split_waves(st_mg_t h, int32_t level, int32_t waves);
 
+/* ---- time-slab sharding (Section 2.1: the all-at-once system is split along time into
+ * groups of consecutive slabs, one per process group; only the block-bidiagonal L couples
+ * a group to the one before it, and the time integration Sigma_t / L_t^{-1} of the nodal
+ * correction, eq. AuxNodalSm, is a recurrence across all of them).  A handle set up for
+ * one contiguous slab range (same mesh, materials and tau; n_batch 1) computes its part
+ * with the calls below; the ranks exchange only one slab of x per residual and one slab
+ * of nodal values per time integration (paper_1911_09548_gb300/shard.py does the
+ * exchange over torch.distributed).  No counterpart in the paper's equations beyond the
+ * splitting itself. ---- */
+
+/* out_dev[row * q + i] = v_dev[row][slab * q + i] for every edge row (nodal = 0) or node
+ * row (nodal = 1) of time level `level`: one slab, e.g. the last slab of x that the next
+ * range needs as its halo.  out_dev: device, rows * q doubles. */
+int st_mg_slab_copy(st_mg_t h, int32_t level, int32_t nodal, const double* v_dev, int32_t slab, double* out_dev);
+
+/* r = f - L x on this handle's slab range when the range is preceded by another: slab 0
+ * also receives the coupling -(N_t (x) M) x_prev of the block-bidiagonal L, x_prev_dev the
+ * last slab of x of the range before ([edge * q + i], from st_mg_slab_copy); NULL = this
+ * range starts at t = 0 (same as st_mg_residual).  Needs n_batch 1. */
+int st_mg_residual_halo(st_mg_t h, int32_t level, const double* f_dev, const double* x_dev, const double* x_prev_dev,
+                        double* r_dev);
+
+/* w = L_t^{-1} z (st_mg_time_integrate) continued from w_{-1} = carry_dev[node * q + i],
+ * the state at the end of the preceding ranges (st_mg_time_carry); NULL = zero. */
+int st_mg_time_integrate_carry(st_mg_t h, int32_t level, const double* z_dev, const double* carry_dev,
+                               double* w_dev);
+
+/* The carry into range n_prev from the ranges before it: ends_dev[k][node * q + i] is the
+ * last slab of range k's own L_t^{-1} z computed from a zero carry (k < n_prev, in time
+ * order); c_0 = 0, c_{k+1} = end_k + T c_k with T = -K_t^{-1} N_t (1 for DG(0),
+ * [[1,1],[0,0]] for DG(1), so T^len = T for any range length).  carry_dev: node rows * q.
+ * n_prev = 0 writes zeros. */
+int st_mg_time_carry(st_mg_t h, int32_t level, const double* ends_dev, int32_t n_prev, double* carry_dev);
+
 /* How a BF16 slab factor (slab_prec 3, DG(1)) is applied on time level `level`:
  * mode 0 (default) the tensor-core kernels (tcgen05); mode 1 the same factor on the CUDA
  * cores with the same operand rounding -- the gathered FP32 right-hand sides rounded to

@@ -101,6 +101,11 @@ _SIGS = {
     "st_mg_memory": [_vp, _P(_i64), _P(_i64)],
     "st_mg_split_waves": [_vp, _i32, _P(_i32)],
     "st_mg_set_split_waves": [_vp, _i32, _i32],
+    "st_mg_set_tc_mode": [_vp, _i32, _i32],
+    "st_mg_slab_copy": [_vp, _i32, _i32, _vp, _i32, _vp],
+    "st_mg_residual_halo": [_vp, _i32, _vp, _vp, _vp, _vp],
+    "st_mg_time_integrate_carry": [_vp, _i32, _vp, _vp, _vp],
+    "st_mg_time_carry": [_vp, _i32, _vp, _i32, _vp],
     "st_mg_cache_stats": [_P(_i64), _P(_i32), _P(_i32), _P(_i64), _P(_i64)],
     "st_mg_cache_trim": [_i64, _P(_i64)],
     "st_mg_batch_zero": [_vp, _i32, _vp],
@@ -333,6 +338,11 @@ def st_mg_batch_norms(h, v_dev, n_batch):
     return out
 
 
+def st_mg_check(h):
+    """Raises StMgError(ST_MG_ERR_TIMEOUT) if a bounded device wait of earlier work gave up."""
+    _check(lib().st_mg_check(_vp(h)), "st_mg_check")
+
+
 def st_mg_batch_zero(h, batch, v_dev):
     _check(lib().st_mg_batch_zero(_vp(h), batch, _vp(_addr(v_dev))), "st_mg_batch_zero")
 
@@ -345,6 +355,34 @@ def st_mg_split_waves(h, level):
 
 def st_mg_set_split_waves(h, level, waves):
     _check(lib().st_mg_set_split_waves(_vp(h), level, waves), "st_mg_set_split_waves")
+
+
+def _opt_addr(t):
+    return None if t is None else _vp(_addr(t))
+
+
+def st_mg_slab_copy(h, level, nodal, v_dev, slab, out_dev):
+    _check(lib().st_mg_slab_copy(_vp(h), level, int(nodal), _vp(_addr(v_dev)), slab, _vp(_addr(out_dev))),
+           "st_mg_slab_copy")
+
+
+def st_mg_residual_halo(h, level, f, x, x_prev, r):
+    _check(lib().st_mg_residual_halo(_vp(h), level, _vp(_addr(f)), _vp(_addr(x)), _opt_addr(x_prev),
+                                     _vp(_addr(r))), "st_mg_residual_halo")
+
+
+def st_mg_time_integrate_carry(h, level, z, carry, w):
+    _check(lib().st_mg_time_integrate_carry(_vp(h), level, _vp(_addr(z)), _opt_addr(carry), _vp(_addr(w))),
+           "st_mg_time_integrate_carry")
+
+
+def st_mg_time_carry(h, level, ends, n_prev, carry):
+    _check(lib().st_mg_time_carry(_vp(h), level, _opt_addr(ends) if n_prev > 0 else None, n_prev,
+                                  _vp(_addr(carry))), "st_mg_time_carry")
+
+
+def st_mg_set_tc_mode(h, level, mode):
+    _check(lib().st_mg_set_tc_mode(_vp(h), level, mode), "st_mg_set_tc_mode")
 
 
 def st_mg_memory(h):

@@ -131,6 +131,11 @@ constexpr int kTcCols = 128;
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
                                float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
                                cudaStream_t st);
+// The same BF16 factor applied on the CUDA cores with the tensor-core kernels'
+// operand rounding (right-hand sides rounded to BF16 as they enter each product, FP32
+// accumulation), tiled at every depth: the element-wise reference of those kernels.
+cudaError_t sn_solve_cplx_bf16_cc(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
+                                  int nrhs, int ld, cudaStream_t st);
 // Pipelined tensor-core depth: assemble the right-hand-side tiles of the depth into
 // Bst (gy * max_stage_tiles tiles), then the products with bulk-copied operand tiles.
 cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
@@ -212,6 +217,16 @@ cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const
                      int ncols, cudaStream_t st);
 // w = L_t^{-1} z per node row (DG(0): running sum; DG(1): upwind recurrence).
 cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st);
+// Time-slab sharding: the scan continued from w_{-1} = carry (q values per node row);
+// one slab of every row, out[row q + i] = v[row ld + off + i]; the history term of a
+// range's first slab, r_0 -= (N_t (x) M) xh; the carry into range n_prev from the end
+// states ends[k][row q + i] of the ranges before it.
+cudaError_t time_integrate_carry(const double* z, const double* carry, double* w, int nrows, int N_t, int degree,
+                                 cudaStream_t st);
+cudaError_t slab_copy(const double* v, int64_t ld, int64_t off, int q, int nrows, double* out, cudaStream_t st);
+cudaError_t halo_history(CsrView A, const double* m, const double* xh, double* r, int64_t ld, int degree,
+                         cudaStream_t st);
+cudaError_t time_carry(const double* ends, int n_prev, int nrows, int degree, double* carry, cudaStream_t st);
 // One damped Jacobi sweep on K_n: zo = zi + wgt * D^{-1} (y - K_n zi).
 cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
                          double* zo, int ncols, double wgt, cudaStream_t st);

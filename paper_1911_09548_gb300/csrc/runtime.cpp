@@ -230,6 +230,7 @@ struct st_mg_s {
     std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
     int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
     int split_waves = 2;                                    // tiled / split-K threshold (autotuned)
+    int tc_mode = 0;                                        // BF16 factor: 0 tensor cores, 1 CUDA-core reference
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
   };
@@ -584,7 +585,10 @@ void level_solve(Handle& h, int l, int cnt) {
   auto& L = h.lv[l];
   SkSync sk = h.sk;
   sk.split_waves = L.split_waves;
-  if (L.prec == 3) {
+  if (L.prec == 3 && L.tc_mode == 1) {
+    CK(sn_solve_cplx_bf16_cc(L.fac->dcb, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
+                             static_cast<float2*>(h.sU), cnt, h.ld_slab, h.stream));
+  } else if (L.prec == 3) {
     CK(sn_solve_cplx_bf16(L.fac->dcb, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
                           static_cast<float2*>(h.sU), static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, sk,
                           h.stream));
@@ -1981,6 +1985,80 @@ int st_mg_set_split_waves(st_mg_t h, int32_t level, int32_t waves) {
   if (int rc = check_level(h, level)) return rc;
   if (waves < 0 || waves > 64) return fail(ST_MG_ERR_INVALID_ARG, "split waves outside [0, 64]");
   h->lv[level].split_waves = waves;
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  return ST_MG_OK;
+}
+
+int st_mg_slab_copy(st_mg_t h, int32_t level, int32_t nodal, const double* v_dev, int32_t slab, double* out_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({v_dev, out_dev})) return rc;
+  const auto& L = h->lv[level];
+  if (slab < 0 || slab >= L.N_t * h->B) return fail(ST_MG_ERR_INVALID_ARG, "slab index out of range");
+  return guarded([&]() {
+    const auto& S = h->space[L.s];
+    const int64_t ld = (int64_t)L.N_t * h->B * h->q;
+    CK(slab_copy(v_dev, ld, (int64_t)slab * h->q, h->q, nodal ? S.nn : S.ne, out_dev, h->stream));
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_residual_halo(st_mg_t h, int32_t level, const double* f_dev, const double* x_dev, const double* x_prev_dev,
+                        double* r_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
+  if (x_prev_dev && !aligned16(x_prev_dev)) return fail(ST_MG_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  if (h->B != 1) return fail(ST_MG_ERR_INVALID_ARG, "time-slab sharding takes one problem per handle");
+  return guarded([&]() {
+    Handle& H = *h;
+    op_residual(H, level, f_dev, x_dev, r_dev, nullptr);
+    if (x_prev_dev) {
+      const auto& L = H.lv[level];
+      const auto& S = H.space[L.s];
+      CK(halo_history(view(S), S.Mv, x_prev_dev, r_dev, (int64_t)L.N_t * H.q, H.prob.degree, H.stream));
+    }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_time_integrate_carry(st_mg_t h, int32_t level, const double* z_dev, const double* carry_dev,
+                               double* w_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (int rc = check_ptrs({z_dev, w_dev})) return rc;
+  if (carry_dev && !aligned16(carry_dev)) return fail(ST_MG_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  if (h->B != 1) return fail(ST_MG_ERR_INVALID_ARG, "time-slab sharding takes one problem per handle");
+  return guarded([&]() {
+    Handle& H = *h;
+    if (!carry_dev) {
+      op_time_integrate(H, level, z_dev, w_dev);
+    } else {
+      const auto& L = H.lv[level];
+      CK(time_integrate_carry(z_dev, carry_dev, w_dev, H.space[L.s].nn, L.N_t, H.prob.degree, H.stream));
+    }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_time_carry(st_mg_t h, int32_t level, const double* ends_dev, int32_t n_prev, double* carry_dev) {
+  if (int rc = check_level(h, level)) return rc;
+  if (n_prev < 0) return fail(ST_MG_ERR_INVALID_ARG, "n_prev < 0");
+  if (int rc = check_ptrs({carry_dev})) return rc;
+  if (n_prev > 0)
+    if (int rc = check_ptrs({ends_dev})) return rc;
+  return guarded([&]() {
+    Handle& H = *h;
+    CK(time_carry(ends_dev, n_prev, H.space[H.lv[level].s].nn, H.prob.degree, carry_dev, H.stream));
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode) {
+  if (int rc = check_level(h, level)) return rc;
+  if (mode < 0 || mode > 1) return fail(ST_MG_ERR_INVALID_ARG, "tensor-core mode must be 0 or 1");
+  if (h->lv[level].prec != 3) return fail(ST_MG_ERR_INVALID_ARG, "level has no BF16 factor (slab_prec 3)");
+  h->lv[level].tc_mode = mode;
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;

@@ -176,6 +176,21 @@ struct PolBF16C {
   static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
 };
 
+// BF16 factor and right-hand sides rounded to BF16 where they enter a product, FP32
+// products and sums: the arithmetic of the tensor-core kernels (whose operand tiles
+// hold BF16 copies of the gathered FP32 right-hand sides) on the CUDA cores, as their
+// element-wise reference.  Only the FP32 summation order differs.
+struct PolBF16CR {
+  using S = float2;
+  using WT = __nv_bfloat162;
+  using A = float2;
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ A from_w(WT w) { return __bfloat1622float2(w); }
+  static __device__ __forceinline__ A from_s(S v) { return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y)); }
+  static __device__ __forceinline__ S to_s(A a) { return a; }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
+};
+
 constexpr int BK = 16;      // depth of one shared-memory stage
 constexpr int NT = 256;     // threads: 16 x 16, micro-tile rows ty + 16 i, cols tx + 16 j
 
@@ -766,6 +781,13 @@ cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float
     sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy.err, st);
   }
   return cudaGetLastError();
+}
+
+cudaError_t sn_solve_cplx_bf16_cc(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
+                                  int nrhs, int ld, cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  SkSync none;
+  return sn_solve_tiled<PolBF16CR, 32, kSkMaxRhsC, kSnBM>(F, Q, Z, U, nullptr, nrhs, ld, none, st);
 }
 
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,

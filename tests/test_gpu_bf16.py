@@ -1,10 +1,18 @@
 """BF16 slab solve on the tensor cores (slab_prec = 3, DG(1)).
 
 The case has enough slabs (N_t = 1024, 8 column blocks of 128) that the deep
-tree depths run the tcgen05 kernels and the top ones the split-K kernels.  The
-BF16 factor is a preconditioner-quality inverse: its error is BF16-sized (checked
-against the oracle's exact slab solve), and the V-cycle still converges to the
-FP64 solution because the residual is FP64-accurate and the coarsest solve FP64
+tree depths run the tcgen05 kernels and the top ones the split-K kernels.  Two checks
+of the slab solve itself (eq. StandardSmoother's slab inverse):
+
+  * differential: the tensor-core kernels against the same BF16 factor applied on the
+    CUDA cores with the same operand rounding (st_mg_set_tc_mode 1), element by
+    element, with every depth forced onto the tiled kernels and then onto the split-K
+    kernels.  Only the FP32 summation order differs, so a layout, epilogue or
+    reduction error of even a fraction of a percent shows;
+  * against the oracle's exact slab solve, to a bound set by BF16 rounding.
+
+The BF16 factor is a preconditioner-quality inverse; the V-cycle still converges to
+the FP64 solution because the residual is FP64-accurate and the coarsest solve FP64
 (the nodal correction runs in FP32)."""
 import numpy as np
 import pytest
@@ -32,15 +40,54 @@ def setup():
     S.close()
 
 
+def _solve(stmg, S, r, level):
+    y = S.slab_solve(r, level=level)
+    torch.cuda.synchronize()
+    stmg.st_mg_check(S.h)
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_bf16_tensor_cores_match_cuda_core_reference(setup, level):
+    """k_tc_assemble + k_sn_tc2 (+ k_sn_tc_reduce) against the CUDA-core product kernels
+    on the same BF16 factor and BF16-rounded operands.  Level 0: 1024 right-hand sides
+    (8 column blocks); level 2: 256 (2 column blocks).  Depths forced tiled (threshold
+    0 waves) and forced split-K (64 waves)."""
+    stmg, S, sl, mg, nu, sigma = setup
+    rng = np.random.default_rng(1 + level)
+    L = S.levels[level]
+    ro = rng.normal(size=(L["N_t"], 2, L["n_edge"]))
+    r = torch.from_numpy(to_lib(ro)).cuda()
+    w0 = stmg.st_mg_split_waves(S.h, level)
+    try:
+        stmg.st_mg_set_tc_mode(S.h, level, 1)
+        y_ref = _solve(stmg, S, r, level)
+        stmg.st_mg_set_tc_mode(S.h, level, 0)
+        for waves in (0, 64):
+            stmg.st_mg_set_split_waves(S.h, level, waves)
+            y_tc = _solve(stmg, S, r, level)
+            d = rel(y_tc, y_ref)
+            print(f"bf16 tc vs cuda-core reference, level {level}, split waves {waves}: {d:.3e}")
+            # measured on GB300: 4.6e-4 / 5.3e-4 (a BF16 rounding of a gathered operand flips
+            # where the FP32 sums differ in their last bits); a wrong tile, epilogue row or
+            # partial sum shows at 1e-2 and above
+            assert d < 2e-3, (level, waves, d)
+    finally:
+        stmg.st_mg_set_tc_mode(S.h, level, 0)
+        stmg.st_mg_set_split_waves(S.h, level, w0)
+
+
 def test_bf16_slab_solve_accuracy(setup):
     stmg, S, sl, mg, nu, sigma = setup
     rng = np.random.default_rng(0)
     L = S.levels[0]
     ro = rng.normal(size=(L["N_t"], 2, L["n_edge"]))
-    y = S.slab_solve(torch.from_numpy(to_lib(ro)).cuda(), level=0)
-    torch.cuda.synchronize()
-    err = rel(from_lib(y.cpu().numpy(), 2), mg.slabs[0].solve(ro))
-    assert 1e-6 < err < 5e-2, err
+    y = _solve(stmg, S, torch.from_numpy(to_lib(ro)).cuda(), 0)
+    err = rel(from_lib(y, 2), mg.slabs[0].solve(ro))
+    print(f"bf16 slab solve vs oracle exact slab solve: {err:.3e}")
+    # BF16 keeps 8 significant bits (unit roundoff 2^-9 = 2e-3); the factor and every
+    # depth's gathered right-hand sides are rounded once (measured on GB300: 4.7e-3)
+    assert 1e-6 < err < 1.5e-2, err
 
 
 def test_bf16_solve_reaches_fp64_solution(setup):
