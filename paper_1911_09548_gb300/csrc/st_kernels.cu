@@ -588,8 +588,14 @@ __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __re
     x2[j] = xv;
   }
 }
+// CARRY: the time grid continues an earlier one whose last slab held w_{-1} = carry[v]
+// (q values per node), the state a time-slab shard receives from the shard before it.
+// The recurrence's homogeneous part is T = -K_t^{-1} N_t: 1 for DG(0), [[1,1],[0,0]]
+// for DG(1), both idempotent (T^k = T), so w_n gains T carry for every n: the running
+// sum starts at carry (DG(0)) or at carry_0 + carry_1 (DG(1)).
+template <bool CARRY>
 __global__ void k_time_integrate(const double* __restrict__ z, double* __restrict__ w, int nrows, int N_t,
-                                 int degree) {
+                                 int degree, const double* __restrict__ carry) {
   const int lane = threadIdx.x & 31;
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (v >= nrows) return;
@@ -607,6 +613,7 @@ __global__ void k_time_integrate(const double* __restrict__ z, double* __restric
     if (lane >= o) incl += t;
   }
   double e = incl - s;   // exclusive carry
+  if (CARRY) e += degree == 0 ? carry[v] : carry[2 * v] + carry[2 * v + 1];
   for (int n = n0; n < n1; ++n) {
     if (degree == 0) {
       e += zr[n];
@@ -618,6 +625,63 @@ __global__ void k_time_integrate(const double* __restrict__ z, double* __restric
       e += z0;
     }
   }
+}
+
+// ---- time-slab sharding (the time axis split into contiguous slab ranges, one per
+// rank, Section 2.1's time-parallel groups): the two couplings between ranges.
+// out[row q + i] = v[row ld + off + i]: one slab of every row (the halo a range sends on).
+__global__ void k_slab_copy(const double* __restrict__ v, int64_t ld, int64_t off, int q, int nrows,
+                            double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrows * q) return;
+  out[t] = v[(t / q) * ld + off + t % q];
+}
+
+// r_0 -= (N_t (x) M) xh: the history term of a range's first slab, xh = the last slab of
+// the range before it (DG(0): N_t = -1; DG(1): N_t = [[-1,-1],[1,1]]).
+__global__ void k_halo_history(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ m, const double* __restrict__ xh, double* __restrict__ r,
+                               int64_t ld, int degree) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrows) return;
+  double mx0 = 0.0, mx1 = 0.0;
+  for (int64_t p = rowptr[e]; p < rowptr[e + 1]; ++p) {
+    if (degree == 0) {
+      mx0 = fma(m[p], xh[col[p]], mx0);
+    } else {
+      mx0 = fma(m[p], xh[2 * (int64_t)col[p]], mx0);
+      mx1 = fma(m[p], xh[2 * (int64_t)col[p] + 1], mx1);
+    }
+  }
+  if (degree == 0) {
+    r[e * ld] += mx0;
+  } else {
+    const double s = mx0 + mx1;
+    r[e * ld] += s;
+    r[e * ld + 1] -= s;
+  }
+}
+
+// Carry into range n_prev from the local end states of the ranges before it (exclusive
+// scan over ranges): c_0 = 0, c_{k+1} = e_k + T c_k, T as in k_time_integrate (every
+// range holds at least one slab, so T^{len} = T).  ends[k][v q + i].
+__global__ void k_time_carry(const double* __restrict__ ends, int n_prev, int nrows, int degree,
+                             double* __restrict__ carry) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nrows) return;
+  const int q = degree + 1;
+  double c0 = 0.0, c1 = 0.0;
+  for (int k = 0; k < n_prev; ++k) {
+    const double* ek = ends + ((int64_t)k * nrows + v) * q;
+    if (degree == 0) {
+      c0 = ek[0] + c0;
+    } else {
+      c0 = ek[0] + (c0 + c1);
+      c1 = ek[1];
+    }
+  }
+  carry[(int64_t)v * q] = c0;
+  if (degree == 1) carry[(int64_t)v * q + 1] = c1;
 }
 
 __global__ void k_nodal_jacobi(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -944,7 +1008,26 @@ cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const
   return cudaGetLastError();
 }
 cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st) {
-  if (nrows > 0) { k_time_integrate<<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree); count_launches(1); }
+  if (nrows > 0) { k_time_integrate<false><<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree, nullptr); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t time_integrate_carry(const double* z, const double* carry, double* w, int nrows, int N_t, int degree,
+                                 cudaStream_t st) {
+  if (nrows > 0) { k_time_integrate<true><<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree, carry); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t slab_copy(const double* v, int64_t ld, int64_t off, int q, int nrows, double* out, cudaStream_t st) {
+  const int64_t n = (int64_t)nrows * q;
+  if (n > 0) { k_slab_copy<<<(unsigned)grid1(n, 256), 256, 0, st>>>(v, ld, off, q, nrows, out); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t halo_history(CsrView A, const double* m, const double* xh, double* r, int64_t ld, int degree,
+                         cudaStream_t st) {
+  if (A.nrows > 0) { k_halo_history<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, xh, r, ld, degree); count_launches(1); }
+  return cudaGetLastError();
+}
+cudaError_t time_carry(const double* ends, int n_prev, int nrows, int degree, double* carry, cudaStream_t st) {
+  if (nrows > 0) { k_time_carry<<<grid1(nrows, 128), 128, 0, st>>>(ends, n_prev, nrows, degree, carry); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
