@@ -36,9 +36,18 @@ METRIC = "space-time DoFs smoothed/s"
 UNIT = "DoF/s"
 CPU_SAMPLE_SLABS = 16
 # DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
-# this workload, from one ncu capture (profiles/sn_slab_solve_kuhn16_dg1_fp64_traffic.md);
-# set to None when those kernels or the factor they read change
+# this workload, from one ncu capture of the same kernels and factor; set to None when those
+# kernels or the factor they read change
 SLAB_SOLVE_TRAFFIC_FP64 = 1.306e9
+
+
+def workload_config(world: int = 1) -> dict:
+    """The workload as the bench line names it (both arms)."""
+    W = WORKLOAD
+    return {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
+            "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "materials": W["materials"],
+            "dofs": 26416 * W["N_t"] * (W["degree"] + 1), "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (129 MB): f, x and r 108 MB each, slab factors read in every V-cycle"}
 
 
 def smoothed_per_cycle(dofs, nu_pre, nu_post):
@@ -106,14 +115,13 @@ def replica_value(world: int, per_cycle: float, steps: int, ms_max: float) -> fl
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(nslabs: int, reps: int, seed: int = 0):
-    """Time `reps` block-Jacobi sweeps S of the oracle on `nslabs` slabs of the
-    workload's finest level (16^3, DG(1), tau = 1/256); factorisation excluded."""
-    import numpy as np
-
+def _oracle_setup(seed: int = 0):
+    """The oracle's finest-level slab operator of the workload (16^3, DG(1), tau = 1/256:
+    SciPy SuperLU factor of the real block slab matrix) and its load; run in a process
+    that never touches CUDA."""
     import st_inputs
     from oracle.load import spacetime_load
-    from oracle.spacetime import SlabOperator, build_space_hierarchy, smoother_S
+    from oracle.spacetime import SlabOperator, build_space_hierarchy
 
     W = WORKLOAD
     nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
@@ -121,31 +129,89 @@ def oracle_sample(nslabs: int, reps: int, seed: int = 0):
     t0 = time.time()
     slab = SlabOperator(sl[0], W["degree"], W["T"] / W["N_t"])
     t_setup = time.time() - t0
-    f = spacetime_load(sl[0].mesh, st_inputs.excitation(seed), W["degree"], W["N_t"], W["T"])[:nslabs]
+    f = spacetime_load(sl[0].mesh, st_inputs.excitation(seed), W["degree"], W["N_t"], W["T"])
+    return slab, f, t_setup
+
+
+def _sweep_worker(slab, f, reps, barrier, q):
+    """One forked worker: `reps` oracle block-Jacobi sweeps S on its slabs, timed."""
+    import numpy as np
+
+    from oracle.spacetime import smoother_S
     x = np.zeros_like(f)
+    barrier.wait(timeout=600)
+    t_start = time.perf_counter()
     times = []
     for _ in range(reps):
-        t0 = time.perf_counter()
+        a = time.perf_counter()
         x = smoother_S(slab, f, x, 0.5)
-        times.append(time.perf_counter() - t0)
-    dofs = f.size
-    return {"times": times, "dofs_per_step": dofs, "setup_s": t_setup}
+        times.append(time.perf_counter() - a)
+    q.put((times, t_start, time.perf_counter()))
 
 
-def _oracle_worker(q, nslabs, reps):
+def host_cores() -> int:
     try:
-        q.put(oracle_sample(nslabs, reps))
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(nslabs: int, reps: int, workers: int, go=None):
+    """The oracle as it stands on `workers` host cores: the slab factor is built once
+    (factorisation excluded from the timing), then `workers` forked single-threaded
+    processes each run `reps` sweeps S on their own `nslabs`-slab sample of the finest
+    level (slabs w*nslabs ... of the 256, wrapping), started together behind a barrier.
+    `go` (an Event) delays the timed sweeps, e.g. until a GPU measurement has ended.
+    Returns the per-worker sweep times and the wall time of the parallel section."""
+    import multiprocessing as mp
+
+    slab, f, t_setup = _oracle_setup()
+    if go is not None:
+        go.wait()
+    ctx = mp.get_context("fork")      # this process has no CUDA context: forking it is safe
+    q = ctx.Queue()
+    bar = ctx.Barrier(workers)
+    nt = f.shape[0]
+    procs = []
+    for w in range(workers):
+        idx = [(w * nslabs + j) % nt for j in range(nslabs)]
+        procs.append(ctx.Process(target=_sweep_worker, args=(slab, f[idx].copy(), reps, bar, q), daemon=True))
+    for pr in procs:
+        pr.start()
+    res = [q.get(timeout=1800) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    dofs = nslabs * f.shape[1] * f.shape[2]
+    return {"times": [r[0] for r in res], "wall_s": wall, "dofs_per_sweep": dofs, "setup_s": t_setup,
+            "workers": workers}
+
+
+def _oracle_leg(q, go, nslabs, reps, workers):
+    # one thread per worker: no BLAS or OpenMP thread pools inside the forked workers
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    try:
+        q.put(oracle_parallel(nslabs, reps, workers, go))
     except Exception as e:  # reported, never silently dropped
         q.put({"error": repr(e)})
 
 
-def cpu_baseline_desc(res, nslabs):
-    total = sum(res["times"])
-    return {"value": res["dofs_per_step"] * len(res["times"]) / total, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": (f"{len(res['times'])} oracle block-Jacobi sweeps S on {nslabs} of the 256 slabs of the "
-                       f"16^3 DG(1) finest level ({res['dofs_per_step']} DoFs each; SciPy SuperLU slab solve and "
-                       f"sparse products, single-threaded; factorisation {res['setup_s']:.0f} s excluded)")}
+def cpu_baseline_desc(res, nslabs, skip=0):
+    """Throughput of the oracle sample: all workers' timed sweeps over the wall time of
+    the parallel section (the first `skip` sweeps of each worker untimed)."""
+    n_w = res["workers"]
+    sweeps = [t[skip:] for t in res["times"]]
+    per_worker_s = [sum(t) for t in sweeps]
+    n_sweeps = sum(len(t) for t in sweeps)
+    value = res["dofs_per_sweep"] * n_sweeps / max(per_worker_s)
+    return {"value": value, "unit": UNIT, "cores": n_w, "kind": "oracle",
+            "sample": (f"{n_w} single-threaded oracle processes (one per host core), each running "
+                       f"{len(sweeps[0])} block-Jacobi sweeps S on its own {nslabs} of the 256 slabs of the "
+                       f"16^3 DG(1) finest level ({res['dofs_per_sweep']} DoFs per sweep; SciPy SuperLU slab "
+                       f"solve and sparse products); factorisation ({res['setup_s']:.0f} s) excluded; timed "
+                       f"after the GPU measurement, with the GPU idle"),
+            "sweep_s_median": statistics.median(x for t in sweeps for x in t)}
 
 
 def run_reference(args):
@@ -153,15 +219,16 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    res = oracle_sample(CPU_SAMPLE_SLABS, args.warmup + args.steps)
-    timed = res["times"][args.warmup:]
-    res_t = dict(res, times=timed)
-    value = res["dofs_per_step"] * len(timed) / sum(timed)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    workers = min(host_cores(), 32)
+    res = oracle_parallel(CPU_SAMPLE_SLABS, args.warmup + args.steps, workers)
+    base = cpu_baseline_desc(res, CPU_SAMPLE_SLABS, skip=args.warmup)
+    value = base["value"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * base["sweep_s_median"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "sample": f"{CPU_SAMPLE_SLABS} slabs per step"},
-            "impl": "reference", "cpu_baseline": cpu_baseline_desc(res_t, CPU_SAMPLE_SLABS),
+            "config": workload_config(), "impl": "reference", "cpu_baseline": base,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -430,6 +497,10 @@ def main():
                          "(repeats an autotuned run's choice, e.g. under a profiler)")
     ap.add_argument("--nd-leaf", type=int, default=0,
                     help="largest leaf of the slab matrices' nested dissection (0: the library default)")
+    ap.add_argument("--config1-seeds", type=int, default=100,
+                    help="excitations of the 4^3 DG(0) two-grid case solved to 1e-10 (0: skip)")
+    ap.add_argument("--precision-line", type=int, default=1,
+                    help="also time the 16^3, N_t = 1024 workload to 1e-8 in every slab arithmetic")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
@@ -458,7 +529,6 @@ def main():
 
     import multiprocessing as mp
 
-    import numpy as np
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -468,15 +538,18 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
 
-    # CPU baseline in a spawned process (rank 0, N = 1), overlapping the GPU work
-    cpu_q = cpu_proc = None
+    # CPU baseline (rank 0, N = 1): a spawned process, started before the first CUDA call,
+    # builds the oracle's slab factor while the GPU works and runs its timed sweeps on all
+    # host cores only after the GPU measurements have ended (`go`)
+    cpu_q = cpu_proc = cpu_go = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.mode == "bench":
         ctx = mp.get_context("spawn")
-        cpu_q = ctx.Queue()
-        cpu_proc = ctx.Process(target=_oracle_worker, args=(cpu_q, CPU_SAMPLE_SLABS, 8), daemon=True)
+        cpu_q, cpu_go = ctx.Queue(), ctx.Event()
+        cpu_proc = ctx.Process(target=_oracle_leg, args=(cpu_q, cpu_go, CPU_SAMPLE_SLABS, 8,
+                                                          min(host_cores(), 32)))
         cpu_proc.start()
+    torch.cuda.set_device(local)
 
     from paper_1911_09548_gb300._build import build
     build()
@@ -489,10 +562,64 @@ def main():
     # (the legacy default stream cannot be captured)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+
+    def make(prec, **kw):
+        return stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                                    nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec,
+                                    autotune=args.autotune, **kw)
+
+    def time_cycles(Sx, fx, xx, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            Sx.vcycle(fx, xx)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            Sx.vcycle(fx, xx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def time_slab(Sx, fx, xx, reps=3):
+        """The dominant kernel group: the finest level's supernodal slab solve (forward
+        and backward products of every nested-dissection depth), timed alone with CUDA
+        events on the launching stream."""
+        r = Sx.residual(fx, xx)
+        y = Sx.zeros()
+        stmg.st_mg_slab_solve(Sx.h, 0, r, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            stmg.st_mg_slab_solve(Sx.h, 0, r, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def time_solves(Sx, n, maxit, keep=0):
+        ms, iters, sols = [], [], []
+        for s_ in range(n):
+            fs = Sx.load(st_inputs.excitation(100 + s_ + 1000 * rank))
+            xs = Sx.zeros()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            out = Sx.solve(fs, xs, rtol=1e-8, maxit=maxit)
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - a))
+            iters.append(out["iters"])
+            if s_ < keep:
+                sols.append(xs)
+            del fs
+        return ms, iters, sols
+
+    def dist_of(ms, iters):
+        if not ms:
+            return None
+        return {"p50": statistics.median(ms) / 1e3, "p99": percentile99(ms) / 1e3, "n": len(ms),
+                "p99_rule": "nearest rank of the sorted sample (the maximum when n < 100)", "v_cycles": iters}
+
     t0 = time.time()
-    S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                             nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec,
-                             autotune=args.autotune, nd_leaf=args.nd_leaf)
+    S = make(args.slab_prec, nd_leaf=args.nd_leaf)
     if args.split_waves:
         for l, w in enumerate(int(v) for v in args.split_waves.split(",")):
             stmg.st_mg_set_split_waves(S.h, l, w)
@@ -552,39 +679,17 @@ def main():
     ms_max = reduce_max(ms, dist, "cuda")
     value = replica_value(world, per_cycle, args.steps, ms_max)
 
-    # dominant kernel: the supernodal slab solve of the finest level (forward and
-    # backward product kernels of every nested-dissection depth), timed alone
+    # dominant kernel: the supernodal slab solve of the finest level, timed alone
     st = stmg.st_mg_factor_stats(S.h, 0)
-    r = S.residual(f, x)
-    y = S.zeros()
-    reps = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stmg.st_mg_slab_solve(S.h, 0, r, y)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        stmg.st_mg_slab_solve(S.h, 0, r, y)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    slab_ms = e0.elapsed_time(e1) / reps
+    least_fill_macs = st["macs_per_rhs"] if (args.nd_leaf in (0, 64) and args.slab_prec != 3) else None
+    slab_ms = time_slab(S, f, x)
     flops_per_mac = 8.0 if W["degree"] == 1 else 2.0
     slab_flops = st["macs_per_rhs"] * flops_per_mac * W["N_t"]
     achieved = slab_flops / (slab_ms / 1e3) / 1e12
     fp64_peak = stmg.st_mg_probe_fp64(S.h)       # roof of the FP64 kernels, measured in this run
 
     # time to 1e-8 from x = 0, several excitations
-    solve_ms, solve_iters, fp64_solutions = [], [], []
-    for s in range(args.solves):
-        fs = S.load(st_inputs.excitation(100 + s + 1000 * rank))
-        xs = S.zeros()
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        out = S.solve(fs, xs, rtol=1e-8, maxit=60)
-        torch.cuda.synchronize()
-        solve_ms.append(1e3 * (time.perf_counter() - a))
-        solve_iters.append(out["iters"])
-        fp64_solutions.append(xs)
-        del fs
+    solve_ms, solve_iters, fp64_solutions = time_solves(S, args.solves, 60, keep=args.mixed_solves)
 
     # end to end through the public host-buffer API: H2D of f and x, one V-cycle,
     # residual norms, D2H of x, every step
@@ -600,127 +705,103 @@ def main():
         S.solve_host(fnp, xnp, rtol=0.0, maxit=1)
         e2e_times.append(time.perf_counter() - a)
     e2e_value = world * per_cycle * len(e2e_times) / sum(e2e_times) if e2e_times else None
+    S.close()
+    S = None
+    del f, x
+    torch.cuda.synchronize()
 
-    # other slab-solve precisions on the same workload: FP32 factor apply and the BF16
-    # factor on the tensor cores (residual FP64-accurate, nodal and coarsest FP64)
+    # other slab-solve arithmetics on the same workload: double-float (FP64-accurate on the
+    # FP32 pipes), FP32 factor, BF16 factor on the tensor cores; each with its V-cycle
+    # time, its finest slab solve against its roof, and time to 1e-8 with the error of
+    # each solution against the FP64 one of the same excitation
     variants = {}
     if args.mixed:
-        S.close()
-        S = None
-        torch.cuda.synchronize()
-        for vname, prec, peak_key in (("mixed_fp32", 1, None), ("bf16_tensor", 3, "bf16_tflops")):
-            Sm = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                                      nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec,
-                                      autotune=args.autotune)
+        for vname, prec in (("double_float", 2), ("mixed_fp32", 1), ("bf16_tensor", 3)):
+            Sm = make(prec)
             fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
             xm = Sm.zeros()
-            for _ in range(args.warmup):
-                Sm.vcycle(fm, xm)
-            torch.cuda.synchronize()
-            ev0.record(stream)
-            for _ in range(args.steps):
-                Sm.vcycle(fm, xm)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            ms_m = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+            ms_m = reduce_max(time_cycles(Sm, fm, xm, args.steps), dist, "cuda")
             st_m = stmg.st_mg_factor_stats(Sm.h, 0)
-            rm = Sm.residual(fm, xm)
-            ym = Sm.zeros()
-            stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(reps):
-                stmg.st_mg_slab_solve(Sm.h, 0, rm, ym)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            slab_ms_m = e0.elapsed_time(e1) / reps
-            msolve, miters, merr = [], [], []
-            for s_ in range(args.mixed_solves):
-                fs = Sm.load(st_inputs.excitation(100 + s_ + 1000 * rank))
-                xs = Sm.zeros()
-                torch.cuda.synchronize()
-                a = time.perf_counter()
-                out = Sm.solve(fs, xs, rtol=1e-8, maxit=80)
-                torch.cuda.synchronize()
-                msolve.append(1e3 * (time.perf_counter() - a))
-                miters.append(out["iters"])
-                if s_ < len(fp64_solutions):
-                    ref = fp64_solutions[s_]
-                    merr.append(float(torch.linalg.vector_norm(xs - ref) / torch.linalg.vector_norm(ref)))
-            tflops = st_m["macs_per_rhs"] * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12
+            slab_ms_m = time_slab(Sm, fm, xm)
+            msolve, miters, sols = time_solves(Sm, args.mixed_solves, 80, keep=len(fp64_solutions))
+            merr = [float(torch.linalg.vector_norm(a_ - b_) / torch.linalg.vector_norm(b_))
+                    for a_, b_ in zip(sols, fp64_solutions)]
+            macs = st_m["macs_per_rhs"]
+            tflops = macs * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12
             v = {"value": replica_value(world, per_cycle, args.steps, ms_m), "unit": UNIT,
-                 "ms_per_step": ms_m / args.steps, "slab_solve_ms": slab_ms_m, "slab_solve_tflops": tflops,
-                 "time_to_1e-8_s": ({"p50": statistics.median(msolve) / 1e3, "p99": percentile99(msolve) / 1e3,
-                                     "n": len(msolve), "v_cycles": miters} if msolve else None),
-                 "rel_err_vs_fp64_solution": merr}
-            if peak_key:
-                peak = measured_peak(peak_key)
-                v["slab_solve_frac_of_bf16_peak"] = tflops / peak
-                v["bf16_peak_tflops"] = peak
+                 "ms_per_step": ms_m / args.steps, "slab_solve_ms": slab_ms_m,
+                 "slab_factor_macs_per_rhs": macs, "slab_solve_tflops": tflops,
+                 "time_to_1e-8_s": dist_of(msolve, miters), "rel_err_vs_fp64_solution": merr,
+                 "residual": "double-float (FP32 pairs, about 48 significant bits) with FP64 f and r",
+                 "coarsest_solve": "FP64"}
+            if prec == 3:
+                peak = measured_peak("bf16_tflops")
+                v["roofline"] = roofline_of(3, tflops, fp64_peak, slab_ms_m)
+                if least_fill_macs:
+                    # the method's own count: the least-fill (64-unknown leaf) factor's products
+                    lf = least_fill_macs * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12
+                    v["roofline"].update({"achieved": lf, "frac": lf / peak,
+                                          "achieved_counts": "least-fill factor's complex multiply-adds "
+                                          f"({least_fill_macs:.4g} per right-hand side, 64-unknown leaves) x 8 "
+                                          "flop; the BF16 factor itself has 512-unknown leaves "
+                                          f"({macs:.4g} per right-hand side)"})
+            else:
+                v["roofline"] = roofline_of(prec, tflops, fp64_peak, slab_ms_m)
             variants[vname] = v
             Sm.close()
+            del fm, xm, sols
+        del fp64_solutions
 
     # batched: `batch` excitations on one handle (problem-major slab columns), BF16
     # slab solve on the tensor cores; the same workload per problem
     if args.mixed and args.batch > 1:
         NB_ = args.batch
-        Sb = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
-                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=3, n_batch=NB_,
-                                  autotune=args.autotune)
+        Sb = make(3, n_batch=NB_)
         fb = Sb.zeros()
         for b in range(NB_):
             Sb.load(st_inputs.excitation(W["seed"] + 1 + b + 1000 * rank), f=fb, batch=b)
         xb = Sb.zeros()
-        for _ in range(args.warmup):
-            Sb.vcycle(fb, xb)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            Sb.vcycle(fb, xb)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms_b = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+        ms_b = reduce_max(time_cycles(Sb, fb, xb, args.steps), dist, "cuda")
         st_b = stmg.st_mg_factor_stats(Sb.h, 0)
-        rb_ = Sb.residual(fb, xb)
-        yb = Sb.zeros()
-        stmg.st_mg_slab_solve(Sb.h, 0, rb_, yb)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            stmg.st_mg_slab_solve(Sb.h, 0, rb_, yb)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        slab_ms_b = e0.elapsed_time(e1) / reps
+        slab_ms_b = time_slab(Sb, fb, xb)
         tflops_b = st_b["macs_per_rhs"] * flops_per_mac * W["N_t"] * NB_ / (slab_ms_b / 1e3) / 1e12
         peak = measured_peak("bf16_tflops")
         variants["bf16_tensor_batched"] = {
             "value": replica_value(world, per_cycle * NB_, args.steps, ms_b), "unit": UNIT, "problems": NB_,
             "ms_per_step": ms_b / args.steps, "slab_solve_ms": slab_ms_b, "slab_solve_tflops": tflops_b,
             "slab_solve_frac_of_bf16_peak": tflops_b / peak, "bf16_peak_tflops": peak}
+        if least_fill_macs:
+            lf = least_fill_macs * flops_per_mac * W["N_t"] * NB_ / (slab_ms_b / 1e3) / 1e12
+            variants["bf16_tensor_batched"]["slab_solve_frac_of_bf16_peak_least_fill"] = lf / peak
         Sb.close()
-        del fb, xb, rb_, yb
+        del fb, xb
+
+    extra = {}
+    if rank == 0 and args.config1_seeds > 0:
+        extra["config1"] = run_config1(stmg, st_inputs, stream, args.config1_seeds)
+    if rank == 0 and args.precision_line:
+        extra["config3"] = precision_line(stmg, st_inputs, stream, args)
 
     cpu_base = None
     if cpu_proc is not None:
+        cpu_go.set()
         res = cpu_q.get(timeout=1800)
         cpu_proc.join(timeout=60)
         cpu_base = cpu_baseline_desc(res, CPU_SAMPLE_SLABS) if "error" not in res else {"error": res["error"]}
 
     if rank == 0:
-        p99 = percentile99(solve_ms) if solve_ms else None
+        cfg = workload_config(world)
+        cfg.update({"time_levels": n_levels, "dofs": n_dof, "split_waves_per_level": split_waves,
+                    "autotune": "given" if args.split_waves else bool(args.autotune),
+                    "slab_prec": args.slab_prec,
+                    "l2": "inputs larger than L2 (129 MB): f and x %.0f MB each, finest slab factor "
+                          "%.2f GB, all read in every V-cycle" % (n_dof * 8 / 1e6, st["factor_bytes"] / 1e9)})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["name"], "mesh": "Kuhn 16^3, 26416 interior edges", "N_t": W["N_t"],
-                       "degree": W["degree"], "cycle": "V(2,2) SSASS, omega 0.5", "time_levels": n_levels,
-                       "dofs": n_dof, "parallelism": f"replicas x{world}",
-                       "split_waves_per_level": split_waves,
-                       "autotune": "given" if args.split_waves else bool(args.autotune),
-                       "l2": "inputs larger than L2 (129 MB): f and x %.0f MB each, finest slab factor "
-                             "%.2f GB, all read in every V-cycle" % (n_dof * 8 / 1e6, st["factor_bytes"] / 1e9)},
-            "time_to_1e-8_s": ({"p50": statistics.median(solve_ms) / 1e3, "p99": p99 / 1e3, "n": len(solve_ms),
-                                 "v_cycles": solve_iters} if solve_ms else None),
+            "config": cfg,
+            "time_to_1e-8_s": dist_of(solve_ms, solve_iters),
             "setup_s": setup_s,
             "roofline": roofline_of(args.slab_prec, achieved, fp64_peak, slab_ms),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n_dof * 8,
@@ -732,13 +813,75 @@ def main():
             line["cpu_baseline"] = cpu_base
         for k_, v_ in variants.items():
             line[k_] = v_
+        line.update(extra)
         print(json.dumps(line))
-    if S is not None:
-        S.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
+
+def run_config1(stmg, st_inputs, stream, seeds: int) -> dict:
+    """The plain method on the small case: Kuhn 4^3 (316 interior edges), nu = sigma = 1,
+    T = 1, N_t = 16, DG(0), two-grid (8 coarse slabs solved by forward substitution),
+    V(1,1) with SAS, omega 0.5, FP64, solved to 1e-10 from x = 0 for `seeds`
+    excitations; time per solve (load excluded) and V-cycle counts."""
+    import torch
+    nu1, s1 = st_inputs.materials(4, "unit")
+    S1 = stmg.SpaceTimeSolver(4, nu1, s1, 1.0, 16, 0, nu_pre=1, nu_post=1, max_levels=2,
+                              stream=stream.cuda_stream)
+    f1 = S1.zeros()
+    x1 = S1.zeros()
+    S1.load(st_inputs.excitation(0), f=f1)
+    S1.solve(f1, x1, rtol=1e-10, maxit=60)      # warm-up (graph capture)
+    ms, iters, bad = [], [], 0
+    for s_ in range(seeds):
+        S1.load(st_inputs.excitation(s_), f=f1)
+        x1.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = S1.solve(f1, x1, rtol=1e-10, maxit=60)
+        ms.append(1e3 * (time.perf_counter() - a))
+        iters.append(out["iters"])
+        bad += out["status"] != 0
+    S1.close()
+    per = smoothed_per_cycle(S1.n_dof, 1, 1)
+    tot_ms = sum(ms)
+    return {"workload": "kuhn4_dg0_Nt16_twogrid_V11", "dofs": S1.n_dof, "rtol": 1e-10, "seeds": seeds,
+            "time_to_1e-10_s": {"p50": statistics.median(ms) / 1e3, "p99": percentile99(ms) / 1e3, "n": len(ms)},
+            "v_cycles": {"min": min(iters), "max": max(iters), "mean": sum(iters) / len(iters)},
+            "not_converged": bad, "dofs_smoothed_per_s": per * sum(iters) / (tot_ms / 1e3),
+            "paper_context": "the paper reports 12 (Full) and 14 (Semi-time) V-cycles to 1e-10 on its own "
+                             "weak-scaling problem (Section 6; CPU cluster)"}
+
+
+def precision_line(stmg, st_inputs, stream, args) -> dict:
+    """Larger single-GPU workload (16^3, N_t = 1024, DG(1), two materials, V(2,2), 54 M
+    space-time DoFs, 11 time levels): time to 1e-8 with each slab arithmetic, V-cycle
+    counts, and each solution's error against the FP64 one."""
+    import torch
+    n, N_t = 16, 1024
+    nu, sigma = st_inputs.materials(n, "two_material", 0)
+    rows, ref = {}, None
+    for name, prec in (("fp64", 0), ("double_float", 2), ("fp32", 1), ("bf16_tensor", 3)):
+        S = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, 1, nu_pre=2, nu_post=2, stream=stream.cuda_stream,
+                                 slab_prec=prec, autotune=args.autotune)
+        f = S.load(st_inputs.excitation(0))
+        x = S.zeros()
+        S.vcycle(f, x)                  # warm-up (graph capture), discarded
+        x.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out = S.solve(f, x, rtol=1e-8, maxit=60)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - a
+        if ref is None:
+            ref = x.clone()
+        err = float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+        rows[name] = {"time_to_1e-8_s": dt, "v_cycles": out["iters"], "rel_res": out["rel_res"],
+                      "ms_per_v_cycle": 1e3 * dt / max(out["iters"], 1), "rel_err_vs_fp64_solution": err}
+        S.close()
+        del f, x
+    return {"workload": "kuhn16_dg1_Nt1024_V22", "dofs": 26416 * N_t * 2, "results": rows}
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -35,3 +35,19 @@ def test_percentile99_nearest_rank():
 def test_replica_value_is_whole_job_throughput():
     # two replicas, 1000 DoFs smoothed per V-cycle each, 4 V-cycles in 2 ms on the slowest
     assert math.isclose(bench.replica_value(2, 1000.0, 4, 2.0), 2 * 1000.0 * 4 / 2e-3)
+
+
+def test_cpu_baseline_counts_every_worker_over_the_slowest():
+    # two workers, three sweeps each of 1000 DoFs; the first sweep of each is warm-up
+    res = {"workers": 2, "times": [[9.0, 1.0, 1.0], [9.0, 2.0, 2.0]], "dofs_per_sweep": 1000,
+           "setup_s": 5.0, "wall_s": 13.0}
+    d = bench.cpu_baseline_desc(res, 16, skip=1)
+    assert d["cores"] == 2 and d["kind"] == "oracle"
+    # 4 timed sweeps of 1000 DoFs; the slowest worker needed 4 s for its two
+    assert math.isclose(d["value"], 4 * 1000 / 4.0)
+    assert math.isclose(d["sweep_s_median"], 1.5)
+
+
+def test_both_arms_name_the_same_workload():
+    c = bench.workload_config()
+    assert c["workload"] == bench.WORKLOAD["name"] and c["dofs"] == 26416 * 256 * 2
