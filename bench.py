@@ -320,6 +320,80 @@ def run_precision(args):
     return 0
 
 
+# ------------------------------------------------------------------ memory-bound steps
+def run_kernels(args):
+    """Each memory-bound step of the hot path alone, on the workload's finest level
+    (16^3, DG(1), N_t = 256: 13.5 M space-time DoFs), through the C ABI: time with CUDA
+    events on the bench's stream, L2 flushed (a 512 MB write) before every repetition,
+    against the step's algorithmic bytes (what it must read and write once).  The
+    NVTX range "kernels" brackets the last repetition of every step (for a profiler)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    import st_inputs
+
+    stmg.st_mg_set_launch_overlap(args.launch_overlap)
+    W = WORKLOAD
+    nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    S = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
+                             nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=args.slab_prec)
+    ne, nn, q, N_t = S.n_edge, S.n_node, S.q, W["N_t"]
+    ncols = N_t * q
+    nnz = int(stmg.st_mg_debug_get(S.h, 5, 0).size)
+    f = S.load(st_inputs.excitation(0))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(S.level_shape(), dtype=torch.float64, device="cuda", generator=gen)
+    r = S.zeros()
+    y = S.zeros(nodal=True)
+    z = torch.rand(S.level_shape(nodal=True), dtype=torch.float64, device="cuda", generator=gen)
+    wv = S.zeros(nodal=True)
+    rc = S.zeros(1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    B = stmg
+    dof, ndof = ne * ncols, nn * ncols
+    steps = {
+        # name: (call, algorithmic bytes)
+        "residual (r = f - L x)": (lambda: B.st_mg_residual(S.h, 0, f, x, r),
+                                   24 * dof + 8 * (ne + 1) + nnz * (4 + 8 * (3 if W["degree"] == 1 else 2))),
+        "G^T r": (lambda: B.st_mg_grad_T(S.h, 0, r, y), 8 * dof + 8 * ndof + 8 * (nn + 1) + 5 * 2 * ne),
+        "time integration L_t^-1": (lambda: B.st_mg_time_integrate(S.h, 0, z, wv), 16 * ndof),
+        "x += G w": (lambda: B.st_mg_grad_add(S.h, 0, wv, x), 16 * dof + 8 * ndof + 8 * ne),
+        "time restriction": (lambda: B.st_mg_restrict(S.h, 0, r, rc), 8 * dof + 4 * dof),
+        "time prolongation-add": (lambda: B.st_mg_prolong_add(S.h, 0, rc, x), 4 * dof + 16 * dof),
+    }
+    peak = measured_peak("hbm_gbs")
+    rows = {}
+    for name, (call, nbytes) in steps.items():
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for rep in range(args.steps):
+            flush.zero_()
+            if rep == args.steps - 1:
+                torch.cuda.nvtx.range_push("kernels")
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep == args.steps - 1:
+                torch.cuda.nvtx.range_pop()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        gbs = nbytes / (t / 1e3) / 1e9
+        rows[name] = {"us": 1e3 * t, "algorithmic_MB": nbytes / 1e6, "GB_s": gbs, "frac_of_hbm": gbs / peak}
+    S.close()
+    print(json.dumps({"mode": "kernels", "workload": W["name"], "slab_prec": args.slab_prec,
+                      "hbm_peak_gbs": peak, "timing": "median of %d, CUDA events, L2 flushed before each" % args.steps,
+                      "steps": rows}))
+    return 0
+
+
 # ------------------------------------------------------------------ convergence rates
 def run_rates(args):
     """Two-grid convergence rates by the power iteration of Section 5.1 on the GPU:
@@ -497,15 +571,18 @@ def main():
                          "(repeats an autotuned run's choice, e.g. under a profiler)")
     ap.add_argument("--nd-leaf", type=int, default=0,
                     help="largest leaf of the slab matrices' nested dissection (0: the library default)")
+    ap.add_argument("--launch-overlap", type=int, default=0, choices=[0, 1],
+                    help="programmatic dependent launch of the library's kernels (st_mg_set_launch_overlap)")
     ap.add_argument("--config1-seeds", type=int, default=100,
                     help="excitations of the 4^3 DG(0) two-grid case solved to 1e-10 (0: skip)")
     ap.add_argument("--precision-line", type=int, default=1,
                     help="also time the 16^3, N_t = 1024 workload to 1e-8 in every slab arithmetic")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
-    ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor cores")
-    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates", "precision"],
+    ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor "
+                         "cores, 4 FP16 tensor cores")
+    ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates", "precision", "kernels"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers); "
                          "serve: the request-loop benchmark (Poisson streams, p50/p99 latency)")
     ap.add_argument("--serve-rates", default="0.5,2,10", help="offered request rates (req/s), one stream each")
@@ -513,7 +590,7 @@ def main():
     ap.add_argument("--serve-meshes", default="8,16,24")
     ap.add_argument("--serve-nt", default="64,2048", help="N_t range (powers of two)")
     ap.add_argument("--serve-slots", type=int, default=2)
-    ap.add_argument("--serve-prec", type=int, default=3, choices=[0, 1, 2, 3])
+    ap.add_argument("--serve-prec", type=int, default=3, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--serve-burst", type=int, default=0,
                     help="instead of Poisson streams: this many requests at once on the 24^3 mesh, N_t uniform "
                          "over {128, 256, 512, 1024}, DG(1) (the batching workload)")
@@ -526,6 +603,8 @@ def main():
         return run_rates(args)
     if args.mode == "precision":
         return run_precision(args)
+    if args.mode == "kernels":
+        return run_kernels(args)
 
     import multiprocessing as mp
 
@@ -556,6 +635,7 @@ def main():
     import paper_1911_09548_gb300 as stmg
     import st_inputs
 
+    stmg.st_mg_set_launch_overlap(args.launch_overlap)
     W = WORKLOAD
     nu, sigma = st_inputs.materials(W["n"], W["materials"], W["seed"])
     # a dedicated stream: the library captures the V-cycle into a CUDA graph on it
@@ -716,7 +796,7 @@ def main():
     # each solution against the FP64 one of the same excitation
     variants = {}
     if args.mixed:
-        for vname, prec in (("double_float", 2), ("mixed_fp32", 1), ("bf16_tensor", 3)):
+        for vname, prec in (("double_float", 2), ("mixed_fp32", 1), ("bf16_tensor", 3), ("fp16_tensor", 4)):
             Sm = make(prec)
             fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
             xm = Sm.zeros()
@@ -734,9 +814,13 @@ def main():
                  "time_to_1e-8_s": dist_of(msolve, miters), "rel_err_vs_fp64_solution": merr,
                  "residual": "double-float (FP32 pairs, about 48 significant bits) with FP64 f and r",
                  "coarsest_solve": "FP64"}
-            if prec == 3:
-                peak = measured_peak("bf16_tflops")
+            if prec in (3, 4):
+                peak = measured_peak("bf16_tflops")     # dense FP16 = dense BF16 rate on this part
                 v["roofline"] = roofline_of(3, tflops, fp64_peak, slab_ms_m)
+                if prec == 4:
+                    v["roofline"]["kernel"] = v["roofline"]["kernel"].replace("BF16", "FP16")
+                    v["roofline"]["peak_source"] = ("measured dense BF16 peak (MEASURED_PEAKS.json); dense FP16 "
+                                                    "runs at the same nominal rate (2.25 PFLOP/s)")
                 if least_fill_macs:
                     # the method's own count: the least-fill (64-unknown leaf) factor's products
                     lf = least_fill_macs * flops_per_mac * W["N_t"] / (slab_ms_m / 1e3) / 1e12
@@ -793,7 +877,7 @@ def main():
         cfg = workload_config(world)
         cfg.update({"time_levels": n_levels, "dofs": n_dof, "split_waves_per_level": split_waves,
                     "autotune": "given" if args.split_waves else bool(args.autotune),
-                    "slab_prec": args.slab_prec,
+                    "slab_prec": args.slab_prec, "launch_overlap": bool(args.launch_overlap),
                     "l2": "inputs larger than L2 (129 MB): f and x %.0f MB each, finest slab factor "
                           "%.2f GB, all read in every V-cycle" % (n_dof * 8 / 1e6, st["factor_bytes"] / 1e9)})
         line = {
@@ -862,7 +946,7 @@ def precision_line(stmg, st_inputs, stream, args) -> dict:
     n, N_t = 16, 1024
     nu, sigma = st_inputs.materials(n, "two_material", 0)
     rows, ref = {}, None
-    for name, prec in (("fp64", 0), ("double_float", 2), ("fp32", 1), ("bf16_tensor", 3)):
+    for name, prec in (("fp64", 0), ("double_float", 2), ("fp32", 1), ("bf16_tensor", 3), ("fp16_tensor", 4)):
         S = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, 1, nu_pre=2, nu_post=2, stream=stream.cuda_stream,
                                  slab_prec=prec, autotune=args.autotune)
         f = S.load(st_inputs.excitation(0))

@@ -128,7 +128,13 @@ typedef struct {
                                 FP32 pipes, which on GB300 run 58x the FP64 rate;
                                 3 (DG(1) only) BF16 factor on the tensor cores (tcgen05, FP32
                                 accumulation in tensor memory), coarsest level in FP64, nodal K_n
-                                solve FP32 as in 1.  Mode 2 solves K_n in double-float, mode 0 in FP64 */
+                                solve FP32 as in 1;
+                                4 (DG(1) only) as 3 with an FP16 factor and FP16 operands: each
+                                right-hand-side column of a slab solve is scaled by a power of two
+                                into [1, 2) before the solve and back after it, since FP16 keeps 11
+                                significant bits but only 5 exponent bits (a factor entry above 16384
+                                in magnitude fails setup with ST_MG_ERR_NUMERIC).
+                                Mode 2 solves K_n in double-float, mode 0 in FP64 */
     int32_t residual_prec;   /* space-time residual arithmetic: 0 FP64; 2 double-float (x split into
                                 FP32 pairs once per call, error-free products and sums, f and r in
                                 FP64); -1 (default): FP64 when slab_prec = 0, double-float otherwise */
@@ -376,6 +382,15 @@ int st_mg_time_carry(st_mg_t h, int32_t level, const double* ends_dev, int32_t n
  * inverse in either case); it is slower.  Drops the captured V-cycle graph.
  * ST_MG_ERR_INVALID_ARG if the level has no BF16 factor or mode is not 0 or 1. */
 int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode);
+
+/* Process-wide: 1 queues the library's kernels with programmatic dependent launch, so
+ * that a kernel's blocks may be scheduled while the previous kernel on the same stream
+ * drains (each waits for that kernel's completion and memory before it reads or writes
+ * anything; results are identical); 0 (default) queues them as plain stream launches,
+ * which measured faster for the V-cycle's launch sequence on GB300.
+ * Applies to launches queued after the call (a V-cycle graph captured earlier keeps its
+ * launches).  No counterpart in the paper: a GPU scheduling choice. */
+int st_mg_set_launch_overlap(int32_t on);
 
 /* Number of CUDA kernels this library has launched since it was loaded (all handles). */
 int st_mg_launch_count(int64_t* count);

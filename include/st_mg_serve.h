@@ -52,7 +52,7 @@ typedef struct {
                                 device memory at creation */
     int32_t max_cycles;      /* V-cycles after which a request returns ST_MG_ERR_NOT_CONVERGED */
     int32_t slab_prec;       /* st_mg_options.slab_prec for DG(1) classes; DG(0) classes use 1 (FP32)
-                                when this is 3 (the tensor-core path is DG(1) only) */
+                                when this is 3 or 4 (the tensor-core paths are DG(1) only) */
     int32_t nu;              /* V(nu, nu) cycle */
     double omega;            /* smoother damping */
     int32_t setup_threads;   /* host threads per class build (0: all cores) */

@@ -102,6 +102,7 @@ _SIGS = {
     "st_mg_split_waves": [_vp, _i32, _P(_i32)],
     "st_mg_set_split_waves": [_vp, _i32, _i32],
     "st_mg_set_tc_mode": [_vp, _i32, _i32],
+    "st_mg_set_launch_overlap": [_i32],
     "st_mg_slab_copy": [_vp, _i32, _i32, _vp, _i32, _vp],
     "st_mg_residual_halo": [_vp, _i32, _vp, _vp, _vp, _vp],
     "st_mg_time_integrate_carry": [_vp, _i32, _vp, _vp, _vp],
@@ -379,6 +380,10 @@ def st_mg_time_integrate_carry(h, level, z, carry, w):
 def st_mg_time_carry(h, level, ends, n_prev, carry):
     _check(lib().st_mg_time_carry(_vp(h), level, _opt_addr(ends) if n_prev > 0 else None, n_prev,
                                   _vp(_addr(carry))), "st_mg_time_carry")
+
+
+def st_mg_set_launch_overlap(on):
+    _check(lib().st_mg_set_launch_overlap(int(on)), "st_mg_set_launch_overlap")
 
 
 def st_mg_set_tc_mode(h, level, mode):

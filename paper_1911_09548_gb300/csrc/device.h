@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -94,6 +95,11 @@ constexpr int kSkMaxRhsR = 32;
 // Number of kernels launched by this library since load (all launchers add to it).
 int64_t launch_count();
 void count_launches(int64_t n);
+// Programmatic dependent launch of the library's kernels (process-wide, default off: it
+// measured slower on GB300): a kernel may be scheduled while the previous one on its
+// stream drains (launch.cuh).
+bool launch_overlap();
+void set_launch_overlap(bool on);
 
 
 // ---- supernodal solve: X = A^{-1} Q on `nrhs` columns, leading dimension ld.
@@ -136,11 +142,26 @@ cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float
 // accumulation), tiled at every depth: the element-wise reference of those kernels.
 cudaError_t sn_solve_cplx_bf16_cc(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
                                   int nrhs, int ld, cudaStream_t st);
+// FP16 factor on the tensor cores (slab_prec 4): the same kernels with FP16 operands.
+// FP16 keeps 3 more significant bits than BF16 but only 5 exponent bits, so the
+// caller scales every right-hand-side column by a power of two first (col_scale).
+cudaError_t sn_solve_cplx_f16(const DevFactor<float2, __half2>& F, float2* Q, float2* Z, float2* U, float2* P,
+                              float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy, cudaStream_t st);
+cudaError_t sn_solve_cplx_f16_cc(const DevFactor<float2, __half2>& F, float2* Q, float2* Z, float2* U, int nrhs,
+                                 int ld, cudaStream_t st);
 // Pipelined tensor-core depth: assemble the right-hand-side tiles of the depth into
 // Bst (gy * max_stage_tiles tiles), then the products with bulk-copied operand tiles.
-cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
-                         float2* Z, float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err,
-                         cudaStream_t st);
+// WT = __nv_bfloat162 (BF16 operands) or __half2 (FP16 operands).
+template <typename WT>
+cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool split, float2* Q, float2* Z,
+                         float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy, cudaStream_t st);
+// Per-column power-of-two scaling of cnt complex columns of Q (rows x ld): colmax
+// (ld unsigned, the bits of max(|re|, |im|) per column) is cleared and filled, then
+// every column is multiplied by s_j = 2^(1 - e_j), e_j the binary exponent of its
+// maximum, so that its largest entry lies in [1, 2) (s_j = 1 for a zero column);
+// col_unscale divides by the same s_j (exact: powers of two).
+cudaError_t col_scale(float2* Q, int nrows, int cnt, int ld, unsigned* colmax, cudaStream_t st);
+cudaError_t col_unscale(float2* Q, int nrows, int cnt, int ld, const unsigned* colmax, cudaStream_t st);
 
 // FP64-accurate double-float path (W as FP32 pairs, FP64 right-hand sides).
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,

@@ -40,6 +40,11 @@ struct CudaError {
   const char* where;
 };
 
+// A factor that the requested arithmetic cannot hold (reported as ST_MG_ERR_NUMERIC).
+struct NumericError {
+  const char* what;
+};
+
 
 // Host-side tile and item lists of one factor (kept alive: the device view points at them).
 struct FactorLists {
@@ -100,6 +105,7 @@ struct SlabFactor {
   DevFactor<double, float2> drd;                          // double-float (FP64-accurate) apply
   DevFactor<double2, float4> dcd;
   DevFactor<float2, __nv_bfloat162> dcb;                  // BF16 factor on the tensor cores
+  DevFactor<float2, __half2> dch;                         // FP16 factor on the tensor cores
   FactorLists lists;
   int64_t w_bytes = 0;                                   // device bytes of the factor blocks
   int64_t u_rows = 0, max_items = 0, max_tc_items = 0, max_stage_tiles = 0;
@@ -254,6 +260,7 @@ struct st_mg_s {
   SkSync sk;                            // persistent split-K solve: barrier words + error flag
   float2* tcP = nullptr;                // tensor-core split-K partials
   uint8_t* tcB = nullptr;               // tensor-core right-hand-side tiles of one depth
+  unsigned* colmax = nullptr;           // FP16 slab solve: per-column maxima (scaling)
   double* load_b = nullptr;             // load assembly staging: space part [n_edge], time part [N_t q]
   double* load_c = nullptr;
   double* bn_partial = nullptr;         // per-problem norm scratch
@@ -283,6 +290,7 @@ inline void to_dev(const cplx& a, double2& b) { b = make_double2(a.re, a.im); }
 inline void to_dev(double a, float& b) { b = (float)a; }
 inline void to_dev(const cplx& a, float2& b) { b = make_float2((float)a.re, (float)a.im); }
 inline void to_dev(const cplx& a, __nv_bfloat162& b) { b = __floats2bfloat162_rn((float)a.re, (float)a.im); }
+inline void to_dev(const cplx& a, __half2& b) { b = __floats2half2_rn((float)a.re, (float)a.im); }
 // double-float pairs: hi = FP32 rounding, lo = FP32 rounding of the remainder
 inline void to_dev(double a, float2& b, int) {
   const float h = (float)a;
@@ -333,12 +341,28 @@ inline uint16_t bf16_bits(float v) {
   return u;
 }
 
+inline uint16_t f16_bits(float v) {
+  __half b = __float2half_rn(v);
+  uint16_t u;
+  std::memcpy(&u, &b, 2);
+  return u;
+}
+
+// Largest |Re| or |Im| of a factor's blocks W_s; an FP16 factor needs it well inside
+// FP16's range (65504), the BF16 one has FP32's exponent range.
+double max_abs_entry(const SupernodalFactor<cplx>& F) {
+  double m = 0.0;
+  for (const cplx& w : F.W) m = std::max(m, std::max(std::fabs(w.re), std::fabs(w.im)));
+  return m;
+}
+
 // Tensor-core operand tiles of a complex factor: for node s, forward tile (rt, ks)
 // holds W rows 64 rt .. 64 rt + 63 and columns 32 ks .. 32 ks + 31, each complex
 // entry a + ib as the real block [[a, -b], [b, a]]; backward tile (rt, ks) holds the
 // same for W^T (rows of W^T = columns of W).  Zero outside the node's block.
-void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<float2, __nv_bfloat162>& D,
-                    FactorLists& Lh) {
+template <typename WT>
+void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<float2, WT>& D, FactorLists& Lh) {
+  const auto bits = [](float v) { return std::is_same<WT, __half2>::value ? f16_bits(v) : bf16_bits(v); };
   const size_t TB = kTcTileBytes;
   std::vector<int4> tnode(F.nodes.size());
   std::vector<int2> tpre(F.nodes.size());
@@ -353,7 +377,7 @@ void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<floa
   }
   std::vector<uint8_t> tf((size_t)nf * TB, 0), tb((size_t)nb * TB, 0);
   auto put = [&](uint8_t* tile, int i, int k, cplx w) {
-    const uint16_t re = bf16_bits((float)w.re), im = bf16_bits((float)w.im), nim = bf16_bits(-(float)w.im);
+    const uint16_t re = bits((float)w.re), im = bits((float)w.im), nim = bits(-(float)w.im);
     std::memcpy(tile + tile_off(2 * i, 2 * k), &re, 2);
     std::memcpy(tile + tile_off(2 * i, 2 * k + 1), &nim, 2);
     std::memcpy(tile + tile_off(2 * i + 1, 2 * k), &im, 2);
@@ -585,7 +609,15 @@ void level_solve(Handle& h, int l, int cnt) {
   auto& L = h.lv[l];
   SkSync sk = h.sk;
   sk.split_waves = L.split_waves;
-  if (L.prec == 3 && L.tc_mode == 1) {
+  if (L.prec == 4) {
+    if (L.tc_mode == 1)
+      CK(sn_solve_cplx_f16_cc(L.fac->dch, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
+                              static_cast<float2*>(h.sU), cnt, h.ld_slab, h.stream));
+    else
+      CK(sn_solve_cplx_f16(L.fac->dch, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
+                           static_cast<float2*>(h.sU), static_cast<float2*>(h.sP), h.tcP, h.tcB, cnt, h.ld_slab, sk,
+                           h.stream));
+  } else if (L.prec == 3 && L.tc_mode == 1) {
     CK(sn_solve_cplx_bf16_cc(L.fac->dcb, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
                              static_cast<float2*>(h.sU), cnt, h.ld_slab, h.stream));
   } else if (L.prec == 3) {
@@ -625,17 +657,20 @@ void op_slab_cols(Handle& h, int l, const double* src, int src_ld, int slab0, in
   const double inv_tau = 1.0 / L.tau;
   const double2 c0 = make_double2(h.c0.x * inv_tau, h.c0.y * inv_tau);
   const double2 c1 = make_double2(h.c1.x * inv_tau, h.c1.y * inv_tau);
-  if (L.prec == 1 || L.prec == 3) {   // FP32 workspace
+  if (L.prec == 1 || L.prec == 3 || L.prec == 4) {   // FP32 workspace
     if (h.prob.degree == 0) {
       float* Q = static_cast<float*>(h.sQ);
       CK(slab_pre_dg0f(src, src_ld, slab0, cnt, L.fac->drf.iperm, S.ne, Q, h.ld_slab, h.stream));
       level_solve(h, l, cnt);
       CK(slab_post_dg0f(Q, h.ld_slab, L.fac->drf.iperm, S.ne, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     } else {
-      const int32_t* ip = L.prec == 3 ? L.fac->dcb.iperm : L.fac->dcf.iperm;
+      const int32_t* ip = L.prec == 3 ? L.fac->dcb.iperm : L.prec == 4 ? L.fac->dch.iperm : L.fac->dcf.iperm;
       float2* Q = static_cast<float2*>(h.sQ);
       CK(slab_pre_dg1f(src, src_ld, slab0, cnt, ip, S.ne, c0, c1, Q, h.ld_slab, h.stream));
+      // FP16 operands: every column scaled into [1, 2) first (the solve is linear per column)
+      if (L.prec == 4) CK(col_scale(Q, S.ne, cnt, h.ld_slab, h.colmax, h.stream));
       level_solve(h, l, cnt);
+      if (L.prec == 4) CK(col_unscale(Q, S.ne, cnt, h.ld_slab, h.colmax, h.stream));
       CK(slab_post_dg1f(Q, h.ld_slab, ip, S.ne, h.s1, dst, dst_ld, dst0, cnt, omega, mode, h.stream));
     }
     return;
@@ -853,7 +888,7 @@ double f_norm(Handle& h, const double* f) {
 // (a shallower tree) at the price of more fill.
 int nd_leaf_of(const st_mg_options& o) {
   if (o.nd_leaf > 0) return o.nd_leaf;
-  return o.slab_prec == 3 ? 512 : 64;
+  return (o.slab_prec == 3 || o.slab_prec == 4) ? 512 : 64;
 }
 
 // smoother pattern: NUL-terminated within the field, letters S and A only
@@ -885,7 +920,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   }
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
-      op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 3 || (op->slab_prec == 3 && pr->degree != 1) ||
+      op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 4 || (op->slab_prec >= 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
       (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
       (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
@@ -1017,7 +1052,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   // slab_prec 1 (FP32) and 3 (BF16) leave the coarsest level in FP64; slab_prec 2
   // (double-float, FP64-accurate) applies to every level
   for (size_t l = 0; l < H.lv.size(); ++l)
-    H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec == 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
+    H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec >= 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
   H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
   H.nodal_prec = op->slab_prec == 0 ? 0 : op->slab_prec == 2 ? 2 : 1;
 
@@ -1281,6 +1316,15 @@ int setup_device(Handle& H) {
           F->max_tc_items = F->dcb.max_tc_items;
           F->max_stage_tiles = F->dcb.max_stage_tiles;
           F->w_bytes = (int64_t)L.fc.W.size() * 4;
+        } else if (L.prec == 4) {
+          if (max_abs_entry(L.fc) > 16384.0)
+            throw NumericError{"a slab factor entry exceeds the FP16 range kept for slab_prec 4 (|w| > 16384)"};
+          make_dev_factor(F->mem, L.fc, F->dch, F->lists);
+          build_tc_tiles(F->mem, L.fc, F->dch, F->lists);
+          F->max_items = F->dch.max_items;
+          F->max_tc_items = F->dch.max_tc_items;
+          F->max_stage_tiles = F->dch.max_stage_tiles;
+          F->w_bytes = (int64_t)L.fc.W.size() * 4;
         } else if (L.prec == 2) {
           make_dev_factor(F->mem, L.fc, F->dcd, F->lists);
           F->max_items = F->dcd.max_items;
@@ -1339,15 +1383,16 @@ int setup_device(Handle& H) {
   H.tc_err = H.flags;
   H.sk.bar = op->persistent_split ? reinterpret_cast<unsigned*>(H.flags + 2) : nullptr;
   H.sk.err = H.flags;
-  if (op->slab_prec == 3) {
+  if (op->slab_prec >= 3) {
+    H.colmax = H.dalloc<unsigned>(H.ld_slab);
     int64_t mt = 1;
     for (auto& L : H.lv)
-      if (L.prec == 3) mt = std::max<int64_t>(mt, L.fac->max_tc_items);
+      if (L.prec >= 3) mt = std::max<int64_t>(mt, L.fac->max_tc_items);
     const int64_t gy = (H.ld_slab + kTcCols - 1) / kTcCols;
     H.tcP = H.dalloc<float2>(mt * gy * kSnBM * kTcCols);
     int64_t ms = 1;
     for (auto& L : H.lv)
-      if (L.prec == 3) ms = std::max<int64_t>(ms, L.fac->max_stage_tiles);
+      if (L.prec >= 3) ms = std::max<int64_t>(ms, L.fac->max_stage_tiles);
     H.tcB = H.dalloc<uint8_t>(ms * gy * kTcTileBytes);
   }
   H.load_b = H.dalloc<double>(H.space[0].ne);
@@ -1385,6 +1430,8 @@ int guarded(Fn fn) {
   } catch (const CudaError& e) {
     return fail(e.e == cudaErrorMemoryAllocation ? ST_MG_ERR_OOM : ST_MG_ERR_CUDA,
                 std::string(e.where) + ": " + cudaGetErrorString(e.e));
+  } catch (const NumericError& e) {
+    return fail(ST_MG_ERR_NUMERIC, e.what);
   } catch (const std::bad_alloc&) {
     return fail(ST_MG_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -2054,10 +2101,17 @@ int st_mg_time_carry(st_mg_t h, int32_t level, const double* ends_dev, int32_t n
   });
 }
 
+int st_mg_set_launch_overlap(int32_t on) {
+  if (on != 0 && on != 1) return fail(ST_MG_ERR_INVALID_ARG, "launch overlap must be 0 or 1");
+  set_launch_overlap(on != 0);
+  return ST_MG_OK;
+}
+
 int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode) {
   if (int rc = check_level(h, level)) return rc;
   if (mode < 0 || mode > 1) return fail(ST_MG_ERR_INVALID_ARG, "tensor-core mode must be 0 or 1");
-  if (h->lv[level].prec != 3) return fail(ST_MG_ERR_INVALID_ARG, "level has no BF16 factor (slab_prec 3)");
+  if (h->lv[level].prec < 3)
+    return fail(ST_MG_ERR_INVALID_ARG, "level has no 16-bit tensor-core factor (slab_prec 3 or 4)");
   h->lv[level].tc_mode = mode;
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
@@ -2070,11 +2124,13 @@ int st_mg_factor_stats(st_mg_t h, int32_t level, double* macs_per_rhs, int64_t* 
   if (int rc = check_level(h, level)) return rc;
   const auto& L = h->lv[level];
   const bool c = h->prob.degree == 1;
-  const double macs = L.prec == 3 ? L.fac->dcb.macs_per_rhs
+  const double macs = L.prec == 4 ? L.fac->dch.macs_per_rhs
+                     : L.prec == 3 ? L.fac->dcb.macs_per_rhs
                      : L.prec == 1 ? (c ? L.fac->dcf.macs_per_rhs : L.fac->drf.macs_per_rhs)
                      : L.prec == 2 ? (c ? L.fac->dcd.macs_per_rhs : L.fac->drd.macs_per_rhs)
                                    : (c ? L.fac->dc.macs_per_rhs : L.fac->dr.macs_per_rhs);
-  const int dep = L.prec == 3 ? L.fac->dcb.max_depth
+  const int dep = L.prec == 4 ? L.fac->dch.max_depth
+                  : L.prec == 3 ? L.fac->dcb.max_depth
                   : L.prec == 1 ? (c ? L.fac->dcf.max_depth : L.fac->drf.max_depth)
                   : L.prec == 2 ? (c ? L.fac->dcd.max_depth : L.fac->drd.max_depth)
                                 : (c ? L.fac->dc.max_depth : L.fac->dr.max_depth);

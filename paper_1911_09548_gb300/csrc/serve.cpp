@@ -204,7 +204,7 @@ Class* start_class(Server& S, const Request& q) {
   st_mg_default_options(&c->opt);
   c->opt.omega = S.opt.omega;
   c->opt.nu_pre = c->opt.nu_post = S.opt.nu;
-  c->opt.slab_prec = (S.opt.slab_prec == 3 && q.degree == 0) ? 1 : S.opt.slab_prec;
+  c->opt.slab_prec = (S.opt.slab_prec >= 3 && q.degree == 0) ? 1 : S.opt.slab_prec;
   c->opt.setup_threads = S.opt.setup_threads;
   c->opt.factor_cache = 1;
   c->opt.use_graph = 1;
@@ -475,7 +475,7 @@ int st_mg_server_default_options(st_mg_server_options* o) {
 int st_mg_server_create(const st_mg_server_options* opt, st_mg_server_t* out) {
   if (!opt || !out) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (opt->slots < 1 || opt->mem_budget < 0 || opt->max_cycles < 1 || opt->slab_prec < 0 || opt->slab_prec > 3 ||
+  if (opt->slots < 1 || opt->mem_budget < 0 || opt->max_cycles < 1 || opt->slab_prec < 0 || opt->slab_prec > 4 ||
       opt->nu < 0 || !(opt->omega > 0) || opt->max_builds < 1)
     return fail(ST_MG_ERR_INVALID_ARG, "invalid server options");
   auto S = std::make_unique<Server>();

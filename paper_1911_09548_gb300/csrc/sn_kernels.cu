@@ -22,6 +22,7 @@
 //     error-free two-sum (Knuth), so one multiply-add costs 12 FP32 instructions
 //     and keeps ~48 significant bits.  Epilogues (pivots, update sums) run in FP64.
 #include "device.h"
+#include "launch.cuh"
 
 namespace stmg {
 namespace {
@@ -191,6 +192,32 @@ struct PolBF16CR {
   static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
 };
 
+// FP16 factor, FP32 arithmetic (split-K path of the FP16 tensor-core solve; its
+// right-hand-side columns arrive scaled by powers of two, see col_scale)
+struct PolF16C {
+  using S = float2;
+  using WT = __half2;
+  using A = float2;
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ A from_w(WT w) { return __half22float2(w); }
+  static __device__ __forceinline__ A from_s(S v) { return v; }
+  static __device__ __forceinline__ S to_s(A a) { return a; }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
+};
+
+// ... and with the right-hand sides rounded to FP16 where they enter a product: the
+// element-wise reference of the FP16 tensor-core kernels, as PolBF16CR is of the BF16 ones
+struct PolF16CR {
+  using S = float2;
+  using WT = __half2;
+  using A = float2;
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ A from_w(WT w) { return __half22float2(w); }
+  static __device__ __forceinline__ A from_s(S v) { return __half22float2(__floats2half2_rn(v.x, v.y)); }
+  static __device__ __forceinline__ S to_s(A a) { return a; }
+  static __device__ __forceinline__ void mac(A& acc, A a, A b) { Ar<float2>::mac(acc, a, b); }
+};
+
 constexpr int BK = 16;      // depth of one shared-memory stage
 constexpr int NT = 256;     // threads: 16 x 16, micro-tile rows ty + 16 i, cols tx + 16 j
 
@@ -208,6 +235,7 @@ __global__ void __launch_bounds__(NT) k_sn_forward(const DevNode* __restrict__ n
                                                    const int32_t* __restrict__ gsrc, const int2* __restrict__ tiles,
                                                    const typename P::S* __restrict__ Q, typename P::S* __restrict__ Z,
                                                    typename P::S* __restrict__ U, int nrhs, int ld) {
+  pdl_entry();
   using S = typename P::S;
   using A = typename P::A;
   constexpr int TN = BN / 16;
@@ -293,6 +321,7 @@ __global__ void __launch_bounds__(NT) k_sn_backward(const DevNode* __restrict__ 
                                                     const int2* __restrict__ tiles,
                                                     const typename P::S* __restrict__ Z,
                                                     typename P::S* __restrict__ X, int nrhs, int ld) {
+  pdl_entry();
   using S = typename P::S;
   using A = typename P::A;
   constexpr int TN = BN / 16;
@@ -502,6 +531,7 @@ __global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
     const int32_t* __restrict__ rows, const int4* __restrict__ items, const typename P::S* __restrict__ Q,
     const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U, const typename P::S* __restrict__ X,
     typename P::S* __restrict__ Pt, int nrhs, int ld) {
+  pdl_entry();
   static_assert(SK_THREADS == 32, "one warp per item: warp-level synchronisation");
   __shared__ typename P::A As[SK_KS][kSkRows + 1];   // + 1: conflict-free stores of row-major factor rows
   __shared__ typename P::A Bs[SK_KS][NB];
@@ -515,6 +545,7 @@ __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
     const DevNode* __restrict__ nodes, const typename P::S* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
     const int4* __restrict__ units, int64_t item_base, int64_t n_items, const typename P::S* __restrict__ Pt,
     typename P::S* __restrict__ Z, typename P::S* __restrict__ U, typename P::S* __restrict__ X, int nrhs, int ld) {
+  pdl_entry();
   using S = typename P::S;
   const int4 un = units[blockIdx.x];
   const DevNode nd = nodes[un.x];
@@ -543,21 +574,22 @@ __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
 
 template <typename P, int NB>
 void skinny_depth(const DevFactor<typename P::S, typename P::WT>& F, int d, bool fwd, typename P::S* Q,
-                  typename P::S* Z, typename P::S* U, typename P::S* Pt, int nrhs, int ld, cudaStream_t st) {
+                  typename P::S* Z, typename P::S* U, typename P::S* Pt, int nrhs, int ld, const SkSync& sy,
+                  cudaStream_t st) {
   const int64_t* io = fwd ? F.h_fs_item_off : F.h_bs_item_off;
   const int64_t* uo = fwd ? F.h_fs_unit_off : F.h_bs_unit_off;
   const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
   if (ib <= ia) return;
   const unsigned gy = (unsigned)((nrhs + NB - 1) / NB);
   if (fwd) {
-    k_sn_skinny_partial<P, NB, true><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
+    launch_k(k_sn_skinny_partial<P, NB, true>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
         F.nodes, F.W, F.gsrc, F.rows, F.fs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
-    k_sn_skinny_reduce<P, NB, true><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
+    launch_k(k_sn_skinny_reduce<P, NB, true>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
         F.nodes, F.Dinv, F.gsrc, F.fs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   } else {
-    k_sn_skinny_partial<P, NB, false><<<dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st>>>(
+    launch_k(k_sn_skinny_partial<P, NB, false>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
         F.nodes, F.W, F.gsrc, F.rows, F.bs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
-    k_sn_skinny_reduce<P, NB, false><<<dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st>>>(
+    launch_k(k_sn_skinny_reduce<P, NB, false>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
         F.nodes, F.Dinv, F.gsrc, F.bs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   }
   count_launches(2);
@@ -681,8 +713,8 @@ cudaError_t sn_solve_skinny(const DevFactor<typename P::S, typename P::WT>& F, t
       return cudaSuccess;
     }
   }
-  for (int d = F.max_depth; d >= 0; --d) skinny_depth<P, NB>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
-  for (int d = 0; d <= F.max_depth; ++d) skinny_depth<P, NB>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
+  for (int d = F.max_depth; d >= 0; --d) skinny_depth<P, NB>(F, d, true, Q, Z, U, Pt, nrhs, ld, sy, st);
+  for (int d = 0; d <= F.max_depth; ++d) skinny_depth<P, NB>(F, d, false, Q, Z, U, Pt, nrhs, ld, sy, st);
   return cudaGetLastError();
 }
 
@@ -699,10 +731,10 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
     const int64_t a = F.h_fwd_off[d], b = F.h_fwd_off[d + 1];
     if (b <= a) continue;
     if (Pt && (b - a) * gy < two_waves) {
-      skinny_depth<P, NBK>(F, d, true, Q, Z, U, Pt, nrhs, ld, st);
+      skinny_depth<P, NBK>(F, d, true, Q, Z, U, Pt, nrhs, ld, sy, st);
       continue;
     }
-    k_sn_forward<P, BN, BM><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.Dinv, F.gsrc, F.fwd_tiles + a,
+    launch_k(k_sn_forward<P, BN, BM>, dim3((unsigned)(b - a), gy), NT, 0, st, F.nodes, F.W, F.Dinv, F.gsrc, F.fwd_tiles + a,
                                                                      Q, Z, U, nrhs, ld);
     count_launches(1);
   }
@@ -710,10 +742,10 @@ cudaError_t sn_solve_tiled(const DevFactor<typename P::S, typename P::WT>& F, ty
     const int64_t a = F.h_bwd_off[d], b = F.h_bwd_off[d + 1];
     if (b <= a) continue;
     if (Pt && (b - a) * gy < two_waves) {
-      skinny_depth<P, NBK>(F, d, false, Q, Z, U, Pt, nrhs, ld, st);
+      skinny_depth<P, NBK>(F, d, false, Q, Z, U, Pt, nrhs, ld, sy, st);
       continue;
     }
-    k_sn_backward<P, BN, BM><<<dim3((unsigned)(b - a), gy), NT, 0, st>>>(F.nodes, F.W, F.rows, F.bwd_tiles + a, Z, Q,
+    launch_k(k_sn_backward<P, BN, BM>, dim3((unsigned)(b - a), gy), NT, 0, st, F.nodes, F.W, F.rows, F.bwd_tiles + a, Z, Q,
                                                                       nrhs, ld);
     count_launches(1);
   }
@@ -761,26 +793,39 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
                            const SkSync& sy, cudaStream_t st) {
   return solve_cplx<PolNative<float2>>(F, Q, Z, U, P, nrhs, ld, sy, st);
 }
-cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
-                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
-                               cudaStream_t st) {
+// 16-bit factor (BF16 or FP16) on the tensor cores: CUDA-core split-K for few
+// right-hand sides, otherwise per depth the tcgen05 kernels (split-K for depths whose
+// tiles fill fewer than sy.split_waves waves of the SMs).
+template <typename PolC, typename WT>
+cudaError_t solve_cplx_tc(const DevFactor<float2, WT>& F, float2* Q, float2* Z, float2* U, float2* P, float2* Ptc,
+                          uint8_t* Bst, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
   if (nrhs <= 0) return cudaSuccess;
-  if (nrhs <= 2) return sn_solve_skinny<PolBF16C, 2>(F, Q, Z, U, P, nrhs, ld, sy, st);
-  if (nrhs <= 8) return sn_solve_skinny<PolBF16C, 8>(F, Q, Z, U, P, nrhs, ld, sy, st);
-  if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolBF16C, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  if (nrhs <= 2) return sn_solve_skinny<PolC, 2>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  if (nrhs <= 8) return sn_solve_skinny<PolC, 8>(F, Q, Z, U, P, nrhs, ld, sy, st);
+  if (nrhs <= kSkMaxRhsC) return sn_solve_skinny<PolC, kSkMaxRhsC>(F, Q, Z, U, P, nrhs, ld, sy, st);
   const int64_t gy = (nrhs + kTcCols - 1) / kTcCols;
   const int64_t two_waves = (int64_t)sy.split_waves * F.n_sm;
   for (int d = F.max_depth; d >= 0; --d) {
     const int64_t tiles = F.h_fwd_off[d + 1] - F.h_fwd_off[d];
     if (tiles <= 0) continue;
-    sn_tc2_depth(F, d, true, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy.err, st);
+    sn_tc2_depth(F, d, true, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy, st);
   }
   for (int d = 0; d <= F.max_depth; ++d) {
     const int64_t tiles = F.h_bwd_off[d + 1] - F.h_bwd_off[d];
     if (tiles <= 0) continue;
-    sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy.err, st);
+    sn_tc2_depth(F, d, false, tiles * gy < two_waves, Q, Z, U, Ptc, Bst, nrhs, ld, sy, st);
   }
   return cudaGetLastError();
+}
+
+cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
+                               float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
+                               cudaStream_t st) {
+  return solve_cplx_tc<PolBF16C>(F, Q, Z, U, P, Ptc, Bst, nrhs, ld, sy, st);
+}
+cudaError_t sn_solve_cplx_f16(const DevFactor<float2, __half2>& F, float2* Q, float2* Z, float2* U, float2* P,
+                              float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
+  return solve_cplx_tc<PolF16C>(F, Q, Z, U, P, Ptc, Bst, nrhs, ld, sy, st);
 }
 
 cudaError_t sn_solve_cplx_bf16_cc(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
@@ -788,6 +833,12 @@ cudaError_t sn_solve_cplx_bf16_cc(const DevFactor<float2, __nv_bfloat162>& F, fl
   if (nrhs <= 0) return cudaSuccess;
   SkSync none;
   return sn_solve_tiled<PolBF16CR, 32, kSkMaxRhsC, kSnBM>(F, Q, Z, U, nullptr, nrhs, ld, none, st);
+}
+cudaError_t sn_solve_cplx_f16_cc(const DevFactor<float2, __half2>& F, float2* Q, float2* Z, float2* U, int nrhs,
+                                 int ld, cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  SkSync none;
+  return sn_solve_tiled<PolF16CR, 32, kSkMaxRhsC, kSnBM>(F, Q, Z, U, nullptr, nrhs, ld, none, st);
 }
 
 cudaError_t sn_solve_real_df(const DevFactor<double, float2>& F, double* Q, double* Z, double* U, double* P, int nrhs,

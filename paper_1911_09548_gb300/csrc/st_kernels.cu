@@ -4,7 +4,10 @@
 // contiguous vector and a warp's loads coalesce.
 #include <atomic>
 
+#include <type_traits>
+
 #include "device.h"
+#include "launch.cuh"
 
 namespace stmg {
 namespace {
@@ -50,6 +53,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial, int seg) {
+  pdl_entry();
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -118,6 +122,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
                                                                  const double* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial, int seg) {
+  pdl_entry();
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -190,6 +195,7 @@ __device__ __forceinline__ void dp_mac(dpair& acc, float2 a, float2 b) {
 __device__ __forceinline__ double dp_join(dpair a) { return (double)a.h + (double)a.l; }
 
 __global__ void k_split_pairs(const double* __restrict__ x, float2* __restrict__ xs, int64_t n) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = x[i];
     const float h = __double2float_rn(v);
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1_df(int nrows, c
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
                                                                     double* __restrict__ partial, int seg) {
+  pdl_entry();
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
                                                                     const float2* __restrict__ xs,
                                                                     double* __restrict__ r, int N_t,
                                                                     double* __restrict__ partial, int seg) {
+  pdl_entry();
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -327,6 +335,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0_df(int nrows, c
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  pdl_entry();
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
   block_sum_store<256>(s, out);
@@ -334,6 +343,7 @@ __global__ void k_reduce_partials(const double* __restrict__ p, int n, double* _
 
 constexpr int NORM_BLOCKS = 1024;
 __global__ void k_norm_partial(const double* __restrict__ v, int64_t n, double* __restrict__ partial) {
+  pdl_entry();
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s = fma(v[i], v[i], s);
@@ -344,6 +354,7 @@ constexpr int SLAB_ROWS = 4;   // rows (one per warp) per block of the permutati
 
 __global__ void k_slab_pre_dg0(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                const int32_t* __restrict__ iperm, double* __restrict__ Q, int ld) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double* src = r + (int64_t)e * src_ld;
@@ -355,6 +366,7 @@ __global__ void k_slab_pre_dg0(int nrows, const double* __restrict__ r, int src_
 __global__ void k_slab_pre_dg1(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                const int32_t* __restrict__ iperm, double2 c0, double2 c1,
                                double2* __restrict__ Q, int ld) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
@@ -368,6 +380,7 @@ __global__ void k_slab_pre_dg1(int nrows, const double* __restrict__ r, int src_
 
 __global__ void k_slab_post_dg0(int nrows, const double* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                 double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double* src = X + (int64_t)iperm[e] * ld;
@@ -383,6 +396,7 @@ __global__ void k_slab_post_dg0(int nrows, const double* __restrict__ X, int ld,
 __global__ void k_slab_post_dg1(int nrows, const double2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                 double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
                                 double omega, int mode) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double2* src = X + (int64_t)iperm[e] * ld;
@@ -405,6 +419,7 @@ __global__ void k_slab_post_dg1(int nrows, const double2* __restrict__ X, int ld
 
 __global__ void k_slab_pre_dg0f(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                 const int32_t* __restrict__ iperm, float* __restrict__ Q, int ld) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double* src = r + (int64_t)e * src_ld;
@@ -416,6 +431,7 @@ __global__ void k_slab_pre_dg0f(int nrows, const double* __restrict__ r, int src
 __global__ void k_slab_pre_dg1f(int nrows, const double* __restrict__ r, int src_ld, int slab0, int cnt,
                                 const int32_t* __restrict__ iperm, double2 c0, double2 c1,
                                 float2* __restrict__ Q, int ld) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
@@ -429,6 +445,7 @@ __global__ void k_slab_pre_dg1f(int nrows, const double* __restrict__ r, int src
 
 __global__ void k_slab_post_dg0f(int nrows, const float* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                  double* __restrict__ x, int dst_ld, int slab0, int cnt, double omega, int mode) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const float* src = X + (int64_t)iperm[e] * ld;
@@ -444,6 +461,7 @@ __global__ void k_slab_post_dg0f(int nrows, const float* __restrict__ X, int ld,
 __global__ void k_slab_post_dg1f(int nrows, const float2* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                  double2 s1, double* __restrict__ x, int dst_ld, int slab0, int cnt,
                                  double omega, int mode) {
+  pdl_entry();
   const int e = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (e >= nrows) return;
   const float2* src = X + (int64_t)iperm[e] * ld;
@@ -468,6 +486,7 @@ __global__ void k_slab_post_dg1f(int nrows, const float2* __restrict__ X, int ld
 template <typename TQ>
 __global__ void k_gather_perm(int nrows, const double* __restrict__ y, int ncols, const int32_t* __restrict__ iperm,
                               TQ* __restrict__ Q, int ld) {
+  pdl_entry();
   const int v = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (v >= nrows) return;
   const double* src = y + (int64_t)v * ncols;
@@ -479,6 +498,7 @@ __global__ void k_gather_perm(int nrows, const double* __restrict__ y, int ncols
 template <typename TQ>
 __global__ void k_scatter_perm(int nrows, const TQ* __restrict__ X, int ld, const int32_t* __restrict__ iperm,
                                double* __restrict__ z, int ncols) {
+  pdl_entry();
   const int v = blockIdx.x * SLAB_ROWS + (threadIdx.x >> 5);   // one warp per row
   if (v >= nrows) return;
   const TQ* src = X + (int64_t)iperm[v] * ld;
@@ -498,6 +518,7 @@ __global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64
                                                           const int8_t* __restrict__ sgn,
                                                           const double* __restrict__ r, double* __restrict__ y,
                                                           int ncols) {
+  pdl_entry();
   __shared__ int s_col[GT_WARPS][32];
   __shared__ int s_sgn[GT_WARPS][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
@@ -555,6 +576,7 @@ __global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64
 // x += G w: one block per interior edge, double2 column pairs.
 __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __restrict__ head,
                            const double* __restrict__ w, double* __restrict__ x, int ncols) {
+  pdl_entry();
   const int e = blockIdx.x;
   const int t = tail[e], h = head[e];
   double* xr = x + (int64_t)e * ncols;
@@ -588,6 +610,54 @@ __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __re
     x2[j] = xv;
   }
 }
+// The same update with one warp per edge (GA_WARPS edges per block) and the loads of
+// GA_UNROLL column pairs per lane issued before their sums: the x row and the two w rows
+// of an edge are in flight together.  Same operations per entry: bit-identical.
+constexpr int GA_WARPS = 8;
+constexpr int GA_UNROLL = 4;
+__global__ void __launch_bounds__(GA_WARPS * 32) k_grad_add_w(const int32_t* __restrict__ tail,
+                                                              const int32_t* __restrict__ head,
+                                                              const double* __restrict__ w, double* __restrict__ x,
+                                                              int nedges, int ncols) {
+  pdl_entry();
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * GA_WARPS + (threadIdx.x >> 5);
+  if (e >= nedges) return;
+  const int t = tail[e], h = head[e];
+  const int n2 = ncols >> 1;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2* x2 = reinterpret_cast<double2*>(x + (int64_t)e * ncols);
+  const double2 zero = make_double2(0.0, 0.0);
+  for (int j0 = 0; j0 < n2; j0 += 32 * GA_UNROLL) {
+    double2 xv[GA_UNROLL], a[GA_UNROLL], b[GA_UNROLL];
+#pragma unroll
+    for (int u = 0; u < GA_UNROLL; ++u) {
+      const int j = j0 + u * 32 + lane;
+      const bool in = j < n2;
+      xv[u] = in ? x2[j] : zero;
+      a[u] = (in && h >= 0) ? w2[(int64_t)h * n2 + j] : zero;
+      b[u] = (in && t >= 0) ? w2[(int64_t)t * n2 + j] : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < GA_UNROLL; ++u) {
+      const int j = j0 + u * 32 + lane;
+      if (j >= n2) continue;
+      double2 d = zero;
+      if (h >= 0) {
+        d.x += a[u].x;
+        d.y += a[u].y;
+      }
+      if (t >= 0) {
+        d.x -= b[u].x;
+        d.y -= b[u].y;
+      }
+      xv[u].x += d.x;
+      xv[u].y += d.y;
+      x2[j] = xv[u];
+    }
+  }
+}
+
 // CARRY: the time grid continues an earlier one whose last slab held w_{-1} = carry[v]
 // (q values per node), the state a time-slab shard receives from the shard before it.
 // The recurrence's homogeneous part is T = -K_t^{-1} N_t: 1 for DG(0), [[1,1],[0,0]]
@@ -596,6 +666,7 @@ __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __re
 template <bool CARRY>
 __global__ void k_time_integrate(const double* __restrict__ z, double* __restrict__ w, int nrows, int N_t,
                                  int degree, const double* __restrict__ carry) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (v >= nrows) return;
@@ -627,11 +698,117 @@ __global__ void k_time_integrate(const double* __restrict__ z, double* __restric
   }
 }
 
+// The same scan with the row staged in shared memory: the row is read and written with
+// coalesced warp-wide accesses (a lane's own chunk of C consecutive slabs is strided by
+// C slabs across the warp in global memory), and the chunks sit Cp >= C + 1 entries
+// apart in shared memory (Cp odd) so that the lanes' chunk reads hit distinct banks.
+// Same chunks, same operations in the same order as k_time_integrate: bit-identical.
+// smem per warp: 32 Cp values of q doubles; rows of up to TI_MAX_SLABS slabs.
+constexpr int TI_MAX_SLABS = 2048;
+template <int Q, bool CARRY>
+__global__ void k_time_integrate_s(const double* __restrict__ z, double* __restrict__ w, int nrows, int N_t,
+                                   const double* __restrict__ carry) {
+  pdl_entry();
+  extern __shared__ __align__(16) double ti_smem[];
+  using V = typename std::conditional<Q == 2, double2, double>::type;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int C = (N_t + 31) / 32;
+  const int Cp = (C + 1) | 1;
+  V* sv = reinterpret_cast<V*>(ti_smem) + (int64_t)wb * 32 * Cp;
+  const int v = blockIdx.x * (blockDim.x >> 5) + wb;
+  if (v >= nrows) return;
+  const V* zr = reinterpret_cast<const V*>(z + (int64_t)v * N_t * Q);
+  V* wr = reinterpret_cast<V*>(w + (int64_t)v * N_t * Q);
+  for (int i = lane; i < N_t; i += 32) sv[(i / C) * Cp + i % C] = zr[i];
+  __syncwarp();
+  const int n0 = lane * C, n1 = min(N_t, n0 + C);
+  V* my = sv + lane * Cp - n0;   // my[n] = slab n of this lane's chunk
+  double s = 0.0;
+  for (int n = n0; n < n1; ++n) {
+    if constexpr (Q == 2) s += my[n].x;
+    else s += my[n];
+  }
+  double incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  double e = incl - s;   // exclusive carry
+  if (CARRY) {
+    if constexpr (Q == 1) e += carry[v];
+    else e += carry[2 * v] + carry[2 * v + 1];
+  }
+  for (int n = n0; n < n1; ++n) {
+    if constexpr (Q == 1) {
+      e += my[n];
+      my[n] = e;
+    } else {
+      const double z0 = my[n].x, z1 = my[n].y;
+      my[n] = make_double2(0.5 * (z0 - z1) + e, 0.5 * (z0 + z1));
+      e += z0;
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < N_t; i += 32) wr[i] = sv[(i / C) * Cp + i % C];
+}
+
+// ---- per-column power-of-two scaling of complex FP32 columns (FP16 slab solve).
+// Thread t of block (bx, by) owns column bx * 128 + t and rows by * COL_ROWS ...: loads
+// of consecutive threads are consecutive columns of one row (coalesced).
+constexpr int COL_THREADS = 128;
+constexpr int COL_ROWS = 256;
+
+__device__ __forceinline__ float col_factor(unsigned bits) {
+  // s = 2^(1 - e) for max = m 2^e, m in [0.5, 1): max * s in [1, 2); 1 for a zero column
+  const float mx = __uint_as_float(bits);
+  if (!(mx > 0.f)) return 1.f;
+  int e;
+  frexpf(mx, &e);
+  return ldexpf(1.f, 1 - e);
+}
+
+__global__ void k_col_absmax(const float2* __restrict__ Q, int nrows, int cnt, int ld, unsigned* __restrict__ colmax) {
+  pdl_entry();
+  const int c = blockIdx.x * COL_THREADS + threadIdx.x;
+  if (c >= cnt) return;
+  const int r0 = blockIdx.y * COL_ROWS, r1 = min(nrows, r0 + COL_ROWS);
+  float m = 0.f;
+  for (int r = r0; r < r1; ++r) {
+    const float2 v = Q[(int64_t)r * ld + c];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  atomicMax(colmax + c, __float_as_uint(m));   // non-negative floats order as their bit patterns
+}
+
+template <bool UNSCALE>
+__global__ void k_col_scale(float2* __restrict__ Q, int nrows, int cnt, int ld, const unsigned* __restrict__ colmax) {
+  pdl_entry();
+  const int c = blockIdx.x * COL_THREADS + threadIdx.x;
+  if (c >= cnt) return;
+  const float s0 = col_factor(colmax[c]);
+  const float s = UNSCALE ? 1.f / s0 : s0;   // exact: a power of two
+  const int r0 = blockIdx.y * COL_ROWS, r1 = min(nrows, r0 + COL_ROWS);
+  for (int r = r0; r < r1; ++r) {
+    float2 v = Q[(int64_t)r * ld + c];
+    v.x *= s;
+    v.y *= s;
+    Q[(int64_t)r * ld + c] = v;
+  }
+}
+
+__global__ void k_fill_u32(unsigned* v, int n, unsigned value) {
+  pdl_entry();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = value;
+}
+
 // ---- time-slab sharding (the time axis split into contiguous slab ranges, one per
 // rank, Section 2.1's time-parallel groups): the two couplings between ranges.
 // out[row q + i] = v[row ld + off + i]: one slab of every row (the halo a range sends on).
 __global__ void k_slab_copy(const double* __restrict__ v, int64_t ld, int64_t off, int q, int nrows,
                             double* __restrict__ out) {
+  pdl_entry();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)nrows * q) return;
   out[t] = v[(t / q) * ld + off + t % q];
@@ -642,6 +819,7 @@ __global__ void k_slab_copy(const double* __restrict__ v, int64_t ld, int64_t of
 __global__ void k_halo_history(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const double* __restrict__ m, const double* __restrict__ xh, double* __restrict__ r,
                                int64_t ld, int degree) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nrows) return;
   double mx0 = 0.0, mx1 = 0.0;
@@ -667,6 +845,7 @@ __global__ void k_halo_history(int nrows, const int64_t* __restrict__ rowptr, co
 // range holds at least one slab, so T^{len} = T).  ends[k][v q + i].
 __global__ void k_time_carry(const double* __restrict__ ends, int n_prev, int nrows, int degree,
                              double* __restrict__ carry) {
+  pdl_entry();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nrows) return;
   const int q = degree + 1;
@@ -688,6 +867,7 @@ __global__ void k_nodal_jacobi(int nrows, const int64_t* __restrict__ rowptr, co
                                const double* __restrict__ kv, const double* __restrict__ dinv,
                                const double* __restrict__ y, const double* __restrict__ zi, double* __restrict__ zo,
                                int ncols, double wgt) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (v >= nrows) return;
@@ -707,6 +887,7 @@ __global__ void k_nodal_jacobi(int nrows, const int64_t* __restrict__ rowptr, co
 // (1, -1/2 + phi_1/2), to the second (1, 1/2 + phi_1/2), i.e. the blocks
 // P0 = [[1, -1/2], [0, 1/2]] and P1 = [[1, 1/2], [0, 1/2]].
 __global__ void k_time_restrict(const double* __restrict__ r, double* __restrict__ rc, int Nc, int degree) {
+  pdl_entry();
   const int e = blockIdx.x;
   if (degree == 0) {
     const double* src = r + (int64_t)e * 2 * Nc;
@@ -723,6 +904,7 @@ __global__ void k_time_restrict(const double* __restrict__ r, double* __restrict
 }
 
 __global__ void k_time_prolong_add(const double* __restrict__ ec, double* __restrict__ x, int Nc, int degree) {
+  pdl_entry();
   const int e = blockIdx.x;
   if (degree == 0) {
     const double* src = ec + (int64_t)e * Nc;
@@ -751,6 +933,7 @@ __global__ void k_time_prolong_add(const double* __restrict__ ec, double* __rest
 __global__ void k_csr_spmm(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const double* __restrict__ pv, const double* __restrict__ in, double* __restrict__ out,
                            int ncols, int beta) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int rrow = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (rrow >= nrows) return;
@@ -766,6 +949,7 @@ __global__ void k_csr_spmm(int nrows, const int64_t* __restrict__ rowptr, const 
 __global__ void k_history_rhs(int nrows, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               const double* __restrict__ m, const double* __restrict__ f,
                               const double* __restrict__ x, double* __restrict__ g, int N_t, int n, int degree) {
+  pdl_entry();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nrows) return;
   const int q = degree + 1;
@@ -788,15 +972,18 @@ __global__ void k_history_rhs(int nrows, const int64_t* __restrict__ rowptr, con
 }
 
 __global__ void k_fill(double* v, int64_t n, double value) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = value;
 }
 __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
 __global__ void k_outer_load(const double* __restrict__ b, const double* __restrict__ c, double* __restrict__ f,
                              int ncols, int row_stride) {
+  pdl_entry();
   const int e = blockIdx.x;
   const double be = b[e];
   for (int j = threadIdx.x; j < ncols; j += blockDim.x) f[(int64_t)e * row_stride + j] = c[j] * be;
@@ -806,6 +993,7 @@ __global__ void k_outer_load(const double* __restrict__ b, const double* __restr
 // sums rows x, x + gridDim.x, ... of problem b in a fixed order.
 __global__ void k_batch_norm_partial(const double* __restrict__ v, int nrows, int nb, int seg,
                                      double* __restrict__ partial) {
+  pdl_entry();
   const int b = blockIdx.y;
   double s = 0.0;
   for (int e = blockIdx.x; e < nrows; e += gridDim.x) {
@@ -816,6 +1004,7 @@ __global__ void k_batch_norm_partial(const double* __restrict__ v, int nrows, in
 }
 
 __global__ void k_batch_norm_final(const double* __restrict__ partial, int g, double* __restrict__ out) {
+  pdl_entry();
   double s = 0.0;
   for (int i = threadIdx.x; i < g; i += blockDim.x) s += partial[(int64_t)blockIdx.x * g + i];
   block_sum_store<256>(s, out + blockIdx.x);
@@ -823,6 +1012,7 @@ __global__ void k_batch_norm_final(const double* __restrict__ partial, int g, do
 
 // v[e * stride + offset + j] = 0 for j < count (one problem's columns of a batched vector)
 __global__ void k_zero_cols(double* __restrict__ v, int nrows, int stride, int offset, int count) {
+  pdl_entry();
   for (int e = blockIdx.x; e < nrows; e += gridDim.x)
     for (int j = threadIdx.x; j < count; j += blockDim.x) v[(int64_t)e * stride + offset + j] = 0.0;
 }
@@ -846,6 +1036,9 @@ std::atomic<int64_t> g_launches{0};
 
 int64_t launch_count() { return g_launches.load(); }
 void count_launches(int64_t n) { g_launches += n; }
+std::atomic<bool> g_overlap{false};
+bool launch_overlap() { return g_overlap.load(std::memory_order_relaxed); }
+void set_launch_overlap(bool on) { g_overlap.store(on); }
 
 int residual_blocks(int nrows) { return (nrows + RES_WARPS - 1) / RES_WARPS; }
 
@@ -864,12 +1057,12 @@ int lanes_per_row(int N_t) {
     if (nblocks) *nblocks = nb;                                                                     \
     if (nb <= 0) break;                                                                             \
     switch (lpr) {                                                                                  \
-      case 1: KERNEL<1><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
-      case 2: KERNEL<2><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
-      case 4: KERNEL<4><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
-      case 8: KERNEL<8><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                         \
-      case 16: KERNEL<16><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                       \
-      default: KERNEL<32><<<nb, RES_WARPS * 32, 0, st>>>(__VA_ARGS__); break;                       \
+      case 1: launch_k(KERNEL<1>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 2: launch_k(KERNEL<2>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 4: launch_k(KERNEL<4>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 8: launch_k(KERNEL<8>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 16: launch_k(KERNEL<16>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      default: launch_k(KERNEL<32>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
     }                                                                                               \
     count_launches(1);                                                                              \
   } while (0)
@@ -892,14 +1085,14 @@ int batch_norm_scratch(int nb) { return nb * BATCH_NORM_BLOCKS; }
 cudaError_t batch_norms_sq(const double* v, int nrows, int nb, int seg, double* partial, double* out,
                            cudaStream_t st) {
   if (nrows <= 0 || nb <= 0) return cudaSuccess;
-  { k_batch_norm_partial<<<dim3(BATCH_NORM_BLOCKS, nb), 256, 0, st>>>(v, nrows, nb, seg, partial); count_launches(1); }
-  { k_batch_norm_final<<<nb, 256, 0, st>>>(partial, BATCH_NORM_BLOCKS, out); count_launches(1); }
+  { launch_k(k_batch_norm_partial, dim3(BATCH_NORM_BLOCKS, nb), 256, 0, st, v, nrows, nb, seg, partial); count_launches(1); }
+  { launch_k(k_batch_norm_final, nb, 256, 0, st, partial, BATCH_NORM_BLOCKS, out); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t zero_cols(double* v, int nrows, int stride, int offset, int count, cudaStream_t st) {
   if (nrows > 0 && count > 0) {
-    k_zero_cols<<<(unsigned)std::min(nrows, 4096), 128, 0, st>>>(v, nrows, stride, offset, count);
+    launch_k(k_zero_cols, (unsigned)std::min(nrows, 4096), 128, 0, st, v, nrows, stride, offset, count);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -911,7 +1104,7 @@ cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st) {
 }
 
 cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st) {
-  if (n > 0) { k_split_pairs<<<(unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st>>>(x, xs, n); count_launches(1); }
+  if (n > 0) { launch_k(k_split_pairs, (unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st, x, xs, n); count_launches(1); }
   return cudaGetLastError();
 }
 
@@ -928,144 +1121,187 @@ cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const 
 }
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st) {
-  { k_reduce_partials<<<1, 256, 0, st>>>(partial, n, out); count_launches(1); }
+  { launch_k(k_reduce_partials, 1, 256, 0, st, partial, n, out); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t norm2_sq(const double* v, int64_t n, double* partial, double* out, cudaStream_t st) {
-  { k_norm_partial<<<NORM_BLOCKS, 256, 0, st>>>(v, n, partial); count_launches(1); }
-  { k_reduce_partials<<<1, 256, 0, st>>>(partial, NORM_BLOCKS, out); count_launches(1); }
+  { launch_k(k_norm_partial, NORM_BLOCKS, 256, 0, st, v, n, partial); count_launches(1); }
+  { launch_k(k_reduce_partials, 1, 256, 0, st, partial, NORM_BLOCKS, out); count_launches(1); }
   return cudaGetLastError();
 }
 
 cudaError_t slab_pre_dg0(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg0<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_pre_dg0, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg1(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                          double2 c0, double2 c1, double2* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg1<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_pre_dg1, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg0(const double* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
                           int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg0<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_post_dg0, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg1(const double2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                           int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg1<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_post_dg1, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg0f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                           float* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg0f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_pre_dg0f, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, r, src_ld, slab0, cnt, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_pre_dg1f(const double* r, int src_ld, int slab0, int cnt, const int32_t* iperm, int nrows,
                           double2 c0, double2 c1, float2* Q, int ld, cudaStream_t st) {
-  if (nrows > 0) { k_slab_pre_dg1f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_pre_dg1f, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, r, src_ld, slab0, cnt, iperm, c0, c1, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg0f(const float* X, int ld, const int32_t* iperm, int nrows, double* x, int dst_ld,
                            int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg0f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_post_dg0f, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t slab_post_dg1f(const float2* X, int ld, const int32_t* iperm, int nrows, double2 s1, double* x,
                            int dst_ld, int slab0, int cnt, double omega, int mode, cudaStream_t st) {
-  if (nrows > 0) { k_slab_post_dg1f<<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
+  if (nrows > 0) { launch_k(k_slab_post_dg1f, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, s1, x, dst_ld, slab0, cnt, omega, mode); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm(const double* y, int ncols, const int32_t* iperm, int nrows, double* Q, int ld,
                         cudaStream_t st) {
-  if (nrows > 0) { k_gather_perm<double><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, y, ncols, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_gather_perm<double>, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm(const double* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                          cudaStream_t st) {
-  if (nrows > 0) { k_scatter_perm<double><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, z, ncols); count_launches(1); }
+  if (nrows > 0) { launch_k(k_scatter_perm<double>, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t gather_perm_f(const double* y, int ncols, const int32_t* iperm, int nrows, float* Q, int ld,
                           cudaStream_t st) {
-  if (nrows > 0) { k_gather_perm<float><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, y, ncols, iperm, Q, ld); count_launches(1); }
+  if (nrows > 0) { launch_k(k_gather_perm<float>, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, y, ncols, iperm, Q, ld); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t scatter_perm_f(const float* X, int ld, const int32_t* iperm, int nrows, double* z, int ncols,
                            cudaStream_t st) {
-  if (nrows > 0) { k_scatter_perm<float><<<grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st>>>(nrows, X, ld, iperm, z, ncols); count_launches(1); }
+  if (nrows > 0) { launch_k(k_scatter_perm<float>, grid1(nrows, SLAB_ROWS), SLAB_ROWS * 32, 0, st, nrows, X, ld, iperm, z, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_T(CsrView GT, const int8_t* gt_sign, const double* r, double* y, int ncols, cudaStream_t st) {
-  if (GT.nrows > 0) { k_grad_T<<<dim3(grid1(GT.nrows, GT_WARPS), (unsigned)std::max<int64_t>(1, grid1(ncols / 2, GT_CHUNK))), GT_WARPS * 32, 0, st>>>(GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols); count_launches(1); }
+  if (GT.nrows > 0) { launch_k(k_grad_T, dim3(grid1(GT.nrows, GT_WARPS), (unsigned)std::max<int64_t>(1, grid1(ncols / 2, GT_CHUNK))), GT_WARPS * 32, 0, st, GT.nrows, GT.rowptr, GT.col, gt_sign, r, y, ncols); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t grad_add(const int32_t* tail, const int32_t* head, int nedges, const double* w, double* x, int ncols,
                      cudaStream_t st) {
-  if (nedges > 0) { k_grad_add<<<nedges, 128, 0, st>>>(tail, head, w, x, ncols); count_launches(1); }
+  if (nedges <= 0) return cudaSuccess;
+  if (ncols & 1)
+    launch_k(k_grad_add, nedges, 128, 0, st, tail, head, w, x, ncols);
+  else
+    launch_k(k_grad_add_w, grid1(nedges, GA_WARPS), GA_WARPS * 32, 0, st, tail, head, w, x, nedges, ncols);
+  count_launches(1);
   return cudaGetLastError();
 }
+// Shared-memory scan when the rows fit (warps per block so that a block holds <= 48 KiB),
+// the register scan otherwise.
+template <bool CARRY>
+void time_integrate_launch(const double* z, const double* carry, double* w, int nrows, int N_t, int degree,
+                           cudaStream_t st) {
+  if (nrows <= 0) return;
+  const int q = degree + 1;
+  const int C = (N_t + 31) / 32;
+  const size_t warp_bytes = (size_t)32 * ((C + 1) | 1) * q * sizeof(double);
+  if (N_t > TI_MAX_SLABS) {
+    launch_k(k_time_integrate<CARRY>, grid1(nrows, 8), 256, 0, st, z, w, nrows, N_t, degree, carry);
+  } else {
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / warp_bytes));
+    const size_t smem = warp_bytes * wpb;
+    if (degree == 0)
+      launch_k(k_time_integrate_s<1, CARRY>, grid1(nrows, wpb), wpb * 32, smem, st, z, w, nrows, N_t, carry);
+    else
+      launch_k(k_time_integrate_s<2, CARRY>, grid1(nrows, wpb), wpb * 32, smem, st, z, w, nrows, N_t, carry);
+  }
+  count_launches(1);
+}
+
 cudaError_t time_integrate(const double* z, double* w, int nrows, int N_t, int degree, cudaStream_t st) {
-  if (nrows > 0) { k_time_integrate<false><<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree, nullptr); count_launches(1); }
+  time_integrate_launch<false>(z, nullptr, w, nrows, N_t, degree, st);
+  return cudaGetLastError();
+}
+cudaError_t col_scale(float2* Q, int nrows, int cnt, int ld, unsigned* colmax, cudaStream_t st) {
+  if (nrows <= 0 || cnt <= 0) return cudaSuccess;
+  const dim3 g(grid1(cnt, COL_THREADS), grid1(nrows, COL_ROWS));
+  launch_k(k_fill_u32, grid1(cnt, 256), 256, 0, st, colmax, cnt, 0u);
+  launch_k(k_col_absmax, g, COL_THREADS, 0, st, Q, nrows, cnt, ld, colmax);
+  launch_k(k_col_scale<false>, g, COL_THREADS, 0, st, Q, nrows, cnt, ld, colmax);
+  count_launches(3);
+  return cudaGetLastError();
+}
+cudaError_t col_unscale(float2* Q, int nrows, int cnt, int ld, const unsigned* colmax, cudaStream_t st) {
+  if (nrows <= 0 || cnt <= 0) return cudaSuccess;
+  const dim3 g(grid1(cnt, COL_THREADS), grid1(nrows, COL_ROWS));
+  launch_k(k_col_scale<true>, g, COL_THREADS, 0, st, Q, nrows, cnt, ld, colmax);
+  count_launches(1);
   return cudaGetLastError();
 }
 cudaError_t time_integrate_carry(const double* z, const double* carry, double* w, int nrows, int N_t, int degree,
                                  cudaStream_t st) {
-  if (nrows > 0) { k_time_integrate<true><<<grid1(nrows, 8), 256, 0, st>>>(z, w, nrows, N_t, degree, carry); count_launches(1); }
+  time_integrate_launch<true>(z, carry, w, nrows, N_t, degree, st);
   return cudaGetLastError();
 }
 cudaError_t slab_copy(const double* v, int64_t ld, int64_t off, int q, int nrows, double* out, cudaStream_t st) {
   const int64_t n = (int64_t)nrows * q;
-  if (n > 0) { k_slab_copy<<<(unsigned)grid1(n, 256), 256, 0, st>>>(v, ld, off, q, nrows, out); count_launches(1); }
+  if (n > 0) { launch_k(k_slab_copy, (unsigned)grid1(n, 256), 256, 0, st, v, ld, off, q, nrows, out); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t halo_history(CsrView A, const double* m, const double* xh, double* r, int64_t ld, int degree,
                          cudaStream_t st) {
-  if (A.nrows > 0) { k_halo_history<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, xh, r, ld, degree); count_launches(1); }
+  if (A.nrows > 0) { launch_k(k_halo_history, grid1(A.nrows, 128), 128, 0, st, A.nrows, A.rowptr, A.col, m, xh, r, ld, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_carry(const double* ends, int n_prev, int nrows, int degree, double* carry, cudaStream_t st) {
-  if (nrows > 0) { k_time_carry<<<grid1(nrows, 128), 128, 0, st>>>(ends, n_prev, nrows, degree, carry); count_launches(1); }
+  if (nrows > 0) { launch_k(k_time_carry, grid1(nrows, 128), 128, 0, st, ends, n_prev, nrows, degree, carry); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
                          double* zo, int ncols, double wgt, cudaStream_t st) {
   if (Kn.nrows > 0)
-    { k_nodal_jacobi<<<grid1(Kn.nrows, 8), 256, 0, st>>>(Kn.nrows, Kn.rowptr, Kn.col, kval, dinv, y, zi, zo, ncols,
+    { launch_k(k_nodal_jacobi, grid1(Kn.nrows, 8), 256, 0, st, Kn.nrows, Kn.rowptr, Kn.col, kval, dinv, y, zi, zo, ncols,
                                                        wgt); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) { k_time_restrict<<<nrows, 128, 0, st>>>(r, rc, Nc, degree); count_launches(1); }
+  if (nrows > 0) { launch_k(k_time_restrict, nrows, 128, 0, st, r, rc, Nc, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) { k_time_prolong_add<<<nrows, 128, 0, st>>>(ec, x, Nc, degree); count_launches(1); }
+  if (nrows > 0) { launch_k(k_time_prolong_add, nrows, 128, 0, st, ec, x, Nc, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,
                      cudaStream_t st) {
-  if (P.nrows > 0) { k_csr_spmm<<<grid1(P.nrows, 8), 256, 0, st>>>(P.nrows, P.rowptr, P.col, pval, in, out, ncols, beta); count_launches(1); }
+  if (P.nrows > 0) { launch_k(k_csr_spmm, grid1(P.nrows, 8), 256, 0, st, P.nrows, P.rowptr, P.col, pval, in, out, ncols, beta); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t history_rhs(CsrView A, const double* m, const double* f, const double* x, double* g, int N_t, int n,
                         int degree, cudaStream_t st) {
-  if (A.nrows > 0) { k_history_rhs<<<grid1(A.nrows, 128), 128, 0, st>>>(A.nrows, A.rowptr, A.col, m, f, x, g, N_t, n, degree); count_launches(1); }
+  if (A.nrows > 0) { launch_k(k_history_rhs, grid1(A.nrows, 128), 128, 0, st, A.nrows, A.rowptr, A.col, m, f, x, g, N_t, n, degree); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t vec_fill(double* v, int64_t n, double value, cudaStream_t st) {
-  if (n > 0) { k_fill<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(v, n, value); count_launches(1); }
+  if (n > 0) { launch_k(k_fill, (unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st, v, n, value); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t vec_copy(const double* a, double* b, int64_t n, cudaStream_t st) {
-  if (n > 0) { k_copy<<<(unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st>>>(a, b, n); count_launches(1); }
+  if (n > 0) { launch_k(k_copy, (unsigned)std::min<int64_t>(grid1(n, 256), 4096), 256, 0, st, a, b, n); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t outer_load(const double* b, const double* c, double* f, int nrows, int ncols, int row_stride,
                        cudaStream_t st) {
-  if (nrows > 0) { k_outer_load<<<nrows, 128, 0, st>>>(b, c, f, ncols, row_stride); count_launches(1); }
+  if (nrows > 0) { launch_k(k_outer_load, nrows, 128, 0, st, b, c, f, ncols, row_stride); count_launches(1); }
   return cudaGetLastError();
 }
 

@@ -18,8 +18,12 @@
 // error in *err, waits (bounded) for its copies and MMAs in flight and skips its
 // epilogue.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "device.h"
+#include "launch.cuh"
 
 namespace stmg {
 namespace {
@@ -52,9 +56,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                              ((uint32_t)(TC_M >> 4) << 24);
+// instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B both BF16
+// (bits 7-9 and 10-12 = 1) or both FP16 (0), both K-major, N >> 3 and M >> 4
+template <bool F16>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (F16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(TC_N >> 3) << 17) |
+         ((uint32_t)(TC_M >> 4) << 24);
+}
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   uint32_t done = 0;
@@ -90,8 +98,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+template <bool F16>
 __device__ __forceinline__ void put_g(uint8_t* Bs, int c, int k, float2 g) {
-  *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(c, 2 * k)) = __floats2bfloat162_rn(g.x, g.y);
+  if (F16)
+    *reinterpret_cast<__half2*>(Bs + core_off(c, 2 * k)) = __floats2half2_rn(g.x, g.y);
+  else
+    *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(c, 2 * k)) = __floats2bfloat162_rn(g.x, g.y);
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -110,6 +122,7 @@ __global__ void __launch_bounds__(256) k_sn_tc_reduce(const DevNode* __restrict_
                                                       int64_t n_items, const float2* __restrict__ P,
                                                       float2* __restrict__ Z, float2* __restrict__ U,
                                                       float2* __restrict__ X, int nrhs, int ld) {
+  pdl_entry();
   const int4 un = units[blockIdx.x];
   const DevNode nd = nodes[un.x];
   const int nc = nd.nc, m = nd.nc + nd.nr;
@@ -168,7 +181,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 // tile gy * pre(node) + ct * kstages(node) + ks of Bst, the (Re, Im) pairs of the
 // gathered right-hand side (forward: Q + children's update rows; backward: z of the
 // node's columns, x of its below-structure rows) rounded to BF16 in operand layout.
-template <bool FWD>
+template <bool FWD, bool F16>
 __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__ nodes,
                                                      const int32_t* __restrict__ gsrc,
                                                      const int32_t* __restrict__ rows,
@@ -177,6 +190,7 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
                                                      const float2* __restrict__ Z, const float2* __restrict__ U,
                                                      const float2* __restrict__ X, uint8_t* __restrict__ Bst, int nrhs,
                                                      int ld) {
+  pdl_entry();
   const int2 it = items[blockIdx.x];
   const int s = it.x, ks = it.y, ct = blockIdx.y, gy = gridDim.y;
   const DevNode nd = nodes[s];
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
         g = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
       }
     }
-    put_g(tile, cl, kk, g);
+    put_g<F16>(tile, cl, kk, g);
   }
   __syncthreads();
   // the finished tile leaves in 16-byte pieces, consecutive threads consecutive pieces
@@ -215,7 +229,7 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
 // SPLIT = false: grid over (node, row tile) tiles, whole K range; SPLIT = true: grid
 // over (node, row tile, k0, k1) items (k0, k1 multiples of 32 complex), partial
 // products to P for k_sn_tc_reduce.
-template <bool FWD, bool SPLIT>
+template <bool FWD, bool SPLIT, bool F16>
 __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict__ nodes,
                                                        const uint8_t* __restrict__ TW,
                                                        const int4* __restrict__ tnode, const int2* __restrict__ tpre,
@@ -226,6 +240,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
                                                        float2* __restrict__ Z, float2* __restrict__ U,
                                                        float2* __restrict__ X, float2* __restrict__ P, int nrhs, int ld,
                                                        int* __restrict__ err) {
+  pdl_entry();
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full[TC2_STAGES], empty[TC2_STAGES], done;
   __shared__ uint32_t tmem_slot;
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+            "l"(ad), "l"(bd), "r"(tc_idesc<F16>()), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty[slot])));
@@ -377,15 +392,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
 
 }  // namespace
 
-cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool fwd, bool split, float2* Q,
-                         float2* Z, float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, int* err,
-                         cudaStream_t st) {
-  static bool attr_set = false;
+template <typename WT>
+cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool split, float2* Q, float2* Z,
+                         float2* U, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy, cudaStream_t st) {
+  constexpr bool H = std::is_same<WT, __half2>::value;
+  int* err = sy.err;
+  static bool attr_set = false;   // per instantiation
   if (!attr_set) {
-    cudaFuncSetAttribute(k_sn_tc2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
-    cudaFuncSetAttribute(k_sn_tc2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
-    cudaFuncSetAttribute(k_sn_tc2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
-    cudaFuncSetAttribute(k_sn_tc2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<true, false, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<false, false, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<true, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc2<false, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
     attr_set = true;
   }
   const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
@@ -393,10 +410,10 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool
   const int64_t aa = ao[d], ab = ao[d + 1];
   if (ab <= aa) return cudaSuccess;
   if (fwd)
-    k_tc_assemble<true><<<dim3((unsigned)(ab - aa), gy), 256, 0, st>>>(F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
+    launch_k(k_tc_assemble<true, H>, dim3((unsigned)(ab - aa), gy), 256, 0, st, F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
                                                                         F.tas_f + aa, Q, Z, U, Q, Bst, nrhs, ld);
   else
-    k_tc_assemble<false><<<dim3((unsigned)(ab - aa), gy), 256, 0, st>>>(F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
+    launch_k(k_tc_assemble<false, H>, dim3((unsigned)(ab - aa), gy), 256, 0, st, F.nodes, F.gsrc, F.rows, F.tnode, F.tpre,
                                                                          F.tas_b + aa, Q, Z, U, Q, Bst, nrhs, ld);
   count_launches(1);
   const uint8_t* TW = fwd ? F.tw_f : F.tw_b;
@@ -405,31 +422,38 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, __nv_bfloat162>& F, int d, bool
     const int64_t a = to[d], b = to[d + 1];
     const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;
     if (fwd)
-      k_sn_tc2<true, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st>>>(
-          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
+      launch_k(k_sn_tc2<true, false, H>, dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st, F.nodes, TW, F.tnode,
+               F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
     else
-      k_sn_tc2<false, false><<<dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st>>>(
-          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
+      launch_k(k_sn_tc2<false, false, H>, dim3((unsigned)(b - a), gy), TC_THREADS, TC2_SMEM, st, F.nodes, TW, F.tnode,
+               F.tpre, Bst, F.Dinv, F.gsrc, tl, nullptr, Z, U, Q, nullptr, nrhs, ld, err);
     count_launches(1);
   } else {
     const int64_t* io = fwd ? F.h_tcf_item_off : F.h_tcb_item_off;
     const int64_t* uo = fwd ? F.h_tcf_unit_off : F.h_tcb_unit_off;
     const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
     const int4* its = (fwd ? F.tcf_items : F.tcb_items) + ia;
+    const int4* uns = (fwd ? F.tcf_units : F.tcb_units) + ua;
     if (fwd) {
-      k_sn_tc2<true, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
-          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
-      k_sn_tc_reduce<true><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcf_units + ua,
-                                                                           ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
+      launch_k(k_sn_tc2<true, true, H>, dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st, F.nodes, TW, F.tnode,
+               F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
+      launch_k(k_sn_tc_reduce<true>, dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st, F.nodes,
+               F.Dinv, F.gsrc, uns, ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
     } else {
-      k_sn_tc2<false, true><<<dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st>>>(
-          F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
-      k_sn_tc_reduce<false><<<dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st>>>(F.nodes, F.Dinv, F.gsrc, F.tcb_units + ua,
-                                                                            ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
+      launch_k(k_sn_tc2<false, true, H>, dim3((unsigned)(ib - ia), gy), TC_THREADS, TC2_SMEM, st, F.nodes, TW,
+               F.tnode, F.tpre, Bst, F.Dinv, F.gsrc, nullptr, its, Z, U, Q, Ptc, nrhs, ld, err);
+      launch_k(k_sn_tc_reduce<false>, dim3((unsigned)(ub - ua), gy, TC_ROWS / TC_RED_ROWS), 256, 0, st, F.nodes,
+               F.Dinv, F.gsrc, uns, ia, ib - ia, Ptc, Z, U, Q, nrhs, ld);
     }
     count_launches(2);
   }
   return cudaGetLastError();
 }
+
+template cudaError_t sn_tc2_depth<__nv_bfloat162>(const DevFactor<float2, __nv_bfloat162>&, int, bool, bool, float2*,
+                                                   float2*, float2*, float2*, uint8_t*, int, int, const SkSync&,
+                                                   cudaStream_t);
+template cudaError_t sn_tc2_depth<__half2>(const DevFactor<float2, __half2>&, int, bool, bool, float2*, float2*,
+                                           float2*, float2*, uint8_t*, int, int, const SkSync&, cudaStream_t);
 
 }  // namespace stmg

@@ -183,3 +183,36 @@ def test_request_failures_reported(stmg):
         with pytest.raises(B.StMgError):
             srv.submit(*args, exc, 1e-8)   # unregistered mesh, degree, N_t, tau, sigma scale
     srv.close()
+
+
+def test_served_request_with_conductivity_scale_matches_oracle_time_stepping(stmg):
+    """A request (s sigma, tau) is served as (sigma, tau / s) by the time rescaling t = s t'
+    (the substitution divides the whole space-time system and its load by s).  The served
+    solution is compared directly with the oracle's sequential time stepping (Section
+    2.1, eq. timeStepping, and its DG(1) form) of the original problem: conductivity
+    s sigma, N_t slabs of step tau, T = N_t tau, both degrees."""
+    from helpers import from_lib
+    from oracle.load import spacetime_load
+    from oracle.spacetime import SlabOperator, build_space_hierarchy, sequential_solve
+
+    n = 4
+    nu, sigma = mats(n)
+    srv = stmg.SpaceTimeServer(slots=2, slab_prec=0, nu=1, max_cycles=80)
+    srv.register(n, MESHES[n], nu, sigma)
+    reqs = [(1, 16, 1 / 16, 4.0, 9), (0, 8, 1 / 4, 0.25, 10)]     # (degree, N_t, tau, s, seed)
+    ids = {srv.submit(n, p, N_t, tau, s, st_inputs.excitation(seed), 1e-12): (p, N_t, tau, s, seed)
+           for p, N_t, tau, s, seed in reqs}
+    done = {}
+    for _ in range(100000):
+        for rid in srv.step():
+            done[ids[rid]] = srv.result(rid)
+        if len(done) == len(reqs):
+            break
+    srv.close()
+    for (p, N_t, tau, s, seed), r in done.items():
+        assert r["status"] == 0 and r["rel_res"] <= 1e-12, r
+        space = build_space_hierarchy(n, 1, nu, s * sigma)[0]
+        f = spacetime_load(space.mesh, st_inputs.excitation(seed), p, N_t, N_t * tau)
+        xs = sequential_solve(SlabOperator(space, p, tau), f)
+        err = rel(from_lib(r["x"], p + 1), xs)
+        assert err < 1e-9, (p, N_t, tau, s, err)

@@ -108,7 +108,7 @@ def test_host_setup_matches_oracle(B, n, nsl, p, coarsen, bc):
 def test_server_options_validated(B):
     o = B.st_mg_server_default_options()
     assert (o.slots, o.max_cycles, o.slab_prec, o.nu, o.omega, o.keep_x, o.max_builds) == (4, 50, 3, 2, 0.5, 1, 2)
-    for field, bad in (("slots", 0), ("max_cycles", 0), ("slab_prec", 4), ("omega", 0.0), ("mem_budget", -1),
+    for field, bad in (("slots", 0), ("max_cycles", 0), ("slab_prec", 5), ("omega", 0.0), ("mem_budget", -1),
                        ("max_builds", 0)):
         o = B.st_mg_server_default_options()
         setattr(o, field, bad)
