@@ -796,8 +796,9 @@ def main():
     # each solution against the FP64 one of the same excitation
     variants = {}
     if args.mixed:
-        for vname, prec in (("double_float", 2), ("mixed_fp32", 1), ("bf16_tensor", 3), ("fp16_tensor", 4)):
-            Sm = make(prec)
+        for vname, prec, kw in (("double_float", 2, {}), ("mixed_fp32", 1, {}), ("bf16_tensor", 3, {}),
+                                ("fp16_tensor", 4, {}), ("bf16_tensor_fp32_residual", 3, {"residual_prec": 1})):
+            Sm = make(prec, **kw)
             fm = Sm.load(st_inputs.excitation(W["seed"] + rank))
             xm = Sm.zeros()
             ms_m = reduce_max(time_cycles(Sm, fm, xm, args.steps), dist, "cuda")
@@ -812,7 +813,9 @@ def main():
                  "ms_per_step": ms_m / args.steps, "slab_solve_ms": slab_ms_m,
                  "slab_factor_macs_per_rhs": macs, "slab_solve_tflops": tflops,
                  "time_to_1e-8_s": dist_of(msolve, miters), "rel_err_vs_fp64_solution": merr,
-                 "residual": "double-float (FP32 pairs, about 48 significant bits) with FP64 f and r",
+                 "residual": ("double-float (FP32 pairs, about 48 significant bits) with FP64 f and r"
+                              if not kw else "FP32 inside each V-cycle, which runs in correction form around a "
+                              "double-float residual (also the stopping test)"),
                  "coarsest_solve": "FP64"}
             if prec in (3, 4):
                 peak = measured_peak("bf16_tflops")     # dense FP16 = dense BF16 rate on this part

@@ -137,7 +137,13 @@ typedef struct {
                                 Mode 2 solves K_n in double-float, mode 0 in FP64 */
     int32_t residual_prec;   /* space-time residual arithmetic: 0 FP64; 2 double-float (x split into
                                 FP32 pairs once per call, error-free products and sums, f and r in
-                                FP64); -1 (default): FP64 when slab_prec = 0, double-float otherwise */
+                                FP64); 1 FP32 inside the V-cycle: each V-cycle runs in correction form
+                                (r = f - L x in double-float, e = V(r) from e = 0 with every residual
+                                of the V-cycle in FP32 arithmetic on an FP32 copy of its iterate, then
+                                x += e), while st_mg_solve's stopping test, st_mg_residual and the
+                                correction's r stay double-float (the iteration's fixed point is
+                                unchanged; the FP32 rounding is relative to r, which shrinks);
+                                -1 (default): FP64 when slab_prec = 0, double-float otherwise */
     int32_t use_graph;       /* 1 (default): st_mg_vcycle / st_mg_solve capture the V-cycle's fixed
                                 launch sequence into a CUDA graph once per (f, x) buffer pair and replay
                                 it (needs a non-default stream; the first call captures, later calls
@@ -286,6 +292,16 @@ int st_mg_debug_get(st_mg_t h, int32_t what, int32_t level, void* host_buf, int6
  * `level`, evaluated on the host with the same factor and complex transformation
  * the device path uses.  r_host, y_host: host arrays in the level's layout. */
 int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, double* y_host);
+
+/* Convergence rate of the V-cycle by the power iteration of Section 5.1: V-cycles with
+ * f = 0 from the start x_dev (device, finest layout, overwritten by the iterates, which
+ * are then the errors), the l2 norm after each (the handle's deterministic reduction);
+ * rates_host[k] = ||x_{k+1}|| / ||x_k|| for the *n_rates cycles run, *rate = the largest.
+ * Stops after max_iter cycles, or when the norm reaches zero or falls below floor times
+ * the start's (Section 5.1 stops at a total reduction of 1e-100 against underflow).
+ * rates_host: host, max_iter doubles.  Blocking. */
+int st_mg_convergence_rate(st_mg_t h, double* x_dev, int32_t max_iter, double floor, double* rates_host,
+                           int32_t* n_rates, double* rate);
 
 /* Measured FP64 FMA throughput of the handle's device in TFLOP/s (about 70 ms of
  * independent FMA chains on 8 blocks per SM; blocking).  The FP64 kernels of this

@@ -103,6 +103,7 @@ _SIGS = {
     "st_mg_set_split_waves": [_vp, _i32, _i32],
     "st_mg_set_tc_mode": [_vp, _i32, _i32],
     "st_mg_set_launch_overlap": [_i32],
+    "st_mg_convergence_rate": [_vp, _vp, _i32, _dbl, _P(_dbl), _P(_i32), _P(_dbl)],
     "st_mg_slab_copy": [_vp, _i32, _i32, _vp, _i32, _vp],
     "st_mg_residual_halo": [_vp, _i32, _vp, _vp, _vp, _vp],
     "st_mg_time_integrate_carry": [_vp, _i32, _vp, _vp, _vp],
@@ -380,6 +381,15 @@ def st_mg_time_integrate_carry(h, level, z, carry, w):
 def st_mg_time_carry(h, level, ends, n_prev, carry):
     _check(lib().st_mg_time_carry(_vp(h), level, _opt_addr(ends) if n_prev > 0 else None, n_prev,
                                   _vp(_addr(carry))), "st_mg_time_carry")
+
+
+def st_mg_convergence_rate(h, x_dev, max_iter, floor):
+    rates = np.zeros(max_iter)
+    n = _i32(0)
+    rate = _dbl(0.0)
+    _check(lib().st_mg_convergence_rate(_vp(h), _vp(_addr(x_dev)), max_iter, floor, _dptr(rates), ctypes.byref(n),
+                                        ctypes.byref(rate)), "st_mg_convergence_rate")
+    return rate.value, list(rates[:n.value])
 
 
 def st_mg_set_launch_overlap(on):

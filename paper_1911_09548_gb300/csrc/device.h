@@ -193,6 +193,16 @@ cudaError_t residual_dg0_df(CsrView A, const float2* a, const float2* m, const d
                             int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
 cudaError_t residual_dg1_df(CsrView A, const float2* m, const float2* k0, const float2* k1, const double* f,
                             const float2* xs, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
+// FP32 residual (the correction-form V-cycle of residual_prec 1): x as FP32 (to_float),
+// FP32 coefficients and sums, f and r in FP64.
+cudaError_t to_float(const double* x, float* xf, int64_t n, cudaStream_t st);
+cudaError_t residual_dg0_f32(CsrView A, const float* a, const float* m, const double* f, const float* xf, double* r,
+                             int N_t, int seg, double* partial, int* nblocks, cudaStream_t st);
+cudaError_t residual_dg1_f32(CsrView A, const float* m, const float* k0, const float* k1, const double* f,
+                             const float* xf, double* r, int N_t, int seg, double* partial, int* nblocks,
+                             cudaStream_t st);
+// b += a
+cudaError_t vec_add(const double* a, double* b, int64_t n, cudaStream_t st);
 // out[0] = sum of partial[0..n) in a fixed order.
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t st);
 // out[0] = sum v^2 over n values (deterministic two-stage); partial has >= 1024 entries.

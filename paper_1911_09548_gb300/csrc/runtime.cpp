@@ -231,6 +231,7 @@ struct st_mg_s {
     double tau = 1.0;
     double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;   // residual coefficients per nnz
     float2 *p0 = nullptr, *p1 = nullptr, *p2 = nullptr;   // the same as (hi, lo) FP32 pairs
+    float *q0 = nullptr, *q1 = nullptr, *q2 = nullptr;    // ... rounded to FP32 (residual_prec 1)
     SupernodalFactor<double> fr;                            // host factors (released after upload)
     SupernodalFactor<cplx> fc;
     std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
@@ -253,7 +254,12 @@ struct st_mg_s {
   double* r0 = nullptr;                 // finest residual
   double* partial = nullptr;
   double* scalar = nullptr;
+  double* zero_f = nullptr;             // finest-level zero load of the rate harness (allocated on first use)
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
+  bool res32 = false;                   // residual_prec 1: FP32 residuals inside a correction-form V-cycle
+  float* xf32 = nullptr;                // x as FP32 for those residuals
+  double* corr_r = nullptr;             // correction form: outer residual r = f - L x (finest level)
+  double* corr_e = nullptr;             //   and the correction e = V(r), x += e
   int nodal_prec = 0;                   // nodal K_n solve: 0 FP64, 1 FP32 (slab_prec 1, 3), 2 double-float
   int* tc_err = nullptr;                // flags[0]: set by a block whose bounded wait timed out
   int* flags = nullptr;                 // [0] wait error, [1] spare, [2..3] grid-barrier words
@@ -580,12 +586,22 @@ int hw_threads(int req) {
 }
 
 // ---------------------------------------------------------------- operations
-void op_residual(Handle& h, int l, const double* f, const double* x, double* r, double* norm_sq_host) {
+// outer: a residual whose accuracy decides the fixed point (the solve's stopping test, the
+// public entry points, the correction form's residual); inner: the smoothers' and the
+// restriction's residuals inside a V-cycle, FP32 with residual_prec 1.
+void op_residual(Handle& h, int l, const double* f, const double* x, double* r, double* norm_sq_host,
+                 bool outer = false) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
   int nb = 0;
   double* part = norm_sq_host ? h.partial : nullptr;
-  if (h.df_residual) {
+  if (h.res32 && !outer) {
+    CK(to_float(x, h.xf32, L.len, h.stream));
+    if (h.prob.degree == 0)
+      CK(residual_dg0_f32(view(S), L.q0, L.q1, f, h.xf32, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+    else
+      CK(residual_dg1_f32(view(S), L.q0, L.q1, L.q2, f, h.xf32, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+  } else if (h.df_residual) {
     CK(split_pairs(x, h.xsplit, L.len, h.stream));
     if (h.prob.degree == 0)
       CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
@@ -838,11 +854,27 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
   op_smooth(h, l, f, x, h.opt.nu_post, true);
 }
 
+// The finest-level V-cycle x <- x + V(f - L x).  With residual_prec 1 it runs in
+// correction form: r = f - L x (outer, double-float), e = V(r) from e = 0 with FP32
+// residuals inside (their rounding is relative to r, which shrinks as x converges),
+// x += e; the same iteration in exact arithmetic, since a V-cycle is affine in (f, x).
+void op_vcycle_top(Handle& h, const double* f, double* x) {
+  if (!h.res32) {
+    op_vcycle(h, 0, f, x);
+    return;
+  }
+  const int64_t len = h.lv[0].len;
+  op_residual(h, 0, f, x, h.corr_r, nullptr, true);
+  CK(vec_fill(h.corr_e, len, 0.0, h.stream));
+  op_vcycle(h, 0, h.corr_r, h.corr_e);
+  CK(vec_add(h.corr_e, x, len, h.stream));
+}
+
 // One V-cycle on the finest level.  With use_graph and a non-default stream the
 // fixed launch sequence is captured once per (f, x) pair and replayed.
 void run_vcycle(Handle& h, const double* f, double* x) {
   if (!h.opt.use_graph || h.stream == nullptr) {
-    op_vcycle(h, 0, f, x);
+    op_vcycle_top(h, f, x);
     return;
   }
   if (!h.graph_exec || h.graph_f != f || h.graph_x != x) {
@@ -854,7 +886,7 @@ void run_vcycle(Handle& h, const double* f, double* x) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
     try {
-      op_vcycle(h, 0, f, x);
+      op_vcycle_top(h, f, x);
     } catch (...) {
       cudaStreamEndCapture(h.stream, &g);
       if (g) cudaGraphDestroy(g);
@@ -923,7 +955,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 4 || (op->slab_prec >= 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
       (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
-      (op->residual_prec != -1 && op->residual_prec != 0 && op->residual_prec != 2))
+      (op->residual_prec < -1 || op->residual_prec > 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = gm ? ((int64_t)gm->n_tet << (3 * gm->n_refine)) : (int64_t)6 * n * n * n;
   for (int64_t t = 0; t < nt; ++t)
@@ -1053,7 +1085,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   // (double-float, FP64-accurate) applies to every level
   for (size_t l = 0; l < H.lv.size(); ++l)
     H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec >= 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
-  H.df_residual = op->residual_prec == 2 || (op->residual_prec < 0 && op->slab_prec != 0);
+  H.res32 = op->residual_prec == 1;
+  H.df_residual = op->residual_prec == 2 || op->residual_prec == 1 || (op->residual_prec < 0 && op->slab_prec != 0);
   H.nodal_prec = op->slab_prec == 0 ? 0 : op->slab_prec == 2 ? 2 : 1;
 
   // ---- factor cache: take every factor an earlier handle left resident
@@ -1265,6 +1298,10 @@ int setup_device(Handle& H) {
         L.p0 = H.upload(convert_pairs<float2>(a));
         L.p1 = H.upload(convert_pairs<float2>(b));
       }
+      if (H.res32) {
+        L.q0 = H.upload(convert<float>(a));
+        L.q1 = H.upload(convert<float>(b));
+      }
       if (!L.fac) {
         auto F = std::make_shared<SlabFactor>();
         F->mem.n_sm = H.n_sm;
@@ -1301,6 +1338,11 @@ int setup_device(Handle& H) {
         L.p0 = H.upload(convert_pairs<float2>(a));
         L.p1 = H.upload(convert_pairs<float2>(b));
         L.p2 = H.upload(convert_pairs<float2>(c));
+      }
+      if (H.res32) {
+        L.q0 = H.upload(convert<float>(a));
+        L.q1 = H.upload(convert<float>(b));
+        L.q2 = H.upload(convert<float>(c));
       }
       if (!L.fac) {
         auto F = std::make_shared<SlabFactor>();
@@ -1378,6 +1420,11 @@ int setup_device(Handle& H) {
   H.g1 = H.dalloc<double>(max_ne * H.q * H.B);
   H.r0 = H.dalloc<double>(H.lv[0].len);
   if (H.df_residual) H.xsplit = H.dalloc<float2>(H.lv[0].len);
+  if (H.res32) {
+    H.xf32 = H.dalloc<float>(H.lv[0].len);
+    H.corr_r = H.dalloc<double>(H.lv[0].len);
+    H.corr_e = H.dalloc<double>(H.lv[0].len);
+  }
   H.flags = H.dalloc<int>(4);
   CK(cudaMemset(H.flags, 0, 4 * sizeof(int)));
   H.tc_err = H.flags;
@@ -1467,7 +1514,7 @@ int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit
   const double fn = f_norm(H, f);
   const double denom = fn > 0 ? fn : 1.0;
   double nsq = 0.0;
-  op_residual(H, 0, f, x, H.r0, &nsq);
+  op_residual(H, 0, f, x, H.r0, &nsq, true);
   double rel = std::sqrt(nsq) / denom;
   const double rel0 = rel;
   if (history) history[0] = rel;
@@ -1476,7 +1523,7 @@ int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit
   while (rel > rtol && it < maxit) {
     run_vcycle(H, f, x);
     if (int rc = check_tc(H)) return rc;
-    op_residual(H, 0, f, x, H.r0, &nsq);
+    op_residual(H, 0, f, x, H.r0, &nsq, true);
     rel = std::sqrt(nsq) / denom;
     ++it;
     if (history) history[it] = rel;
@@ -1665,7 +1712,7 @@ int st_mg_residual(st_mg_t h, int32_t level, const double* f_dev, const double* 
   if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
   return guarded([&]() {
     double nsq = 0.0;
-    op_residual(*h, level, f_dev, x_dev, r_dev, norm_out ? &nsq : nullptr);
+    op_residual(*h, level, f_dev, x_dev, r_dev, norm_out ? &nsq : nullptr, true);
     if (norm_out) *norm_out = std::sqrt(nsq);
     return ST_MG_OK;
   });
@@ -1774,7 +1821,7 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
     if (rel_res_out) {
       const double fn = f_norm(*h, f_dev);
       double nsq = 0.0;
-      op_residual(*h, 0, f_dev, x_dev, h->r0, &nsq);
+      op_residual(*h, 0, f_dev, x_dev, h->r0, &nsq, true);
       *rel_res_out = std::sqrt(nsq) / (fn > 0 ? fn : 1.0);
     }
     return ST_MG_OK;
@@ -1786,7 +1833,7 @@ int st_mg_vcycle_residual_async(st_mg_t h, const double* f_dev, double* x_dev, d
   if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
   return guarded([&]() {
     run_vcycle(*h, f_dev, x_dev);
-    op_residual(*h, 0, f_dev, x_dev, r_dev, nullptr);
+    op_residual(*h, 0, f_dev, x_dev, r_dev, nullptr, true);
     return ST_MG_OK;
   });
 }
@@ -1886,6 +1933,38 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
         }
       }
     }
+    return ST_MG_OK;
+  });
+}
+
+int st_mg_convergence_rate(st_mg_t h, double* x_dev, int32_t max_iter, double floor, double* rates_host,
+                           int32_t* n_rates, double* rate) {
+  if (int rc = check_dev(h)) return rc;
+  if (int rc = check_ptrs({x_dev})) return rc;
+  if (max_iter < 1 || !(floor >= 0.0) || !rates_host || !n_rates || !rate)
+    return fail(ST_MG_ERR_INVALID_ARG, "max_iter >= 1, floor >= 0 and non-null outputs required");
+  return guarded([&]() {
+    Handle& H = *h;
+    const int64_t len = H.lv[0].len;
+    if (!H.zero_f) {
+      H.zero_f = H.dalloc<double>(len);
+      CK(cudaMemsetAsync(H.zero_f, 0, len * sizeof(double), H.stream));
+    }
+    const double n0 = f_norm(H, x_dev);       // the handle's deterministic l2 norm (blocking)
+    double prev = n0, best = 0.0;
+    int n = 0;
+    while (n < max_iter) {
+      run_vcycle(H, H.zero_f, x_dev);          // f = 0: x is the error of the iteration
+      if (int rc = check_tc(H)) return rc;
+      const double nx = f_norm(H, x_dev);
+      const double q = prev > 0.0 ? nx / prev : 0.0;
+      rates_host[n++] = q;
+      best = std::max(best, q);
+      prev = nx;
+      if (nx == 0.0 || nx < floor * n0) break;
+    }
+    *n_rates = n;
+    *rate = best;
     return ST_MG_OK;
   });
 }
@@ -2060,7 +2139,7 @@ int st_mg_residual_halo(st_mg_t h, int32_t level, const double* f_dev, const dou
   if (h->B != 1) return fail(ST_MG_ERR_INVALID_ARG, "time-slab sharding takes one problem per handle");
   return guarded([&]() {
     Handle& H = *h;
-    op_residual(H, level, f_dev, x_dev, r_dev, nullptr);
+    op_residual(H, level, f_dev, x_dev, r_dev, nullptr, true);
     if (x_prev_dev) {
       const auto& L = H.lv[level];
       const auto& S = H.space[L.s];

@@ -38,22 +38,26 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
   }
 }
 
+// T = double: the FP64 residual.  T = float: the same operations in FP32 on an FP32 copy
+// of x and FP32 coefficients, f and r in FP64 (the residual of a correction equation,
+// whose right-hand side is itself a residual: the rounding error is relative to it).
 // r_n = f_n - (K_t (x) M + M_t (x) K) x_n - (N_t (x) M) x_{n-1} for DG(1), with
 // K_t = [[1,1],[-1,1]], M_t = tau diag(1, 1/3), N_t = [[-1,-1],[1,1]]:
 //   r0 = f0 - (A0 + A1 + B0) + c,  r1 = f1 - (A1 - A0 + B1) - c
 // where A_i = M x_i, B0 = tau K x0, B1 = (tau/3) K x1 on slab n and
 // c = (M (x0 + x1)) of slab n-1 = A0 + A1 of the previous slab.
-template <int LPR>
+template <int LPR, typename T>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, const int64_t* __restrict__ rowptr,
                                                                  const int32_t* __restrict__ col,
-                                                                 const double* __restrict__ m,
-                                                                 const double* __restrict__ k0,
-                                                                 const double* __restrict__ k1,
+                                                                 const T* __restrict__ m,
+                                                                 const T* __restrict__ k0,
+                                                                 const T* __restrict__ k1,
                                                                  const double* __restrict__ f,
-                                                                 const double* __restrict__ x,
+                                                                 const T* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial, int seg) {
   pdl_entry();
+  using V2 = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
   // LPR lanes per row, 32 / LPR rows per warp (few slabs on coarse time levels)
   const int lane = threadIdx.x & (LPR - 1);
   const int row = (blockIdx.x * RES_WARPS + (threadIdx.x >> 5)) * (32 / LPR) + ((threadIdx.x & 31) / LPR);
@@ -65,20 +69,20 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
     const int64_t ld = 2 * (int64_t)N_t;
     const double2* f2 = reinterpret_cast<const double2*>(f + row * ld);
     double2* r2 = reinterpret_cast<double2*>(r + row * ld);
-    double carry = 0.0;   // A0 + A1 of the slab before this pass
+    T carry = T(0);   // A0 + A1 of the slab before this pass
     for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
-      double A0[SPL], A1[SPL], B0[SPL], B1[SPL];
+      T A0[SPL], A1[SPL], B0[SPL], B1[SPL];
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = 0.0;
+      for (int j = 0; j < SPL; ++j) A0[j] = A1[j] = B0[j] = B1[j] = T(0);
       for (int64_t q = beg; q < end; ++q) {
         const int64_t c = col[q];
-        const double mv = m[q], kv0 = k0[q], kv1 = k1[q];
-        const double2* xr = reinterpret_cast<const double2*>(x + c * ld);
+        const T mv = m[q], kv0 = k0[q], kv1 = k1[q];
+        const V2* xr = reinterpret_cast<const V2*>(x + c * ld);
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
           const int n = n0 + LPR * j + lane;
           if (n < N_t) {
-            const double2 v = xr[n];
+            const V2 v = xr[n];
             A0[j] = fma(mv, v.x, A0[j]);
             A1[j] = fma(mv, v.y, A1[j]);
             B0[j] = fma(kv0, v.x, B0[j]);
@@ -86,21 +90,21 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
           }
         }
       }
-      double prevA = carry;
+      T prevA = carry;
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
-        const double As = A0[j] + A1[j];
-        const double up = __shfl_up_sync(FULL, As, 1, LPR);
-        const double from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
-        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        const T As = A0[j] + A1[j];
+        const T up = __shfl_up_sync(FULL, As, 1, LPR);
+        const T from31 = __shfl_sync(FULL, prevA, LPR - 1, LPR);
+        T c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prevA = As;
         const int n = n0 + LPR * j + lane;
-        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
+        if (n % seg == 0) c = T(0);   // first slab of a problem: no history
         if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
-          rv.x = fv.x - (As + B0[j]) + c;
-          rv.y = fv.y - ((A1[j] - A0[j]) + B1[j]) - c;
+          rv.x = fv.x - (double)(As + B0[j]) + (double)c;
+          rv.y = fv.y - (double)((A1[j] - A0[j]) + B1[j]) - (double)c;
           r2[n] = rv;
           sq = fma(rv.x, rv.x, sq);
           sq = fma(rv.y, rv.y, sq);
@@ -113,13 +117,13 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
 }
 
 // DG(0) (implicit Euler, eq. timeStepping): r_n = f_n - (M + tau K) x_n + M x_{n-1}.
-template <int LPR>
+template <int LPR, typename T>
 __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, const int64_t* __restrict__ rowptr,
                                                                  const int32_t* __restrict__ col,
-                                                                 const double* __restrict__ a,
-                                                                 const double* __restrict__ m,
+                                                                 const T* __restrict__ a,
+                                                                 const T* __restrict__ m,
                                                                  const double* __restrict__ f,
-                                                                 const double* __restrict__ x,
+                                                                 const T* __restrict__ x,
                                                                  double* __restrict__ r, int N_t,
                                                                  double* __restrict__ partial, int seg) {
   pdl_entry();
@@ -132,36 +136,36 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg0(int nrows, cons
     const bool valid = row < nrows;
     const int64_t beg = valid ? rowptr[row] : 0, end = valid ? rowptr[row + 1] : 0;
     const int64_t ld = N_t;
-    double carry = 0.0;
+    T carry = T(0);
     for (int n0 = 0; n0 < N_t; n0 += LPR * SPL) {
-      double Ax[SPL], Mx[SPL];
+      T Ax[SPL], Mx[SPL];
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = 0.0;
+      for (int j = 0; j < SPL; ++j) Ax[j] = Mx[j] = T(0);
       for (int64_t q = beg; q < end; ++q) {
         const int64_t c = col[q];
-        const double av = a[q], mv = m[q];
-        const double* xr = x + c * ld;
+        const T av = a[q], mv = m[q];
+        const T* xr = x + c * ld;
 #pragma unroll
         for (int j = 0; j < SPL; ++j) {
           const int n = n0 + LPR * j + lane;
           if (n < N_t) {
-            const double v = xr[n];
+            const T v = xr[n];
             Ax[j] = fma(av, v, Ax[j]);
             Mx[j] = fma(mv, v, Mx[j]);
           }
         }
       }
-      double prev = carry;
+      T prev = carry;
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
-        const double up = __shfl_up_sync(FULL, Mx[j], 1, LPR);
-        const double from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
-        double c = (lane > 0) ? up : (j == 0 ? carry : from31);
+        const T up = __shfl_up_sync(FULL, Mx[j], 1, LPR);
+        const T from31 = __shfl_sync(FULL, prev, LPR - 1, LPR);
+        T c = (lane > 0) ? up : (j == 0 ? carry : from31);
         prev = Mx[j];
         const int n = n0 + LPR * j + lane;
-        if (n % seg == 0) c = 0.0;   // first slab of a problem: no history
+        if (n % seg == 0) c = T(0);   // first slab of a problem: no history
         if (valid && n < N_t) {
-          const double rv = f[row * ld + n] - Ax[j] + c;
+          const double rv = f[row * ld + n] - (double)Ax[j] + (double)c;
           r[row * ld + n] = rv;
           sq = fma(rv, rv, sq);
         }
@@ -193,6 +197,19 @@ __device__ __forceinline__ void dp_mac(dpair& acc, float2 a, float2 b) {
   acc.h = s;
 }
 __device__ __forceinline__ double dp_join(dpair a) { return (double)a.h + (double)a.l; }
+
+__global__ void k_to_float(const double* __restrict__ x, float* __restrict__ xf, int64_t n) {
+  pdl_entry();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    xf[i] = (float)x[i];
+}
+
+// b += a
+__global__ void k_vec_add(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  pdl_entry();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] += a[i];
+}
 
 __global__ void k_split_pairs(const double* __restrict__ x, float2* __restrict__ xs, int64_t n) {
   pdl_entry();
@@ -520,7 +537,7 @@ __global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64
                                                           int ncols) {
   pdl_entry();
   __shared__ int s_col[GT_WARPS][32];
-  __shared__ int s_sgn[GT_WARPS][32];
+  __shared__ double s_sgn[GT_WARPS][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int v = blockIdx.x * GT_WARPS + wb;
   if (v >= nrows) return;
@@ -540,11 +557,11 @@ __global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64
   }
   if (lane < nq) {
     s_col[wb][lane] = col[beg + lane];
-    s_sgn[wb][lane] = sgn[beg + lane];
+    s_sgn[wb][lane] = sgn[beg + lane] > 0 ? 1.0 : -1.0;
   }
   __syncwarp();
   const int* cq = s_col[wb];
-  const int* sq = s_sgn[wb];
+  const double* sq = s_sgn[wb];
   const int n2 = ncols >> 1;
   const double2* r2 = reinterpret_cast<const double2*>(r);
   double2* y2 = reinterpret_cast<double2*>(y + (int64_t)v * ncols);
@@ -557,18 +574,18 @@ __global__ void __launch_bounds__(GT_WARPS * 32) k_grad_T(int nrows, const int64
       double2 rv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) rv[u] = r2[(int64_t)cq[q + u] * n2 + j];
+      // sum +- r as one FMA with the sign +-1 (the product is exact: the same rounding as
+      // the add or subtract, one FP64 operation; this kernel is bound by the FP64 pipe)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const bool plus = sq[q + u] > 0;
-        sum.x = plus ? sum.x + rv[u].x : sum.x - rv[u].x;
-        sum.y = plus ? sum.y + rv[u].y : sum.y - rv[u].y;
+        sum.x = fma(sq[q + u], rv[u].x, sum.x);
+        sum.y = fma(sq[q + u], rv[u].y, sum.y);
       }
     }
     for (; q < nq; ++q) {
       const double2 rv = r2[(int64_t)cq[q] * n2 + j];
-      const bool plus = sq[q] > 0;
-      sum.x = plus ? sum.x + rv.x : sum.x - rv.x;
-      sum.y = plus ? sum.y + rv.y : sum.y - rv.y;
+      sum.x = fma(sq[q], rv.x, sum.x);
+      sum.y = fma(sq[q], rv.y, sum.y);
     }
     y2[j] = sum;
   }
@@ -612,7 +629,7 @@ __global__ void k_grad_add(const int32_t* __restrict__ tail, const int32_t* __re
 }
 // The same update with one warp per edge (GA_WARPS edges per block) and the loads of
 // GA_UNROLL column pairs per lane issued before their sums: the x row and the two w rows
-// of an edge are in flight together.  Same operations per entry: bit-identical.
+// of an edge are in flight together.  The same values up to the sign of an exact zero.
 constexpr int GA_WARPS = 8;
 constexpr int GA_UNROLL = 4;
 __global__ void __launch_bounds__(GA_WARPS * 32) k_grad_add_w(const int32_t* __restrict__ tail,
@@ -642,14 +659,19 @@ __global__ void __launch_bounds__(GA_WARPS * 32) k_grad_add_w(const int32_t* __r
     for (int u = 0; u < GA_UNROLL; ++u) {
       const int j = j0 + u * 32 + lane;
       if (j >= n2) continue;
-      double2 d = zero;
-      if (h >= 0) {
-        d.x += a[u].x;
-        d.y += a[u].y;
-      }
-      if (t >= 0) {
-        d.x -= b[u].x;
-        d.y -= b[u].y;
+      // w_head - w_tail once, then x += it: two FP64 operations per entry (the FP64 pipe
+      // bounds this kernel); a boundary endpoint contributes nothing
+      double2 d;
+      if (h >= 0 && t >= 0) {
+        d.x = a[u].x - b[u].x;
+        d.y = a[u].y - b[u].y;
+      } else if (h >= 0) {
+        d = a[u];
+      } else if (t >= 0) {
+        d.x = -b[u].x;
+        d.y = -b[u].y;
+      } else {
+        d = zero;
       }
       xv[u].x += d.x;
       xv[u].y += d.y;
@@ -1049,6 +1071,24 @@ int lanes_per_row(int N_t) {
   return l;
 }
 
+#define STMG_RES_DISPATCH_T(KERNEL, T, ...)                                                              \
+  do {                                                                                              \
+    const int lpr = lanes_per_row(N_t);                                                             \
+    const int rows_per_block = RES_WARPS * (32 / lpr);                                              \
+    const int nb = (A.nrows + rows_per_block - 1) / rows_per_block;                                 \
+    if (nblocks) *nblocks = nb;                                                                     \
+    if (nb <= 0) break;                                                                             \
+    switch (lpr) {                                                                                  \
+      case 1: launch_k(KERNEL<1, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 2: launch_k(KERNEL<2, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 4: launch_k(KERNEL<4, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 8: launch_k(KERNEL<8, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 16: launch_k(KERNEL<16, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      default: launch_k(KERNEL<32, T>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+    }                                                                                               \
+    count_launches(1);                                                                              \
+  } while (0)
+
 #define STMG_RES_DISPATCH(KERNEL, ...)                                                              \
   do {                                                                                              \
     const int lpr = lanes_per_row(N_t);                                                             \
@@ -1057,25 +1097,25 @@ int lanes_per_row(int N_t) {
     if (nblocks) *nblocks = nb;                                                                     \
     if (nb <= 0) break;                                                                             \
     switch (lpr) {                                                                                  \
-      case 1: launch_k(KERNEL<1>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
-      case 2: launch_k(KERNEL<2>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
-      case 4: launch_k(KERNEL<4>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
-      case 8: launch_k(KERNEL<8>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
-      case 16: launch_k(KERNEL<16>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
-      default: launch_k(KERNEL<32>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break; \
+      case 1: launch_k(KERNEL<1>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                   \
+      case 2: launch_k(KERNEL<2>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                   \
+      case 4: launch_k(KERNEL<4>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                   \
+      case 8: launch_k(KERNEL<8>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                   \
+      case 16: launch_k(KERNEL<16>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                 \
+      default: launch_k(KERNEL<32>, nb, RES_WARPS * 32, 0, st, __VA_ARGS__); break;                 \
     }                                                                                               \
     count_launches(1);                                                                              \
   } while (0)
 
 cudaError_t residual_dg0(CsrView A, const double* a, const double* m, const double* f, const double* x, double* r,
                          int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg0, A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial, seg);
+  STMG_RES_DISPATCH_T(k_residual_dg0, double, A.nrows, A.rowptr, A.col, a, m, f, x, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
 cudaError_t residual_dg1(CsrView A, const double* m, const double* k0, const double* k1, const double* f,
                          const double* x, double* r, int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
-  STMG_RES_DISPATCH(k_residual_dg1, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial, seg);
+  STMG_RES_DISPATCH_T(k_residual_dg1, double, A.nrows, A.rowptr, A.col, m, k0, k1, f, x, r, N_t, partial, seg);
   return cudaGetLastError();
 }
 
@@ -1103,6 +1143,31 @@ cudaError_t fp64_probe(double* out, int blocks, int iters, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t residual_dg0_f32(CsrView A, const float* a, const float* m, const double* f, const float* xf, double* r,
+                             int N_t, int seg, double* partial, int* nblocks, cudaStream_t st) {
+  STMG_RES_DISPATCH_T(k_residual_dg0, float, A.nrows, A.rowptr, A.col, a, m, f, xf, r, N_t, partial, seg);
+  return cudaGetLastError();
+}
+cudaError_t residual_dg1_f32(CsrView A, const float* m, const float* k0, const float* k1, const double* f,
+                             const float* xf, double* r, int N_t, int seg, double* partial, int* nblocks,
+                             cudaStream_t st) {
+  STMG_RES_DISPATCH_T(k_residual_dg1, float, A.nrows, A.rowptr, A.col, m, k0, k1, f, xf, r, N_t, partial, seg);
+  return cudaGetLastError();
+}
+cudaError_t to_float(const double* x, float* xf, int64_t n, cudaStream_t st) {
+  if (n > 0) {
+    launch_k(k_to_float, (unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st, x, xf, n);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+cudaError_t vec_add(const double* a, double* b, int64_t n, cudaStream_t st) {
+  if (n > 0) {
+    launch_k(k_vec_add, (unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st, a, b, n);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
 cudaError_t split_pairs(const double* x, float2* xs, int64_t n, cudaStream_t st) {
   if (n > 0) { launch_k(k_split_pairs, (unsigned)std::min<int64_t>(grid1(n, 256), 8 * 1024), 256, 0, st, x, xs, n); count_launches(1); }
   return cudaGetLastError();

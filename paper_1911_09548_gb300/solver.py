@@ -120,32 +120,13 @@ class SpaceTimeSolver:
         return B.st_mg_solve_host(self.h, f_host, x_host, rtol, maxit)
 
     def convergence_rate(self, x0, max_iter=200, floor=1e-100):
-        """Section 5.1's power iteration: V-cycles with f = 0 from a random start; the
-        largest per-cycle reduction of the l2 norm is the rate.  Stops when the total
-        reduction falls below `floor` (the paper's 1e-100, to avoid underflow).
-        x0: device tensor (modified).  Norms come from the handle's own deterministic
-        reduction (st_mg_batch_norms: per-handle scratch, queued on the handle's stream,
-        which the call synchronises before it returns the values; over a batch the norm
-        of the whole vector is the root of the problems' sums of squares)."""
+        """Section 5.1's power iteration (st_mg_convergence_rate): V-cycles with f = 0 from
+        the start x0 (device tensor, overwritten); returns (largest per-cycle reduction of
+        the l2 norm, all per-cycle reductions)."""
         import torch
-        f = self.zeros()
-        x = x0
-        # f and x0 were written on torch's current stream; the V-cycles run on the handle's
+        # x0 was written on torch's current stream; the V-cycles run on the handle's
         torch.cuda.current_stream().synchronize()
-
-        def norm(v):
-            return float(np.sqrt(np.sum(B.st_mg_batch_norms(self.h, v, self.n_batch) ** 2)))
-
-        n0 = nprev = norm(x)
-        rates = []
-        for _ in range(max_iter):
-            B.st_mg_vcycle(self.h, f, x, False)
-            nx = norm(x)
-            rates.append(nx / nprev)
-            nprev = nx
-            if nx == 0.0 or nx / n0 < floor:
-                break
-        return max(rates), rates
+        return B.st_mg_convergence_rate(self.h, x0, max_iter, floor)
 
     def debug(self, what, space_level=0):
         return B.st_mg_debug_get(self.h, what, space_level)

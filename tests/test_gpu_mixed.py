@@ -75,3 +75,28 @@ def test_mixed_solve_reaches_fp64_solution(stmg, name):
         assert rel(from_lib(x, p + 1), xs) < 1e-8
     # the FP32 slab apply costs at most a couple of extra V-cycles
     assert res[1][0]["iters"] <= res[0][0]["iters"] + 2
+
+
+@pytest.mark.parametrize("slab_prec", [1, 3])
+def test_fp32_residual_correction_form_reaches_fp64_solution(stmg, slab_prec):
+    """residual_prec 1: every residual inside the V-cycle in FP32, each V-cycle in correction
+    form around a double-float residual.  The iteration still reaches the FP64 solution (to
+    1e-8 of the exact space-time solution) in at most two more V-cycles than the FP64 path."""
+    n, nsl, p, N_t, mat, opts = CASES["dg1"]
+    nu, sigma = st_inputs.materials(n, mat, 4)
+    res = {}
+    for prec, rp in ((0, -1), (slab_prec, 1)):
+        S = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, p, n_space_levels=nsl, slab_prec=prec, residual_prec=rp,
+                                 **opts)
+        f = S.load(st_inputs.excitation(9))
+        x = S.zeros()
+        out = S.solve(f, x, rtol=1e-10, maxit=60)
+        torch.cuda.synchronize()
+        res[rp] = (out, x.cpu().numpy(), f.cpu().numpy())
+        S.close()
+    sl, tl, mg = oracle_mg(n, nsl, nu, sigma, 1.0, N_t, p)
+    xs = sequential_solve(mg.slabs[0], from_lib(res[-1][2], p + 1))
+    out, x, _ = res[1]
+    assert out["status"] == 0 and out["rel_res"] <= 1e-10, out
+    assert rel(from_lib(x, p + 1), xs) < 1e-8
+    assert out["iters"] <= res[-1][0]["iters"] + 2
