@@ -569,6 +569,8 @@ def main():
     ap.add_argument("--split-waves", default="",
                     help="comma-separated tiled / split-K threshold per time level, set after setup "
                          "(repeats an autotuned run's choice, e.g. under a profiler)")
+    ap.add_argument("--split-k", type=int, default=0,
+                    help="K columns of a split-K work item (0: the library default)")
     ap.add_argument("--nd-leaf", type=int, default=0,
                     help="largest leaf of the slab matrices' nested dissection (0: the library default)")
     ap.add_argument("--launch-overlap", type=int, default=0, choices=[0, 1],
@@ -646,7 +648,7 @@ def main():
     def make(prec, **kw):
         return stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
                                     nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec,
-                                    autotune=args.autotune, **kw)
+                                    autotune=args.autotune, split_k=args.split_k, **kw)
 
     def time_cycles(Sx, fx, xx, steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -881,6 +883,7 @@ def main():
         cfg.update({"time_levels": n_levels, "dofs": n_dof, "split_waves_per_level": split_waves,
                     "autotune": "given" if args.split_waves else bool(args.autotune),
                     "slab_prec": args.slab_prec, "launch_overlap": bool(args.launch_overlap),
+                    "split_k": args.split_k or 32,
                     "l2": "inputs larger than L2 (129 MB): f and x %.0f MB each, finest slab factor "
                           "%.2f GB, all read in every V-cycle" % (n_dof * 8 / 1e6, st["factor_bytes"] / 1e9)})
         line = {

@@ -171,6 +171,12 @@ typedef struct {
                                 (BF16 solves are bound by the latency of the tree's dependent depths),
                                 else 64 (the other solves are bound by arithmetic, so the least fill
                                 wins).  Larger leaves mean a shallower tree and more fill */
+    int32_t split_k;         /* K columns (unknowns of a supernode's column range) of one split-K work
+                                item of the supernodal products (a warp multiplies kSkRows = 32 rows by
+                                this many columns, then a fixed-order reduction sums the items of a
+                                row block): 16 .. 1024, a multiple of 16; 0 (default): 32.  Narrower
+                                items mean more items in flight and a shorter chain per item, more
+                                partial sums to reduce; results change at rounding level */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

@@ -88,7 +88,7 @@ constexpr int kTcSplitK = 256;      // complex K columns per tensor-core split-K
 // Split-K path: rows per item, columns per item, and the largest right-hand-side
 // count it serves (complex: kSkMaxRhsC, real: kSkMaxRhsR).
 constexpr int kSkRows = 32;
-constexpr int kSkK = 128;
+constexpr int kSkK = 32;     // default K columns per item (st_mg_options.split_k)
 constexpr int kSkMaxRhsC = 16;
 constexpr int kSkMaxRhsR = 32;
 

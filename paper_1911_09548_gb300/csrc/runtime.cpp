@@ -255,6 +255,7 @@ struct st_mg_s {
   double* partial = nullptr;
   double* scalar = nullptr;
   double* zero_f = nullptr;             // finest-level zero load of the rate harness (allocated on first use)
+  int sk_k = kSkK;                      // K columns of a split-K work item (st_mg_options.split_k)
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
   bool res32 = false;                   // residual_prec 1: FP32 residuals inside a correction-form V-cycle
   float* xf32 = nullptr;                // x as FP32 for those residuals
@@ -438,7 +439,7 @@ void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<floa
 }
 
 template <typename T, typename DT, typename WT>
-void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh,
+void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh, int sk_k,
                      int bm = kSnBM) {
   std::vector<int64_t>& fo = Lh.fo;
   std::vector<int64_t>& bo = Lh.bo;
@@ -487,12 +488,12 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
       for (int r0 = 0; r0 < m; r0 += kSkRows) {
         const int kend = (r0 + kSkRows <= a.nc) ? r0 + kSkRows : a.nc;
         const int first = (int)fsi.size();
-        for (int k0 = 0; k0 < kend; k0 += kSkK) fsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + kSkK, kend)));
+        for (int k0 = 0; k0 < kend; k0 += sk_k) fsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + sk_k, kend)));
         fsu.push_back(make_int4((int)s, r0, first, (int)fsi.size()));
       }
       for (int r0 = 0; r0 < a.nc; r0 += kSkRows) {
         const int first = (int)bsi.size();
-        for (int k0 = r0; k0 < m; k0 += kSkK) bsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + kSkK, m)));
+        for (int k0 = r0; k0 < m; k0 += sk_k) bsi.push_back(make_int4((int)s, r0, k0, std::min(k0 + sk_k, m)));
         bsu.push_back(make_int4((int)s, r0, first, (int)bsi.size()));
       }
     }
@@ -955,6 +956,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 4 || (op->slab_prec >= 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
       (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
+      op->split_k < 0 || op->split_k > 1024 || (op->split_k % 16) != 0 ||
       (op->residual_prec < -1 || op->residual_prec > 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = gm ? ((int64_t)gm->n_tet << (3 * gm->n_refine)) : (int64_t)6 * n * n * n;
@@ -1086,6 +1088,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   for (size_t l = 0; l < H.lv.size(); ++l)
     H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec >= 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
   H.res32 = op->residual_prec == 1;
+  H.sk_k = op->split_k > 0 ? op->split_k : kSkK;
   H.df_residual = op->residual_prec == 2 || op->residual_prec == 1 || (op->residual_prec < 0 && op->slab_prec != 0);
   H.nodal_prec = op->slab_prec == 0 ? 0 : op->slab_prec == 2 ? 2 : 1;
 
@@ -1108,12 +1111,12 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     char buf[192];
     for (size_t l = 0; l < H.lv.size(); ++l) {
       const auto& L = H.lv[l];
-      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d tau%a mat%016llx", H.device, n, L.s,
-                    pr->degree, L.prec, nd_leaf_of(*op), L.tau, (unsigned long long)H.mat_hash);
+      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d sk%d tau%a mat%016llx", H.device, n,
+                    L.s, pr->degree, L.prec, nd_leaf_of(*op), H.sk_k, L.tau, (unsigned long long)H.mat_hash);
       lkey[l] = buf;
     }
     for (size_t sl = 0; sl < H.space.size(); ++sl) {
-      std::snprintf(buf, sizeof buf, "nodal dev%d n%d s%d np%d mat%016llx", H.device, n, (int)sl, H.nodal_prec,
+      std::snprintf(buf, sizeof buf, "nodal dev%d n%d s%d np%d sk%d mat%016llx", H.device, n, (int)sl, H.nodal_prec, H.sk_k,
                     (unsigned long long)H.mat_hash);
       skey[sl] = buf;
     }
@@ -1272,9 +1275,9 @@ int setup_device(Handle& H) {
     if (!S.nf) {
       auto N = std::make_shared<NodalFactor>();
       N->mem.n_sm = H.n_sm;
-      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists, kSnBmFP64);
-      if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists);
-      if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists);
+      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists, H.sk_k, kSnBmFP64);
+      if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists, H.sk_k);
+      if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists, H.sk_k);
       N->u_rows = N->kn.u_rows;
       N->max_items = N->kn.max_items;
       S.nf = N;
@@ -1306,15 +1309,15 @@ int setup_device(Handle& H) {
         auto F = std::make_shared<SlabFactor>();
         F->mem.n_sm = H.n_sm;
         if (L.prec == 1) {
-          make_dev_factor(F->mem, L.fr, F->drf, F->lists);
+          make_dev_factor(F->mem, L.fr, F->drf, F->lists, H.sk_k);
           F->max_items = F->drf.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 4;
         } else if (L.prec == 2) {
-          make_dev_factor(F->mem, L.fr, F->drd, F->lists);
+          make_dev_factor(F->mem, L.fr, F->drd, F->lists, H.sk_k);
           F->max_items = F->drd.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         } else {
-          make_dev_factor(F->mem, L.fr, F->dr, F->lists, kSnBmFP64);
+          make_dev_factor(F->mem, L.fr, F->dr, F->lists, H.sk_k, kSnBmFP64);
           F->max_items = F->dr.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         }
@@ -1348,11 +1351,11 @@ int setup_device(Handle& H) {
         auto F = std::make_shared<SlabFactor>();
         F->mem.n_sm = H.n_sm;
         if (L.prec == 1) {
-          make_dev_factor(F->mem, L.fc, F->dcf, F->lists);
+          make_dev_factor(F->mem, L.fc, F->dcf, F->lists, H.sk_k);
           F->max_items = F->dcf.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 8;
         } else if (L.prec == 3) {
-          make_dev_factor(F->mem, L.fc, F->dcb, F->lists);
+          make_dev_factor(F->mem, L.fc, F->dcb, F->lists, H.sk_k);
           build_tc_tiles(F->mem, L.fc, F->dcb, F->lists);
           F->max_items = F->dcb.max_items;
           F->max_tc_items = F->dcb.max_tc_items;
@@ -1361,18 +1364,18 @@ int setup_device(Handle& H) {
         } else if (L.prec == 4) {
           if (max_abs_entry(L.fc) > 16384.0)
             throw NumericError{"a slab factor entry exceeds the FP16 range kept for slab_prec 4 (|w| > 16384)"};
-          make_dev_factor(F->mem, L.fc, F->dch, F->lists);
+          make_dev_factor(F->mem, L.fc, F->dch, F->lists, H.sk_k);
           build_tc_tiles(F->mem, L.fc, F->dch, F->lists);
           F->max_items = F->dch.max_items;
           F->max_tc_items = F->dch.max_tc_items;
           F->max_stage_tiles = F->dch.max_stage_tiles;
           F->w_bytes = (int64_t)L.fc.W.size() * 4;
         } else if (L.prec == 2) {
-          make_dev_factor(F->mem, L.fc, F->dcd, F->lists);
+          make_dev_factor(F->mem, L.fc, F->dcd, F->lists, H.sk_k);
           F->max_items = F->dcd.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         } else {
-          make_dev_factor(F->mem, L.fc, F->dc, F->lists, kSnBmFP64);
+          make_dev_factor(F->mem, L.fc, F->dc, F->lists, H.sk_k, kSnBmFP64);
           F->max_items = F->dc.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         }
@@ -1607,6 +1610,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->factor_cache = 0;
   o->autotune = 0;
   o->nd_leaf = 0;
+  o->split_k = 0;
   return ST_MG_OK;
 }
 
