@@ -38,7 +38,7 @@ CPU_SAMPLE_SLABS = 16
 # DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
 # this workload, from one ncu capture of the same kernels and factor; set to None when those
 # kernels or the factor they read change
-SLAB_SOLVE_TRAFFIC_FP64 = 1.306e9
+SLAB_SOLVE_TRAFFIC_FP64 = None
 
 
 def workload_config(world: int = 1) -> dict:
@@ -294,7 +294,7 @@ def run_precision(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     rows, ref = {}, None
-    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16_tensor", 3)):
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16_tensor", 3), ("fp16_tensor", 4)):
         S = stmg.SpaceTimeSolver(n, nu, sigma, 1.0, N_t, 1, nu_pre=2, nu_post=2, stream=stream.cuda_stream,
                                  slab_prec=prec, autotune=args.autotune)
         f = S.load(st_inputs.excitation(0))

@@ -102,6 +102,21 @@ typedef struct {
                                 correction G z does not depend on the choice) */
     const st_mg_mesh* mesh;  /* NULL: the Kuhn mesh of the unit cube with n_cube cubes per side;
                                 else a general start mesh refined mesh->n_refine times */
+    const int32_t* batch_nt; /* NULL: every problem of a batch has N_t slabs.  Else (n_batch > 1) host
+                                [n_batch]: problem b has batch_nt[b] slabs of step T / batch_nt[b] over
+                                the same horizon T, batch_nt[b] = N_t / 2^k (a "ragged" batch, N_t =
+                                the largest).  Problem b then enters the time hierarchy at the level
+                                whose step is its own, and every level holds the problems that have
+                                entered with that level's slab count, so the levels share one slab
+                                factor each and one V-cycle advances every problem by one of its own
+                                V-cycles.  The caller's f and x hold, per edge row, the problems one
+                                after the other: problem b at columns sum_{b' < b} batch_nt[b'] q + n q
+                                + i.  Needs time-only coarsening (coarsen = 1, or n_space_levels = 1).
+                                st_mg_vcycle, st_mg_solve(_host), st_mg_assemble_load_batch and
+                                st_mg_sizes use that layout; the per-level step entry points act on a
+                                level's own layout (its problems' columns, level_info's N_t each);
+                                st_mg_batch_norms, st_mg_batch_zero and st_mg_vcycle_residual_async
+                                are not available */
 } st_mg_problem;
 
 /* Method parameters (Sections 2.1, 2.2, 4, 5). */

@@ -31,7 +31,7 @@ class Mesh(ctypes.Structure):
 class Problem(ctypes.Structure):
     _fields_ = [("n_cube", _i32), ("n_space_levels", _i32), ("nu", _P(_dbl)), ("sigma", _P(_dbl)),
                 ("T", _dbl), ("N_t", _i32), ("degree", _i32), ("n_batch", _i32), ("bc", _i32),
-                ("mesh", _P(Mesh))]
+                ("mesh", _P(Mesh)), ("batch_nt", _P(_i32))]
 
 
 class Options(ctypes.Structure):
@@ -183,13 +183,18 @@ def st_mg_default_options() -> Options:
     return o
 
 
-def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1, bc=0, mesh=None):
+def make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch=1, bc=0, mesh=None, batch_nt=None):
     """mesh: None (Kuhn mesh with n_cube cubes per side) or (xyz, tets, n_refine), a general
-    start mesh refined n_refine times (n_cube is then ignored)."""
+    start mesh refined n_refine times (n_cube is then ignored).  batch_nt: per-problem slab
+    counts of a ragged batch (None: every problem has N_t)."""
     nu = np.ascontiguousarray(nu, dtype=np.float64)
     sigma = np.ascontiguousarray(sigma, dtype=np.float64)
-    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch, bc, None)
+    p = Problem(n_cube, n_space_levels, _dptr(nu), _dptr(sigma), float(T), N_t, degree, n_batch, bc, None, None)
     keep = [nu, sigma]
+    if batch_nt is not None:
+        bnt = np.ascontiguousarray(batch_nt, dtype=np.int32)
+        p.batch_nt = bnt.ctypes.data_as(_P(_i32))
+        keep.append(bnt)
     if mesh is not None:
         xyz, tets, n_refine = mesh
         xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)

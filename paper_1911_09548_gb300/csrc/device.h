@@ -262,9 +262,13 @@ cudaError_t time_carry(const double* ends, int n_prev, int nrows, int degree, do
 cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, const double* y, const double* zi,
                          double* zo, int ncols, double wgt, cudaStream_t st);
 
-// Time transfers between N_t (fine) and N_t/2 (coarse) slabs, same space level.
-cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st);
-cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st);
+// Time transfers between N_t (fine) and N_t/2 (coarse) slabs, same space level; nrows =
+// edges x Bf rows of one problem each, the coarse level has Bc >= Bf problems per edge row
+// (a ragged batch; Bf = Bc = 1 by default: contiguous rows).
+cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st, int Bf = 1,
+                          int Bc = 1);
+cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st, int Bf = 1,
+                             int Bc = 1);
 // Space transfers per time column: out = P in (P given as CSR rows), beta 0 overwrite / 1 add.
 cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,
                      cudaStream_t st);

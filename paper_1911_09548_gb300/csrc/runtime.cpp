@@ -196,6 +196,14 @@ struct st_mg_s {
   double* stage_x = nullptr;
   int q = 1;
   int B = 1;                            // problems solved together (batch)
+  // ragged batch (st_mg_problem.batch_nt): problem b has pnt[b] slabs of its own step T / pnt[b];
+  // it enters the time hierarchy at level pent[b] (whose step equals its own) in slot pslot[b],
+  // and the caller's vectors hold its columns at poff[b] .. poff[b] + pnt[b] q of rows of prow
+  bool ragged = false;
+  std::vector<int> pnt, pent, pslot;
+  std::vector<int64_t> poff;
+  int64_t prow = 0;
+  int64_t user_len = 0;                 // length of the caller's f and x (edges x prow)
   DevArena mem;                         // the handle's own device buffers
   uint64_t mat_hash = 0;                // of (n_cube, nu, sigma): the factor cache's material key
   bool use_cache = false;               // factors from / into the process-wide cache
@@ -228,6 +236,7 @@ struct st_mg_s {
 
   struct Level {
     int s = 0, N_t = 1;
+    int B = 1;                                              // problems on this level (ragged: fewer on finer levels)
     double tau = 1.0;
     double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;   // residual coefficients per nnz
     float2 *p0 = nullptr, *p1 = nullptr, *p2 = nullptr;   // the same as (hi, lo) FP32 pairs
@@ -599,19 +608,19 @@ void op_residual(Handle& h, int l, const double* f, const double* x, double* r, 
   if (h.res32 && !outer) {
     CK(to_float(x, h.xf32, L.len, h.stream));
     if (h.prob.degree == 0)
-      CK(residual_dg0_f32(view(S), L.q0, L.q1, f, h.xf32, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+      CK(residual_dg0_f32(view(S), L.q0, L.q1, f, h.xf32, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
     else
-      CK(residual_dg1_f32(view(S), L.q0, L.q1, L.q2, f, h.xf32, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+      CK(residual_dg1_f32(view(S), L.q0, L.q1, L.q2, f, h.xf32, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
   } else if (h.df_residual) {
     CK(split_pairs(x, h.xsplit, L.len, h.stream));
     if (h.prob.degree == 0)
-      CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+      CK(residual_dg0_df(view(S), L.p0, L.p1, f, h.xsplit, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
     else
-      CK(residual_dg1_df(view(S), L.p0, L.p1, L.p2, f, h.xsplit, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+      CK(residual_dg1_df(view(S), L.p0, L.p1, L.p2, f, h.xsplit, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
   } else if (h.prob.degree == 0) {
-    CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+    CK(residual_dg0(view(S), L.v0, L.v1, f, x, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
   } else {
-    CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t * h.B, L.N_t, part, &nb, h.stream));
+    CK(residual_dg1(view(S), L.v0, L.v1, L.v2, f, x, r, L.N_t * L.B, L.N_t, part, &nb, h.stream));
   }
   if (norm_sq_host) {
     CK(reduce_partials(h.partial, nb, h.scalar, h.stream));
@@ -713,20 +722,20 @@ void op_smooth_S(Handle& h, int l, const double* f, double* x) {
   auto& L = h.lv[l];
   double* r = level_r(h, l);
   op_residual(h, l, f, x, r, nullptr);
-  const int ld = L.N_t * h.B * h.q;
-  op_slab_cols(h, l, r, ld, 0, L.N_t * h.B, x, ld, 0, h.opt.omega, 1);
+  const int ld = L.N_t * L.B * h.q;
+  op_slab_cols(h, l, r, ld, 0, L.N_t * L.B, x, ld, 0, h.opt.omega, 1);
 }
 
 void op_grad_T(Handle& h, int l, const double* r, double* y) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  CK(grad_T(CsrView{S.nn, S.gt_rowptr, S.gt_col}, S.gt_sign_d, r, y, L.N_t * h.B * h.q, h.stream));
+  CK(grad_T(CsrView{S.nn, S.gt_rowptr, S.gt_col}, S.gt_sign_d, r, y, L.N_t * L.B * h.q, h.stream));
 }
 
 void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  const int ncols = L.N_t * h.B * h.q;
+  const int ncols = L.N_t * L.B * h.q;
   if (h.opt.nodal_solve == 0) {
     CK(gather_perm(y, ncols, S.nf->kn.iperm, S.nn, h.nQ, h.ld_nod, h.stream));
     if (h.nodal_prec == 1) {
@@ -759,13 +768,13 @@ void op_nodal_solve(Handle& h, int l, const double* y, double* z) {
 void op_time_integrate(Handle& h, int l, const double* z, double* w) {
   auto& L = h.lv[l];
   // each problem's slabs of a node are one contiguous segment: nn * B independent scans
-  CK(time_integrate(z, w, h.space[L.s].nn * h.B, L.N_t, h.prob.degree, h.stream));
+  CK(time_integrate(z, w, h.space[L.s].nn * L.B, L.N_t, h.prob.degree, h.stream));
 }
 
 void op_grad_add(Handle& h, int l, const double* w, double* x) {
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  CK(grad_add(S.gtail_d, S.ghead_d, S.ne, w, x, L.N_t * h.B * h.q, h.stream));
+  CK(grad_add(S.gtail_d, S.ghead_d, S.ne, w, x, L.N_t * L.B * h.q, h.stream));
 }
 
 void op_correct_A(Handle& h, int l, const double* f, double* x) {
@@ -783,12 +792,13 @@ void op_restrict(Handle& h, int l, const double* r, double* rc) {
   auto& L = h.lv[l];
   auto& Sf = h.space[L.s];
   const int Nc = h.lv[l + 1].N_t;
-  if (space_coarsened(h, l)) {
-    CK(time_restrict(r, h.tmp_fine, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
-    CK(csr_spmm(CsrView{Sf.PxT.nrows, Sf.pxt_rowptr, Sf.pxt_col}, Sf.pxt_val, h.tmp_fine, rc, Nc * h.B * h.q, 0,
+  if (space_coarsened(h, l)) {   // (never on a ragged batch: checked at setup)
+    CK(time_restrict(r, h.tmp_fine, Sf.ne * L.B, Nc, h.prob.degree, h.stream));
+    CK(csr_spmm(CsrView{Sf.PxT.nrows, Sf.pxt_rowptr, Sf.pxt_col}, Sf.pxt_val, h.tmp_fine, rc, Nc * L.B * h.q, 0,
                 h.stream));
   } else {
-    CK(time_restrict(r, rc, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
+    // the coarse level's first L.B problems of every edge row are this level's problems
+    CK(time_restrict(r, rc, Sf.ne * L.B, Nc, h.prob.degree, h.stream, L.B, h.lv[l + 1].B));
   }
 }
 
@@ -797,11 +807,11 @@ void op_prolong_add(Handle& h, int l, const double* ec, double* x) {
   auto& Sf = h.space[L.s];
   const int Nc = h.lv[l + 1].N_t;
   if (space_coarsened(h, l)) {
-    CK(csr_spmm(CsrView{Sf.Px.nrows, Sf.px_rowptr, Sf.px_col}, Sf.px_val, ec, h.tmp_fine, Nc * h.B * h.q, 0,
+    CK(csr_spmm(CsrView{Sf.Px.nrows, Sf.px_rowptr, Sf.px_col}, Sf.px_val, ec, h.tmp_fine, Nc * L.B * h.q, 0,
                 h.stream));
-    CK(time_prolong_add(h.tmp_fine, x, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
+    CK(time_prolong_add(h.tmp_fine, x, Sf.ne * L.B, Nc, h.prob.degree, h.stream));
   } else {
-    CK(time_prolong_add(ec, x, Sf.ne * h.B, Nc, h.prob.degree, h.stream));
+    CK(time_prolong_add(ec, x, Sf.ne * L.B, Nc, h.prob.degree, h.stream, L.B, h.lv[l + 1].B));
   }
 }
 
@@ -809,9 +819,9 @@ void op_coarse_solve(Handle& h, const double* f, double* x) {
   const int l = (int)h.lv.size() - 1;
   auto& L = h.lv[l];
   auto& S = h.space[L.s];
-  const int ld = L.N_t * h.B * h.q;
+  const int ld = L.N_t * L.B * h.q;
   if (L.N_t == 1) {   // one slab per problem: one solve over the batch
-    op_slab_cols(h, l, f, ld, 0, h.B, x, ld, 0, 1.0, 0);
+    op_slab_cols(h, l, f, ld, 0, L.B, x, ld, 0, 1.0, 0);
     return;
   }
   for (int n = 0; n < L.N_t; ++n) {
@@ -849,10 +859,106 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
   op_residual(h, l, f, x, r, nullptr);
   auto& C = h.lv[l + 1];
   op_restrict(h, l, r, C.f);
-  CK(vec_fill(C.x, C.len, 0.0, h.stream));
+  if (C.B == h.lv[l].B) {
+    CK(vec_fill(C.x, C.len, 0.0, h.stream));
+  } else {   // ragged: the coarse level's own problems keep their iterates
+    const int cq = C.N_t * h.q;
+    CK(zero_cols(C.x, h.space[C.s].ne, cq * C.B, 0, cq * h.lv[l].B, h.stream));
+  }
   op_vcycle(h, l + 1, C.f, C.x);
   op_prolong_add(h, l, C.x, x);
   op_smooth(h, l, f, x, h.opt.nu_post, true);
+}
+
+// ---- ragged batches: the caller's rows hold problem b at columns poff[b] .. poff[b] +
+// pnt[b] q; its finest level is level pent[b], where it has slot pslot[b] (the level's rows
+// hold B problems of N_t q columns each).  Runs of problems with consecutive columns on both
+// sides move as one strided copy.
+template <typename Fn>
+void ragged_runs(const Handle& h, Fn fn) {
+  int b = 0;
+  while (b < h.B) {
+    int e = b + 1;
+    while (e < h.B && h.pent[e] == h.pent[b] && h.pslot[e] == h.pslot[e - 1] + 1 &&
+           h.poff[e] == h.poff[e - 1] + (int64_t)h.pnt[e - 1] * h.q)
+      ++e;
+    fn(b, e);
+    b = e;
+  }
+}
+
+// caller's vector -> the level vectors (which = 0: f, 1: x)
+void ragged_in(Handle& h, const double* user, int which) {
+  ragged_runs(h, [&](int b, int e) {
+    auto& L = h.lv[h.pent[b]];
+    const int64_t seg = (int64_t)L.N_t * h.q;
+    double* dst = (which ? L.x : L.f) + h.pslot[b] * seg;
+    CK(cudaMemcpy2DAsync(dst, L.B * seg * sizeof(double), user + h.poff[b], h.prow * sizeof(double),
+                         (e - b) * seg * sizeof(double), h.space[0].ne, cudaMemcpyDeviceToDevice, h.stream));
+  });
+}
+
+// the level vectors' x -> caller's vector
+void ragged_out(Handle& h, double* user) {
+  ragged_runs(h, [&](int b, int e) {
+    auto& L = h.lv[h.pent[b]];
+    const int64_t seg = (int64_t)L.N_t * h.q;
+    CK(cudaMemcpy2DAsync(user + h.poff[b], h.prow * sizeof(double), L.x + h.pslot[b] * seg,
+                         L.B * seg * sizeof(double), (e - b) * seg * sizeof(double), h.space[0].ne,
+                         cudaMemcpyDeviceToDevice, h.stream));
+  });
+}
+
+// Sum of the squared residuals of every problem on its own finest level (f and x already
+// in the level vectors): the level's residual over all its slots, the sums of squares of
+// the slots of the problems that start there (blocking).
+double ragged_res_norm_sq(Handle& h) {
+  double total = 0.0;
+  std::vector<double> sq(h.B);
+  for (size_t l = 0; l < h.lv.size(); ++l) {
+    auto& L = h.lv[l];
+    const int first = l > 0 ? h.lv[l - 1].B : 0;
+    if (L.B == first) continue;
+    double* r = level_r(h, (int)l);
+    op_residual(h, (int)l, L.f, L.x, r, nullptr, true);
+    CK(batch_norms_sq(r, h.space[L.s].ne, L.B, L.N_t * h.q, h.bn_partial, h.bn_out, h.stream));
+    CK(cudaMemcpyAsync(sq.data(), h.bn_out, L.B * sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+    CK(cudaStreamSynchronize(h.stream));
+    for (int b = first; b < L.B; ++b) total += sq[b];
+  }
+  return total;
+}
+
+// One V-cycle of every problem of a ragged batch: each problem's load and iterate are
+// copied into its slot on its own finest level, the V-cycle runs from level 0 (a level's
+// smoothing covers every problem on it, the restriction fills the descending problems'
+// slots of the coarser level, whose own problems keep their load and iterate), and the
+// iterates are copied back.  In correction form (residual_prec 1) every problem's slot
+// first receives its residual in place of its load and a zero iterate, and the caller's x
+// gains the correction.
+void ragged_vcycle(Handle& h, const double* f, double* x) {
+  ragged_in(h, f, 0);
+  ragged_in(h, x, 1);
+  if (h.res32) {
+    for (size_t l = 0; l < h.lv.size(); ++l) {
+      auto& L = h.lv[l];
+      const int first = l > 0 ? h.lv[l - 1].B : 0;
+      if (L.B == first) continue;
+      double* r = level_r(h, (int)l);
+      op_residual(h, (int)l, L.f, L.x, r, nullptr, true);
+      const int64_t seg = (int64_t)L.N_t * h.q;
+      const int64_t pitch = L.B * seg * sizeof(double);
+      CK(cudaMemcpy2DAsync(L.f + first * seg, pitch, r + first * seg, pitch, (L.B - first) * seg * sizeof(double),
+                           h.space[L.s].ne, cudaMemcpyDeviceToDevice, h.stream));
+      CK(zero_cols(L.x, h.space[L.s].ne, (int)(L.B * seg), (int)(first * seg), (int)((L.B - first) * seg), h.stream));
+    }
+    op_vcycle(h, 0, h.lv[0].f, h.lv[0].x);
+    ragged_out(h, h.corr_e);
+    CK(vec_add(h.corr_e, x, h.user_len, h.stream));
+    return;
+  }
+  op_vcycle(h, 0, h.lv[0].f, h.lv[0].x);
+  ragged_out(h, x);
 }
 
 // The finest-level V-cycle x <- x + V(f - L x).  With residual_prec 1 it runs in
@@ -860,6 +966,10 @@ void op_vcycle(Handle& h, int l, const double* f, double* x) {
 // residuals inside (their rounding is relative to r, which shrinks as x converges),
 // x += e; the same iteration in exact arithmetic, since a V-cycle is affine in (f, x).
 void op_vcycle_top(Handle& h, const double* f, double* x) {
+  if (h.ragged) {
+    ragged_vcycle(h, f, x);
+    return;
+  }
   if (!h.res32) {
     op_vcycle(h, 0, f, x);
     return;
@@ -906,9 +1016,11 @@ void run_vcycle(Handle& h, const double* f, double* x) {
   count_launches(h.graph_launches);
 }
 
+// l2 norm of a caller's vector (h.user_len doubles: the finest level, or a ragged batch's
+// rows), deterministic, blocking
 double f_norm(Handle& h, const double* f) {
   double v = 0.0;
-  CK(norm2_sq(f, h.lv[0].len, h.partial, h.scalar, h.stream));
+  CK(norm2_sq(f, h.user_len, h.partial, h.scalar, h.stream));
   CK(cudaMemcpyAsync(&v, h.scalar, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
   CK(cudaStreamSynchronize(h.stream));
   return std::sqrt(v);
@@ -972,7 +1084,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   H.sigma.assign(pr->sigma, pr->sigma + nt);
   H.prob.nu = H.nu.data();
   H.prob.sigma = H.sigma.data();
-  H.prob.mesh = nullptr;   // the caller's mesh is read during this call only
+  H.prob.mesh = nullptr;   // the caller's mesh and batch_nt are read during this call only
+  H.prob.batch_nt = nullptr;
   H.stream = static_cast<cudaStream_t>(stream);
   H.q = pr->degree + 1;
   H.B = pr->n_batch > 1 ? pr->n_batch : 1;
@@ -1188,7 +1301,46 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (H.B > 1 && H.lv.back().N_t != 1)
     return fail(ST_MG_ERR_INVALID_ARG, "n_batch > 1 needs a hierarchy that coarsens time to one slab "
                                        "(N_t a power of two, no max_levels cap)");
-  for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q * H.B;
+  for (auto& L : H.lv) L.B = H.B;
+  if (H.B > 1 && pr->batch_nt) {
+    // ragged batch: problem b enters the time hierarchy at the level whose slab count is
+    // its own (the steps agree there: T / pnt[b]); the finer levels do not hold it
+    H.pnt.assign(pr->batch_nt, pr->batch_nt + H.B);
+    H.ragged = false;
+    for (int b = 0; b < H.B; ++b) {
+      const int nt = H.pnt[b];
+      if (nt < 1 || nt > pr->N_t || (pr->N_t % nt) != 0 || ((pr->N_t / nt) & (pr->N_t / nt - 1)) != 0)
+        return fail(ST_MG_ERR_INVALID_ARG, "batch_nt[b] must be N_t divided by a power of two");
+      if (nt != pr->N_t) H.ragged = true;
+    }
+  }
+  if (H.ragged) {
+    for (const auto& L : H.lv)
+      if (L.s != 0)
+        return fail(ST_MG_ERR_INVALID_ARG, "a ragged batch needs time-only coarsening (coarsen = 1 or one space "
+                                           "level)");
+    H.pent.assign(H.B, 0);
+    H.pslot.assign(H.B, 0);
+    for (size_t l = 0; l < H.lv.size(); ++l) {
+      auto& L = H.lv[l];
+      int count = l > 0 ? H.lv[l - 1].B : 0;
+      for (int b = 0; b < H.B; ++b)
+        if (H.pnt[b] == L.N_t) {
+          H.pent[b] = (int)l;
+          H.pslot[b] = count++;
+        }
+      L.B = count;
+    }
+    H.poff.assign(H.B, 0);
+    int64_t off = 0;
+    for (int b = 0; b < H.B; ++b) {
+      H.poff[b] = off;
+      off += (int64_t)H.pnt[b] * H.q;
+    }
+    H.prow = off;
+  }
+  for (auto& L : H.lv) L.len = (int64_t)H.space[L.s].ne * L.N_t * H.q * L.B;
+  H.user_len = H.ragged ? (int64_t)H.space[0].ne * H.prow : H.lv[0].len;
   H.pending_upload = !host_only;
   *out = h.release();
   return ST_MG_OK;
@@ -1205,7 +1357,7 @@ void autotune_split(Handle& H) {
   CK(cudaEventCreate(&e1));
   for (size_t l = 0; l < H.lv.size(); ++l) {
     auto& L = H.lv[l];
-    const int cnt = L.N_t * H.B;
+    const int cnt = L.N_t * L.B;
     const int skinny_max = (H.prob.degree == 0) ? kSkMaxRhsR : kSkMaxRhsC;
     if (cnt <= skinny_max) continue;
     float best = 0.f;
@@ -1286,6 +1438,7 @@ int setup_device(Handle& H) {
     S.knF = SupernodalFactor<double>();   // host copy no longer needed
   }
   int64_t max_ne = 0, max_u = 0, max_nn = 0, max_un = 0, max_len_fine_tmp = 0, max_items = 0, max_kn_items = 0;
+  int64_t max_len = 0;
   for (auto& S : H.space) max_kn_items = std::max<int64_t>(max_kn_items, S.nf->kn.max_items);
   int max_nt = 1;
   for (size_t l = 0; l < H.lv.size(); ++l) {
@@ -1387,17 +1540,18 @@ int setup_device(Handle& H) {
       max_items = std::max<int64_t>(max_items, L.fac->max_items);
       max_u = std::max<int64_t>(max_u, L.fac->u_rows);
     }
-    L.len = (int64_t)S.ne * L.N_t * H.q * H.B;
-    if (l > 0) {
+    L.len = (int64_t)S.ne * L.N_t * H.q * L.B;
+    max_len = std::max(max_len, L.len);
+    if (l > 0 || H.ragged) {
       L.f = H.dalloc<double>(L.len);
       L.x = H.dalloc<double>(L.len);
-      L.r = H.dalloc<double>(L.len);
+      if (l > 0) L.r = H.dalloc<double>(L.len);
     }
     if (l + 1 < H.lv.size() && H.lv[l + 1].s != L.s)
       max_len_fine_tmp = std::max<int64_t>(max_len_fine_tmp, (int64_t)S.ne * H.lv[l + 1].N_t * H.q * H.B);
     max_ne = std::max<int64_t>(max_ne, S.ne);
     max_nn = std::max<int64_t>(max_nn, S.nn);
-    max_nt = std::max(max_nt, L.N_t * H.B);
+    max_nt = std::max(max_nt, L.N_t * L.B);
     max_un = std::max<int64_t>(max_un, S.nf->kn.u_rows);
   }
   const size_t esz = pr->degree == 0 ? sizeof(double) : sizeof(double2);
@@ -1422,11 +1576,11 @@ int setup_device(Handle& H) {
   H.tmp_fine = H.dalloc<double>(std::max<int64_t>(max_len_fine_tmp, 1));
   H.g1 = H.dalloc<double>(max_ne * H.q * H.B);
   H.r0 = H.dalloc<double>(H.lv[0].len);
-  if (H.df_residual) H.xsplit = H.dalloc<float2>(H.lv[0].len);
+  if (H.df_residual) H.xsplit = H.dalloc<float2>(max_len);
   if (H.res32) {
-    H.xf32 = H.dalloc<float>(H.lv[0].len);
+    H.xf32 = H.dalloc<float>(max_len);
     H.corr_r = H.dalloc<double>(H.lv[0].len);
-    H.corr_e = H.dalloc<double>(H.lv[0].len);
+    H.corr_e = H.dalloc<double>(std::max(H.lv[0].len, H.user_len));
   }
   H.flags = H.dalloc<int>(4);
   CK(cudaMemset(H.flags, 0, 4 * sizeof(int)));
@@ -1512,12 +1666,24 @@ int check_ptrs(std::initializer_list<const void*> ps) {
   return ST_MG_OK;
 }
 
+// ||f - L x||^2 of a caller's f and x (every problem on its own finest level for a
+// ragged batch), FP64-accurate, blocking
+double outer_res_norm_sq(Handle& H, const double* f, const double* x) {
+  if (H.ragged) {
+    ragged_in(H, f, 0);
+    ragged_in(H, x, 1);
+    return ragged_res_norm_sq(H);
+  }
+  double nsq = 0.0;
+  op_residual(H, 0, f, x, H.r0, &nsq, true);
+  return nsq;
+}
+
 int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit, int32_t* iters, double* rel_res,
                double* history) {
   const double fn = f_norm(H, f);
   const double denom = fn > 0 ? fn : 1.0;
-  double nsq = 0.0;
-  op_residual(H, 0, f, x, H.r0, &nsq, true);
+  double nsq = outer_res_norm_sq(H, f, x);
   double rel = std::sqrt(nsq) / denom;
   const double rel0 = rel;
   if (history) history[0] = rel;
@@ -1526,7 +1692,7 @@ int solve_loop(Handle& H, const double* f, double* x, double rtol, int32_t maxit
   while (rel > rtol && it < maxit) {
     run_vcycle(H, f, x);
     if (int rc = check_tc(H)) return rc;
-    op_residual(H, 0, f, x, H.r0, &nsq, true);
+    nsq = outer_res_norm_sq(H, f, x);
     rel = std::sqrt(nsq) / denom;
     ++it;
     if (history) history[it] = rel;
@@ -1651,7 +1817,7 @@ int st_mg_sizes(st_mg_t h, int64_t* n_edge, int64_t* n_node, int64_t* n_dof, int
   if (!h) return fail(ST_MG_ERR_INVALID_ARG, "null handle");
   if (n_edge) *n_edge = h->space[0].ne;
   if (n_node) *n_node = h->space[0].nn;
-  if (n_dof) *n_dof = h->lv[0].len;
+  if (n_dof) *n_dof = h->user_len;
   if (n_levels) *n_levels = (int32_t)h->lv.size();
   return ST_MG_OK;
 }
@@ -1685,17 +1851,19 @@ int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const d
     std::vector<double> b;
     space_load(H.space[0].mesh, n_modes, a, k, phase, b);
     // time weights c[n q + i] = int_{I_n} g(t) phi_i dt, 3-point Gauss-Legendre per slab
-    const auto& L = H.lv[0];
+    // (a problem of a ragged batch: its own slab count over the common horizon T)
+    const int Nb = H.ragged ? H.pnt[batch] : H.lv[0].N_t;
+    const double taub = H.prob.T / Nb;
     const double x3 = std::sqrt(0.6);
     const double gx[3] = {0.5 * (1.0 - x3), 0.5, 0.5 * (1.0 + x3)};
     const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-    std::vector<double> c((size_t)L.N_t * H.q, 0.0);
-    for (int n = 0; n < L.N_t; ++n)
+    std::vector<double> c((size_t)Nb * H.q, 0.0);
+    for (int n = 0; n < Nb; ++n)
       for (int p = 0; p < 3; ++p) {
-        const double t = (n + gx[p]) * L.tau;
+        const double t = (n + gx[p]) * taub;
         const double g = std::sin(M_PI * t / H.prob.T) + 1.0;
-        c[(size_t)n * H.q] += L.tau * gw[p] * g;
-        if (H.q == 2) c[(size_t)n * 2 + 1] += L.tau * gw[p] * g * (2.0 * gx[p] - 1.0);
+        c[(size_t)n * H.q] += taub * gw[p] * g;
+        if (H.q == 2) c[(size_t)n * 2 + 1] += taub * gw[p] * g * (2.0 * gx[p] - 1.0);
       }
     // staging buffers of the handle (no allocation here: a cudaFree would wait for
     // every stream of the device)
@@ -1703,8 +1871,11 @@ int st_mg_assemble_load_batch(st_mg_t h, int32_t batch, int32_t n_modes, const d
     double* dc = H.load_c;
     CK(cudaMemcpyAsync(db, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
     CK(cudaMemcpyAsync(dc, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, H.stream));
-    const int seg = L.N_t * H.q;
-    CK(outer_load(db, dc, f_dev + (int64_t)batch * seg, H.space[0].ne, seg, seg * H.B, H.stream));
+    const int seg = Nb * H.q;
+    if (H.ragged)
+      CK(outer_load(db, dc, f_dev + H.poff[batch], H.space[0].ne, seg, (int)H.prow, H.stream));
+    else
+      CK(outer_load(db, dc, f_dev + (int64_t)batch * seg, H.space[0].ne, seg, seg * H.B, H.stream));
     CK(cudaStreamSynchronize(H.stream));
     return ST_MG_OK;
   });
@@ -1726,7 +1897,7 @@ int st_mg_slab_solve(st_mg_t h, int32_t level, const double* r_dev, double* y_de
   if (int rc = check_level(h, level)) return rc;
   if (int rc = check_ptrs({r_dev, y_dev})) return rc;
   return guarded([&]() {
-    const int cols = h->lv[level].N_t * h->B;
+    const int cols = h->lv[level].N_t * h->lv[level].B;
     const int ld = cols * h->q;
     op_slab_cols(*h, level, r_dev, ld, 0, cols, y_dev, ld, 0, 1.0, 0);
     return check_tc(*h);
@@ -1824,8 +1995,7 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
     if (int rc = check_tc(*h)) return rc;
     if (rel_res_out) {
       const double fn = f_norm(*h, f_dev);
-      double nsq = 0.0;
-      op_residual(*h, 0, f_dev, x_dev, h->r0, &nsq, true);
+      const double nsq = outer_res_norm_sq(*h, f_dev, x_dev);
       *rel_res_out = std::sqrt(nsq) / (fn > 0 ? fn : 1.0);
     }
     return ST_MG_OK;
@@ -1834,6 +2004,7 @@ int st_mg_vcycle(st_mg_t h, const double* f_dev, double* x_dev, double* rel_res_
 
 int st_mg_vcycle_residual_async(st_mg_t h, const double* f_dev, double* x_dev, double* r_dev) {
   if (int rc = check_dev(h)) return rc;
+  if (h->ragged) return fail(ST_MG_ERR_INVALID_ARG, "not available for a ragged batch (batch_nt)");
   if (int rc = check_ptrs({f_dev, x_dev, r_dev})) return rc;
   return guarded([&]() {
     run_vcycle(*h, f_dev, x_dev);
@@ -1856,7 +2027,7 @@ int st_mg_solve_host(st_mg_t h, const double* f_host, double* x_host, double rto
   if (!f_host || !x_host || maxit < 0) return fail(ST_MG_ERR_INVALID_ARG, "bad solve arguments");
   return guarded([&]() {
     Handle& H = *h;
-    const int64_t n = H.lv[0].len;
+    const int64_t n = H.user_len;
     // device staging buffers are allocated on the first call and kept by the handle
     if (!H.stage_f) {
       H.stage_f = H.dalloc<double>(n);
@@ -1918,8 +2089,8 @@ int st_mg_debug_host_slab_solve(st_mg_t h, int32_t level, const double* r_host, 
   return guarded([&]() {
     Handle& H = *h;
     const auto& L = H.lv[level];
-    const int ne = H.space[L.s].ne, q = H.q, ld = L.N_t * H.B * q;
-    for (int n = 0; n < L.N_t * H.B; ++n) {
+    const int ne = H.space[L.s].ne, q = H.q, ld = L.N_t * L.B * q;
+    for (int n = 0; n < L.N_t * L.B; ++n) {
       if (q == 1) {
         std::vector<double> b(ne);
         for (int e = 0; e < ne; ++e) b[e] = r_host[(int64_t)e * ld + n];
@@ -1949,7 +2120,7 @@ int st_mg_convergence_rate(st_mg_t h, double* x_dev, int32_t max_iter, double fl
     return fail(ST_MG_ERR_INVALID_ARG, "max_iter >= 1, floor >= 0 and non-null outputs required");
   return guarded([&]() {
     Handle& H = *h;
-    const int64_t len = H.lv[0].len;
+    const int64_t len = H.user_len;
     if (!H.zero_f) {
       H.zero_f = H.dalloc<double>(len);
       CK(cudaMemsetAsync(H.zero_f, 0, len * sizeof(double), H.stream));
@@ -1998,6 +2169,7 @@ int st_mg_probe_fp64(st_mg_t h, double* tflops) {
 
 int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host) {
   if (int rc = check_dev(h)) return rc;
+  if (h->ragged) return fail(ST_MG_ERR_INVALID_ARG, "not available for a ragged batch (batch_nt)");
   if (!norms_host) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   if (int rc = check_ptrs({v_dev})) return rc;
   return guarded([&]() {
@@ -2015,6 +2187,7 @@ int st_mg_batch_norms(st_mg_t h, const double* v_dev, double* norms_host) {
 
 int st_mg_batch_norms_async(st_mg_t h, const double* v_dev, double* norms_sq_dev) {
   if (int rc = check_dev(h)) return rc;
+  if (h->ragged) return fail(ST_MG_ERR_INVALID_ARG, "not available for a ragged batch (batch_nt)");
   if (int rc = check_ptrs({v_dev})) return rc;
   if (!norms_sq_dev) return fail(ST_MG_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
@@ -2031,6 +2204,7 @@ int st_mg_check(st_mg_t h) {
 
 int st_mg_batch_zero(st_mg_t h, int32_t batch, double* v_dev) {
   if (int rc = check_dev(h)) return rc;
+  if (h->ragged) return fail(ST_MG_ERR_INVALID_ARG, "not available for a ragged batch (batch_nt)");
   if (batch < 0 || batch >= h->B) return fail(ST_MG_ERR_INVALID_ARG, "batch index out of range");
   if (int rc = check_ptrs({v_dev})) return rc;
   return guarded([&]() {

@@ -908,15 +908,21 @@ __global__ void k_nodal_jacobi(int nrows, const int64_t* __restrict__ rowptr, co
 // Legendre basis: coarse (1, 2s-1) restricted to the first fine half is
 // (1, -1/2 + phi_1/2), to the second (1, 1/2 + phi_1/2), i.e. the blocks
 // P0 = [[1, -1/2], [0, 1/2]] and P1 = [[1, 1/2], [0, 1/2]].
-__global__ void k_time_restrict(const double* __restrict__ r, double* __restrict__ rc, int Nc, int degree) {
+// Row blockIdx.x = (edge e, problem p) of the fine level, Bf problems per edge row; the
+// coarse level holds Bc >= Bf problems per edge row (a ragged batch adds the problems
+// whose own finest level it is after the fine level's ones), so row (e, p) lands at
+// e Bc + p.  Bf = Bc: contiguous rows.
+__global__ void k_time_restrict(const double* __restrict__ r, double* __restrict__ rc, int Nc, int degree, int Bf,
+                                int Bc) {
   pdl_entry();
-  const int e = blockIdx.x;
+  const int ef = blockIdx.x;
+  const int e = (Bf == Bc) ? ef : (ef / Bf) * Bc + ef % Bf;
   if (degree == 0) {
-    const double* src = r + (int64_t)e * 2 * Nc;
+    const double* src = r + (int64_t)ef * 2 * Nc;
     double* dst = rc + (int64_t)e * Nc;
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) dst[k] = src[2 * k] + src[2 * k + 1];
   } else {
-    const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * 4 * Nc);
+    const double2* src = reinterpret_cast<const double2*>(r + (int64_t)ef * 4 * Nc);
     double2* dst = reinterpret_cast<double2*>(rc + (int64_t)e * 2 * Nc);
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
       const double2 a = src[2 * k], b = src[2 * k + 1];   // fine slab 2k and 2k+1, (i=0, i=1)
@@ -925,12 +931,16 @@ __global__ void k_time_restrict(const double* __restrict__ r, double* __restrict
   }
 }
 
-__global__ void k_time_prolong_add(const double* __restrict__ ec, double* __restrict__ x, int Nc, int degree) {
+// Row blockIdx.x = (edge e, problem p) of the fine level; its coarse row is e Bc + p (see
+// k_time_restrict).
+__global__ void k_time_prolong_add(const double* __restrict__ ec, double* __restrict__ x, int Nc, int degree, int Bf,
+                                   int Bc) {
   pdl_entry();
-  const int e = blockIdx.x;
+  const int ef = blockIdx.x;
+  const int e = (Bf == Bc) ? ef : (ef / Bf) * Bc + ef % Bf;
   if (degree == 0) {
     const double* src = ec + (int64_t)e * Nc;
-    double* dst = x + (int64_t)e * 2 * Nc;
+    double* dst = x + (int64_t)ef * 2 * Nc;
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
       const double v = src[k];
       dst[2 * k] += v;
@@ -938,7 +948,7 @@ __global__ void k_time_prolong_add(const double* __restrict__ ec, double* __rest
     }
   } else {
     const double2* src = reinterpret_cast<const double2*>(ec + (int64_t)e * 2 * Nc);
-    double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * 4 * Nc);
+    double2* dst = reinterpret_cast<double2*>(x + (int64_t)ef * 4 * Nc);
     for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
       const double2 v = src[k];
       double2 a = dst[2 * k], b = dst[2 * k + 1];
@@ -1338,12 +1348,14 @@ cudaError_t nodal_jacobi(CsrView Kn, const double* kval, const double* dinv, con
                                                        wgt); count_launches(1); }
   return cudaGetLastError();
 }
-cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) { launch_k(k_time_restrict, nrows, 128, 0, st, r, rc, Nc, degree); count_launches(1); }
+cudaError_t time_restrict(const double* r, double* rc, int nrows, int Nc, int degree, cudaStream_t st, int Bf,
+                          int Bc) {
+  if (nrows > 0) { launch_k(k_time_restrict, nrows, 128, 0, st, r, rc, Nc, degree, Bf, Bc); count_launches(1); }
   return cudaGetLastError();
 }
-cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st) {
-  if (nrows > 0) { launch_k(k_time_prolong_add, nrows, 128, 0, st, ec, x, Nc, degree); count_launches(1); }
+cudaError_t time_prolong_add(const double* ec, double* x, int nrows, int Nc, int degree, cudaStream_t st, int Bf,
+                             int Bc) {
+  if (nrows > 0) { launch_k(k_time_prolong_add, nrows, 128, 0, st, ec, x, Nc, degree, Bf, Bc); count_launches(1); }
   return cudaGetLastError();
 }
 cudaError_t csr_spmm(CsrView P, const double* pval, const double* in, double* out, int ncols, int beta,

@@ -12,11 +12,13 @@ from . import binding as B
 
 class SpaceTimeSolver:
     def __init__(self, n_cube, nu, sigma, T, N_t, degree, n_space_levels=1, stream=None, host_only=False,
-                 n_batch=1, bc=0, mesh=None, **options):
+                 n_batch=1, bc=0, mesh=None, batch_nt=None, **options):
         """n_cube: Kuhn cubes per side, or mesh = (xyz, tets, n_refine) for a general start mesh
-        refined n_refine times (n_cube ignored; nu, sigma per finest tet, child k of tet t = 8 t + k)."""
-        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch, bc, mesh)
+        refined n_refine times (n_cube ignored; nu, sigma per finest tet, child k of tet t = 8 t + k).
+        batch_nt: per-problem slab counts of a ragged batch (N_t divided by powers of two)."""
+        self.prob = B.make_problem(n_cube, n_space_levels, nu, sigma, T, N_t, degree, n_batch, bc, mesh, batch_nt)
         self.n_batch = n_batch
+        self.batch_nt = None if batch_nt is None else [int(v) for v in batch_nt]
         self.opt = B.st_mg_default_options()
         for k, v in options.items():
             if not hasattr(self.opt, k):
@@ -49,9 +51,19 @@ class SpaceTimeSolver:
 
     # ---- buffers
     def level_shape(self, level=0, nodal=False):
+        """Shape of a vector of a level; level 0 of a ragged batch: the caller's layout (the
+        problems' own slab counts one after the other per edge row)."""
         L = self.levels[level]
         rows = L["n_node"] if nodal else L["n_edge"]
+        if self.batch_nt is not None and level == 0:
+            return (rows, sum(self.batch_nt) * self.q)
         return (rows, self.n_batch * L["N_t"] * self.q)
+
+    def problem_cols(self, b):
+        """Columns of problem b in a caller's vector (ragged or not)."""
+        nts = self.batch_nt or [self.levels[0]["N_t"]] * self.n_batch
+        a = sum(nts[:b]) * self.q
+        return slice(a, a + nts[b] * self.q)
 
     def zeros(self, level=0, nodal=False):
         import torch
