@@ -38,7 +38,7 @@ CPU_SAMPLE_SLABS = 16
 # DRAM bytes (read + write) of the supernodal products of one finest-level FP64 slab solve of
 # this workload, from one ncu capture of the same kernels and factor; set to None when those
 # kernels or the factor they read change
-SLAB_SOLVE_TRAFFIC_FP64 = None
+SLAB_SOLVE_TRAFFIC_FP64 = 2.396e9
 
 
 def workload_config(world: int = 1) -> dict:
@@ -571,6 +571,8 @@ def main():
                          "(repeats an autotuned run's choice, e.g. under a profiler)")
     ap.add_argument("--split-k", type=int, default=0,
                     help="K columns of a split-K work item (0: the library default)")
+    ap.add_argument("--tc-split-k", type=int, default=0,
+                    help="complex K columns of a tensor-core split-K item (0: the library default)")
     ap.add_argument("--nd-leaf", type=int, default=0,
                     help="largest leaf of the slab matrices' nested dissection (0: the library default)")
     ap.add_argument("--launch-overlap", type=int, default=0, choices=[0, 1],
@@ -579,6 +581,8 @@ def main():
                     help="excitations of the 4^3 DG(0) two-grid case solved to 1e-10 (0: skip)")
     ap.add_argument("--precision-line", type=int, default=1,
                     help="also time the 16^3, N_t = 1024 workload to 1e-8 in every slab arithmetic")
+    ap.add_argument("--ragged", type=int, default=8,
+                    help="excitations of the ragged-batch variant (N_t from {128, 256, 512, 1024}; 0: skip)")
     ap.add_argument("--batch", type=int, default=8,
                     help="problems per handle of the batched BF16 variant (0: skip it)")
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3, 4],
@@ -648,7 +652,8 @@ def main():
     def make(prec, **kw):
         return stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], W["N_t"], W["degree"], nu_pre=W["nu_pre"],
                                     nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=prec,
-                                    autotune=args.autotune, split_k=args.split_k, **kw)
+                                    autotune=args.autotune, split_k=args.split_k,
+                                    tc_split_k=args.tc_split_k, **kw)
 
     def time_cycles(Sx, fx, xx, steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -864,6 +869,37 @@ def main():
             variants["bf16_tensor_batched"]["slab_solve_frac_of_bf16_peak_least_fill"] = lf / peak
         Sb.close()
         del fb, xb
+
+    # ragged batch: excitations with different slab counts over one horizon in one handle
+    # (the batching configuration's N_t mix at the size of this workload's mesh)
+    if args.mixed and args.ragged > 0:
+        import numpy as np
+        rng = np.random.Generator(np.random.PCG64(4242))
+        nts = [int(v) for v in rng.permutation(np.repeat([1024, 512, 256, 128], (args.ragged + 3) // 4))[:args.ragged]]
+        Sr = stmg.SpaceTimeSolver(W["n"], nu, sigma, W["T"], max(nts), W["degree"], nu_pre=W["nu_pre"],
+                                  nu_post=W["nu_post"], stream=stream.cuda_stream, slab_prec=3, residual_prec=1,
+                                  autotune=args.autotune, split_k=args.split_k, tc_split_k=args.tc_split_k,
+                                  n_batch=len(nts), batch_nt=nts)
+        fr = Sr.zeros()
+        for b in range(len(nts)):
+            Sr.load(st_inputs.excitation(W["seed"] + 200 + b + 1000 * rank), f=fr, batch=b)
+        xr = Sr.zeros()
+        ms_r = reduce_max(time_cycles(Sr, fr, xr, args.steps), dist, "cuda")
+        per_r = smoothed_per_cycle(Sr.n_dof, W["nu_pre"], W["nu_post"])
+        xr.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        out_r = Sr.solve(fr, xr, rtol=1e-8, maxit=80)
+        torch.cuda.synchronize()
+        t_r = time.perf_counter() - a
+        variants["ragged_batch_bf16_fp32_residual"] = {
+            "value": replica_value(world, per_r, args.steps, ms_r), "unit": UNIT, "problems": len(nts),
+            "N_t_per_problem": nts, "dofs": Sr.n_dof, "ms_per_step": ms_r / args.steps,
+            "time_to_1e-8_s": t_r, "v_cycles": out_r["iters"], "rel_res": out_r["rel_res"],
+            "layout": "one handle: each problem enters the time hierarchy at the level whose step is its own; "
+                      "one V-cycle advances all"}
+        Sr.close()
+        del fr, xr
 
     extra = {}
     if rank == 0 and args.config1_seeds > 0:

@@ -192,6 +192,9 @@ typedef struct {
                                 row block): 16 .. 1024, a multiple of 16; 0 (default): 32.  Narrower
                                 items mean more items in flight and a shorter chain per item, more
                                 partial sums to reduce; results change at rounding level */
+    int32_t tc_split_k;      /* the same for the tensor-core split-K items of the 16-bit factors
+                                (slab_prec 3, 4; complex columns, a multiple of the 32-column MMA
+                                stage, 32 .. 4096); 0 (default): 256 */
 } st_mg_options;
 
 /* Fill *opt with the paper's defaults: omega 0.5, V(1,1), lambda_crit 0.1,

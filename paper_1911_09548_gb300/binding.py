@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("nodal_solve", _i32), ("nodal_jacobi_sweeps", _i32), ("use_A", _i32),
                 ("setup_threads", _i32), ("slab_prec", _i32), ("residual_prec", _i32), ("use_graph", _i32),
                 ("smoother", ctypes.c_char * 16), ("persistent_split", _i32), ("factor_cache", _i32),
-                ("autotune", _i32), ("nd_leaf", _i32), ("split_k", _i32)]
+                ("autotune", _i32), ("nd_leaf", _i32), ("split_k", _i32), ("tc_split_k", _i32)]
 
 
 class ServerOptions(ctypes.Structure):

@@ -265,6 +265,7 @@ struct st_mg_s {
   double* scalar = nullptr;
   double* zero_f = nullptr;             // finest-level zero load of the rate harness (allocated on first use)
   int sk_k = kSkK;                      // K columns of a split-K work item (st_mg_options.split_k)
+  int tc_k = kTcSplitK;                 // ... of a tensor-core split-K item (st_mg_options.tc_split_k)
   float2* xsplit = nullptr;             // x as FP32 pairs for the double-float residual
   bool res32 = false;                   // residual_prec 1: FP32 residuals inside a correction-form V-cycle
   float* xf32 = nullptr;                // x as FP32 for those residuals
@@ -449,7 +450,7 @@ void build_tc_tiles(DevArena& h, const SupernodalFactor<cplx>& F, DevFactor<floa
 
 template <typename T, typename DT, typename WT>
 void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT>& D, FactorLists& Lh, int sk_k,
-                     int bm = kSnBM) {
+                     int tc_k, int bm = kSnBM) {
   std::vector<int64_t>& fo = Lh.fo;
   std::vector<int64_t>& bo = Lh.bo;
   D.n = F.n;
@@ -527,7 +528,8 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
   D.d_bs_unit_off = h.upload(Lh.bsu);
   D.max_items = max_items;
   D.n_sm = h.n_sm;
-  // tensor-core split-K items: the tiles above, each cut into kTcSplitK-wide K chunks
+  // tensor-core split-K items: the tiles above, each cut into tc_k-wide K chunks (a multiple
+  // of the 32-column stage)
   std::vector<int4> tfi, tfu, tbi, tbu;
   Lh.tfi.assign(F.max_depth + 2, 0);
   Lh.tfu.assign(F.max_depth + 2, 0);
@@ -547,15 +549,15 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
         const int r0 = rt * kSnBM;
         const int kend = (r0 + kSnBM <= a.nc) ? r0 + kSnBM : a.nc;
         const int first = (int)tfi.size();
-        for (int k0 = 0; k0 < kend; k0 += kTcSplitK)
-          tfi.push_back(make_int4((int)s, rt, k0, std::min(k0 + kTcSplitK, kend)));
+        for (int k0 = 0; k0 < kend; k0 += tc_k)
+          tfi.push_back(make_int4((int)s, rt, k0, std::min(k0 + tc_k, kend)));
         tfu.push_back(make_int4((int)s, rt, first, (int)tfi.size()));
       }
       for (int rt = 0; rt * kSnBM < a.nc; ++rt) {
         const int r0 = rt * kSnBM;
         const int kbeg = (r0 / 32) * 32;   // the tensor-core stage width
         const int first = (int)tbi.size();
-        for (int k0 = kbeg; k0 < m; k0 += kTcSplitK) tbi.push_back(make_int4((int)s, rt, k0, std::min(k0 + kTcSplitK, m)));
+        for (int k0 = kbeg; k0 < m; k0 += tc_k) tbi.push_back(make_int4((int)s, rt, k0, std::min(k0 + tc_k, m)));
         tbu.push_back(make_int4((int)s, rt, first, (int)tbi.size()));
       }
     }
@@ -1068,7 +1070,8 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 4 || (op->slab_prec >= 3 && pr->degree != 1) ||
       (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
       (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
-      op->split_k < 0 || op->split_k > 1024 || (op->split_k % 16) != 0 ||
+      op->split_k < 0 || op->split_k > 1024 || (op->split_k % 16) != 0 || op->tc_split_k < 0 ||
+      op->tc_split_k > 4096 || (op->tc_split_k % 32) != 0 ||
       (op->residual_prec < -1 || op->residual_prec > 2))
     return fail(ST_MG_ERR_INVALID_ARG, "invalid options");
   const int64_t nt = gm ? ((int64_t)gm->n_tet << (3 * gm->n_refine)) : (int64_t)6 * n * n * n;
@@ -1202,6 +1205,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     H.lv[l].prec = ((op->slab_prec == 1 || op->slab_prec >= 3) && l + 1 == H.lv.size()) ? 0 : op->slab_prec;
   H.res32 = op->residual_prec == 1;
   H.sk_k = op->split_k > 0 ? op->split_k : kSkK;
+  H.tc_k = op->tc_split_k > 0 ? op->tc_split_k : kTcSplitK;
   H.df_residual = op->residual_prec == 2 || op->residual_prec == 1 || (op->residual_prec < 0 && op->slab_prec != 0);
   H.nodal_prec = op->slab_prec == 0 ? 0 : op->slab_prec == 2 ? 2 : 1;
 
@@ -1224,8 +1228,9 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
     char buf[192];
     for (size_t l = 0; l < H.lv.size(); ++l) {
       const auto& L = H.lv[l];
-      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d sk%d tau%a mat%016llx", H.device, n,
-                    L.s, pr->degree, L.prec, nd_leaf_of(*op), H.sk_k, L.tau, (unsigned long long)H.mat_hash);
+      std::snprintf(buf, sizeof buf, "slab dev%d n%d s%d deg%d prec%d leaf%d sk%d tc%d tau%a mat%016llx",
+                    H.device, n, L.s, pr->degree, L.prec, nd_leaf_of(*op), H.sk_k, H.tc_k, L.tau,
+                    (unsigned long long)H.mat_hash);
       lkey[l] = buf;
     }
     for (size_t sl = 0; sl < H.space.size(); ++sl) {
@@ -1427,9 +1432,9 @@ int setup_device(Handle& H) {
     if (!S.nf) {
       auto N = std::make_shared<NodalFactor>();
       N->mem.n_sm = H.n_sm;
-      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists, H.sk_k, kSnBmFP64);
-      if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists, H.sk_k);
-      if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists, H.sk_k);
+      make_dev_factor(N->mem, S.knF, N->kn, N->kn_lists, H.sk_k, H.tc_k, kSnBmFP64);
+      if (H.nodal_prec == 2) make_dev_factor(N->mem, S.knF, N->kn_df, N->kn_df_lists, H.sk_k, H.tc_k);
+      if (H.nodal_prec == 1) make_dev_factor(N->mem, S.knF, N->kn_f, N->kn_f_lists, H.sk_k, H.tc_k);
       N->u_rows = N->kn.u_rows;
       N->max_items = N->kn.max_items;
       S.nf = N;
@@ -1462,15 +1467,15 @@ int setup_device(Handle& H) {
         auto F = std::make_shared<SlabFactor>();
         F->mem.n_sm = H.n_sm;
         if (L.prec == 1) {
-          make_dev_factor(F->mem, L.fr, F->drf, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fr, F->drf, F->lists, H.sk_k, H.tc_k);
           F->max_items = F->drf.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 4;
         } else if (L.prec == 2) {
-          make_dev_factor(F->mem, L.fr, F->drd, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fr, F->drd, F->lists, H.sk_k, H.tc_k);
           F->max_items = F->drd.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         } else {
-          make_dev_factor(F->mem, L.fr, F->dr, F->lists, H.sk_k, kSnBmFP64);
+          make_dev_factor(F->mem, L.fr, F->dr, F->lists, H.sk_k, H.tc_k, kSnBmFP64);
           F->max_items = F->dr.max_items;
           F->w_bytes = (int64_t)L.fr.W.size() * 8;
         }
@@ -1504,11 +1509,11 @@ int setup_device(Handle& H) {
         auto F = std::make_shared<SlabFactor>();
         F->mem.n_sm = H.n_sm;
         if (L.prec == 1) {
-          make_dev_factor(F->mem, L.fc, F->dcf, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fc, F->dcf, F->lists, H.sk_k, H.tc_k);
           F->max_items = F->dcf.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 8;
         } else if (L.prec == 3) {
-          make_dev_factor(F->mem, L.fc, F->dcb, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fc, F->dcb, F->lists, H.sk_k, H.tc_k);
           build_tc_tiles(F->mem, L.fc, F->dcb, F->lists);
           F->max_items = F->dcb.max_items;
           F->max_tc_items = F->dcb.max_tc_items;
@@ -1517,18 +1522,18 @@ int setup_device(Handle& H) {
         } else if (L.prec == 4) {
           if (max_abs_entry(L.fc) > 16384.0)
             throw NumericError{"a slab factor entry exceeds the FP16 range kept for slab_prec 4 (|w| > 16384)"};
-          make_dev_factor(F->mem, L.fc, F->dch, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fc, F->dch, F->lists, H.sk_k, H.tc_k);
           build_tc_tiles(F->mem, L.fc, F->dch, F->lists);
           F->max_items = F->dch.max_items;
           F->max_tc_items = F->dch.max_tc_items;
           F->max_stage_tiles = F->dch.max_stage_tiles;
           F->w_bytes = (int64_t)L.fc.W.size() * 4;
         } else if (L.prec == 2) {
-          make_dev_factor(F->mem, L.fc, F->dcd, F->lists, H.sk_k);
+          make_dev_factor(F->mem, L.fc, F->dcd, F->lists, H.sk_k, H.tc_k);
           F->max_items = F->dcd.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         } else {
-          make_dev_factor(F->mem, L.fc, F->dc, F->lists, H.sk_k, kSnBmFP64);
+          make_dev_factor(F->mem, L.fc, F->dc, F->lists, H.sk_k, H.tc_k, kSnBmFP64);
           F->max_items = F->dc.max_items;
           F->w_bytes = (int64_t)L.fc.W.size() * 16;
         }
@@ -1777,6 +1782,7 @@ int st_mg_default_options(st_mg_options* o) {
   o->autotune = 0;
   o->nd_leaf = 0;
   o->split_k = 0;
+  o->tc_split_k = 0;
   return ST_MG_OK;
 }
 
