@@ -588,6 +588,10 @@ def main():
     ap.add_argument("--slab-prec", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="slab-solve arithmetic of the main line: 0 FP64, 1 FP32, 2 double-float, 3 BF16 tensor "
                          "cores, 4 FP16 tensor cores")
+    ap.add_argument("--residual-prec", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="residual arithmetic of the main line (st_mg_options.residual_prec)")
+    ap.add_argument("--tc-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core mode of every 16-bit level of the main line (st_mg_set_tc_mode)")
     ap.add_argument("--mode", default="bench", choices=["bench", "slab", "serve", "rates", "precision", "kernels"],
                     help="slab: set up the workload, run two finest-level slab solves and exit (for profilers); "
                          "serve: the request-loop benchmark (Poisson streams, p50/p99 latency)")
@@ -706,7 +710,13 @@ def main():
                 "p99_rule": "nearest rank of the sorted sample (the maximum when n < 100)", "v_cycles": iters}
 
     t0 = time.time()
-    S = make(args.slab_prec, nd_leaf=args.nd_leaf)
+    S = make(args.slab_prec, nd_leaf=args.nd_leaf, residual_prec=args.residual_prec)
+    if args.tc_mode and args.slab_prec >= 3:
+        for l in range(S.n_levels):
+            try:
+                stmg.st_mg_set_tc_mode(S.h, l, args.tc_mode)
+            except RuntimeError:
+                pass   # a level without a 16-bit factor (the coarsest solve is FP64)
     if args.split_waves:
         for l, w in enumerate(int(v) for v in args.split_waves.split(",")):
             stmg.st_mg_set_split_waves(S.h, l, w)

@@ -114,6 +114,8 @@ struct SkSync {
   int* err = nullptr;
   int split_waves = 2;   // a tree depth runs split-K when its tiles fill fewer than this many
                          // waves of the SMs (setup may tune it per level)
+  bool tc_persist = false;   // tiled tensor-core depths: one persistent CTA per SM walking the
+                            // depth's tiles (true) or one CTA per tile (false)
 };
 
 cudaError_t sn_solve_real(const DevFactor<double>& F, double* Q, double* Z, double* U, double* P, int nrhs, int ld,

@@ -246,7 +246,8 @@ struct st_mg_s {
     std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
     int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
     int split_waves = 2;                                    // tiled / split-K threshold (autotuned)
-    int tc_mode = 0;                                        // BF16 factor: 0 tensor cores, 1 CUDA-core reference
+    int tc_mode = 0;                                        // 16-bit factor: 0 tensor cores, 1 CUDA-core reference,
+                                                            // 2 tensor cores with persistent tiled depths
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
   };
@@ -637,6 +638,7 @@ void level_solve(Handle& h, int l, int cnt) {
   auto& L = h.lv[l];
   SkSync sk = h.sk;
   sk.split_waves = L.split_waves;
+  sk.tc_persist = L.tc_mode == 2;
   if (L.prec == 4) {
     if (L.tc_mode == 1)
       CK(sn_solve_cplx_f16_cc(L.fac->dch, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),
@@ -2372,7 +2374,7 @@ int st_mg_set_launch_overlap(int32_t on) {
 
 int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode) {
   if (int rc = check_level(h, level)) return rc;
-  if (mode < 0 || mode > 1) return fail(ST_MG_ERR_INVALID_ARG, "tensor-core mode must be 0 or 1");
+  if (mode < 0 || mode > 2) return fail(ST_MG_ERR_INVALID_ARG, "tensor-core mode must be 0, 1 or 2");
   if (h->lv[level].prec < 3)
     return fail(ST_MG_ERR_INVALID_ARG, "level has no 16-bit tensor-core factor (slab_prec 3 or 4)");
   h->lv[level].tc_mode = mode;

@@ -107,8 +107,11 @@ __device__ __forceinline__ void put_g(uint8_t* Bs, int c, int k, float2 g) {
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// one rounded product and one fused multiply-add per part, spelled out so that every
+// kernel here rounds the same way (left to the compiler, the contraction may differ
+// between kernels)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 
 // One block per (unit = node row tile, column tile, group of TC_RED_ROWS rows): sums
@@ -390,6 +393,241 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
   if (warp == 0) tmem_dealloc(tmem);
 }
 
+// ---------------------------------------------------------------- persistent tiled path
+// One CTA per SM walks the depth's (row tile, column block) tasks t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with three roles: warp 0 (lane 0) streams the operand tiles
+// of all its tasks through a TC3_STAGES-deep ring of shared-memory stages, warp 1 (lane 0)
+// issues the MMAs of a task into one of two TMEM accumulators (columns 0..127 or
+// 128..255), and warps 2..5 read a finished accumulator straight from TMEM (warp w reads
+// TMEM lanes 32 (w % 4) ..), apply the epilogue and store, while the next task's MMAs run
+// into the other accumulator.  The ring never drains between tasks, so a CTA's short K
+// loops no longer pay the pipeline fill each.  Products and epilogue are those of
+// k_sn_tc2 (same stage order, FP32 accumulation, same complex multiply), so the results
+// are the same bit for bit.
+// Barriers: full/empty per stage (producer <-> MMA), accf/acce per accumulator (MMA <->
+// epilogue); every wait is bounded; a role whose wait gives up sets *err and stops, the
+// others then stop at their own bounded waits, and the CTA waits (bounded) for its MMAs
+// and copies in flight before it frees TMEM.
+constexpr int TC3_STAGES = 4;
+constexpr int TC3_THREADS = 192;
+constexpr int TC3_SMEM = TC3_STAGES * 2 * kTcTileBytes + 1024;
+constexpr uint32_t TC3_TMEM_COLS = 2 * TC_N;
+
+// task t of a depth: tile t / gy (node, row tile), column block t % gy, and its K stages
+// (forward: up to the tile's last row inside L11^{-1}; backward: from the tile's first row)
+template <bool FWD>
+__device__ __forceinline__ void tc3_task(int t, int gy, const int2* __restrict__ tiles,
+                                         const DevNode* __restrict__ nodes, const int4* __restrict__ tnode,
+                                         const int2* __restrict__ tpre, int& node, int& rtile, int& ct, int& ks0,
+                                         int& ks1, int& nks, int& pre) {
+  const int2 tl = tiles[t / gy];
+  ct = t % gy;
+  node = tl.x;
+  rtile = tl.y;
+  const int nc = nodes[node].nc;
+  const int4 tn = tnode[node];
+  nks = FWD ? tn.y : tn.w;
+  pre = FWD ? tpre[node].x : tpre[node].y;
+  const int row0 = rtile * TC_ROWS;
+  if (FWD) {
+    ks0 = 0;
+    ks1 = ((row0 + TC_ROWS <= nc ? row0 + TC_ROWS : nc) + TC_KC - 1) / TC_KC;
+  } else {
+    ks0 = row0 / TC_KC;
+    ks1 = nks;
+  }
+}
+
+template <bool FWD, bool F16>
+__global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __restrict__ nodes,
+                                                           const uint8_t* __restrict__ TW,
+                                                           const int4* __restrict__ tnode,
+                                                           const int2* __restrict__ tpre,
+                                                           const uint8_t* __restrict__ Bst,
+                                                           const float2* __restrict__ Dinv,
+                                                           const int32_t* __restrict__ gsrc,
+                                                           const int2* __restrict__ tiles, int ntiles, int gy,
+                                                           float2* __restrict__ Z, float2* __restrict__ U,
+                                                           float2* __restrict__ X, int nrhs, int ld,
+                                                           int* __restrict__ err) {
+  pdl_entry();
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full[TC3_STAGES], empty[TC3_STAGES], accf[2], acce[2], done;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  const int ntasks = ntiles * gy;
+  if (tid == 0) {
+    for (int i = 0; i < TC3_STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acce[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TC3_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  int issued = 0;   // producer: stages whose copies it started
+  bool pfail = false;
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    int g = 0;
+    for (int t = blockIdx.x; t < ntasks && !pfail; t += gridDim.x) {
+      int node, rtile, ct, ks0, ks1, nks, pre;
+      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
+      const int4 tn = tnode[node];
+      const uint8_t* atiles = TW + ((int64_t)(FWD ? tn.x : tn.z) + (int64_t)rtile * nks) * kTcTileBytes;
+      const uint8_t* btiles = Bst + ((int64_t)gy * pre + (int64_t)ct * nks) * kTcTileBytes;
+      for (int ks = ks0; ks < ks1; ++ks, ++g) {
+        const int slot = g % TC3_STAGES;
+        const uint32_t ph = (uint32_t)((g / TC3_STAGES) & 1);
+        if (!mbar_wait(&empty[slot], ph ^ 1u)) { pfail = true; break; }
+        uint8_t* a = base + slot * 2 * kTcTileBytes;
+        mbar_arrive_tx(&full[slot], 2 * kTcTileBytes);
+        bulk_g2s(smem_u32(a), atiles + (int64_t)ks * kTcTileBytes, kTcTileBytes, &full[slot]);
+        bulk_g2s(smem_u32(a + kTcTileBytes), btiles + (int64_t)ks * kTcTileBytes, kTcTileBytes, &full[slot]);
+        issued = g + 1;
+      }
+    }
+    if (pfail) atomicExch(err, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    bool fail = false;
+    int g = 0, j = 0;
+    for (int t = blockIdx.x; t < ntasks && !fail; t += gridDim.x, ++j) {
+      int node, rtile, ct, ks0, ks1, nks, pre;
+      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
+      const int abuf = j & 1;
+      const uint32_t aph = (uint32_t)((j >> 1) & 1);
+      if (!mbar_wait(&acce[abuf], aph ^ 1u)) { fail = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t acc_addr = tmem + (uint32_t)(abuf * TC_N);
+      for (int i = 0; i < ks1 - ks0; ++i, ++g) {
+        const int slot = g % TC3_STAGES;
+        const uint32_t ph = (uint32_t)((g / TC3_STAGES) & 1);
+        if (!mbar_wait(&full[slot], ph)) { fail = true; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint8_t* a = base + slot * 2 * kTcTileBytes;
+#pragma unroll
+        for (int s4 = 0; s4 < (2 * TC_KC) / 16; ++s4) {
+          const uint64_t ad = smem_desc(smem_u32(a) + s4 * 2 * CORE_K);
+          const uint64_t bd = smem_desc(smem_u32(a + kTcTileBytes) + s4 * 2 * CORE_K);
+          const uint32_t accum = (i == 0 && s4 == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+              "l"(ad), "l"(bd), "r"(tc_idesc<F16>()), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&empty[slot])));
+      }
+      if (fail) break;
+      // the accumulator is complete once every MMA issued so far has finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&accf[abuf])));
+    }
+    if (fail) atomicExch(err, 1);
+    // tracks every MMA issued: nobody frees TMEM or leaves before they finish
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&done)));
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lane R = real accumulator row (complex row R / 2, real part on
+    // even lanes); after pairing the two lanes of a complex row, the even lane writes its
+    // columns cb .. cb + 15 and the odd lane cb + 16 .. cb + 31 (128 contiguous bytes each)
+    bool fail = false;
+    const uint32_t lq = (uint32_t)(warp & 3) * 32u;   // first TMEM lane of this warp
+    const int R = (int)lq + lane;
+    const int il = R >> 1;
+    const bool odd = (R & 1) != 0;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntasks && !fail; t += gridDim.x, ++j) {
+      int node, rtile, ct, ks0, ks1, nks, pre;
+      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
+      const int abuf = j & 1;
+      const uint32_t aph = (uint32_t)((j >> 1) & 1);
+      // warp-uniform outcome: the TMEM loads below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(&accf[abuf], aph))) { fail = true; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const DevNode nd = nodes[node];
+      const int nc = nd.nc, m = nc + nd.nr;
+      const int rows_out = FWD ? m : nc;
+      const int i = rtile * TC_ROWS + il;   // complex row of the node's block
+      const int c0 = ct * TC_N;
+      const int32_t* gs = gsrc + nd.g_off * 2;
+      // a task without K stages has no product (the per-tile kernel writes nothing either)
+      for (int cb = 0; cb < (ks1 > ks0 ? TC_N : 0); cb += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (lq << 16) + (uint32_t)(abuf * TC_N + cb), v);
+        float2 y[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          // even lane keeps Re of column q, receives its Im; odd lane keeps Im of
+          // column 16 + q, receives its Re
+          const float lo = __uint_as_float(v[q]), hi = __uint_as_float(v[16 + q]);
+          const float mine = odd ? hi : lo;
+          const float give = odd ? lo : hi;
+          const float got = __shfl_xor_sync(0xffffffffu, give, 1);
+          y[q] = odd ? make_float2(got, mine) : make_float2(mine, got);
+        }
+        const int cfirst = c0 + cb + (odd ? 16 : 0);
+        if (i >= rows_out) continue;
+        if (FWD && i < nc) {
+          const float2 dv = Dinv[nd.col0 + i];
+          float2* zr = Z + (int64_t)(nd.col0 + i) * ld;
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cfirst + q < nrhs) zr[cfirst + q] = cmul(dv, y[q]);
+        } else if (FWD) {
+          const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
+          float2* ur = U + (int64_t)(nd.u_off + i - nc) * ld;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int c = cfirst + q;
+            if (c >= nrhs) continue;
+            float2 u = y[q];
+            if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
+            if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
+            ur[c] = u;
+          }
+        } else {
+          float2* xr = X + (int64_t)(nd.col0 + i) * ld;
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cfirst + q < nrhs) xr[cfirst + q] = y[q];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[abuf])));
+    }
+    if (fail && lane == 0) atomicExch(err, 1);
+  }
+  // ---- teardown: every MMA finished, every bulk copy landed, then TMEM is freed
+  __syncthreads();
+  if (tid == 0 && !mbar_wait(&done, 0)) atomicExch(err, 1);
+  if (warp == 0 && lane == 0 && pfail) {
+    // copies issued but never consumed land in this CTA's shared memory: wait (bounded)
+    for (int g = issued > TC3_STAGES ? issued - TC3_STAGES : 0; g < issued; ++g)
+      mbar_wait(&full[g % TC3_STAGES], (uint32_t)((g / TC3_STAGES) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC3_TMEM_COLS));
+}
+
 }  // namespace
 
 template <typename WT>
@@ -403,6 +641,8 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool s
     cudaFuncSetAttribute(k_sn_tc2<false, false, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
     cudaFuncSetAttribute(k_sn_tc2<true, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
     cudaFuncSetAttribute(k_sn_tc2<false, true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC2_SMEM);
+    cudaFuncSetAttribute(k_sn_tc3<true, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
+    cudaFuncSetAttribute(k_sn_tc3<false, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
     attr_set = true;
   }
   const unsigned gy = (unsigned)((nrhs + TC_N - 1) / TC_N);
@@ -417,7 +657,20 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool s
                                                                          F.tas_b + aa, Q, Z, U, Q, Bst, nrhs, ld);
   count_launches(1);
   const uint8_t* TW = fwd ? F.tw_f : F.tw_b;
-  if (!split) {
+  if (!split && sy.tc_persist) {
+    const int64_t* to = fwd ? F.h_fwd_off : F.h_bwd_off;
+    const int64_t a = to[d], b = to[d + 1];
+    const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;
+    const int64_t ntasks = (b - a) * (int64_t)gy;
+    const unsigned grid = (unsigned)(ntasks < F.n_sm ? ntasks : F.n_sm);
+    if (fwd)
+      launch_k(k_sn_tc3<true, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv,
+               F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
+    else
+      launch_k(k_sn_tc3<false, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv,
+               F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
+    count_launches(1);
+  } else if (!split) {
     const int64_t* to = fwd ? F.h_fwd_off : F.h_bwd_off;
     const int64_t a = to[d], b = to[d + 1];
     const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;

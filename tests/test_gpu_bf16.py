@@ -77,6 +77,43 @@ def test_bf16_tensor_cores_match_cuda_core_reference(setup, level):
         stmg.st_mg_set_split_waves(S.h, level, w0)
 
 
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_bf16_persistent_tiled_depths_match_per_tile_kernel(setup, level):
+    """Tensor-core mode 2: every tiled depth runs as one persistent CTA per SM that walks
+    the depth's (row tile, column block) tasks with a bulk-copy ring that never drains
+    and two TMEM accumulators.  The MMAs of a task are issued in the same order on the
+    same operand tiles as in the one-CTA-per-tile kernel, and the epilogue does the same
+    arithmetic, so with every depth forced tiled the two solves agree bit for bit; both
+    stay within the operand-rounding bound of the CUDA-core reference."""
+    stmg, S, *_ = setup
+    rng = np.random.default_rng(21 + level)
+    L = S.levels[level]
+    ro = rng.normal(size=(L["N_t"], 2, L["n_edge"]))
+    r = torch.from_numpy(to_lib(ro)).cuda()
+    w0 = stmg.st_mg_split_waves(S.h, level)
+    try:
+        stmg.st_mg_set_tc_mode(S.h, level, 1)
+        y_ref = _solve(stmg, S, r, level)
+        stmg.st_mg_set_split_waves(S.h, level, 0)
+        stmg.st_mg_set_tc_mode(S.h, level, 0)
+        y_tile = _solve(stmg, S, r, level)
+        stmg.st_mg_set_tc_mode(S.h, level, 2)
+        y_pers = _solve(stmg, S, r, level)
+        d = rel(y_pers, y_ref)
+        print(f"bf16 persistent tiled vs cuda-core reference, level {level}: {d:.3e}")
+        neq = y_pers != y_tile
+        assert not neq.any(), (int(neq.sum()), int(neq.any(axis=1).sum()), int(neq.any(axis=0).sum()),
+                               rel(y_pers, y_tile))
+        assert d < 2e-3, (level, d)
+        # the default split threshold: split-K depths unchanged, tiled ones persistent
+        stmg.st_mg_set_split_waves(S.h, level, w0)
+        y_mix = _solve(stmg, S, r, level)
+        assert rel(y_mix, y_ref) < 2e-3
+    finally:
+        stmg.st_mg_set_tc_mode(S.h, level, 0)
+        stmg.st_mg_set_split_waves(S.h, level, w0)
+
 def test_bf16_slab_solve_accuracy(setup):
     stmg, S, sl, mg, nu, sigma = setup
     rng = np.random.default_rng(0)
