@@ -76,7 +76,8 @@ def roofline_of(slab_prec: int, achieved: float, fp64_peak: float, slab_ms: floa
         peak = measured_peak("bf16_tflops")
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "supernodal slab solve, finest level, BF16 on the tensor cores "
-                "(k_tc_assemble, k_sn_tc2, k_sn_tc_reduce)", "achieved_counts": counts + " (4 real BF16 ones)",
+                "(k_tc_assemble, k_sn_tc3 on tiled depths, k_sn_tc2 + k_sn_tc_reduce on split-K ones)",
+                "achieved_counts": counts + " (4 real BF16 ones)",
                 "peak_source": "measured dense BF16 peak (MEASURED_PEAKS.json)", "ms_per_launch_group": slab_ms}
     if slab_prec in (1, 2):
         return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

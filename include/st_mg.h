@@ -413,14 +413,19 @@ int st_mg_time_integrate_carry(st_mg_t h, int32_t level, const double* z_dev, co
  * n_prev = 0 writes zeros. */
 int st_mg_time_carry(st_mg_t h, int32_t level, const double* ends_dev, int32_t n_prev, double* carry_dev);
 
-/* How a BF16 slab factor (slab_prec 3, DG(1)) is applied on time level `level`:
- * mode 0 (default) the tensor-core kernels (tcgen05); mode 1 the same factor on the CUDA
- * cores with the same operand rounding -- the gathered FP32 right-hand sides rounded to
- * BF16 where they enter each product, products and sums in FP32, every tree depth tiled
- * -- so that the two differ only in the FP32 summation order.  Mode 1 is the element-wise
- * reference the tensor-core kernels are tested against (eq. StandardSmoother's slab
- * inverse in either case); it is slower.  Drops the captured V-cycle graph.
- * ST_MG_ERR_INVALID_ARG if the level has no BF16 factor or mode is not 0 or 1. */
+/* How a 16-bit slab factor (slab_prec 3 BF16 or 4 FP16, DG(1)) is applied on time level
+ * `level` (eq. StandardSmoother's slab inverse in every mode):
+ *   0 (default) the tensor-core kernels (tcgen05); a tree depth with enough tiles runs as
+ *     one persistent CTA per SM that walks the depth's (row tile, column block) tasks;
+ *   1 the same factor on the CUDA cores with the same operand rounding -- the gathered
+ *     FP32 right-hand sides rounded to 16 bits where they enter each product, products
+ *     and sums in FP32, every tree depth tiled -- so that it differs from the tensor
+ *     cores only in the FP32 summation order: the element-wise reference the tensor-core
+ *     kernels are tested against (slower);
+ *   2 the tensor-core kernels with one CTA per tile on those depths (the same products,
+ *     results identical to mode 0 bit for bit).
+ * Drops the captured V-cycle graph.  ST_MG_ERR_INVALID_ARG if the level has no 16-bit
+ * factor or mode is not 0, 1 or 2. */
 int st_mg_set_tc_mode(st_mg_t h, int32_t level, int32_t mode);
 
 /* Process-wide: 1 queues the library's kernels with programmatic dependent launch, so

@@ -246,8 +246,8 @@ struct st_mg_s {
     std::shared_ptr<SlabFactor> fac;                        // device factor (own, or from the cache)
     int prec = 0;                                           // 0 FP64, 1 FP32, 2 double-float, 3 BF16
     int split_waves = 2;                                    // tiled / split-K threshold (autotuned)
-    int tc_mode = 0;                                        // 16-bit factor: 0 tensor cores, 1 CUDA-core reference,
-                                                            // 2 tensor cores with persistent tiled depths
+    int tc_mode = 0;                                        // 16-bit factor: 0 tensor cores (persistent tiled depths),
+                                                            // 1 CUDA-core reference, 2 tensor cores one CTA per tile
     double *f = nullptr, *x = nullptr, *r = nullptr;      // level vectors (levels >= 1)
     int64_t len = 0;
   };
@@ -476,6 +476,15 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
       for (int t = 0; t < mf; ++t) ft.push_back(make_int2((int)s, t));
       for (int t = 0; t < mb; ++t) bt.push_back(make_int2((int)s, t));
     }
+    // longest K range first (stable): blocks, and the tasks a persistent kernel deals out
+    // round robin, then start with the long tiles and the depth ends with short ones
+    auto kf = [&](const int2& t) { return std::min((t.y + 1) * bm, F.nodes[t.x].nc); };
+    auto kb = [&](const int2& t) {
+      const auto& a = F.nodes[t.x];
+      return a.nc + a.nr - (t.y * bm / 32) * 32;
+    };
+    std::stable_sort(ft.begin() + fo[d], ft.end(), [&](const int2& x, const int2& y) { return kf(x) > kf(y); });
+    std::stable_sort(bt.begin() + bo[d], bt.end(), [&](const int2& x, const int2& y) { return kb(x) > kb(y); });
   }
   fo[F.max_depth + 1] = (int64_t)ft.size();
   bo[F.max_depth + 1] = (int64_t)bt.size();
@@ -638,7 +647,7 @@ void level_solve(Handle& h, int l, int cnt) {
   auto& L = h.lv[l];
   SkSync sk = h.sk;
   sk.split_waves = L.split_waves;
-  sk.tc_persist = L.tc_mode == 2;
+  sk.tc_persist = L.tc_mode != 2;
   if (L.prec == 4) {
     if (L.tc_mode == 1)
       CK(sn_solve_cplx_f16_cc(L.fac->dch, static_cast<float2*>(h.sQ), static_cast<float2*>(h.sZ),

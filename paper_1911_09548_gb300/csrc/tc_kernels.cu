@@ -98,12 +98,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
+// complex K rows k (even) and k + 1 of column c: four adjacent 16-bit values, one 8-byte store
 template <bool F16>
-__device__ __forceinline__ void put_g(uint8_t* Bs, int c, int k, float2 g) {
-  if (F16)
-    *reinterpret_cast<__half2*>(Bs + core_off(c, 2 * k)) = __floats2half2_rn(g.x, g.y);
-  else
-    *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(c, 2 * k)) = __floats2bfloat162_rn(g.x, g.y);
+__device__ __forceinline__ void put_g2(uint8_t* Bs, int c, int k, float2 g0, float2 g1) {
+  uint2 w;
+  if (F16) {
+    const __half2 a = __floats2half2_rn(g0.x, g0.y), b = __floats2half2_rn(g1.x, g1.y);
+    w = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  } else {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(g0.x, g0.y), b = __floats2bfloat162_rn(g1.x, g1.y);
+    w = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  }
+  *reinterpret_cast<uint2*>(Bs + core_off(c, 2 * k)) = w;
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -206,21 +212,60 @@ __global__ void __launch_bounds__(256) k_tc_assemble(const DevNode* __restrict__
   const int32_t* gs = gsrc + nd.g_off * 2;
   const int32_t* rw = rows + nd.row_off;
   const int kend = FWD ? nc : m;
-  for (int t = threadIdx.x; t < TC_N * TC_KC; t += blockDim.x) {
-    const int kk = t / TC_N, cl = t % TC_N;
-    const int k = ks * TC_KC + kk, c = ct * TC_N + cl;
-    float2 g = make_float2(0.f, 0.f);
-    if (k < kend && c < nrhs) {
+  // thread: column cl, rows kk = 4 j + 2 kp + h (kp = thread / TC_N, h = 0, 1), eight rows
+  // per batch.  A batch first loads the rows' gather indices, then every value, then sums
+  // (in the order Q + U_s0 + U_s1), so a block waits for a few memory round trips
+  // instead of two per row
+  const int cl = threadIdx.x % TC_N, kp = threadIdx.x / TC_N;
+  const int c = ct * TC_N + cl;
+  const bool col_ok = c < nrhs;
+  constexpr int RB = 8;   // rows per batch
+  static_assert(TC_KC == 2 * 2 * RB, "two batches of eight rows per thread");
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    int s0[RB], s1[RB];
+    bool ok[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int kk = 4 * (b * (RB / 2) + r / 2) + 2 * kp + (r & 1);
+      const int k = ks * TC_KC + kk;
+      ok[r] = col_ok && k < kend;
+      s0[r] = s1[r] = -1;
       if (FWD) {
-        g = Q[(int64_t)(nd.col0 + k) * ld + c];
-        const int s0 = gs[2 * k], s1 = gs[2 * k + 1];
-        if (s0 >= 0) g = cadd(g, U[(int64_t)s0 * ld + c]);
-        if (s1 >= 0) g = cadd(g, U[(int64_t)s1 * ld + c]);
-      } else {
-        g = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)rw[k - nc] * ld + c];
+        if (ok[r]) {
+          s0[r] = gs[2 * k];
+          s1[r] = gs[2 * k + 1];
+        }
+      } else if (ok[r] && k >= nc) {
+        s0[r] = rw[k - nc];
       }
     }
-    put_g<F16>(tile, cl, kk, g);
+    float2 v[RB], u0[RB], u1[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int kk = 4 * (b * (RB / 2) + r / 2) + 2 * kp + (r & 1);
+      const int k = ks * TC_KC + kk;
+      v[r] = u0[r] = u1[r] = make_float2(0.f, 0.f);
+      if (FWD) {
+        if (ok[r]) v[r] = Q[(int64_t)(nd.col0 + k) * ld + c];
+        if (s0[r] >= 0) u0[r] = U[(int64_t)s0[r] * ld + c];
+        if (s1[r] >= 0) u1[r] = U[(int64_t)s1[r] * ld + c];
+      } else if (ok[r]) {
+        v[r] = (k < nc) ? Z[(int64_t)(nd.col0 + k) * ld + c] : X[(int64_t)s0[r] * ld + c];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; r += 2) {
+      const int kk = 4 * (b * (RB / 2) + r / 2) + 2 * kp;
+      float2 g0 = v[r], g1 = v[r + 1];
+      if (FWD) {
+        if (s0[r] >= 0) g0 = cadd(g0, u0[r]);
+        if (s1[r] >= 0) g0 = cadd(g0, u1[r]);
+        if (s0[r + 1] >= 0) g1 = cadd(g1, u0[r + 1]);
+        if (s1[r + 1] >= 0) g1 = cadd(g1, u1[r + 1]);
+      }
+      put_g2<F16>(tile, cl, kk, g0, g1);
+    }
   }
   __syncthreads();
   // the finished tile leaves in 16-byte pieces, consecutive threads consecutive pieces
@@ -398,9 +443,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
 // blockIdx.x + gridDim.x, ... with three roles: warp 0 (lane 0) streams the operand tiles
 // of all its tasks through a TC3_STAGES-deep ring of shared-memory stages, warp 1 (lane 0)
 // issues the MMAs of a task into one of two TMEM accumulators (columns 0..127 or
-// 128..255), and warps 2..5 read a finished accumulator straight from TMEM (warp w reads
-// TMEM lanes 32 (w % 4) ..), apply the epilogue and store, while the next task's MMAs run
-// into the other accumulator.  The ring never drains between tasks, so a CTA's short K
+// 128..255), and warps 2..9 read a finished accumulator straight from TMEM (warp w reads
+// TMEM lanes 32 (w % 4) .., two warps per lane quarter splitting the columns), apply the
+// epilogue and store, while the next task's MMAs run into the other accumulator.  The ring never drains between tasks, so a CTA's short K
 // loops no longer pay the pipeline fill each.  Products and epilogue are those of
 // k_sn_tc2 (same stage order, FP32 accumulation, same complex multiply), so the results
 // are the same bit for bit.
@@ -409,7 +454,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
 // others then stop at their own bounded waits, and the CTA waits (bounded) for its MMAs
 // and copies in flight before it frees TMEM.
 constexpr int TC3_STAGES = 4;
-constexpr int TC3_THREADS = 192;
+constexpr int TC3_THREADS = 320;   // producer warp, MMA warp, eight epilogue warps
 constexpr int TC3_SMEM = TC3_STAGES * 2 * kTcTileBytes + 1024;
 constexpr uint32_t TC3_TMEM_COLS = 2 * TC_N;
 
@@ -464,7 +509,7 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
     }
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acce[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&acce[i])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -544,10 +589,15 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
         smem_u32(&done)));
   } else if (warp >= 2) {
     // ---- epilogue: TMEM lane R = real accumulator row (complex row R / 2, real part on
-    // even lanes); after pairing the two lanes of a complex row, the even lane writes its
-    // columns cb .. cb + 15 and the odd lane cb + 16 .. cb + 31 (128 contiguous bytes each)
+    // even lanes).  Warp w reads TMEM lanes 32 (w % 4) .. and columns 64 hc .. 64 hc + 63
+    // (hc = (w - 2) / 4) in two 32-column chunks; after pairing the two lanes of a complex
+    // row, the even lane writes columns cb .. cb + 15 of a chunk and the odd lane
+    // cb + 16 .. cb + 31.  The values the epilogue adds (D^{-1}, the children's update
+    // rows) do not depend on the product, so they are loaded before the accumulator is
+    // waited for (first chunk) or while the previous chunk is stored (second chunk).
     bool fail = false;
     const uint32_t lq = (uint32_t)(warp & 3) * 32u;   // first TMEM lane of this warp
+    const int hc = (warp - 2) >> 2;
     const int R = (int)lq + lane;
     const int il = R >> 1;
     const bool odd = (R & 1) != 0;
@@ -557,19 +607,38 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
       tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
       const int abuf = j & 1;
       const uint32_t aph = (uint32_t)((j >> 1) & 1);
+      const DevNode nd = nodes[node];
+      const int nc = nd.nc, m = nc + nd.nr;
+      const int i = rtile * TC_ROWS + il;   // complex row of the node's block
+      // a task without K stages has no product (the per-tile kernel writes nothing either)
+      const bool row_ok = i < (FWD ? m : nc) && ks1 > ks0;
+      const bool upd = FWD && row_ok && i >= nc;
+      int s0 = -1, s1 = -1;
+      float2 dv = make_float2(0.f, 0.f);
+      if (FWD && row_ok && i < nc) dv = Dinv[nd.col0 + i];
+      if (upd) {
+        const int32_t* gs = gsrc + nd.g_off * 2;
+        s0 = gs[2 * i];
+        s1 = gs[2 * i + 1];
+      }
+      const int cbase = ct * TC_N + hc * 64 + (odd ? 16 : 0);   // first column of chunk 0
+      float2 ua[16], ub[16];
+      auto prefetch = [&](int cfirst) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int c = cfirst + q;
+          ua[q] = (s0 >= 0 && c < nrhs) ? U[(int64_t)s0 * ld + c] : make_float2(0.f, 0.f);
+          ub[q] = (s1 >= 0 && c < nrhs) ? U[(int64_t)s1 * ld + c] : make_float2(0.f, 0.f);
+        }
+      };
+      if (upd) prefetch(cbase);
       // warp-uniform outcome: the TMEM loads below are warp-collective
       if (!__all_sync(0xffffffffu, mbar_wait(&accf[abuf], aph))) { fail = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const DevNode nd = nodes[node];
-      const int nc = nd.nc, m = nc + nd.nr;
-      const int rows_out = FWD ? m : nc;
-      const int i = rtile * TC_ROWS + il;   // complex row of the node's block
-      const int c0 = ct * TC_N;
-      const int32_t* gs = gsrc + nd.g_off * 2;
-      // a task without K stages has no product (the per-tile kernel writes nothing either)
-      for (int cb = 0; cb < (ks1 > ks0 ? TC_N : 0); cb += 32) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
         uint32_t v[32];
-        tmem_ld32(tmem + (lq << 16) + (uint32_t)(abuf * TC_N + cb), v);
+        tmem_ld32(tmem + (lq << 16) + (uint32_t)(abuf * TC_N + hc * 64 + h * 32), v);
         float2 y[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -581,32 +650,30 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
           const float got = __shfl_xor_sync(0xffffffffu, give, 1);
           y[q] = odd ? make_float2(got, mine) : make_float2(mine, got);
         }
-        const int cfirst = c0 + cb + (odd ? 16 : 0);
-        if (i >= rows_out) continue;
-        if (FWD && i < nc) {
-          const float2 dv = Dinv[nd.col0 + i];
-          float2* zr = Z + (int64_t)(nd.col0 + i) * ld;
+        const int cfirst = cbase + h * 32;
+        if (row_ok) {
+          if (FWD && i < nc) {
+            float2* zr = Z + (int64_t)(nd.col0 + i) * ld;
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (cfirst + q < nrhs) zr[cfirst + q] = cmul(dv, y[q]);
-        } else if (FWD) {
-          const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
-          float2* ur = U + (int64_t)(nd.u_off + i - nc) * ld;
+            for (int q = 0; q < 16; ++q)
+              if (cfirst + q < nrhs) zr[cfirst + q] = cmul(dv, y[q]);
+          } else if (FWD) {
+            float2* ur = U + (int64_t)(nd.u_off + i - nc) * ld;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int c = cfirst + q;
-            if (c >= nrhs) continue;
-            float2 u = y[q];
-            if (s0 >= 0) u = cadd(u, U[(int64_t)s0 * ld + c]);
-            if (s1 >= 0) u = cadd(u, U[(int64_t)s1 * ld + c]);
-            ur[c] = u;
+            for (int q = 0; q < 16; ++q) {
+              float2 u = y[q];
+              if (s0 >= 0) u = cadd(u, ua[q]);
+              if (s1 >= 0) u = cadd(u, ub[q]);
+              if (cfirst + q < nrhs) ur[cfirst + q] = u;
+            }
+          } else {
+            float2* xr = X + (int64_t)(nd.col0 + i) * ld;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (cfirst + q < nrhs) xr[cfirst + q] = y[q];
           }
-        } else {
-          float2* xr = X + (int64_t)(nd.col0 + i) * ld;
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            if (cfirst + q < nrhs) xr[cfirst + q] = y[q];
         }
+        if (h == 0 && upd) prefetch(cbase + 32);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();

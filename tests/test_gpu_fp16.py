@@ -75,9 +75,9 @@ def test_fp16_tensor_cores_match_cuda_core_reference(setup, level):
 
 @pytest.mark.parametrize("level", [0, 2])
 def test_fp16_persistent_tiled_depths_match_per_tile_kernel(setup, level):
-    """Tensor-core mode 2: every tiled depth runs as one persistent CTA per SM that walks
-    the depth's (row tile, column block) tasks with a bulk-copy ring that never drains
-    and two TMEM accumulators.  The MMAs of a task are issued in the same order on the
+    """Tensor-core mode 0 (default): every tiled depth runs as one persistent CTA per SM
+    that walks the depth's (row tile, column block) tasks with a bulk-copy ring that
+    never drains and two TMEM accumulators; mode 2 runs one CTA per tile.  The MMAs of a task are issued in the same order on the
     same operand tiles as in the one-CTA-per-tile kernel, and the epilogue does the same
     arithmetic, so with every depth forced tiled the two solves agree bit for bit; both
     stay within the operand-rounding bound of the CUDA-core reference."""
@@ -91,9 +91,9 @@ def test_fp16_persistent_tiled_depths_match_per_tile_kernel(setup, level):
         stmg.st_mg_set_tc_mode(S.h, level, 1)
         y_ref = _solve(stmg, S, r, level)
         stmg.st_mg_set_split_waves(S.h, level, 0)
-        stmg.st_mg_set_tc_mode(S.h, level, 0)
-        y_tile = _solve(stmg, S, r, level)
         stmg.st_mg_set_tc_mode(S.h, level, 2)
+        y_tile = _solve(stmg, S, r, level)
+        stmg.st_mg_set_tc_mode(S.h, level, 0)
         y_pers = _solve(stmg, S, r, level)
         d = rel(y_pers, y_ref)
         print(f"fp16 persistent tiled vs cuda-core reference, level {level}: {d:.3e}")
