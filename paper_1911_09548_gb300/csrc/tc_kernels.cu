@@ -455,33 +455,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
 // and copies in flight before it frees TMEM.
 constexpr int TC3_STAGES = 4;
 constexpr int TC3_THREADS = 320;   // producer warp, MMA warp, eight epilogue warps
-constexpr int TC3_SMEM = TC3_STAGES * 2 * kTcTileBytes + 1024;
 constexpr uint32_t TC3_TMEM_COLS = 2 * TC_N;
 
-// task t of a depth: tile t / gy (node, row tile), column block t % gy, and its K stages
-// (forward: up to the tile's last row inside L11^{-1}; backward: from the tile's first row)
-template <bool FWD>
-__device__ __forceinline__ void tc3_task(int t, int gy, const int2* __restrict__ tiles,
-                                         const DevNode* __restrict__ nodes, const int4* __restrict__ tnode,
-                                         const int2* __restrict__ tpre, int& node, int& rtile, int& ct, int& ks0,
-                                         int& ks1, int& nks, int& pre) {
-  const int2 tl = tiles[t / gy];
-  ct = t % gy;
-  node = tl.x;
-  rtile = tl.y;
-  const int nc = nodes[node].nc;
-  const int4 tn = tnode[node];
-  nks = FWD ? tn.y : tn.w;
-  pre = FWD ? tpre[node].x : tpre[node].y;
-  const int row0 = rtile * TC_ROWS;
-  if (FWD) {
-    ks0 = 0;
-    ks1 = ((row0 + TC_ROWS <= nc ? row0 + TC_ROWS : nc) + TC_KC - 1) / TC_KC;
-  } else {
-    ks0 = row0 / TC_KC;
-    ks1 = nks;
-  }
-}
+// A task's descriptor, computed once per kernel for each of the CTA's tasks (all threads
+// together, before the roles start) and kept in shared memory, so that no role waits on
+// a chain of dependent index loads between tasks.  Task t of a depth: tile t / gy (node,
+// row tile), column block t % gy; K stages ks0 .. ks1 - 1 (forward: up to the tile's last
+// row inside L11^{-1}; backward: from the tile's first row).
+struct Tc3Task {
+  int32_t ks0, ks1;   // K stages
+  int32_t a0, b0;     // operand tile index of stage 0: factor (TW), right-hand side (Bst)
+  int32_t col0, nc, m, row0, c0, pad;
+  int64_t u_off, g_off;
+};
+constexpr int TC3_MAX_TASKS = 160;   // tasks per CTA (the host takes the per-tile kernel beyond)
+constexpr int TC3_EPI_ROWS = 16;     // complex rows of an epilogue warp
+constexpr int TC3_EPI_LD = 66;       // floats per staged row: 32 complex columns + 2 (conflict-free)
+constexpr int TC3_SMEM = TC3_STAGES * 2 * kTcTileBytes + 1024 + TC3_MAX_TASKS * (int)sizeof(Tc3Task) +
+                         8 * TC3_EPI_ROWS * TC3_EPI_LD * 4;
 
 template <bool FWD, bool F16>
 __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __restrict__ nodes,
@@ -501,7 +492,39 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  Tc3Task* task = reinterpret_cast<Tc3Task*>(base + TC3_STAGES * 2 * kTcTileBytes);
   const int ntasks = ntiles * gy;
+  // this CTA's tasks: t = blockIdx.x + k gridDim.x, k < nmine (<= TC3_MAX_TASKS, host-checked)
+  const int nmine = blockIdx.x < ntasks ? (ntasks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  for (int k = tid; k < nmine && k < TC3_MAX_TASKS; k += blockDim.x) {
+    const int t = blockIdx.x + k * gridDim.x;
+    const int2 tl = tiles[t / gy];
+    const int ct = t % gy, node = tl.x, rtile = tl.y;
+    const DevNode nd = nodes[node];
+    const int4 tn = tnode[node];
+    const int nks = FWD ? tn.y : tn.w;
+    const int pre = FWD ? tpre[node].x : tpre[node].y;
+    const int row0 = rtile * TC_ROWS;
+    Tc3Task d;
+    if (FWD) {
+      d.ks0 = 0;
+      d.ks1 = ((row0 + TC_ROWS <= nd.nc ? row0 + TC_ROWS : nd.nc) + TC_KC - 1) / TC_KC;
+    } else {
+      d.ks0 = row0 / TC_KC;
+      d.ks1 = nks;
+    }
+    d.a0 = (FWD ? tn.x : tn.z) + rtile * nks;
+    d.b0 = gy * pre + ct * nks;
+    d.col0 = nd.col0;
+    d.nc = nd.nc;
+    d.m = nd.nc + nd.nr;
+    d.row0 = row0;
+    d.c0 = ct * TC_N;
+    d.pad = 0;
+    d.u_off = nd.u_off;
+    d.g_off = nd.g_off;
+    task[k] = d;
+  }
   if (tid == 0) {
     for (int i = 0; i < TC3_STAGES; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
@@ -524,18 +547,17 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
+  const int ntask = nmine < TC3_MAX_TASKS ? nmine : TC3_MAX_TASKS;
   int issued = 0;   // producer: stages whose copies it started
   bool pfail = false;
   if (warp == 0 && lane == 0) {
     // ---- producer
     int g = 0;
-    for (int t = blockIdx.x; t < ntasks && !pfail; t += gridDim.x) {
-      int node, rtile, ct, ks0, ks1, nks, pre;
-      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
-      const int4 tn = tnode[node];
-      const uint8_t* atiles = TW + ((int64_t)(FWD ? tn.x : tn.z) + (int64_t)rtile * nks) * kTcTileBytes;
-      const uint8_t* btiles = Bst + ((int64_t)gy * pre + (int64_t)ct * nks) * kTcTileBytes;
-      for (int ks = ks0; ks < ks1; ++ks, ++g) {
+    for (int k = 0; k < ntask && !pfail; ++k) {
+      const Tc3Task& d = task[k];
+      const uint8_t* atiles = TW + (int64_t)d.a0 * kTcTileBytes;
+      const uint8_t* btiles = Bst + (int64_t)d.b0 * kTcTileBytes;
+      for (int ks = d.ks0; ks < d.ks1; ++ks, ++g) {
         const int slot = g % TC3_STAGES;
         const uint32_t ph = (uint32_t)((g / TC3_STAGES) & 1);
         if (!mbar_wait(&empty[slot], ph ^ 1u)) { pfail = true; break; }
@@ -550,16 +572,15 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     bool fail = false;
-    int g = 0, j = 0;
-    for (int t = blockIdx.x; t < ntasks && !fail; t += gridDim.x, ++j) {
-      int node, rtile, ct, ks0, ks1, nks, pre;
-      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
-      const int abuf = j & 1;
-      const uint32_t aph = (uint32_t)((j >> 1) & 1);
+    int g = 0;
+    for (int k = 0; k < ntask && !fail; ++k) {
+      const Tc3Task& d = task[k];
+      const int abuf = k & 1;
+      const uint32_t aph = (uint32_t)((k >> 1) & 1);
       if (!mbar_wait(&acce[abuf], aph ^ 1u)) { fail = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t acc_addr = tmem + (uint32_t)(abuf * TC_N);
-      for (int i = 0; i < ks1 - ks0; ++i, ++g) {
+      for (int i = 0; i < d.ks1 - d.ks0; ++i, ++g) {
         const int slot = g % TC3_STAGES;
         const uint32_t ph = (uint32_t)((g / TC3_STAGES) & 1);
         if (!mbar_wait(&full[slot], ph)) { fail = true; break; }
@@ -588,50 +609,51 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_u32(&done)));
   } else if (warp >= 2) {
-    // ---- epilogue: TMEM lane R = real accumulator row (complex row R / 2, real part on
-    // even lanes).  Warp w reads TMEM lanes 32 (w % 4) .. and columns 64 hc .. 64 hc + 63
-    // (hc = (w - 2) / 4) in two 32-column chunks; after pairing the two lanes of a complex
-    // row, the even lane writes columns cb .. cb + 15 of a chunk and the odd lane
-    // cb + 16 .. cb + 31.  The values the epilogue adds (D^{-1}, the children's update
-    // rows) do not depend on the product, so they are loaded before the accumulator is
-    // waited for (first chunk) or while the previous chunk is stored (second chunk).
+    // ---- epilogue.  Warp w owns TMEM lanes 32 (w % 4) .. (real accumulator rows; complex
+    // row R / 2, real part on even lanes) and columns 64 hc .. 64 hc + 63 (hc = (w - 2) / 4),
+    // read as two 32-column chunks.  A chunk goes through the warp's shared-memory stage
+    // (16 complex rows x 32 columns) so that afterwards lane = column: every global load
+    // and store of the epilogue is one row's 32 consecutive complex values per
+    // instruction.  D^{-1} and the children's update rows do not depend on the product;
+    // they are loaded before the accumulator is waited for (first chunk) or while the
+    // previous chunk is stored (second chunk).
     bool fail = false;
     const uint32_t lq = (uint32_t)(warp & 3) * 32u;   // first TMEM lane of this warp
     const int hc = (warp - 2) >> 2;
-    const int R = (int)lq + lane;
-    const int il = R >> 1;
-    const bool odd = (R & 1) != 0;
-    int j = 0;
-    for (int t = blockIdx.x; t < ntasks && !fail; t += gridDim.x, ++j) {
-      int node, rtile, ct, ks0, ks1, nks, pre;
-      tc3_task<FWD>(t, gy, tiles, nodes, tnode, tpre, node, rtile, ct, ks0, ks1, nks, pre);
-      const int abuf = j & 1;
-      const uint32_t aph = (uint32_t)((j >> 1) & 1);
-      const DevNode nd = nodes[node];
-      const int nc = nd.nc, m = nc + nd.nr;
-      const int i = rtile * TC_ROWS + il;   // complex row of the node's block
+    float* stg = reinterpret_cast<float*>(base + TC3_STAGES * 2 * kTcTileBytes + TC3_MAX_TASKS * sizeof(Tc3Task)) +
+                 (warp - 2) * (TC3_EPI_ROWS * TC3_EPI_LD);
+    for (int k = 0; k < ntask && !fail; ++k) {
+      const Tc3Task& d = task[k];
+      const int abuf = k & 1;
+      const uint32_t aph = (uint32_t)((k >> 1) & 1);
+      const int nc = d.nc;
+      const int rows_out = FWD ? d.m : nc;
+      const int i0 = d.row0 + (int)(lq >> 1);   // first complex row of this warp
       // a task without K stages has no product (the per-tile kernel writes nothing either)
-      const bool row_ok = i < (FWD ? m : nc) && ks1 > ks0;
-      const bool upd = FWD && row_ok && i >= nc;
-      int s0 = -1, s1 = -1;
-      float2 dv = make_float2(0.f, 0.f);
-      if (FWD && row_ok && i < nc) dv = Dinv[nd.col0 + i];
-      if (upd) {
-        const int32_t* gs = gsrc + nd.g_off * 2;
-        s0 = gs[2 * i];
-        s1 = gs[2 * i + 1];
-      }
-      const int cbase = ct * TC_N + hc * 64 + (odd ? 16 : 0);   // first column of chunk 0
-      float2 ua[16], ub[16];
-      auto prefetch = [&](int cfirst) {
+      const bool any = d.ks1 > d.ks0;
+      const int cw = d.c0 + hc * 64 + lane;     // this lane's column in chunk 0
+      float2 dv[TC3_EPI_ROWS], ua[TC3_EPI_ROWS], ub[TC3_EPI_ROWS];
+      const int32_t* gs = gsrc + d.g_off * 2;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int c = cfirst + q;
-          ua[q] = (s0 >= 0 && c < nrhs) ? U[(int64_t)s0 * ld + c] : make_float2(0.f, 0.f);
-          ub[q] = (s1 >= 0 && c < nrhs) ? U[(int64_t)s1 * ld + c] : make_float2(0.f, 0.f);
+      for (int r = 0; r < TC3_EPI_ROWS; ++r) {
+        const int i = i0 + r;
+        dv[r] = (FWD && any && i < nc) ? Dinv[d.col0 + i] : make_float2(0.f, 0.f);
+      }
+      // children's update rows (zero where a row has no such child: adding +0 changes no
+      // value but the sign of a zero)
+      auto prefetch = [&](int c) {
+#pragma unroll
+        for (int r = 0; r < TC3_EPI_ROWS; ++r) {
+          const int i = i0 + r;
+          ua[r] = ub[r] = make_float2(0.f, 0.f);
+          if (FWD && any && i >= nc && i < rows_out && c < nrhs) {
+            const int s0 = gs[2 * i], s1 = gs[2 * i + 1];
+            if (s0 >= 0) ua[r] = U[(int64_t)s0 * ld + c];
+            if (s1 >= 0) ub[r] = U[(int64_t)s1 * ld + c];
+          }
         }
       };
-      if (upd) prefetch(cbase);
+      if (FWD) prefetch(cw);
       // warp-uniform outcome: the TMEM loads below are warp-collective
       if (!__all_sync(0xffffffffu, mbar_wait(&accf[abuf], aph))) { fail = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -639,41 +661,26 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
       for (int h = 0; h < 2; ++h) {
         uint32_t v[32];
         tmem_ld32(tmem + (lq << 16) + (uint32_t)(abuf * TC_N + hc * 64 + h * 32), v);
-        float2 y[16];
+        // lane = real row: complex row lane / 2, real part on even lanes
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          // even lane keeps Re of column q, receives its Im; odd lane keeps Im of
-          // column 16 + q, receives its Re
-          const float lo = __uint_as_float(v[q]), hi = __uint_as_float(v[16 + q]);
-          const float mine = odd ? hi : lo;
-          const float give = odd ? lo : hi;
-          const float got = __shfl_xor_sync(0xffffffffu, give, 1);
-          y[q] = odd ? make_float2(got, mine) : make_float2(mine, got);
-        }
-        const int cfirst = cbase + h * 32;
-        if (row_ok) {
+        for (int j = 0; j < 32; ++j) stg[(lane >> 1) * TC3_EPI_LD + 2 * j + (lane & 1)] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int c = cw + h * 32;
+#pragma unroll
+        for (int r = 0; r < TC3_EPI_ROWS; ++r) {
+          const int i = i0 + r;
+          if (!any || i >= rows_out || c >= nrhs) continue;
+          const float2 y = *reinterpret_cast<const float2*>(stg + r * TC3_EPI_LD + 2 * lane);
           if (FWD && i < nc) {
-            float2* zr = Z + (int64_t)(nd.col0 + i) * ld;
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (cfirst + q < nrhs) zr[cfirst + q] = cmul(dv, y[q]);
+            Z[(int64_t)(d.col0 + i) * ld + c] = cmul(dv[r], y);
           } else if (FWD) {
-            float2* ur = U + (int64_t)(nd.u_off + i - nc) * ld;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              float2 u = y[q];
-              if (s0 >= 0) u = cadd(u, ua[q]);
-              if (s1 >= 0) u = cadd(u, ub[q]);
-              if (cfirst + q < nrhs) ur[cfirst + q] = u;
-            }
+            U[(int64_t)(d.u_off + i - nc) * ld + c] = cadd(cadd(y, ua[r]), ub[r]);
           } else {
-            float2* xr = X + (int64_t)(nd.col0 + i) * ld;
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (cfirst + q < nrhs) xr[cfirst + q] = y[q];
+            X[(int64_t)(d.col0 + i) * ld + c] = y;
           }
         }
-        if (h == 0 && upd) prefetch(cbase + 32);
+        __syncwarp();
+        if (FWD && h == 0) prefetch(cw + 32);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -724,12 +731,13 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool s
                                                                          F.tas_b + aa, Q, Z, U, Q, Bst, nrhs, ld);
   count_launches(1);
   const uint8_t* TW = fwd ? F.tw_f : F.tw_b;
-  if (!split && sy.tc_persist) {
-    const int64_t* to = fwd ? F.h_fwd_off : F.h_bwd_off;
-    const int64_t a = to[d], b = to[d + 1];
+  const int64_t* tof = fwd ? F.h_fwd_off : F.h_bwd_off;
+  const int64_t ntasks = (tof[d + 1] - tof[d]) * (int64_t)gy;
+  const int64_t grid3 = ntasks < F.n_sm ? ntasks : F.n_sm;
+  if (!split && sy.tc_persist && grid3 > 0 && (ntasks + grid3 - 1) / grid3 <= TC3_MAX_TASKS) {
+    const int64_t a = tof[d], b = tof[d + 1];
     const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;
-    const int64_t ntasks = (b - a) * (int64_t)gy;
-    const unsigned grid = (unsigned)(ntasks < F.n_sm ? ntasks : F.n_sm);
+    const unsigned grid = (unsigned)grid3;
     if (fwd)
       launch_k(k_sn_tc3<true, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv,
                F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
