@@ -103,11 +103,20 @@ __global__ void __launch_bounds__(RES_WARPS * 32) k_residual_dg1(int nrows, cons
         if (valid && n < N_t) {
           const double2 fv = f2[n];
           double2 rv;
-          rv.x = fv.x - (double)(As + B0[j]) + (double)c;
-          rv.y = fv.y - (double)((A1[j] - A0[j]) + B1[j]) - (double)c;
+          if (std::is_same<T, double>::value) {
+            rv.x = fv.x - (double)(As + B0[j]) + (double)c;
+            rv.y = fv.y - (double)((A1[j] - A0[j]) + B1[j]) - (double)c;
+          } else {
+            // FP32: the operator applied in FP32 and one FP64 subtraction from f per value
+            // (the FP64 pipe is the scarce one)
+            rv.x = fv.x - (double)((As + B0[j]) - c);
+            rv.y = fv.y - (double)(((A1[j] - A0[j]) + B1[j]) + c);
+          }
           r2[n] = rv;
-          sq = fma(rv.x, rv.x, sq);
-          sq = fma(rv.y, rv.y, sq);
+          if (partial) {
+            sq = fma(rv.x, rv.x, sq);
+            sq = fma(rv.y, rv.y, sq);
+          }
         }
       }
       carry = __shfl_sync(FULL, prevA, LPR - 1, LPR);
@@ -453,10 +462,14 @@ __global__ void k_slab_pre_dg1f(int nrows, const double* __restrict__ r, int src
   if (e >= nrows) return;
   const double2* src = reinterpret_cast<const double2*>(r + (int64_t)e * src_ld);
   float2* dst = Q + (int64_t)iperm[e] * ld;
+  // the transform in FP32 (its result is rounded to FP32 anyway): two conversions per
+  // value on the FP64 pipe instead of four FP64 multiply-adds and two conversions
+  const float a0 = (float)c0.x, a1 = (float)c1.x, b0 = (float)c0.y, b1 = (float)c1.y;
 #pragma unroll 4
   for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const double2 v = src[slab0 + k];
-    dst[k] = make_float2((float)(c0.x * v.x + c1.x * v.y), (float)(c0.y * v.x + c1.y * v.y));
+    const float vx = (float)v.x, vy = (float)v.y;
+    dst[k] = make_float2(fmaf(a0, vx, a1 * vy), fmaf(b0, vx, b1 * vy));
   }
 }
 
@@ -483,18 +496,21 @@ __global__ void k_slab_post_dg1f(int nrows, const float2* __restrict__ X, int ld
   if (e >= nrows) return;
   const float2* src = X + (int64_t)iperm[e] * ld;
   double2* dst = reinterpret_cast<double2*>(x + (int64_t)e * dst_ld) + slab0;
+  // the back transform and the damping in FP32 (the solution is an FP32 value), then one
+  // FP64 addition per value
+  const float w = (float)(mode == 0 ? 1.0 : omega);
+  const float t0 = 2.0f * w, t1 = (float)(2.0 * s1.x) * w, t2 = (float)(2.0 * s1.y) * w;
 #pragma unroll 4
   for (int k = threadIdx.x & 31; k < cnt; k += 32) {
     const float2 vf = src[k];
-    const double vx = vf.x, vy = vf.y;
-    const double u0 = 2.0 * vx;
-    const double u1 = 2.0 * (s1.x * vx - s1.y * vy);
+    const float u0 = t0 * vf.x;
+    const float u1 = fmaf(t1, vf.x, -(t2 * vf.y));
     if (mode == 0) {
-      dst[k] = make_double2(u0, u1);
+      dst[k] = make_double2((double)u0, (double)u1);
     } else {
       double2 o = dst[k];
-      o.x = fma(omega, u0, o.x);
-      o.y = fma(omega, u1, o.y);
+      o.x += (double)u0;
+      o.y += (double)u1;
       dst[k] = o;
     }
   }
