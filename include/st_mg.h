@@ -168,10 +168,12 @@ typedef struct {
                                 most 15 letters: the pre-smoother applies it right to left, the
                                 post-smoother the same factors left to right.  Empty (default):
                                 S^nu_pre A S^nu_pre and S^nu_post A S^nu_post (A only if use_A) */
-    int32_t persistent_split;/* 1: slab and K_n solves with few right-hand sides (coarse time levels)
-                                run as two cooperative launches that walk every tree depth with grid
-                                barriers in between, instead of two launches per depth; 0 (default):
-                                per-depth launches (faster on GB300 at 16^3, see the design notes) */
+    int32_t persistent_split;/* How slab and K_n solves with few right-hand sides (coarse time levels)
+                                walk the tree depths: 0 two launches (product, reduction) per depth
+                                and sweep; 1 one cooperative launch per sweep with grid barriers
+                                between depths; 2 one launch per sweep in which every task waits only
+                                for the tasks it reads from (children forward, parent backward).
+                                Results are identical in all three. */
     int32_t factor_cache;    /* 1: take slab and K_n factors from, and leave new ones in, the
                                 process-wide factor cache (key: device, mesh, space level, materials,
                                 DG degree, tau, precision), so handles that share a mesh and a tau

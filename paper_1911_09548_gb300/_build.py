@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libstmg.so")
 
-CU_SOURCES = ["sn_kernels.cu", "st_kernels.cu", "tc_kernels.cu", "noalloc.cu"]
+CU_SOURCES = ["sn_kernels.cu", "sn_mixed.cu", "sn_dfc.cu", "sn_tc.cu", "st_kernels.cu", "tc_kernels.cu", "noalloc.cu"]
 CPP_SOURCES = ["runtime.cpp", "mesh.cpp", "factor.cpp", "serve.cpp"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -40,7 +40,7 @@ def _sources():
 
 
 def _headers():
-    return [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")] + [
+    return [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + [
         os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
 
 

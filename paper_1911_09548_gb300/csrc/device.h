@@ -57,6 +57,19 @@ struct DevFactor {
   int64_t* h_bs_item_off = nullptr;
   int64_t* h_bs_unit_off = nullptr;
   int64_t max_items = 0;              // largest item count of one depth (partial buffer rows / kSkRows)
+  // dataflow split-K solve: tasks (0, item) / (1, unit) in topological order per sweep,
+  // the unit of every item, units per node, and per node the nodes it waits for
+  // (forward: children; backward: (parent, -1))
+  int2* df_tasks_f = nullptr;
+  int2* df_tasks_b = nullptr;
+  int32_t* df_item_unit_f = nullptr;
+  int32_t* df_item_unit_b = nullptr;
+  int32_t* df_node_units_f = nullptr;
+  int32_t* df_node_units_b = nullptr;
+  int2* df_children = nullptr;
+  int2* df_parent = nullptr;
+  int64_t n_df_tasks_f = 0, n_df_tasks_b = 0;
+  int64_t n_fs_items = 0, n_bs_items = 0, n_fs_units = 0, n_bs_units = 0;   // totals over all depths
   int32_t n_sm = 152;                 // multiprocessors of the device (wave size of the tiled path)
   // tensor-core split-K: per depth, items (node, row tile, k0, k1) of kTcSplitK complex
   // columns and units (node, row tile, item_begin, item_end)
@@ -114,6 +127,7 @@ struct SkSync {
   int* err = nullptr;
   int split_waves = 2;   // a tree depth runs split-K when its tiles fill fewer than this many
                          // waves of the SMs (setup may tune it per level)
+  unsigned* df = nullptr;    // dataflow split-K solve: counter words (null: per-depth launches)
   bool tc_persist = false;   // tiled tensor-core depths: one persistent CTA per SM walking the
                             // depth's tiles (true) or one CTA per tile (false)
 };

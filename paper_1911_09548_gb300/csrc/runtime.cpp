@@ -49,6 +49,8 @@ struct NumericError {
 // Host-side tile and item lists of one factor (kept alive: the device view points at them).
 struct FactorLists {
   std::vector<int64_t> fo, bo, fsi, fsu, bsi, bsu, tfi, tfu, tbi, tbu, asf, asb;
+  int64_t df_items = 0;   // split-K items of the larger sweep (partial blocks of a dataflow solve)
+  int64_t df_words = 0;   // counter words of a dataflow sweep: 1 + units + nodes
 };
 
 #define CK(call)                                                    \
@@ -538,6 +540,49 @@ void make_dev_factor(DevArena& h, const SupernodalFactor<T>& F, DevFactor<DT, WT
   D.d_bs_unit_off = h.upload(Lh.bsu);
   D.max_items = max_items;
   D.n_sm = h.n_sm;
+  // dataflow split-K solve: one task list per sweep in topological order (forward:
+  // deepest depth first; backward: root first; each depth's items before its units)
+  {
+    const size_t nn = F.nodes.size();
+    std::vector<int2> tf, tb, ch(nn), par(nn);
+    std::vector<int32_t> iuf(fsi.size(), 0), iub(bsi.size(), 0), nuf(nn, 0), nub(nn, 0);
+    for (size_t u = 0; u < fsu.size(); ++u) {
+      for (int q = fsu[u].z; q < fsu[u].w; ++q) iuf[q] = (int32_t)u;
+      ++nuf[fsu[u].x];
+    }
+    for (size_t u = 0; u < bsu.size(); ++u) {
+      for (int q = bsu[u].z; q < bsu[u].w; ++q) iub[q] = (int32_t)u;
+      ++nub[bsu[u].x];
+    }
+    for (int d = F.max_depth; d >= 0; --d) {
+      for (int64_t q = Lh.fsi[d]; q < Lh.fsi[d + 1]; ++q) tf.push_back(make_int2(0, (int)q));
+      for (int64_t u = Lh.fsu[d]; u < Lh.fsu[d + 1]; ++u) tf.push_back(make_int2(1, (int)u));
+    }
+    for (int d = 0; d <= F.max_depth; ++d) {
+      for (int64_t q = Lh.bsi[d]; q < Lh.bsi[d + 1]; ++q) tb.push_back(make_int2(0, (int)q));
+      for (int64_t u = Lh.bsu[d]; u < Lh.bsu[d + 1]; ++u) tb.push_back(make_int2(1, (int)u));
+    }
+    for (size_t t = 0; t < nn; ++t) {
+      ch[t] = make_int2(F.nodes[t].child[0], F.nodes[t].child[1]);
+      par[t] = make_int2(F.nodes[t].parent, -1);
+    }
+    D.df_tasks_f = h.upload(tf);
+    D.df_tasks_b = h.upload(tb);
+    D.df_item_unit_f = h.upload(iuf);
+    D.df_item_unit_b = h.upload(iub);
+    D.df_node_units_f = h.upload(nuf);
+    D.df_node_units_b = h.upload(nub);
+    D.df_children = h.upload(ch);
+    D.df_parent = h.upload(par);
+    D.n_df_tasks_f = (int64_t)tf.size();
+    D.n_df_tasks_b = (int64_t)tb.size();
+    D.n_fs_items = (int64_t)fsi.size();
+    D.n_bs_items = (int64_t)bsi.size();
+    D.n_fs_units = (int64_t)fsu.size();
+    D.n_bs_units = (int64_t)bsu.size();
+    Lh.df_items = std::max<int64_t>(D.n_fs_items, D.n_bs_items);
+    Lh.df_words = 1 + std::max<int64_t>(D.n_fs_units, D.n_bs_units) + (int64_t)nn;
+  }
   // tensor-core split-K items: the tiles above, each cut into tc_k-wide K chunks (a multiple
   // of the 32-column stage)
   std::vector<int4> tfi, tfu, tbi, tbu;
@@ -1079,7 +1124,7 @@ int do_setup(const st_mg_problem* pr, const st_mg_options* op, void* stream, st_
   if (!(op->omega > 0) || op->nu_pre < 0 || op->nu_post < 0 || op->min_coarse_slabs < 1 || op->max_levels < 0 ||
       op->coarsen < 0 || op->coarsen > 2 || (op->nodal_solve != 0 && op->nodal_solve != 1) ||
       op->nodal_jacobi_sweeps < 0 || op->slab_prec < 0 || op->slab_prec > 4 || (op->slab_prec >= 3 && pr->degree != 1) ||
-      (op->persistent_split != 0 && op->persistent_split != 1) || !valid_pattern(op->smoother) ||
+      op->persistent_split < 0 || op->persistent_split > 2 || !valid_pattern(op->smoother) ||
       (op->autotune != 0 && op->autotune != 1) || op->nd_leaf < 0 || op->nd_leaf > 4096 ||
       op->split_k < 0 || op->split_k > 1024 || (op->split_k % 16) != 0 || op->tc_split_k < 0 ||
       op->tc_split_k > 4096 || (op->tc_split_k % 32) != 0 ||
@@ -1575,17 +1620,31 @@ int setup_device(Handle& H) {
   H.sQ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
   H.sZ = H.dalloc<char>((int64_t)(max_ne * H.ld_slab * esz));
   H.sU = H.dalloc<char>((int64_t)(std::max<int64_t>(max_u, 1) * H.ld_slab * esz));
+  int64_t df_items = 0, df_kn_items = 0, df_words = 1;   // dataflow split-K solves
+  if (op->persistent_split == 2) {
+    for (auto& L : H.lv) {
+      df_items = std::max(df_items, L.fac->lists.df_items);
+      df_words = std::max(df_words, L.fac->lists.df_words);
+    }
+    for (auto& S : H.space) {
+      df_kn_items = std::max(df_kn_items, S.nf->kn_lists.df_items);
+      df_words = std::max(df_words, S.nf->kn_lists.df_words);
+    }
+  }
   {
     const int nbk = pr->degree == 0 ? kSkMaxRhsR : kSkMaxRhsC;
     const int64_t cols = (int64_t)((H.ld_slab + nbk - 1) / nbk) * nbk;
-    H.sP = H.dalloc<char>((int64_t)(std::max<int64_t>(max_items, 1) * kSkRows * cols * esz));
+    H.sP = H.dalloc<char>((int64_t)(std::max<int64_t>(std::max<int64_t>(max_items, 1) * cols, df_items * nbk) *
+                                    kSkRows * esz));
   }
   H.ld_nod = max_nt * H.q;
   H.nQ = H.dalloc<double>(max_nn * H.ld_nod);
   H.nZ = H.dalloc<double>(max_nn * H.ld_nod);
   H.nU = H.dalloc<double>(std::max<int64_t>(max_un, 1) * H.ld_nod);
-  H.nP = H.dalloc<double>(std::max<int64_t>(max_kn_items, 1) * kSkRows *
-                          ((int64_t)((H.ld_nod + kSkMaxRhsR - 1) / kSkMaxRhsR) * kSkMaxRhsR));
+  H.nP = H.dalloc<double>(std::max<int64_t>(std::max<int64_t>(max_kn_items, 1) *
+                                               ((int64_t)((H.ld_nod + kSkMaxRhsR - 1) / kSkMaxRhsR) * kSkMaxRhsR),
+                                           df_kn_items * kSkMaxRhsR) *
+                          kSkRows);
   H.ny = H.dalloc<double>(max_nn * H.ld_nod);
   H.nz = H.dalloc<double>(max_nn * H.ld_nod);
   H.nw = H.dalloc<double>(max_nn * H.ld_nod);
@@ -1601,7 +1660,8 @@ int setup_device(Handle& H) {
   H.flags = H.dalloc<int>(4);
   CK(cudaMemset(H.flags, 0, 4 * sizeof(int)));
   H.tc_err = H.flags;
-  H.sk.bar = op->persistent_split ? reinterpret_cast<unsigned*>(H.flags + 2) : nullptr;
+  H.sk.bar = op->persistent_split == 1 ? reinterpret_cast<unsigned*>(H.flags + 2) : nullptr;
+  if (op->persistent_split == 2) H.sk.df = H.dalloc<unsigned>(df_words);
   H.sk.err = H.flags;
   if (op->slab_prec >= 3) {
     H.colmax = H.dalloc<unsigned>(H.ld_slab);

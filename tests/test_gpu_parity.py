@@ -35,6 +35,9 @@ CASES = {
     # coarse-level solves as persistent cooperative launches (grid barriers between depths)
     "dg1_ragged_persistent": (8, 1, 1, 20, "two_material", dict(nu_pre=2, nu_post=2, persistent_split=1)),
     "dg0_long_df_persistent": (8, 1, 0, 300, "two_material", dict(slab_prec=2, persistent_split=1)),
+    # coarse-level solves as dataflow launches (every task waits only for what it reads)
+    "dg1_ragged_dataflow": (8, 1, 1, 20, "two_material", dict(nu_pre=2, nu_post=2, persistent_split=2)),
+    "dg0_long_df_dataflow": (8, 1, 0, 300, "two_material", dict(slab_prec=2, persistent_split=2)),
     # other hybrid-smoother orderings (Section 4): "SSA" (pre A, S, S; post S, S, A), "SA"
     "dg1_ragged_SSA": (8, 1, 1, 20, "two_material", dict(smoother="SSA")),
     "dg0_two_grid_SA": (4, 1, 0, 16, "unit", dict(max_levels=2, smoother="SA")),
@@ -265,13 +268,15 @@ def test_graph_replay_matches_direct_launches(lib_built):
     assert out[0][1] == out[1][1] > 0
 
 
-@pytest.mark.parametrize("slab_prec", [0, 1, 3])
+@pytest.mark.parametrize("slab_prec", [0, 1, 2, 3, 4])
 def test_persistent_split_matches_per_depth_launches(slab_prec, lib_built):
-    """The persistent split-K solve runs the same items, partial layout and summation
-    order as the per-depth kernels: a V-cycle must agree bit for bit."""
+    """The persistent split-K solve (grid barriers between depths) and the dataflow one
+    (every task waits only for the tasks it reads from) run the same items, partial
+    layout and summation order as the per-depth kernels: a V-cycle must agree bit for
+    bit, for the slab solves of the coarse time levels and the nodal solves alike."""
     nu, sigma = st_inputs.materials(8, "two_material", 4)
     xs = []
-    for ps in (0, 1):
+    for ps in (0, 1, 2):
         S = lib_built.SpaceTimeSolver(8, nu, sigma, 1.0, 64, 1, nu_pre=2, nu_post=2, slab_prec=slab_prec,
                                       persistent_split=ps)
         f = S.load(st_inputs.excitation(6))
@@ -281,6 +286,7 @@ def test_persistent_split_matches_per_depth_launches(slab_prec, lib_built):
         xs.append(host(x))
         S.close()
     assert np.array_equal(xs[0], xs[1])
+    assert np.array_equal(xs[0], xs[2])
 
 
 def test_autotune_choices_valid(lib_built):
