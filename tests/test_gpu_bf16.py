@@ -114,6 +114,37 @@ def test_bf16_persistent_tiled_depths_match_per_tile_kernel(setup, level):
         stmg.st_mg_set_tc_mode(S.h, level, 0)
         stmg.st_mg_set_split_waves(S.h, level, w0)
 
+
+@pytest.mark.parametrize("slab_prec", [3, 4])
+def test_tensor_core_kernels_ragged_column_count(slab_prec):
+    """398 slabs (the fine level's 398 right-hand sides are three full column blocks of the
+    tensor-core kernels and one of 14 columns; the coarsest level, 199 slabs, is FP64).
+    Persistent tiled, per-tile and split-K depths against the CUDA-core apply of the same
+    factor, element by element."""
+    from paper_1911_09548_gb300._build import build
+    build()
+    import paper_1911_09548_gb300 as stmg
+    nu, sigma = st_inputs.materials(N_CUBE, "two_material", 9)
+    S = stmg.SpaceTimeSolver(N_CUBE, nu, sigma, 1.0, 398, 1, slab_prec=slab_prec)
+    try:
+        L = S.levels[0]
+        assert L["N_t"] == 398 and S.n_levels == 2
+        rng = np.random.default_rng(31)
+        r = torch.from_numpy(to_lib(rng.normal(size=(398, 2, L["n_edge"])))).cuda()
+        stmg.st_mg_set_tc_mode(S.h, 0, 1)
+        y_ref = _solve(stmg, S, r, 0)
+        out = {}
+        for mode, waves in ((0, 0), (2, 0), (0, 64)):
+            stmg.st_mg_set_tc_mode(S.h, 0, mode)
+            stmg.st_mg_set_split_waves(S.h, 0, waves)
+            out[(mode, waves)] = _solve(stmg, S, r, 0)
+            d = rel(out[(mode, waves)], y_ref)
+            print(f"prec {slab_prec} 398 columns, mode {mode}, split waves {waves}: {d:.3e}")
+            assert d < (2e-3 if slab_prec == 3 else 5e-4), (mode, waves, d)
+        assert np.array_equal(out[(0, 0)], out[(2, 0)])
+    finally:
+        S.close()
+
 def test_bf16_slab_solve_accuracy(setup):
     stmg, S, sl, mg, nu, sigma = setup
     rng = np.random.default_rng(0)
