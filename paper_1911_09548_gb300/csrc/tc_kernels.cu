@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
                                                            float2* __restrict__ Z, float2* __restrict__ U,
                                                            float2* __restrict__ X, int nrhs, int ld,
                                                            int* __restrict__ err) {
-  pdl_entry();
+  // launched with programmatic stream serialisation: the prologue below (task descriptors
+  // from the factor's static lists, barriers, TMEM) may overlap the end of the kernel
+  // before (the depth's right-hand-side assembly); nothing written by a kernel is read
+  // before griddepcontrol.wait
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full[TC3_STAGES], empty[TC3_STAGES], accf[2], acce[2], done;
   __shared__ uint32_t tmem_slot;
@@ -546,6 +549,7 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k_sn_tc3(const DevNode* __rest
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
+  pdl_entry();
   const uint32_t tmem = tmem_slot;
   const int ntask = nmine < TC3_MAX_TASKS ? nmine : TC3_MAX_TASKS;
   int issued = 0;   // producer: stages whose copies it started
@@ -739,11 +743,11 @@ cudaError_t sn_tc2_depth(const DevFactor<float2, WT>& F, int d, bool fwd, bool s
     const int2* tl = (fwd ? F.fwd_tiles : F.bwd_tiles) + a;
     const unsigned grid = (unsigned)grid3;
     if (fwd)
-      launch_k(k_sn_tc3<true, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv,
-               F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
+      launch_k_overlap(k_sn_tc3<true, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst,
+                       F.Dinv, F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
     else
-      launch_k(k_sn_tc3<false, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst, F.Dinv,
-               F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
+      launch_k_overlap(k_sn_tc3<false, H>, dim3(grid), TC3_THREADS, TC3_SMEM, st, F.nodes, TW, F.tnode, F.tpre, Bst,
+                       F.Dinv, F.gsrc, tl, (int)(b - a), (int)gy, Z, U, Q, nrhs, ld, err);
     count_launches(1);
   } else if (!split) {
     const int64_t* to = fwd ? F.h_fwd_off : F.h_bwd_off;
