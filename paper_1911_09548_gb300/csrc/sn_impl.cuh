@@ -28,6 +28,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "device.h"
 #include "launch.cuh"
@@ -426,7 +427,7 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
                                         const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U,
                                         const typename P::S* __restrict__ X, typename P::S* __restrict__ out,
                                         int nrhs, int ld, typename P::A (*As)[kSkRows + 1],
-                                        typename P::A (*Bs)[NB], int lane) {
+                                        typename P::A (*Bs)[NB], int lane, bool pdl_wait = false) {
   using S = typename P::S;
   using A = typename P::A;
   static_assert(SK_THREADS == 32, "one warp per item: warp-level synchronisation below");
@@ -446,7 +447,7 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
   // current stage is multiplied out of shared memory
   typename P::WT ra[NA];   // raw factor entries (converted on the way into shared memory)
   S rb[NBL];
-  auto load = [&](int ks) {
+  auto load_w = [&](int ks) {
 #pragma unroll
     for (int u = 0; u < NA; ++u) {
       const int t = tid + u * SK_THREADS;
@@ -459,6 +460,8 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
       else { if (r < nc && k < k1) a = Ws[(int64_t)k * nc + r]; }
       ra[u] = a;
     }
+  };
+  auto load_b = [&](int ks) {
 #pragma unroll
     for (int u = 0; u < NBL; ++u) {
       const int t = tid + u * SK_THREADS;
@@ -480,7 +483,11 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
       rb[u] = v;
     }
   };
-  if (k0 < k1) load(k0);
+  // the factor is static: its first stage is requested before waiting for the kernel
+  // that wrote the right-hand sides (pdl_wait: launched with programmatic serialisation)
+  if (k0 < k1) load_w(k0);
+  if (pdl_wait) pdl_entry();
+  if (k0 < k1) load_b(k0);
   for (int ks = k0; ks < k1; ks += SK_KS) {
 #pragma unroll
     for (int u = 0; u < NA; ++u) {
@@ -494,7 +501,10 @@ __device__ __forceinline__ void sk_item(const DevNode* __restrict__ nodes, const
       if (t < SK_KS * NB) Bs[t / NB][t % NB] = P::from_s(rb[u]);
     }
     __syncwarp();
-    if (ks + SK_KS < k1) load(ks + SK_KS);
+    if (ks + SK_KS < k1) {
+      load_w(ks + SK_KS);
+      load_b(ks + SK_KS);
+    }
 #pragma unroll
     for (int kk = 0; kk < SK_KS; ++kk) {
       const A a = As[kk][tid];
@@ -550,13 +560,15 @@ __global__ void __launch_bounds__(SK_THREADS) k_sn_skinny_partial(
     const int32_t* __restrict__ rows, const int4* __restrict__ items, const typename P::S* __restrict__ Q,
     const typename P::S* __restrict__ Z, const typename P::S* __restrict__ U, const typename P::S* __restrict__ X,
     typename P::S* __restrict__ Pt, int nrhs, int ld) {
-  pdl_entry();
+  // sk_item calls pdl_entry() after requesting the item's first factor stage (static
+  // data), before it reads a right-hand side or writes its partial, so that under
+  // programmatic serialisation the request overlaps the end of the previous kernel
   static_assert(SK_THREADS == 32, "one warp per item: warp-level synchronisation");
   __shared__ typename P::A As[SK_KS][kSkRows + 1];   // + 1: conflict-free stores of row-major factor rows
   __shared__ typename P::A Bs[SK_KS][NB];
   typename P::S* out = Pt + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kSkRows * NB;
   sk_item<P, NB, FWD>(nodes, W, gsrc, rows, items[blockIdx.x], blockIdx.y * NB, Q, Z, U, X, out, nrhs, ld, As, Bs,
-                      threadIdx.x);
+                      threadIdx.x, true);
 }
 
 template <typename P, int NB, bool FWD>
@@ -564,10 +576,12 @@ __global__ void __launch_bounds__(kSkRows * NB) k_sn_skinny_reduce(
     const DevNode* __restrict__ nodes, const typename P::S* __restrict__ Dinv, const int32_t* __restrict__ gsrc,
     const int4* __restrict__ units, int64_t item_base, int64_t n_items, const typename P::S* __restrict__ Pt,
     typename P::S* __restrict__ Z, typename P::S* __restrict__ U, typename P::S* __restrict__ X, int nrhs, int ld) {
-  pdl_entry();
+  // the unit's static description is read before waiting for the partials' kernel (an
+  // overlap under programmatic serialisation)
   using S = typename P::S;
   const int4 un = units[blockIdx.x];
   const DevNode nd = nodes[un.x];
+  pdl_entry();
   const int nc = nd.nc, m = nd.nc + nd.nr;
   const int i = threadIdx.x / NB, cl = threadIdx.x % NB, c = blockIdx.y * NB + cl;
   const int r = un.y + i;
@@ -600,15 +614,20 @@ void skinny_depth(const DevFactor<typename P::S, typename P::WT>& F, int d, bool
   const int64_t ia = io[d], ib = io[d + 1], ua = uo[d], ub = uo[d + 1];
   if (ib <= ia) return;
   const unsigned gy = (unsigned)((nrhs + NB - 1) / NB);
+  // FP32 right-hand sides (FP32 and 16-bit factors): each kernel's static prologue overlaps
+  // the previous kernel's end.  The FP64 and double-float solves measured slower that way
+  // (their kernels keep the FP64 or FP32 pipe busy to the end), so they queue plainly.
+  constexpr bool fp32_rhs = std::is_same<typename P::S, float>::value || std::is_same<typename P::S, float2>::value;
+  const bool ov = fp32_rhs || launch_overlap();
   if (fwd) {
-    launch_k(k_sn_skinny_partial<P, NB, true>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
+    launch_cfg(ov, k_sn_skinny_partial<P, NB, true>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
         F.nodes, F.W, F.gsrc, F.rows, F.fs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
-    launch_k(k_sn_skinny_reduce<P, NB, true>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
+    launch_cfg(ov, k_sn_skinny_reduce<P, NB, true>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
         F.nodes, F.Dinv, F.gsrc, F.fs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   } else {
-    launch_k(k_sn_skinny_partial<P, NB, false>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
+    launch_cfg(ov, k_sn_skinny_partial<P, NB, false>, dim3((unsigned)(ib - ia), gy), SK_THREADS, 0, st,
         F.nodes, F.W, F.gsrc, F.rows, F.bs_items + ia, Q, Z, U, Q, Pt, nrhs, ld);
-    launch_k(k_sn_skinny_reduce<P, NB, false>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
+    launch_cfg(ov, k_sn_skinny_reduce<P, NB, false>, dim3((unsigned)(ub - ua), gy), kSkRows * NB, 0, st,
         F.nodes, F.Dinv, F.gsrc, F.bs_units + ua, ia, ib - ia, Pt, Z, U, Q, nrhs, ld);
   }
   count_launches(2);
