@@ -132,6 +132,23 @@ def test_smoother_pattern_validated(B):
 
 
 
+def test_split_solve_mode_validated(B):
+    """persistent_split selects how few-right-hand-side solves walk the tree depths: 0 per-depth
+    launches, 1 grid barriers, 2 dataflow; other values are rejected at setup."""
+    nu, sigma = st_inputs.materials(4, "unit")
+    prob = B.make_problem(4, 1, nu, sigma, 1.0, 8, 1)
+    for ok in (0, 1, 2):
+        opt = B.st_mg_default_options()
+        opt.persistent_split = ok
+        B.st_mg_destroy(B.st_mg_setup_host(prob, opt))
+    for bad in (-1, 3):
+        opt = B.st_mg_default_options()
+        opt.persistent_split = bad
+        with pytest.raises(B.StMgError) as e:
+            B.st_mg_setup_host(prob, opt)
+        assert e.value.status == 1
+
+
 def test_split_waves_setter_needs_device_state(B):
     """The tiled / split-K threshold is device state: host-only handles reject both calls."""
     nu, sigma = st_inputs.materials(4, "unit")
