@@ -145,10 +145,11 @@ cudaError_t sn_solve_cplxf(const DevFactor<float2>& F, float2* Q, float2* Z, flo
                            const SkSync& sy, cudaStream_t st);
 
 // BF16 factor on the tensor cores (DG(1)): W as complex BF16, right-hand sides and
-// accumulation in FP32.  Depths with enough tiles run the tcgen05 kernels (64
-// complex rows x kTcCols right-hand sides per block), the others split K into
-// chunks (Ptc: max_tc_items * ceil(nrhs / kTcCols) * kSnBM * kTcCols float2); small
-// nrhs takes the CUDA-core split-K path.  sy.err: set to 1 if a bounded wait timed out.
+// accumulation in FP32.  Depths with enough tiles run the tcgen05 kernels on tasks of 64
+// complex rows x kTcCols right-hand sides (sy.tc_persist: one persistent CTA per SM
+// walking the depth's tasks, else one CTA per task), the others split K into chunks
+// (Ptc: max_tc_items * ceil(nrhs / kTcCols) * kSnBM * kTcCols float2); small nrhs takes
+// the CUDA-core split-K path.  sy.err: set to 1 if a bounded wait timed out.
 constexpr int kTcCols = 128;
 cudaError_t sn_solve_cplx_bf16(const DevFactor<float2, __nv_bfloat162>& F, float2* Q, float2* Z, float2* U,
                                float2* P, float2* Ptc, uint8_t* Bst, int nrhs, int ld, const SkSync& sy,
