@@ -443,12 +443,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_sn_tc2(const DevNode* __restrict
 // blockIdx.x + gridDim.x, ... with three roles: warp 0 (lane 0) streams the operand tiles
 // of all its tasks through a TC3_STAGES-deep ring of shared-memory stages, warp 1 (lane 0)
 // issues the MMAs of a task into one of two TMEM accumulators (columns 0..127 or
-// 128..255), and warps 2..9 read a finished accumulator straight from TMEM (warp w reads
-// TMEM lanes 32 (w % 4) .., two warps per lane quarter splitting the columns), apply the
-// epilogue and store, while the next task's MMAs run into the other accumulator.  The ring never drains between tasks, so a CTA's short K
-// loops no longer pay the pipeline fill each.  Products and epilogue are those of
-// k_sn_tc2 (same stage order, FP32 accumulation, same complex multiply), so the results
-// are the same bit for bit.
+// 128..255), and warps 2..9 read a finished accumulator from TMEM (warp w reads TMEM
+// lanes 32 (w % 4) .., two warps per lane quarter splitting the columns), apply the
+// epilogue and store, while the next task's MMAs run into the other accumulator.  The
+// ring never drains between tasks, so a CTA's short K loops no longer pay the pipeline
+// fill each.  Products and epilogue are those of k_sn_tc2 (same stage order, FP32
+// accumulation, same complex multiply), so the results are the same bit for bit.
 // Barriers: full/empty per stage (producer <-> MMA), accf/acce per accumulator (MMA <->
 // epilogue); every wait is bounded; a role whose wait gives up sets *err and stops, the
 // others then stop at their own bounded waits, and the CTA waits (bounded) for its MMAs
